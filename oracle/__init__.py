@@ -1,0 +1,293 @@
+"""FP64 CPU oracle of the damped-current PML PIC step (arXiv:2201.09084).
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The product path (``paper_2201_09084_gb300``) never imports it and
+shares no code with it.
+
+The arithmetic lives in ``picpml_oracle.c`` (plain loops, FP64), compiled with
+gcc into ``liboracle_picpml.so`` next to it; this module only marshals numpy
+arrays.  Each C function cites the passage of the paper it follows.
+
+Functions without an independent pin: none at present; the pins are the
+``tests/test_oracle_*.py`` files (listed in the C file's header).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "picpml_oracle.c")
+LIB = os.path.join(HERE, "liboracle_picpml.so")
+
+C_LIGHT = 299792458.0
+EPS0 = 8.8541878128e-12
+Q_E = 1.602176634e-19
+M_E = 9.1093837015e-31
+M_P = 1.67262192369e-27
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compiles the oracle with gcc (no FMA contraction, portable flags)."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        tmp = LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+             "-o", tmp, SRC, "-lm"])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(LIB)
+            dp = C.POINTER(C.c_double)
+            ip = C.POINTER(C.c_int)
+            L.ora_create.restype = C.c_void_p
+            L.ora_create.argtypes = [C.c_int, ip, ip, dp, C.c_double, C.c_int, C.c_int,
+                                     C.c_double, C.c_double, C.c_double, C.c_double]
+            L.ora_destroy.argtypes = [C.c_void_p]
+            L.ora_set_prescribed.argtypes = [C.c_void_p, C.c_int]
+            L.ora_add_particles.restype = C.c_long
+            L.ora_add_particles.argtypes = [C.c_void_p, C.c_long] + [dp] * 7 + [C.c_double, C.c_double, C.c_int]
+            L.ora_num_particles.restype = C.c_long
+            L.ora_num_particles.argtypes = [C.c_void_p]
+            L.ora_get_particles.argtypes = [C.c_void_p] + [dp] * 6 + [ip]
+            for f in ("ora_push", "ora_deposit", "ora_deposit_raw", "ora_damp_J", "ora_zero_J",
+                      "ora_field_E", "ora_field_B"):
+                getattr(L, f).argtypes = [C.c_void_p]
+            L.ora_step.argtypes = [C.c_void_p, C.c_int]
+            L.ora_get_field.argtypes = [C.c_void_p, C.c_int, dp]
+            L.ora_get_field.restype = C.c_int
+            L.ora_set_field.argtypes = [C.c_void_p, C.c_int, dp]
+            L.ora_set_field.restype = C.c_int
+            L.ora_rho.argtypes = [C.c_void_p, dp]
+            L.ora_divE.argtypes = [C.c_void_p, dp]
+            L.ora_get_table.argtypes = [C.c_void_p, C.c_int, C.c_int, dp]
+            L.ora_dims.argtypes = [C.c_void_p, C.POINTER(C.c_long)]
+            L.ora_sigma_over_eps0.restype = C.c_double
+            L.ora_sigma_over_eps0.argtypes = [C.c_double] * 4 + [C.c_double]
+            L.ora_alpha.restype = C.c_double
+            L.ora_alpha.argtypes = [C.c_double] * 5 + [C.c_int]
+            L.ora_shape.restype = C.c_double
+            L.ora_shape.argtypes = [C.c_int, C.c_double]
+            L.ora_boris.argtypes = [dp, dp, dp, C.c_double, C.c_double, C.c_double]
+            L.ora_esirkepov.argtypes = [C.c_void_p, dp, dp, C.c_double, C.c_double]
+            L.ora_gather.argtypes = [C.c_void_p, dp, dp, dp]
+            _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+ALPHA_MODES = {"zero": 0, "one": 1, "damped": 2}
+
+
+def alpha(dcells, coef=4.0, delta=6.0, p=2.0, v=C_LIGHT, mode="damped"):
+    """Eq. alpha at depth ``dcells`` (cells) into a face."""
+    return lib().ora_alpha(float(dcells), coef, delta, p, v, ALPHA_MODES[mode])
+
+
+def sigma_over_eps0(dcells, Delta, coef=4.0, delta=6.0, p=2.0):
+    """Eq. conductivity divided by eps0, at depth ``dcells`` (cells)."""
+    return lib().ora_sigma_over_eps0(float(dcells), Delta, coef, delta, p)
+
+
+def shape(order, r):
+    return lib().ora_shape(int(order), float(r))
+
+
+def boris(u, E, B, q, m, dt):
+    """One Boris rotation of u = p/(mc) (returns the new u)."""
+    u = _f64(u).copy()
+    lib().ora_boris(_dp(u), _dp(_f64(E)), _dp(_f64(B)), q, m, dt)
+    return u
+
+
+def yee_dt(d, cfl, dim):
+    """dt = cfl * Courant limit of the Yee scheme, 1/(c sqrt(sum 1/d_i^2))."""
+    axes = (0, 1, 2) if dim == 3 else (0, 2)
+    return cfl / (C_LIGHT * np.sqrt(sum(1.0 / d[a] ** 2 for a in axes)))
+
+
+class OracleSim:
+    """One FP64 simulation box: physical cells plus PML cells on every face.
+
+    n: physical cells (nx, ny, nz) (ny ignored in 2D); pml: cells on the
+    (-x, +x, -y, +y, -z, +z) faces; d: cell sizes in metres.
+    """
+
+    def __init__(self, dim, n, pml, d, dt, order=1, alpha_mode="damped",
+                 sig_coef=4.0, delta=6.0, sig_exp=2.0, v_assumed=C_LIGHT):
+        L = lib()
+        self.dim = dim
+        n3 = (C.c_int * 3)(*[int(v) for v in n])
+        p6 = (C.c_int * 6)(*[int(v) for v in pml])
+        d3 = (C.c_double * 3)(*[float(v) for v in d])
+        mode = ALPHA_MODES[alpha_mode] if isinstance(alpha_mode, str) else int(alpha_mode)
+        self._h = L.ora_create(dim, n3, p6, d3, float(dt), int(order), mode,
+                               float(sig_coef), float(delta), float(sig_exp), float(v_assumed))
+        if not self._h:
+            raise ValueError("oracle: bad grid description")
+        nn = (C.c_long * 3)()
+        L.ora_dims(self._h, nn)
+        self.nn = (nn[0], nn[1], nn[2])
+        self.n = tuple(n)
+        self.pml = tuple(pml)
+        self.d = tuple(float(v) for v in d)
+        self.dt = float(dt)
+        self.order = order
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            lib().ora_destroy(h)
+            self._h = None
+
+    # particles -----------------------------------------------------------
+    def add_particles(self, X, Y, Z, ux, uy, uz, w, q, m, immobile=False):
+        n = len(X)
+        arrs = [_f64(a) for a in (X, Y, Z, ux, uy, uz, w)]
+        r = lib().ora_add_particles(self._h, n, *[_dp(a) for a in arrs], float(q), float(m),
+                                    int(bool(immobile)))
+        if r < 0:
+            raise ValueError("oracle: bad particles")
+        return r
+
+    def set_prescribed(self, flag=True):
+        lib().ora_set_prescribed(self._h, int(bool(flag)))
+
+    def particles(self):
+        n = lib().ora_num_particles(self._h)
+        out = [np.zeros(n) for _ in range(6)]
+        alive = np.zeros(n, dtype=np.int32)
+        lib().ora_get_particles(self._h, *[_dp(a) for a in out],
+                                alive.ctypes.data_as(C.POINTER(C.c_int)))
+        return dict(X=out[0], Y=out[1], Z=out[2], ux=out[3], uy=out[4], uz=out[5],
+                    alive=alive.astype(bool))
+
+    # stepping ------------------------------------------------------------
+    def step(self, n=1):
+        lib().ora_step(self._h, int(n))
+
+    def push(self):
+        lib().ora_push(self._h)
+
+    def deposit(self):
+        lib().ora_deposit(self._h)
+
+    def deposit_raw(self):
+        lib().ora_deposit_raw(self._h)
+
+    def damp_J(self):
+        lib().ora_damp_J(self._h)
+
+    def zero_J(self):
+        lib().ora_zero_J(self._h)
+
+    def field_E(self):
+        lib().ora_field_E(self._h)
+
+    def field_B(self):
+        lib().ora_field_B(self._h)
+
+    def esirkepov(self, X0, X1, qw, vy=0.0):
+        lib().ora_esirkepov(self._h, _dp(_f64(X0)), _dp(_f64(X1)), float(qw), float(vy))
+
+    def gather(self, X):
+        E = np.zeros(3)
+        B = np.zeros(3)
+        lib().ora_gather(self._h, _dp(_f64(X)), _dp(E), _dp(B))
+        return E, B
+
+    # fields ------------------------------------------------------------
+    def _shape3(self, a):
+        # arrays are laid out i + nx (j + ny k): return as [k, j, i]
+        return a.reshape(self.nn[2], self.nn[1], self.nn[0])
+
+    def field(self, which):
+        """which: 'Ex'..'Bz' (B at integer time), 'Jx'..'Jz', 'Bhx'.. (B^{n+1/2}),
+        'Bpx'.. (B^{n-1/2}).  Returns an array indexed [k, j, i]."""
+        base = {"E": 0, "B": 3, "J": 6, "Bh": 9, "Bp": 12}[which[:-1]]
+        c = "xyz".index(which[-1])
+        out = np.zeros(self.nn[0] * self.nn[1] * self.nn[2])
+        lib().ora_get_field(self._h, base + c, _dp(out))
+        return self._shape3(out)
+
+    def set_field(self, which, arr):
+        base = {"E": 0, "Bh": 9, "Bp": 12}[which[:-1]]
+        c = "xyz".index(which[-1])
+        a = _f64(np.asarray(arr)).reshape(-1)
+        assert a.size == self.nn[0] * self.nn[1] * self.nn[2]
+        if lib().ora_set_field(self._h, base + c, _dp(a)) != 0:
+            raise ValueError(which)
+
+    def rho(self):
+        out = np.zeros(self.nn[0] * self.nn[1] * self.nn[2])
+        lib().ora_rho(self._h, _dp(out))
+        return self._shape3(out)
+
+    def divE(self):
+        out = np.zeros(self.nn[0] * self.nn[1] * self.nn[2])
+        lib().ora_divE(self._h, _dp(out))
+        return self._shape3(out)
+
+    def table(self, which, axis):
+        """which: 's_node', 's_cent', 'a_node', 'a_cent' (sigma/eps0 or alpha)."""
+        k = ["s_node", "s_cent", "a_node", "a_cent"].index(which)
+        out = np.zeros(self.nn[axis])
+        lib().ora_get_table(self._h, k, axis, _dp(out))
+        return out
+
+
+def rel_error(sim, ref, offset=(0, 0, 0)):
+    """Eq. error: int[(E-Eref)^2 + c^2 (B-Bref)^2] / int[Eref^2 + c^2 Bref^2]
+    over the physical cells of ``sim``; ``offset`` is the node index of sim's
+    node (0,0,0) inside ``ref``.  Every component is sampled at its own
+    staggered points that lie in the closed physical box."""
+    num = 0.0
+    den = 0.0
+    lo = [sim.pml[0], sim.pml[2], sim.pml[4]]
+    hi = [lo[0] + sim.n[0], lo[1] + (sim.n[1] if sim.dim == 3 else 0), lo[2] + sim.n[2]]
+    # staggered along its own axis for E, along the two others for B
+    for fam, scale in (("E", 1.0), ("B", C_LIGHT ** 2)):
+        for c in "xyz":
+            a = sim.field(fam + c)
+            b = ref.field(fam + c)
+            ax = "xyz".index(c)
+            stag = [0, 0, 0]
+            if fam == "E":
+                stag[ax] = 1
+            else:
+                stag = [1, 1, 1]
+                stag[ax] = 0
+            if sim.dim == 2:
+                stag[1] = 0
+            sl = []
+            slr = []
+            for q, (l, h) in enumerate(zip(lo, hi)):
+                top = h - 1 if stag[q] else h
+                sl.append(slice(l, top + 1))
+                slr.append(slice(l + offset[q], top + 1 + offset[q]))
+            A = a[sl[2], sl[1], sl[0]]
+            Bv = b[slr[2], slr[1], slr[0]]
+            num += scale * np.sum((A - Bv) ** 2)
+            den += scale * np.sum(Bv ** 2)
+    return num / den

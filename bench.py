@@ -1,0 +1,349 @@
+"""Benchmark of the damped-current PML PIC step on GB300.
+
+Workload (one step = one PIC time step over the whole particle set, i.e. all
+hot-path stages: sort every 20 steps, gather + Boris push + move + Esirkepov
+deposit + alpha-damped flush, split-field PML Yee update):
+  3D FP32 fields, 128^3 physical cells + 16-cell PML on every face (160^3),
+  a relativistic electron beam of 4,194,304 macroparticles (Gaussian,
+  sigma 4 cells transverse, 8 cells along the axis, u_z ~ N(50, 0.5), 1 nC),
+  centred 24 cells (3 sigma_z) before the +z PML interface so that it
+  crosses into the damped-current PML during the timed steps; shape order 1
+  (order 3 selectable), dt = 0.99 x Courant limit, seed-generated.
+Metric: particle-steps/s (live particles pushed per second, counted on the
+device); cell-updates/s of the Yee/PML update is reported beside it.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload (see cpu_sample()).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NPHYS = (128, 128, 128)
+PML = (16,) * 6
+D = (1e-6, 1e-6, 1e-6)
+NPART = 4_194_304
+SORT_EVERY = 20
+METRIC = "particle-steps/s"
+
+
+def beam_center():
+    return (PML[0] + NPHYS[0] / 2 + 0.3, PML[2] + NPHYS[1] / 2 + 0.1, PML[4] + NPHYS[2] - 24 + 0.2)
+
+
+def workload(order, theta, prec):
+    return {"workload": f"3D beam exiting +z PML: {NPHYS[0]}^3 + {PML[0]}-cell PML, {NPART} macroparticles, "
+                        f"order {order}, theta {theta} deg, {prec} fields + fp64 PML splits",
+            "grid": [n + 2 * p for n, p in zip(NPHYS, PML[::2])], "particles": NPART,
+            "shape_order": order, "theta_deg": theta, "alpha": "damped (Eq. alpha, v=c)",
+            "sort_every": SORT_EVERY, "l2": "working set > L2 (particles 134 MB + fields ~550 MB)",
+            "data": "synthetic"}
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def algorithmic_bytes(n_live, occ_cells, n_int, n_pml, prec):
+    """Algorithmic bytes of one step: each operand read once, each result
+    written once.  Particle (3D FP32): 32 B read + 28 B written; occupied cell
+    gather/deposit: 9 field words read + 3 current words written (48 B; 96 B
+    in FP64).  Yee interior cell: E, B, J read, E, B written (60 B FP32,
+    120 B FP64); PML cell: 12 FP64 split parts read+written, J read, E, B
+    written (228 B; 252 B FP64)."""
+    e = 8 if prec == "fp64" else 4
+    part = (60 if prec != "fp64" else 104) * n_live + 12 * e * occ_cells
+    field = (15 * e) * n_int + (192 + 9 * e) * n_pml
+    return part, field
+
+
+def count_cells():
+    N = [n + 2 * p for n, p in zip(NPHYS, PML[::2])]
+    total = N[0] * N[1] * N[2]
+    interior = NPHYS[0] * NPHYS[1] * NPHYS[2]
+    return total, interior, total - interior
+
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_2201_09084_gb300 import inputs as I
+    from paper_2201_09084_gb300.api import Sim, pack_particles
+    from paper_2201_09084_gb300 import build as B
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    parts = I.beam(3, NPART, NPHYS, PML, beam_center(), theta_deg=args.theta)[0]
+    stream = torch.cuda.current_stream()
+    sim = Sim(3, NPHYS, D, PML, cfl=0.99, order=args.order, prec=args.prec, alpha_mode="damped",
+              sort_every=0, stream=stream)
+    pos, mom = pack_particles(parts["cell"], parts["off"], parts["u"], parts["w"], args.prec)
+    sim.add_species(pos, mom, NPART, parts["q"], parts["m"])
+    pos0, mom0 = pos.clone(), mom.clone()
+
+    def one_step(i, ev=None):
+        if i % SORT_EVERY == 0:
+            sim.sort()
+        if ev is not None:
+            ev[0].record(stream)
+        sim.push_deposit()
+        if ev is not None:
+            ev[1].record(stream)
+        sim.field_step()
+        if ev is not None:
+            ev[2].record(stream)
+
+    for i in range(args.warmup):
+        one_step(i)
+    sim.sync()
+    ps0 = sim.particle_steps()
+    l0 = sim.launch_count()
+    # occupied cells at the start of the timed region (for the byte model)
+    cells = mom.view(torch.int32)[:, 3]
+    occ = int(torch.unique(cells[cells >= 0]).numel())
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t0.record(stream)
+    for i in range(args.steps):
+        one_step(args.warmup + i, evs[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    sim.sync()
+    ms = t0.elapsed_time(t1)
+    psteps = sim.particle_steps() - ps0
+    launches = sim.launch_count() - l0
+    t_pd = np.mean([e[0].elapsed_time(e[1]) for e in evs])
+    t_f = np.mean([e[1].elapsed_time(e[2]) for e in evs])
+
+    # ---- end to end through the public API from pinned host buffers ----
+    hpos = pos0.cpu().pin_memory()
+    hmom = mom0.cpu().pin_memory()
+    sim2 = Sim(3, NPHYS, D, PML, cfl=0.99, order=args.order, prec=args.prec, alpha_mode="damped",
+               sort_every=SORT_EVERY, stream=stream)
+    dpos = torch.empty_like(pos0)
+    dmom = torch.empty_like(mom0)
+    sim2.add_species(dpos, dmom, NPART, parts["q"], parts["m"])
+    result = torch.zeros(1, dtype=torch.int64).pin_memory()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    dpos.copy_(hpos, non_blocking=True)
+    dmom.copy_(hmom, non_blocking=True)
+    sim2.step(args.warmup + args.steps)
+    e1.record(stream)
+    ps_e2e = sim2.particle_steps()   # synchronising read of the run's result
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+    nsteps_e2e = args.warmup + args.steps
+
+    # ---- reductions over ranks ----
+    vals = torch.tensor([ms, psteps, ms_e2e, ps_e2e], dtype=torch.float64, device="cuda")
+    if world > 1:
+        mx = vals.clone()
+        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+        sm = vals.clone()
+        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+        ms, ms_e2e = float(mx[0]), float(mx[2])
+        psteps, ps_e2e = float(sm[1]), float(sm[3])
+    value = psteps / (ms / 1e3)
+    total_cells, n_int, n_pml = count_cells()
+    cell_updates = world * total_cells * args.steps / (ms / 1e3)
+    n_live_avg = (psteps / world) / args.steps
+    b_part, b_field = algorithmic_bytes(n_live_avg, occ, n_int, n_pml, args.prec)
+    peak, peak_kind = measured_peak()
+    if t_pd >= t_f:
+        dom, t_dom, b_dom = "push_deposit (k_particles fused)", t_pd, b_part
+    else:
+        dom, t_dom, b_dom = "field_step (k_field_E + k_field_B)", t_f, b_field
+    achieved = b_dom / (t_dom / 1e3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "f64",
+        "data": "synthetic",
+        "config": dict(workload(args.order, args.theta, args.prec), parallelism=f"replicas x{world}"),
+        "cell_updates_per_s": cell_updates,
+        "kernel_ms": {"push_deposit": t_pd, "field_step": t_f},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} (copy)", "traffic": None,
+                     "algorithmic_bytes_per_launch": b_dom},
+        "e2e": {"value": ps_e2e / (ms_e2e / 1e3), "unit": "particle-steps/s",
+                "h2d_bytes_per_step": 2 * NPART * (32 if args.prec == "fp64" else 16) / nsteps_e2e,
+                "d2h_bytes_per_step": 8 / nsteps_e2e,
+                "note": f"pinned host particles copied in once per run of {nsteps_e2e} steps "
+                        "(step_n with sorting), particle-step count read back; bytes are per step"},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    return out
+
+
+# ----------------------------------------------------------------------------
+def cpu_sample(order, theta, sample, steps):
+    """The oracle on a bounded sample of the workload: the full 160^3 grid,
+    `sample` beam particles (weights scaled to the same charge), `steps` time
+    steps.  Returns (particle-steps/s scaled to the full particle count,
+    description).  The particle stages are timed separately from the field
+    update so the full-workload rate is t_field + N t_particle per step."""
+    import oracle as O
+    from paper_2201_09084_gb300 import inputs as I
+    oracle_build = O.build()
+    dt = O.yee_dt(D, 0.99, 3)
+    parts = I.beam(3, sample, NPHYS, PML, beam_center(), theta_deg=theta)[0]
+    sim = O.OracleSim(3, NPHYS, PML, D, dt, order=order, alpha_mode="damped")
+    X = I.absolute(parts["cell"], parts["off"])
+    u = parts["u"].astype(np.float64)
+    sim.add_particles(X[:, 0], X[:, 1], X[:, 2], u[:, 0], u[:, 1], u[:, 2],
+                      parts["w"].astype(np.float64) * (NPART / sample), parts["q"], parts["m"])
+    t_part = t_field = 0.0
+    for _ in range(steps):
+        a = time.perf_counter()
+        sim.push()
+        sim.deposit()
+        b = time.perf_counter()
+        sim.field_E()
+        sim.field_B()
+        c = time.perf_counter()
+        t_part += b - a
+        t_field += c - b
+    per_particle = t_part / steps / sample
+    step_full = t_field / steps + per_particle * NPART
+    value = NPART / step_full
+    desc = (f"FP64 C oracle, 1 thread: {steps} steps of the full 160^3 grid with a {sample}-particle "
+            f"sample of the beam; rate = N / (t_field + N t_particle), N = {NPART}")
+    return value, desc, step_full
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    sample = max(16384, int(262144 / max(1, (args.steps + args.warmup) / 20)))
+    v, desc, step_full = cpu_sample(args.order, args.theta, sample, args.steps + args.warmup)
+    out = {"metric": METRIC, "value": v, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": step_full * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": dict(workload(args.order, args.theta, "fp64"), parallelism="cpu oracle"),
+           "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle", "sample": desc},
+           "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--order", type=int, default=1, choices=[1, 3])
+    ap.add_argument("--theta", type=float, default=0.0)
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        torch.distributed.init_process_group("nccl" if args.impl == "gb300" else "gloo")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_gpu(args, rank, world)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            v, desc, _ = cpu_sample(args.order, args.theta, 65536, 8)
+            out["cpu_baseline"] = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                                   "sample": desc}
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

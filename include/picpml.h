@@ -1,0 +1,221 @@
+/*
+ * picpml.h -- C ABI of the GB300 (sm_103a) electromagnetic PIC step with the
+ * damped-current perfectly matched layer of Lehe et al., "Absorption of
+ * charged particles in Perfectly-Matched-Layers by optimal damping of the
+ * deposited current" (arXiv:2201.09084).
+ *
+ * One time step (Sec. II.A-B of the paper, App. A for the scheme choices):
+ *   gather E^n, B^n at each macroparticle (B-spline shape of order 1 or 3),
+ *   Boris push u^{n-1/2} -> u^{n+1/2} and move x^n -> x^{n+1},
+ *   charge-conserving Esirkepov deposition of J^{n+1/2},
+ *   damping of the current deposited in PML cells, J_c <- alpha_c J_c, with
+ *     alpha(z) = exp(-int_0^z sigma/(eps0 v) dz')              (Eq. alpha)
+ *     evaluated at each component's staggered Yee location (Sec. II.B),
+ *   Yee update E^{n+1} = E^n + dt (c^2 curl B^{n+1/2} - J/eps0) and
+ *     B^{n+3/2} = B^{n+1/2} - dt curl E^{n+1}, with the split-field PML of
+ *     Eqs. MaxwellE, MaxwellB, MaxwellSum in cells where sigma > 0.
+ *
+ * Conventions for every entry point:
+ *   - Returns a pic_status (0 = success, < 0 = error); nothing is thrown
+ *     across the ABI.  pic_last_error(ctx) gives a one-line message.
+ *   - Work is enqueued on the context's CUDA stream (given at pic_init) and is
+ *     asynchronous unless stated.  Device-side faults of the method (a particle
+ *     outside the grid, a fixed-point overflow) set a status word that is
+ *     reported by pic_sync() and pic_diag().
+ *   - Memory: particle arrays are CALLER-owned device memory registered with
+ *     pic_add_species and must outlive the context; fields, PML split
+ *     components, coefficient tables and scratch are LIBRARY-owned (allocated
+ *     at pml_init / pic_add_species, freed by pic_destroy).
+ *   - Units: SI (metres, seconds, V/m, tesla, A/m^2, coulomb, kilogram).
+ *     Momenta are u = p/(m c).  Positions are an int32 cell index plus an
+ *     in-cell offset in [0,1) per axis, in units of the cell size.
+ *   - 2D runs are the (x,z) plane with d/dy = 0 (Sec. II.A, last paragraph);
+ *     a 2D macroparticle is a line charge 1 m long along y.
+ */
+#ifndef PICPML_H
+#define PICPML_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct picpml_ctx picpml_ctx; /* opaque, library-owned */
+
+typedef enum {
+  PIC_OK = 0,
+  PIC_EINVAL = -1,      /* bad argument or description */
+  PIC_ENOMEM = -2,      /* device allocation failed */
+  PIC_ECUDA = -3,       /* a CUDA runtime call failed */
+  PIC_ECFL = -4,        /* dt above the Yee Courant limit */
+  PIC_EOVERFLOW = -5,   /* fixed-point current accumulator overflow */
+  PIC_ETIMEOUT = -6,    /* a bounded device wait gave up */
+  PIC_ENOTIMPL = -7,    /* combination not built */
+  PIC_ESTATE = -8,      /* call out of order (e.g. push before pml_init) */
+  PIC_EPARTICLE = -9    /* a particle was found outside its allowed cells */
+} pic_status;
+
+typedef enum {
+  PIC_FP32 = 0,         /* FP32 fields, momenta and offsets; FP64 PML splits */
+  PIC_FP64 = 1,         /* everything FP64 (the plain FP64 form) */
+  PIC_FP32_FIXED64 = 2  /* as PIC_FP32, current accumulated in int64 fixed
+                           point: deterministic, bit-identical J */
+} pic_prec;
+
+typedef enum {
+  PML_ALPHA_ZERO = 0,   /* alpha = 0 in the PML: Berenger's PML, particles
+                           removed on entering it (Sec. I, Eq. MaxwellE) */
+  PML_ALPHA_ONE = 1,    /* alpha = 1: undamped deposition in the PML */
+  PML_ALPHA_DAMPED = 2  /* alpha of Eq. alpha (the paper's scheme) */
+} pml_alpha_mode;
+
+/* Grid description.  n[] counts PHYSICAL cells (the PML cells of pml_desc
+ * are added outside them); n[1] is ignored in 2D.  dt <= 0 selects
+ * cfl * (Yee Courant limit 1/(c sqrt(sum 1/d_i^2))). */
+typedef struct pic_grid_desc {
+  int dim;              /* 2 or 3 */
+  int n[3];             /* physical cells per axis */
+  double d[3];          /* cell sizes (m) */
+  double dt;            /* time step (s), or <= 0 for cfl * Courant limit */
+  double cfl;           /* used when dt <= 0, e.g. 0.99 */
+  int shape_order;      /* 1 (linear) or 3 (cubic spline), App. A */
+  int prec;             /* pic_prec */
+  int sort_every;       /* step_n sorts particles by cell every this many
+                           steps (0 = never) */
+} pic_grid_desc;
+
+/* PML description: conductivity sigma(d) = coef eps0 c / Delta (d/delta)^p at
+ * depth d into a face (Eq. conductivity: coef 4, delta 6 cells, p 2).  alpha
+ * in a corner is the product of the faces' alpha values. */
+typedef struct pml_desc {
+  int ncell[6];         /* PML cells on the -x,+x,-y,+y,-z,+z faces */
+  double sigma_max_coef;/* coef */
+  double delta_cells;   /* delta, in cells */
+  double exponent;      /* p */
+  int alpha_mode;       /* pml_alpha_mode */
+  double v_assumed;     /* v of Eq. alpha (m/s); <= 0 selects c */
+} pml_desc;
+
+/* A species: caller-owned device arrays of `capacity` particles, n of them
+ * live.  PIC_FP32 / PIC_FP32_FIXED64: pos = float4 (ox, oy, oz, w), mom =
+ * float4 (ux, uy, uz, cell) where cell is an int32 stored in the float's
+ * bits: i | j << 10 | k << 20 (i, j < 1024, k < 2048; -1 = removed).
+ * PIC_FP64: the same fields as four doubles each (cell as int64 bits).
+ * q, m: charge and mass of one physical particle; w is the macroparticle
+ * weight. */
+typedef struct pic_species {
+  void* pos;
+  void* mom;
+  long long n;
+  long long capacity;
+  double q;
+  double m;
+  int immobile;         /* 1: never pushed (e.g. the motionless partner of
+                           App. A); deposits no current */
+} pic_species;
+
+/* Creates a context on the current CUDA device.  stream: a cudaStream_t (NULL
+ * = legacy default stream).  Validates the description (PIC_EINVAL, PIC_ECFL)
+ * and allocates nothing on the device yet. */
+int pic_init(picpml_ctx** ctx, const pic_grid_desc* grid, void* stream);
+
+/* Builds the sigma / alpha / exponential-differencing tables per axis at
+ * nodes and cell centres (Eq. conductivity, Eq. alpha; Sec. II.B: closed
+ * forms evaluated at the staggered points) and allocates the fields (zeroed).
+ * Must be called once, after pic_init.  A PML of 0 cells on a face gives a
+ * perfectly conducting wall there. */
+int pml_init(picpml_ctx* ctx, const pml_desc* pml);
+
+/* Registers caller-owned particle arrays (see pic_species); returns the
+ * species id in *sid.  The library allocates per-species scratch (the
+ * positions saved by push() for a later deposit()). */
+int pic_add_species(picpml_ctx* ctx, const pic_species* sp, int* sid);
+
+/* Gather + Boris push + move of every live particle of every species; a
+ * particle whose new position leaves the allowed region is removed (cell set
+ * to -1): at the physical-domain boundary in PML_ALPHA_ZERO mode (Sec. I),
+ * else once its shape would reach the outer PML edge.  Saves x^n for
+ * deposit(). */
+int push(picpml_ctx* ctx);
+
+/* Esirkepov deposition of J^{n+1/2} from the positions saved by push() to the
+ * current ones, with the PML damping alpha_c applied in the flush to the grid
+ * (Eq. MaxwellE source term, Eq. alpha).  Accumulates into J, which the next
+ * field_step() consumes and zeroes. */
+int deposit(picpml_ctx* ctx);
+
+/* Field update: E^{n+1} = E^n + dt (c^2 curl B^{n+1/2} - J/eps0), then
+ * B^{n+3/2} = B^{n+1/2} - dt curl E^{n+1}; split-field PML components in
+ * every location with sigma > 0 (Eqs. MaxwellE, MaxwellB, MaxwellSum), FP64.
+ * Consumes and zeroes J. */
+int field_step(picpml_ctx* ctx);
+
+/* The particle half of a time step in one fused kernel per species: gather,
+ * Boris push, move (+ removal), Esirkepov deposition and the alpha-damped
+ * flush into J.  step_n() is push_deposit() followed by field_step(). */
+int push_deposit(picpml_ctx* ctx);
+
+/* n full time steps: fused gather/push/move/deposit/damp kernel per species,
+ * then field_step; particles are sorted by cell every sort_every steps. */
+int step_n(picpml_ctx* ctx, int n);
+
+/* Sorts every species by cell index (stable counting sort) and drops removed
+ * particles; the live count is updated on the device. */
+int pic_sort(picpml_ctx* ctx);
+
+/* Node counts of the field arrays (nx, ny, nz): N+1 per axis (ny = 1 in 2D),
+ * N = physical + PML cells. */
+int pic_grid_info(picpml_ctx* ctx, int* nn3, double* dt);
+
+/* Copies one field component into dst (caller-owned device buffer of
+ * nx*ny*nz elements, index i + nx (j + ny k)), as double if as_double else
+ * float.  which: 0-2 E^n; 3-5 B^n = (B^{n-1/2}+B^{n+1/2})/2; 6-8 the last
+ * deposited current (damped, A/m^2; zero after field_step); 9-11 B^{n+1/2};
+ * 12-14 B^{n-1/2}.  SI units. */
+int pic_get_field(picpml_ctx* ctx, int which, void* dst, int as_double);
+
+/* Sets one field component from src (same layout as pic_get_field).  which:
+ * 0-2 E^n, 9-11 B^{n+1/2}, 12-14 B^{n-1/2}.  At a split PML location the
+ * whole value goes into the first split part. */
+int pic_set_field(picpml_ctx* ctx, int which, const void* src, int as_double);
+
+/* 1: particles keep their momentum (no gather/push; they still move and
+ * deposit), for prescribed-trajectory studies. */
+int pic_set_prescribed(picpml_ctx* ctx, int flag);
+
+/* Live particle count of a species (synchronises the stream). */
+int pic_num_particles(picpml_ctx* ctx, int sid, long long* n);
+
+/* Diagnostics (synchronise the stream).  gauss: max |div E - rho/eps0| over
+ * nodes at least one cell inside the physical region, in V/m^2; rho_scale:
+ * max |rho/eps0| there; energy: field energy integral of
+ * (eps0 E^2 + B^2/mu0)/2 over the whole grid (J per m in 2D). */
+int pic_diag(picpml_ctx* ctx, double* gauss, double* rho_scale, double* energy);
+
+/* Particle-steps done so far: the number of live particles each push has
+ * moved, summed over all pushes since pml_init (synchronises the stream). */
+int pic_particle_steps(picpml_ctx* ctx, long long* n);
+
+/* Number of CUDA kernels this context has launched so far. */
+int pic_launch_count(picpml_ctx* ctx, long long* n);
+
+/* Waits for the stream and reports any device-side status word. */
+int pic_sync(picpml_ctx* ctx);
+
+/* Checkpoint: bytes needed for the field state (fields, both B half steps,
+ * PML split parts); copy it to / from caller-owned host memory.  Particles
+ * are caller-owned and saved by the caller. */
+int pic_state_size(picpml_ctx* ctx, long long* bytes);
+int pic_get_state(picpml_ctx* ctx, void* host_dst);
+int pic_set_state(picpml_ctx* ctx, const void* host_src);
+
+/* Last error message of this context (or of the last failed pic_init when
+ * ctx is NULL).  Valid until the next call on the context. */
+const char* pic_last_error(picpml_ctx* ctx);
+
+/* Frees all library-owned device memory; does not touch particle arrays. */
+void pic_destroy(picpml_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PICPML_H */

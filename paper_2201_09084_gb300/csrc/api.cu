@@ -1,0 +1,641 @@
+// Host side of libpicpml: the C ABI of include/picpml.h.
+//
+// The context owns the fields (E, B at two half steps, J), the FP64 PML split
+// parts, the per-axis coefficient tables and scratch; particle arrays belong
+// to the caller.  Every entry point validates, enqueues kernels on the
+// context's stream and returns a pic_status.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/picpml.h"
+#include "picpml_internal.cuh"
+
+namespace picpml {
+template <typename T>
+cudaError_t launch_field_E(const Geom&, const Tables&, const FieldPtrs<T>&, cudaStream_t);
+template <typename T>
+cudaError_t launch_field_B(const Geom&, const Tables&, const FieldPtrs<T>&, cudaStream_t);
+template <typename T>
+cudaError_t launch_particles(int mode, int order, const Geom&, const Tables&, const FieldPtrs<T>&,
+                             const SpeciesPtrs<T>&, int prescribed, unsigned* status, unsigned long long* pushed,
+                             int nsm, cudaStream_t);
+template <typename T>
+cudaError_t launch_rho(int order, const Geom&, const void*, const void*, const long long*, long long, double,
+                       double*, cudaStream_t);
+template <typename T>
+cudaError_t launch_gauss(const Geom&, const FieldPtrs<T>&, const double*, const double*, double*, cudaStream_t);
+template <typename T>
+cudaError_t launch_export(const Geom&, const T*, const T*, double, void*, int, cudaStream_t);
+template <typename T>
+cudaError_t launch_import(const Geom&, const void*, int, double, T*, double*, double*, cudaStream_t);
+long long sort_scratch_words(long long ncell);
+int sort_launches(long long ncell);
+cudaError_t launch_sort(const Geom&, int pbytes, void* pos, void* mom, long long* n_dev, long long cap,
+                        unsigned* scratch, void* tmp_pos, void* tmp_mom, cudaStream_t);
+}  // namespace picpml
+
+using namespace picpml;
+
+namespace {
+
+struct Species {
+  pic_species desc{};
+  long long* n_dev = nullptr;
+  void* save = nullptr;      // x^n saved by push() for deposit()
+  void* tmp_pos = nullptr;   // sort scratch, allocated at the first sort
+  void* tmp_mom = nullptr;
+  double ke = 0, cj[3] = {0, 0, 0}, cjy2d = 0;
+};
+
+thread_local std::string g_init_error;
+
+}  // namespace
+
+struct picpml_ctx {
+  pic_grid_desc gd{};
+  pml_desc pd{};
+  bool ready = false;
+  cudaStream_t stream = nullptr;
+  int nsm = 148;
+  double dt = 0;
+  Geom g{};
+  Tables tb{};
+  FieldPtrs<float> ff{};
+  FieldPtrs<double> fd{};
+  std::vector<void*> allocs;
+  unsigned* status = nullptr;
+  unsigned long long* pushed = nullptr;  // particles pushed since pml_init
+  double* diag = nullptr;
+  double* rho = nullptr;
+  unsigned* sort_scratch = nullptr;
+  std::vector<Species> sp;
+  int prescribed = 0;
+  long long steps_done = 0;
+  long long launches = 0;
+  std::string err;
+  int elem() const { return gd.prec == PIC_FP64 ? 8 : 4; }
+  int pbytes() const { return gd.prec == PIC_FP64 ? 32 : 16; }
+};
+
+namespace {
+
+int fail(picpml_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_init_error = msg;
+  return code;
+}
+
+int cuda_fail(picpml_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, PIC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);       \
+  } while (0)
+
+void* dev_alloc(picpml_ctx* ctx, size_t bytes) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) return nullptr;
+  ctx->allocs.push_back(p);
+  return p;
+}
+
+double courant_limit(const pic_grid_desc& g) {
+  double s = 1.0 / (g.d[0] * g.d[0]) + 1.0 / (g.d[2] * g.d[2]);
+  if (g.dim == 3) s += 1.0 / (g.d[1] * g.d[1]);
+  return 1.0 / (kC * std::sqrt(s));
+}
+
+// sigma/eps0 at depth dc cells into a face (Eq. conductivity generalised)
+double sigma_eps0(const pml_desc& p, double Delta, double dc) {
+  if (dc <= 0.0) return 0.0;
+  return p.sigma_max_coef * kC / Delta * std::pow(dc / p.delta_cells, p.exponent);
+}
+
+// Eq. alpha in closed form for the power-law profile: the exponent is
+// int_0^d sigma/(eps0 v) dz = coef (c/v) delta (d/delta)^{p+1}/(p+1), d in cells.
+double alpha_of(const pml_desc& p, double dc) {
+  if (dc <= 0.0) return 1.0;
+  if (p.alpha_mode == PML_ALPHA_ZERO) return 0.0;
+  if (p.alpha_mode == PML_ALPHA_ONE) return 1.0;
+  const double v = p.v_assumed > 0 ? p.v_assumed : kC;
+  const double e = p.sigma_max_coef * (kC / v) * p.delta_cells *
+                   std::pow(dc / p.delta_cells, p.exponent + 1.0) / (p.exponent + 1.0);
+  return std::exp(-e);
+}
+
+template <typename T>
+FieldPtrs<T>& fields(picpml_ctx* c);
+template <>
+FieldPtrs<float>& fields<float>(picpml_ctx* c) { return c->ff; }
+template <>
+FieldPtrs<double>& fields<double>(picpml_ctx* c) { return c->fd; }
+
+template <typename T>
+SpeciesPtrs<T> species_ptrs(picpml_ctx* ctx, Species& s) {
+  SpeciesPtrs<T> p{};
+  p.pos = s.desc.pos;
+  p.mom = s.desc.mom;
+  p.n_dev = s.n_dev;
+  p.capacity = s.desc.capacity;
+  p.ke = (T)s.ke;
+  for (int a = 0; a < 3; ++a) p.cj[a] = (T)s.cj[a];
+  p.cjy2d = (T)s.cjy2d;
+  p.immobile = s.desc.immobile;
+  p.save_pos = reinterpret_cast<float4*>(s.save);
+  p.save_mom = nullptr;
+  return p;
+}
+
+template <typename T>
+int run_particles(picpml_ctx* ctx, int mode) {
+  for (auto& s : ctx->sp) {
+    if (s.desc.immobile && mode != 0) continue;
+    SpeciesPtrs<T> p = species_ptrs<T>(ctx, s);
+    if (s.desc.capacity <= 0) continue;
+    CK(launch_particles<T>(mode, ctx->gd.shape_order, ctx->g, ctx->tb, fields<T>(ctx), p, ctx->prescribed,
+                           ctx->status, ctx->pushed, ctx->nsm, ctx->stream));
+    ctx->launches += 1;
+  }
+  return PIC_OK;
+}
+
+template <typename T>
+int run_field(picpml_ctx* ctx) {
+  FieldPtrs<T>& f = fields<T>(ctx);
+  CK(launch_field_E<T>(ctx->g, ctx->tb, f, ctx->stream));
+  CK(launch_field_B<T>(ctx->g, ctx->tb, f, ctx->stream));
+  ctx->launches += 2;
+  for (int c = 0; c < 3; ++c) std::swap(f.Bh[c], f.Bp[c]);
+  return PIC_OK;
+}
+
+int check_ready(picpml_ctx* ctx) {
+  if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
+  if (!ctx->ready) return fail(ctx, PIC_ESTATE, "pml_init has not been called");
+  return PIC_OK;
+}
+
+template <typename T>
+int do_sort(picpml_ctx* ctx) {
+  const long long ncell = (long long)ctx->g.N[0] * (ctx->g.dim == 3 ? ctx->g.N[1] : 1) * ctx->g.N[2];
+  if (!ctx->sort_scratch) {
+    ctx->sort_scratch = (unsigned*)dev_alloc(ctx, sort_scratch_words(ncell) * sizeof(unsigned));
+    if (!ctx->sort_scratch) return fail(ctx, PIC_ENOMEM, "sort scratch");
+  }
+  for (auto& s : ctx->sp) {
+    if (!s.tmp_pos) {
+      s.tmp_pos = dev_alloc(ctx, (size_t)s.desc.capacity * ctx->pbytes());
+      s.tmp_mom = dev_alloc(ctx, (size_t)s.desc.capacity * ctx->pbytes());
+      if (!s.tmp_pos || !s.tmp_mom) return fail(ctx, PIC_ENOMEM, "sort buffers");
+    }
+    CK(launch_sort(ctx->g, ctx->pbytes(), s.desc.pos, s.desc.mom, s.n_dev, s.desc.capacity, ctx->sort_scratch,
+                   s.tmp_pos, s.tmp_mom, ctx->stream));
+    ctx->launches += sort_launches(ncell);
+  }
+  return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pic_init(picpml_ctx** out, const pic_grid_desc* g, void* stream) {
+  if (!out || !g) return fail(nullptr, PIC_EINVAL, "null argument");
+  *out = nullptr;
+  if (g->dim != 2 && g->dim != 3) return fail(nullptr, PIC_EINVAL, "dim must be 2 or 3");
+  if (g->shape_order != 1 && g->shape_order != 3) return fail(nullptr, PIC_EINVAL, "shape_order must be 1 or 3");
+  if (g->prec != PIC_FP32 && g->prec != PIC_FP64 && g->prec != PIC_FP32_FIXED64)
+    return fail(nullptr, PIC_EINVAL, "bad prec");
+  if (g->prec == PIC_FP32_FIXED64) return fail(nullptr, PIC_ENOTIMPL, "fixed-point deposition is not built yet");
+  for (int a = 0; a < 3; ++a) {
+    if (g->dim == 2 && a == 1) continue;
+    if (g->n[a] < 1 || !(g->d[a] > 0)) return fail(nullptr, PIC_EINVAL, "cells and cell sizes must be positive");
+  }
+  pic_grid_desc gd = *g;
+  if (gd.dim == 2) {
+    gd.n[1] = 0;
+    gd.d[1] = 1.0;
+  }
+  const double lim = courant_limit(gd);
+  double dt = gd.dt;
+  if (!(dt > 0)) {
+    if (!(gd.cfl > 0 && gd.cfl <= 1.0)) return fail(nullptr, PIC_EINVAL, "dt <= 0 needs 0 < cfl <= 1");
+    dt = gd.cfl * lim;
+  }
+  if (dt > lim * (1 + 1e-12)) return fail(nullptr, PIC_ECFL, "dt above the Yee Courant limit");
+  picpml_ctx* ctx = new picpml_ctx();
+  ctx->gd = gd;
+  ctx->dt = dt;
+  ctx->stream = (cudaStream_t)stream;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, dev);
+  *out = ctx;
+  return PIC_OK;
+}
+
+int pml_init(picpml_ctx* ctx, const pml_desc* p) {
+  if (!ctx || !p) return fail(ctx, PIC_EINVAL, "null argument");
+  if (ctx->ready) return fail(ctx, PIC_ESTATE, "pml_init called twice");
+  if (p->alpha_mode < 0 || p->alpha_mode > 2) return fail(ctx, PIC_EINVAL, "bad alpha_mode");
+  if (p->sigma_max_coef < 0 || !(p->delta_cells > 0) || p->exponent < 0)
+    return fail(ctx, PIC_EINVAL, "bad conductivity profile");
+  const pic_grid_desc& gd = ctx->gd;
+  ctx->pd = *p;
+  Geom& g = ctx->g;
+  g.dim = gd.dim;
+  const int margin = gd.shape_order == 1 ? 2 : 3;
+  for (int a = 0; a < 3; ++a) {
+    if (gd.dim == 2 && a == 1) {
+      g.N[1] = 0; g.nn[1] = 1; g.plo[1] = 0; g.nph[1] = 0; g.rmin[1] = 0; g.rmax[1] = 1 << 30;
+      g.S[1] = 0.0;
+      continue;
+    }
+    const int lo = p->ncell[2 * a], hi = p->ncell[2 * a + 1];
+    if (lo < 0 || hi < 0) return fail(ctx, PIC_EINVAL, "negative PML width");
+    g.plo[a] = lo;
+    g.nph[a] = gd.n[a];
+    g.N[a] = gd.n[a] + lo + hi;
+    g.nn[a] = g.N[a] + 1;
+    g.S[a] = kC * ctx->dt / gd.d[a];
+    int rmin = margin, rmax = g.N[a] - margin;
+    if (p->alpha_mode == PML_ALPHA_ZERO) {
+      rmin = std::max(rmin, lo);
+      rmax = std::min(rmax, lo + gd.n[a]);
+    }
+    g.rmin[a] = rmin;
+    g.rmax[a] = rmax;
+    if (rmax <= rmin) return fail(ctx, PIC_EINVAL, "grid too small for the particle shape");
+  }
+  if (g.N[0] > 1023 || g.N[1] > 1023 || g.N[2] > 2047)
+    return fail(ctx, PIC_EINVAL, "grid too large for the packed cell index (1023 x 1023 x 2047 cells)");
+  g.px = (g.nn[0] + 7) / 8 * 8;
+  g.sy = g.px;
+  g.sz = (long long)g.px * g.nn[1];
+  g.size = g.sz * g.nn[2];
+
+  // per-axis tables at nodes and centres
+  std::vector<double> host;
+  const int nt = 10;  // ea_n eb_n sdt_n ea_c eb_c sdt_c al_nd al_cd (+2 float arrays packed after)
+  size_t total = 0;
+  for (int a = 0; a < 3; ++a) total += (size_t)g.nn[a];
+  host.assign(total * nt, 0.0);
+  std::vector<float> hostf(total * 2, 0.f);
+  double* td = (double*)dev_alloc(ctx, host.size() * sizeof(double));
+  float* tf = (float*)dev_alloc(ctx, hostf.size() * sizeof(float));
+  if (!td || !tf) return fail(ctx, PIC_ENOMEM, "tables");
+  size_t off = 0;
+  for (int a = 0; a < 3; ++a) {
+    const int nn = g.nn[a];
+    const double Delta = gd.d[a];
+    for (int i = 0; i < nn; ++i) {
+      for (int stag = 0; stag < 2; ++stag) {
+        double x = i + 0.5 * stag, dc = 0.0;
+        if (!(gd.dim == 2 && a == 1)) {
+          const double lo = g.plo[a], hi = g.plo[a] + g.nph[a];
+          dc = x < lo ? lo - x : (x > hi ? x - hi : 0.0);
+        }
+        const double s = sigma_eps0(*p, Delta, dc);
+        const double sdt = s * ctx->dt;
+        const double ea = std::exp(-sdt);
+        const double eb = sdt > 0 ? -std::expm1(-sdt) / sdt : 1.0;
+        const double al = alpha_of(*p, dc);
+        const size_t base = off + i;
+        host[(stag * 3 + 0) * total + base] = ea;
+        host[(stag * 3 + 1) * total + base] = eb;
+        host[(stag * 3 + 2) * total + base] = sdt;
+        host[(6 + stag) * total + base] = al;
+        hostf[stag * total + base] = (float)al;
+      }
+    }
+    ctx->tb.ea_n[a] = td + 0 * total + off;
+    ctx->tb.eb_n[a] = td + 1 * total + off;
+    ctx->tb.sdt_n[a] = td + 2 * total + off;
+    ctx->tb.ea_c[a] = td + 3 * total + off;
+    ctx->tb.eb_c[a] = td + 4 * total + off;
+    ctx->tb.sdt_c[a] = td + 5 * total + off;
+    ctx->tb.al_nd[a] = td + 6 * total + off;
+    ctx->tb.al_cd[a] = td + 7 * total + off;
+    ctx->tb.al_nf[a] = tf + off;
+    ctx->tb.al_cf[a] = tf + total + off;
+    off += nn;
+  }
+  CK(cudaMemcpyAsync(td, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(tf, hostf.data(), hostf.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+
+  // fields: 12 arrays of the field type + 12 FP64 split arrays, zeroed
+  const size_t es = ctx->elem();
+  const size_t fbytes = (size_t)g.size * (12 * es + 12 * 8);
+  char* fm = (char*)dev_alloc(ctx, fbytes);
+  if (!fm) return fail(ctx, PIC_ENOMEM, "fields");
+  CK(cudaMemsetAsync(fm, 0, fbytes, ctx->stream));
+  char* q = fm;
+  for (int c = 0; c < 3; ++c) {
+    void* arr[4];
+    for (int t = 0; t < 4; ++t) { arr[t] = q; q += (size_t)g.size * es; }
+    if (gd.prec == PIC_FP64) {
+      ctx->fd.E[c] = (double*)arr[0]; ctx->fd.Bh[c] = (double*)arr[1];
+      ctx->fd.Bp[c] = (double*)arr[2]; ctx->fd.J[c] = (double*)arr[3];
+    } else {
+      ctx->ff.E[c] = (float*)arr[0]; ctx->ff.Bh[c] = (float*)arr[1];
+      ctx->ff.Bp[c] = (float*)arr[2]; ctx->ff.J[c] = (float*)arr[3];
+    }
+  }
+  for (int c = 0; c < 3; ++c)
+    for (int h = 0; h < 2; ++h) {
+      double* e = (double*)q; q += (size_t)g.size * 8;
+      double* b = (double*)q; q += (size_t)g.size * 8;
+      ctx->ff.Es[c][h] = ctx->fd.Es[c][h] = e;
+      ctx->ff.Bs[c][h] = ctx->fd.Bs[c][h] = b;
+    }
+  ctx->status = (unsigned*)dev_alloc(ctx, 64);
+  ctx->pushed = (unsigned long long*)(ctx->status + 8);
+  ctx->diag = (double*)dev_alloc(ctx, 8 * sizeof(double));
+  if (!ctx->status || !ctx->diag) return fail(ctx, PIC_ENOMEM, "status");
+  CK(cudaMemsetAsync(ctx->status, 0, 64, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->ready = true;
+  return PIC_OK;
+}
+
+int pic_add_species(picpml_ctx* ctx, const pic_species* s, int* sid) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (!s || !sid) return fail(ctx, PIC_EINVAL, "null argument");
+  if (s->n < 0 || s->capacity < s->n || (s->capacity > 0 && (!s->pos || !s->mom)))
+    return fail(ctx, PIC_EINVAL, "bad particle arrays");
+  if (!(s->m > 0)) return fail(ctx, PIC_EINVAL, "mass must be positive");
+  if ((reinterpret_cast<uintptr_t>(s->pos) | reinterpret_cast<uintptr_t>(s->mom)) % ctx->pbytes())
+    return fail(ctx, PIC_EINVAL, "particle arrays must be aligned to one particle record");
+  Species sp;
+  sp.desc = *s;
+  sp.n_dev = (long long*)dev_alloc(ctx, sizeof(long long));
+  sp.save = dev_alloc(ctx, (size_t)std::max<long long>(s->capacity, 1) * ctx->pbytes());
+  if (!sp.n_dev || !sp.save) return fail(ctx, PIC_ENOMEM, "species scratch");
+  CK(cudaMemcpyAsync(sp.n_dev, &s->n, sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
+  const pic_grid_desc& gd = ctx->gd;
+  const double q = s->q, dt = ctx->dt;
+  sp.ke = q * dt / (2.0 * s->m * kC);
+  if (gd.dim == 3) {
+    sp.cj[0] = -q / (kEps0 * gd.d[1] * gd.d[2]);
+    sp.cj[1] = -q / (kEps0 * gd.d[0] * gd.d[2]);
+    sp.cj[2] = -q / (kEps0 * gd.d[0] * gd.d[1]);
+  } else {
+    const double Ly = 1.0;  // a 2D macroparticle is a line charge of 1 m along y
+    sp.cj[0] = -q / (kEps0 * gd.d[2] * Ly);
+    sp.cj[2] = -q / (kEps0 * gd.d[0] * Ly);
+    sp.cjy2d = q * dt * kC / (kEps0 * gd.d[0] * gd.d[2] * Ly);
+  }
+  ctx->sp.push_back(sp);
+  *sid = (int)ctx->sp.size() - 1;
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PIC_OK;
+}
+
+int push(picpml_ctx* ctx) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  return ctx->gd.prec == PIC_FP64 ? run_particles<double>(ctx, 0) : run_particles<float>(ctx, 0);
+}
+
+int deposit(picpml_ctx* ctx) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  return ctx->gd.prec == PIC_FP64 ? run_particles<double>(ctx, 1) : run_particles<float>(ctx, 1);
+}
+
+int field_step(picpml_ctx* ctx) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  return ctx->gd.prec == PIC_FP64 ? run_field<double>(ctx) : run_field<float>(ctx);
+}
+
+int pic_sort(picpml_ctx* ctx) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  return ctx->gd.prec == PIC_FP64 ? do_sort<double>(ctx) : do_sort<float>(ctx);
+}
+
+int push_deposit(picpml_ctx* ctx) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  return ctx->gd.prec == PIC_FP64 ? run_particles<double>(ctx, 2) : run_particles<float>(ctx, 2);
+}
+
+int pic_particle_steps(picpml_ctx* ctx, long long* n) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (!n) return fail(ctx, PIC_EINVAL, "null argument");
+  unsigned long long v = 0;
+  CK(cudaMemcpyAsync(&v, ctx->pushed, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *n = (long long)v;
+  return PIC_OK;
+}
+
+int pic_launch_count(picpml_ctx* ctx, long long* n) {
+  if (!ctx || !n) return fail(ctx, PIC_EINVAL, "null argument");
+  *n = ctx->launches;
+  return PIC_OK;
+}
+
+int step_n(picpml_ctx* ctx, int n) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (n < 0) return fail(ctx, PIC_EINVAL, "negative step count");
+  const bool f64 = ctx->gd.prec == PIC_FP64;
+  for (int s = 0; s < n; ++s) {
+    if (ctx->gd.sort_every > 0 && ctx->steps_done % ctx->gd.sort_every == 0) {
+      r = f64 ? do_sort<double>(ctx) : do_sort<float>(ctx);
+      if (r) return r;
+    }
+    r = f64 ? run_particles<double>(ctx, 2) : run_particles<float>(ctx, 2);
+    if (r) return r;
+    r = f64 ? run_field<double>(ctx) : run_field<float>(ctx);
+    if (r) return r;
+    ctx->steps_done++;
+  }
+  return PIC_OK;
+}
+
+int pic_grid_info(picpml_ctx* ctx, int* nn3, double* dt) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (nn3) for (int a = 0; a < 3; ++a) nn3[a] = ctx->g.nn[a];
+  if (dt) *dt = ctx->dt;
+  return PIC_OK;
+}
+
+int pic_get_field(picpml_ctx* ctx, int which, void* dst, int as_double) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (!dst || which < 0 || which > 14) return fail(ctx, PIC_EINVAL, "bad field selector");
+  const int c = which % 3, kind = which / 3;
+  const double scale = kind == 0 ? 1.0 : kind == 2 ? kEps0 / ctx->dt : 1.0 / kC;
+  if (ctx->gd.prec == PIC_FP64) {
+    FieldPtrs<double>& f = ctx->fd;
+    const double* a = kind == 0 ? f.E[c] : kind == 2 ? f.J[c] : kind == 4 ? f.Bp[c] : f.Bh[c];
+    const double* b = kind == 1 ? f.Bp[c] : nullptr;
+    CK(launch_export<double>(ctx->g, a, b, scale, dst, as_double, ctx->stream));
+  } else {
+    FieldPtrs<float>& f = ctx->ff;
+    const float* a = kind == 0 ? f.E[c] : kind == 2 ? f.J[c] : kind == 4 ? f.Bp[c] : f.Bh[c];
+    const float* b = kind == 1 ? f.Bp[c] : nullptr;
+    CK(launch_export<float>(ctx->g, a, b, scale, dst, as_double, ctx->stream));
+  }
+  return PIC_OK;
+}
+
+int pic_set_field(picpml_ctx* ctx, int which, const void* src, int as_double) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (!src || !(which / 3 == 0 || which / 3 == 3 || which / 3 == 4)) return fail(ctx, PIC_EINVAL, "bad field selector");
+  const int c = which % 3, kind = which / 3;
+  const double scale = kind == 0 ? 1.0 : kC;
+  double* s0 = kind == 0 ? ctx->fd.Es[c][0] : kind == 3 ? ctx->fd.Bs[c][0] : nullptr;
+  double* s1 = kind == 0 ? ctx->fd.Es[c][1] : kind == 3 ? ctx->fd.Bs[c][1] : nullptr;
+  if (ctx->gd.prec == PIC_FP64) {
+    double* a = kind == 0 ? ctx->fd.E[c] : kind == 3 ? ctx->fd.Bh[c] : ctx->fd.Bp[c];
+    CK(launch_import<double>(ctx->g, src, as_double, scale, a, s0, s1, ctx->stream));
+  } else {
+    float* a = kind == 0 ? ctx->ff.E[c] : kind == 3 ? ctx->ff.Bh[c] : ctx->ff.Bp[c];
+    CK(launch_import<float>(ctx->g, src, as_double, scale, a, s0, s1, ctx->stream));
+  }
+  return PIC_OK;
+}
+
+int pic_set_prescribed(picpml_ctx* ctx, int flag) {
+  if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
+  ctx->prescribed = flag ? 1 : 0;
+  return PIC_OK;
+}
+
+int pic_num_particles(picpml_ctx* ctx, int sid, long long* n) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (sid < 0 || sid >= (int)ctx->sp.size() || !n) return fail(ctx, PIC_EINVAL, "bad species id");
+  CK(cudaMemcpyAsync(n, ctx->sp[sid].n_dev, sizeof(long long), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PIC_OK;
+}
+
+int pic_sync(picpml_ctx* ctx) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  CK(cudaStreamSynchronize(ctx->stream));
+  unsigned st = 0;
+  CK(cudaMemcpy(&st, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (st & ST_BAD_PARTICLE) return fail(ctx, PIC_EPARTICLE, "a particle was outside its allowed cells (skipped)");
+  if (st & ST_FIXED_OVERFLOW) return fail(ctx, PIC_EOVERFLOW, "fixed-point current overflow");
+  return PIC_OK;
+}
+
+int pic_diag(picpml_ctx* ctx, double* gauss, double* rho_scale, double* energy) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (!ctx->rho) {
+    ctx->rho = (double*)dev_alloc(ctx, (size_t)ctx->g.size * sizeof(double));
+    if (!ctx->rho) return fail(ctx, PIC_ENOMEM, "rho");
+  }
+  CK(cudaMemsetAsync(ctx->rho, 0, (size_t)ctx->g.size * sizeof(double), ctx->stream));
+  CK(cudaMemsetAsync(ctx->diag, 0, 8 * sizeof(double), ctx->stream));
+  const pic_grid_desc& gd = ctx->gd;
+  const double V = gd.d[0] * gd.d[2] * (gd.dim == 3 ? gd.d[1] : 1.0);
+  for (auto& s : ctx->sp) {
+    const double qoe = s.desc.q / (kEps0 * V);
+    if (gd.prec == PIC_FP64)
+      CK(launch_rho<double>(gd.shape_order, ctx->g, s.desc.pos, s.desc.mom, s.n_dev, s.desc.capacity, qoe, ctx->rho,
+                            ctx->stream));
+    else
+      CK(launch_rho<float>(gd.shape_order, ctx->g, s.desc.pos, s.desc.mom, s.n_dev, s.desc.capacity, qoe, ctx->rho,
+                           ctx->stream));
+  }
+  if (gd.prec == PIC_FP64) CK(launch_gauss<double>(ctx->g, ctx->fd, ctx->rho, gd.d, ctx->diag, ctx->stream));
+  else CK(launch_gauss<float>(ctx->g, ctx->ff, ctx->rho, gd.d, ctx->diag, ctx->stream));
+  double h[3];
+  CK(cudaMemcpyAsync(h, ctx->diag, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (gauss) *gauss = h[0];
+  if (rho_scale) *rho_scale = h[1];
+  if (energy) *energy = h[2];
+  return pic_sync(ctx);
+}
+
+int pic_state_size(picpml_ctx* ctx, long long* bytes) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (!bytes) return fail(ctx, PIC_EINVAL, "null argument");
+  *bytes = (long long)ctx->g.size * (12 * ctx->elem() + 12 * 8);
+  return PIC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+void state_arrays(picpml_ctx* ctx, FieldPtrs<T>& f, std::vector<std::pair<void*, size_t>>& v) {
+  const size_t n = (size_t)ctx->g.size;
+  for (int c = 0; c < 3; ++c) {
+    v.push_back({f.E[c], n * sizeof(T)});
+    v.push_back({f.Bh[c], n * sizeof(T)});
+    v.push_back({f.Bp[c], n * sizeof(T)});
+    v.push_back({f.J[c], n * sizeof(T)});
+  }
+  for (int c = 0; c < 3; ++c)
+    for (int h = 0; h < 2; ++h) {
+      v.push_back({f.Es[c][h], n * 8});
+      v.push_back({f.Bs[c][h], n * 8});
+    }
+}
+}  // namespace
+
+extern "C" {
+
+int pic_get_state(picpml_ctx* ctx, void* host_dst) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (!host_dst) return fail(ctx, PIC_EINVAL, "null argument");
+  std::vector<std::pair<void*, size_t>> v;
+  if (ctx->gd.prec == PIC_FP64) state_arrays(ctx, ctx->fd, v);
+  else state_arrays(ctx, ctx->ff, v);
+  char* q = (char*)host_dst;
+  for (auto& a : v) {
+    CK(cudaMemcpyAsync(q, a.first, a.second, cudaMemcpyDeviceToHost, ctx->stream));
+    q += a.second;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PIC_OK;
+}
+
+int pic_set_state(picpml_ctx* ctx, const void* host_src) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (!host_src) return fail(ctx, PIC_EINVAL, "null argument");
+  std::vector<std::pair<void*, size_t>> v;
+  if (ctx->gd.prec == PIC_FP64) state_arrays(ctx, ctx->fd, v);
+  else state_arrays(ctx, ctx->ff, v);
+  const char* q = (const char*)host_src;
+  for (auto& a : v) {
+    CK(cudaMemcpyAsync(a.first, q, a.second, cudaMemcpyHostToDevice, ctx->stream));
+    q += a.second;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PIC_OK;
+}
+
+const char* pic_last_error(picpml_ctx* ctx) { return ctx ? ctx->err.c_str() : g_init_error.c_str(); }
+
+void pic_destroy(picpml_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (void* p : ctx->allocs) cudaFree(p);
+  delete ctx;
+}
+
+}  // extern "C"

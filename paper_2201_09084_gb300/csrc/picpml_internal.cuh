@@ -1,0 +1,94 @@
+// Internal definitions of libpicpml (not part of the ABI).
+//
+// Field normalisation used by every kernel: E' = E (V/m), B' = c B (V/m),
+// J' = J dt / eps0 (V/m).  The Yee update is then
+//   E' += S_a (B'_+ - B'_-) - J',   B' -= S_a (E'_+ - E'_-),
+// with Courant numbers S_a = c dt / Delta_a, and the Boris push uses the one
+// constant ke = q dt / (2 m c) for both E' and B' (Sec. II.B: the alpha terms
+// leave the usual FDTD discretisation unchanged).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace picpml {
+
+constexpr double kC = 299792458.0;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kMu0 = 1.0 / (kEps0 * kC * kC);
+
+// Packed cell index: i | j << 10 | k << 20; -1 marks a removed particle.
+__host__ __device__ inline int cell_i(int c) { return c & 1023; }
+__host__ __device__ inline int cell_j(int c) { return (c >> 10) & 1023; }
+__host__ __device__ inline int cell_k(int c) { return (c >> 20) & 2047; }
+__host__ __device__ inline int pack_cell(int i, int j, int k) { return i | (j << 10) | (k << 20); }
+
+// Grid geometry, passed by value to kernels.
+struct Geom {
+  int dim;
+  int N[3];        // total cells per axis (physical + PML); N[1] = 0 in 2D
+  int nn[3];       // nodes per axis stored: N + 1 (1 for y in 2D)
+  int px;          // x pitch of the field arrays (elements)
+  long long sy;    // stride of j
+  long long sz;    // stride of k
+  long long size;  // elements per field array
+  double S[3];     // Courant numbers c dt / d_a
+  int plo[3];      // PML cells on the low face
+  int nph[3];      // physical cells
+  int rmin[3], rmax[3];  // a particle at X = i + f stays while rmin <= X <= rmax
+  __host__ __device__ long long idx(int i, int j, int k) const {
+    return (long long)i + sy * j + sz * k;
+  }
+};
+
+// Per-axis 1-D coefficient tables (device pointers), Sec. II.B: sigma and
+// alpha at the nodes and the cell centres of the staggered grid.
+struct Tables {
+  // exponential differencing of d/dt F = R - s F over dt, normalised so that
+  // F <- ea F + eb (R dt):  ea = exp(-s dt), eb = (1 - ea)/(s dt) (1 if s = 0)
+  const double* ea_n[3];
+  const double* eb_n[3];
+  const double* sdt_n[3];   // s dt at the nodes (to pick the source split)
+  const double* ea_c[3];
+  const double* eb_c[3];
+  const double* sdt_c[3];
+  const float* al_nf[3];    // alpha at nodes / centres, FP32 copy
+  const float* al_cf[3];
+  const double* al_nd[3];   // FP64 copy
+  const double* al_cd[3];
+};
+
+template <typename T>
+struct FieldPtrs {
+  T* E[3];
+  T* Bh[3];   // B'^{n+1/2}
+  T* Bp[3];   // B'^{n-1/2} (overwritten with B'^{n+3/2} by the B pass)
+  T* J[3];    // J' (dt/eps0 units)
+  double* Es[3][2];
+  double* Bs[3][2];
+};
+
+// Particle data of one species for a kernel.
+template <typename T>
+struct SpeciesPtrs {
+  void* pos;
+  void* mom;
+  const long long* n_dev;   // live count on the device (upper bound of indices)
+  long long capacity;
+  T ke;                     // q dt / (2 m c)
+  T cj[3];                  // J' per unit weight: -q/(eps0 d_b d_c) (3D)
+  T cjy2d;                  // 2D out-of-plane: q dt c /(eps0 dx dz Ly)
+  int immobile;
+  float4* save_pos;         // scratch of push(): x^n (FP32 layout)
+  float4* save_mom;
+};
+
+// 32-byte aligned quadruple of doubles (FP64 particle layout).
+struct __align__(32) dbl4 {
+  double x, y, z, w;
+};
+
+// Device status word bits.
+enum : unsigned { ST_BAD_PARTICLE = 1u, ST_FIXED_OVERFLOW = 2u };
+
+}  // namespace picpml

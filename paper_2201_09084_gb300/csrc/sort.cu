@@ -1,0 +1,164 @@
+// Counting sort of one species by cell index, dropping removed particles.
+// Consecutive particles then share their cell, so the gather hits the same
+// field lines and the deposit hits the same current lines (L1/L2 locality).
+//   1. histogram of the linear cell index (atomics),
+//   2. exclusive scan of the histogram (block scans + recursive carry),
+//   3. scatter into scratch arrays (order within a cell is not kept),
+//   4. copy back, live count := number of kept particles.
+#include "picpml_internal.cuh"
+
+namespace picpml {
+
+namespace {
+
+__device__ __forceinline__ long long lin_cell(const Geom& g, int cell) {
+  return (long long)cell_i(cell) + (long long)g.N[0] * ((long long)cell_j(cell) + (long long)(g.dim == 3 ? g.N[1] : 1) * cell_k(cell));
+}
+
+template <int PB>
+__device__ __forceinline__ int read_cell(const void* mom, long long p) {
+  if (PB == 16) return __float_as_int(reinterpret_cast<const float4*>(mom)[p].w);
+  return (int)__double_as_longlong(reinterpret_cast<const dbl4*>(mom)[p].w);
+}
+
+template <int PB>
+__global__ void k_hist(Geom g, const void* mom, const long long* n_dev, unsigned* cnt) {
+  const long long n = *n_dev;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    int c = read_cell<PB>(mom, p);
+    if (c >= 0) atomicAdd(cnt + lin_cell(g, c), 1u);
+  }
+}
+
+// Exclusive scan of 2*blockDim elements per block; block totals to sums.
+__global__ void k_scan_block(unsigned* data, long long n, unsigned* sums) {
+  extern __shared__ unsigned sh[];
+  const int t = threadIdx.x, B = blockDim.x;
+  const long long base = (long long)blockIdx.x * 2 * B;
+  sh[t] = base + t < n ? data[base + t] : 0u;
+  sh[t + B] = base + t + B < n ? data[base + t + B] : 0u;
+  // up-sweep
+  int off = 1;
+  for (int d = B; d > 0; d >>= 1) {
+    __syncthreads();
+    if (t < d) {
+      int ai = off * (2 * t + 1) - 1, bi = off * (2 * t + 2) - 1;
+      sh[bi] += sh[ai];
+    }
+    off <<= 1;
+  }
+  if (t == 0) {
+    if (sums) sums[blockIdx.x] = sh[2 * B - 1];
+    sh[2 * B - 1] = 0;
+  }
+  // down-sweep
+  for (int d = 1; d < 2 * B; d <<= 1) {
+    off >>= 1;
+    __syncthreads();
+    if (t < d) {
+      int ai = off * (2 * t + 1) - 1, bi = off * (2 * t + 2) - 1;
+      unsigned v = sh[ai];
+      sh[ai] = sh[bi];
+      sh[bi] += v;
+    }
+  }
+  __syncthreads();
+  if (base + t < n) data[base + t] = sh[t];
+  if (base + t + B < n) data[base + t + B] = sh[t + B];
+}
+
+__global__ void k_add_carry(unsigned* data, long long n, const unsigned* sums) {
+  const long long base = (long long)blockIdx.x * 2 * blockDim.x;
+  const unsigned c = sums[blockIdx.x];
+  for (int q = 0; q < 2; ++q) {
+    long long t = base + threadIdx.x + q * blockDim.x;
+    if (t < n) data[t] += c;
+  }
+}
+
+template <int PB>
+__global__ void k_scatter(Geom g, const void* pos, const void* mom, const long long* n_dev, unsigned* cursor,
+                          void* pos_out, void* mom_out) {
+  const long long n = *n_dev;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    int c = read_cell<PB>(mom, p);
+    if (c < 0) continue;
+    unsigned d = atomicAdd(cursor + lin_cell(g, c), 1u);
+    if (PB == 16) {
+      reinterpret_cast<float4*>(pos_out)[d] = reinterpret_cast<const float4*>(pos)[p];
+      reinterpret_cast<float4*>(mom_out)[d] = reinterpret_cast<const float4*>(mom)[p];
+    } else {
+      reinterpret_cast<dbl4*>(pos_out)[d] = reinterpret_cast<const dbl4*>(pos)[p];
+      reinterpret_cast<dbl4*>(mom_out)[d] = reinterpret_cast<const dbl4*>(mom)[p];
+    }
+  }
+}
+
+// After the scatter every cursor holds the end offset of its cell, so the
+// last one is the number of kept particles.
+__global__ void k_set_count(const unsigned* cursor, long long ncell, long long* n_dev) {
+  *n_dev = (long long)cursor[ncell - 1];
+}
+
+constexpr int kScanT = 512;
+
+cudaError_t scan(unsigned* data, long long n, unsigned* tmp, cudaStream_t s) {
+  const long long per = 2LL * kScanT;
+  const long long nb = (n + per - 1) / per;
+  unsigned* sums = tmp;
+  k_scan_block<<<(unsigned)nb, kScanT, 2 * kScanT * sizeof(unsigned), s>>>(data, n, nb > 1 ? sums : nullptr);
+  if (nb > 1) {
+    cudaError_t e = scan(sums, nb, tmp + nb, s);
+    if (e != cudaSuccess) return e;
+    k_add_carry<<<(unsigned)nb, kScanT, 0, s>>>(data, n, sums);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// Kernels one sort launches: histogram, the scan levels with their carry
+// passes, scatter, count.
+int sort_launches(long long ncell) {
+  int k = 3;
+  long long n = ncell;
+  for (;;) {
+    const long long nb = (n + 2LL * kScanT - 1) / (2LL * kScanT);
+    k += 1;
+    if (nb <= 1) break;
+    k += 1;
+    n = nb;
+  }
+  return k;
+}
+
+// Scratch needed: hist (ncell+1) + scan carries (< ncell/512) unsigned.
+long long sort_scratch_words(long long ncell) { return ncell + 1 + ncell / 512 + 64; }
+
+cudaError_t launch_sort(const Geom& g, int pbytes, void* pos, void* mom, long long* n_dev, long long cap,
+                        unsigned* scratch, void* tmp_pos, void* tmp_mom, cudaStream_t s) {
+  const long long ncell = (long long)g.N[0] * (g.dim == 3 ? g.N[1] : 1) * g.N[2];
+  unsigned* hist = scratch;
+  unsigned* carry = scratch + ncell + 1;
+  cudaError_t e = cudaMemsetAsync(hist, 0, (ncell + 1) * sizeof(unsigned), s);
+  if (e != cudaSuccess) return e;
+  int blocks = (int)((cap + 255) / 256);
+  if (blocks > 8192) blocks = 8192;
+  if (blocks < 1) blocks = 1;
+  if (pbytes == 16) k_hist<16><<<blocks, 256, 0, s>>>(g, mom, n_dev, hist);
+  else k_hist<32><<<blocks, 256, 0, s>>>(g, mom, n_dev, hist);
+  e = scan(hist, ncell, carry, s);
+  if (e != cudaSuccess) return e;
+  if (pbytes == 16) k_scatter<16><<<blocks, 256, 0, s>>>(g, pos, mom, n_dev, hist, tmp_pos, tmp_mom);
+  else k_scatter<32><<<blocks, 256, 0, s>>>(g, pos, mom, n_dev, hist, tmp_pos, tmp_mom);
+  k_set_count<<<1, 1, 0, s>>>(hist, ncell, n_dev);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(pos, tmp_pos, cap * pbytes, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyAsync(mom, tmp_mom, cap * pbytes, cudaMemcpyDeviceToDevice, s);
+}
+
+}  // namespace picpml

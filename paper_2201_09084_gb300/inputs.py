@@ -1,0 +1,109 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the bench.
+
+Only random draws and unit bookkeeping live here (no step of the PIC method):
+each generator returns particles as an int cell index per axis plus an FP32
+in-cell offset, FP32 momenta u = p/(mc) and FP32 weights.  The oracle reads
+the same numbers as absolute FP64 positions cell + offset (exact), the CUDA
+path packs them into its particle records, so both start from bit-identical
+inputs.
+
+Workloads (the paper's single-particle studies, App. A, and the beam/plasma
+shapes of the benchmark configurations) are synthetic stand-ins: the paper
+used WarpX runs whose inputs and data are not available here.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+Q_E = 1.602176634e-19
+M_E = 9.1093837015e-31
+M_P = 1.67262192369e-27
+SEED_BASE = 20220121
+
+
+def split_position(X):
+    """Absolute positions (cell units, float64, shape (n,3)) -> (cell int32,
+    offset float32 in [0,1)), exactly representable on both sides."""
+    X = np.asarray(X, dtype=np.float64)
+    cell = np.floor(X).astype(np.int64)
+    off = (X - cell).astype(np.float32)
+    bump = off >= np.float32(1.0)
+    cell[bump] += 1
+    off[bump] = 0.0
+    return cell.astype(np.int32), off
+
+
+def absolute(cell, off):
+    """cell + offset as FP64 (what the oracle consumes)."""
+    return np.asarray(cell, dtype=np.float64) + np.asarray(off, dtype=np.float64)
+
+
+def _pack(X, u, w, dim):
+    X = np.array(X, dtype=np.float64, ndmin=2)
+    if dim == 2:
+        X[:, 1] = 0.0
+    cell, off = split_position(X)
+    if dim == 2:
+        cell[:, 1] = 0
+        off[:, 1] = 0.0
+    return dict(cell=cell, off=off, u=np.asarray(u, dtype=np.float32).reshape(-1, 3),
+                w=np.asarray(w, dtype=np.float32).reshape(-1))
+
+
+def single_pair(dim, nphys, pml, gamma, theta_deg=0.0, start=None, q=-Q_E, m=M_E):
+    """One macroparticle of Lorentz factor gamma moving in the x-z plane at
+    theta_deg from +z, and its motionless opposite-charge partner at the same
+    place (App. A, single-particle simulations).  start: absolute position in
+    cells (default: centre of the physical box, off the nodes)."""
+    lo = np.array([pml[0], pml[2], pml[4]], dtype=np.float64)
+    if start is None:
+        start = lo + 0.5 * np.array([nphys[0], nphys[1] if dim == 3 else 0, nphys[2]]) + [0.3, 0.1, 0.2]
+    u = np.sqrt(gamma ** 2 - 1.0)
+    th = np.radians(theta_deg)
+    mover = _pack([start], [[u * np.sin(th), 0.0, u * np.cos(th)]], [1.0], dim)
+    partner = _pack([start], [[0.0, 0.0, 0.0]], [1.0], dim)
+    return [dict(mover, q=q, m=m, immobile=False), dict(partner, q=-q, m=m, immobile=True)]
+
+
+def beam(dim, n_particles, nphys, pml, center, sigma=(4.0, 4.0, 8.0), uz_mean=50.0, uz_rms=0.5,
+         theta_deg=0.0, total_charge=1e-9, seed=SEED_BASE + 1, clip=3.5, q=-Q_E, m=M_E):
+    """Relativistic Gaussian electron beam: rms sizes `sigma` (cells, along
+    x, y and the beam axis), u along the beam axis ~ N(uz_mean, uz_rms), the
+    beam axis rotated by theta_deg from +z towards +x.  Draws beyond `clip`
+    standard deviations are redrawn.  Weights give `total_charge` coulombs."""
+    rng = np.random.default_rng(seed)
+    sig = np.asarray(sigma, dtype=np.float64)
+    P = np.empty((0, 3))
+    while len(P) < n_particles:
+        d = rng.standard_normal((n_particles, 3))
+        d = d[np.all(np.abs(d) <= clip, axis=1)]
+        P = np.concatenate([P, d * sig])
+    P = P[:n_particles]
+    uz = rng.normal(uz_mean, uz_rms, n_particles)
+    th = np.radians(theta_deg)
+    c, s = np.cos(th), np.sin(th)
+    X = np.empty_like(P)
+    X[:, 0] = center[0] + c * P[:, 0] + s * P[:, 2]
+    X[:, 1] = center[1] + P[:, 1]
+    X[:, 2] = center[2] - s * P[:, 0] + c * P[:, 2]
+    u = np.zeros((n_particles, 3))
+    u[:, 0] = s * uz
+    u[:, 2] = c * uz
+    if dim == 2:
+        u[:, 1] = 0.0
+    w = np.full(n_particles, total_charge / (Q_E * n_particles))
+    key = (np.floor(X[:, 2]) * 4096 + np.floor(X[:, 1])) * 4096 + np.floor(X[:, 0])
+    order = np.argsort(key, kind="stable")   # cell-ordered start
+    out = _pack(X[order], u[order], w, dim)
+    return [dict(out, q=q, m=m, immobile=False)]
+
+
+def random_particles(dim, n_particles, lo, hi, u_rms=0.5, seed=SEED_BASE + 7, q=-Q_E, m=M_E, w=1.0):
+    """Uniform positions in the box [lo, hi) (cells), Gaussian momenta."""
+    rng = np.random.default_rng(seed)
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    X = lo + rng.random((n_particles, 3)) * (hi - lo)
+    u = rng.normal(0.0, u_rms, (n_particles, 3))
+    out = _pack(X, u, np.full(n_particles, w), dim)
+    return [dict(out, q=q, m=m, immobile=False)]

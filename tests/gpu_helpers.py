@@ -1,0 +1,57 @@
+"""Shared set-up for the GPU parity tests: one oracle box and one CUDA box built
+from the same seeded inputs (paper_2201_09084_gb300.inputs)."""
+import numpy as np
+
+import oracle as O
+from paper_2201_09084_gb300 import inputs as I
+
+# Tolerances (max |GPU - oracle| / max |oracle| over a whole field array):
+# FP32 kernels: 1e-5 (the target accuracy of the FP32 form against the FP64
+# oracle); FP64 kernels: 1e-11 (only the summation order of the current
+# atomics and of the split sums differs from the oracle).
+TOL = {"fp32": 1e-5, "fp64": 1e-11}
+
+
+def make_pair(dim, nphys, pml, d, parts, order=1, prec="fp32", alpha_mode="damped", cfl=0.99,
+              sigma_coef=4.0, delta=6.0, exponent=2.0, v_assumed=O.C_LIGHT, prescribed=False, sort_every=0):
+    import torch
+    from paper_2201_09084_gb300.api import Sim, pack_particles
+    dt = O.yee_dt(d, cfl, dim)
+    ora = O.OracleSim(dim, nphys, pml, d, dt, order=order, alpha_mode=alpha_mode, sig_coef=sigma_coef,
+                      delta=delta, sig_exp=exponent, v_assumed=v_assumed)
+    gpu = Sim(dim, nphys, d, pml, dt=dt, order=order, prec=prec, alpha_mode=alpha_mode,
+              sigma_coef=sigma_coef, delta=delta, exponent=exponent, v_assumed=v_assumed,
+              sort_every=sort_every)
+    for sp in parts:
+        X = I.absolute(sp["cell"], sp["off"])
+        u = sp["u"].astype(np.float64)
+        w = sp["w"].astype(np.float64)
+        refused = ora.add_particles(X[:, 0], X[:, 1], X[:, 2], u[:, 0], u[:, 1], u[:, 2], w,
+                                    sp["q"], sp["m"], sp["immobile"])
+        assert refused == 0
+        pos, mom = pack_particles(sp["cell"], sp["off"], sp["u"], sp["w"], prec)
+        gpu.add_species(pos, mom, len(w), sp["q"], sp["m"], sp["immobile"])
+    if prescribed:
+        ora.set_prescribed(True)
+        gpu.set_prescribed(True)
+    torch.cuda.synchronize()
+    return ora, gpu
+
+
+def field_err(ora, gpu, name):
+    a = ora.field(name)
+    b = gpu.field(name).cpu().numpy()
+    scale = np.abs(a).max()
+    if scale == 0:
+        return float(np.abs(b).max())
+    return float(np.abs(a - b).max() / scale)
+
+
+def max_field_err(ora, gpu, names=("Ex", "Ey", "Ez", "Bx", "By", "Bz")):
+    return {n: field_err(ora, gpu, n) for n in names}
+
+
+def gpu_positions(gpu, sid):
+    p = gpu.particles(sid)
+    X = p["cell"].astype(np.float64) + p["off"].astype(np.float64)
+    return X, p["u"].astype(np.float64), p["alive"]

@@ -52,6 +52,10 @@ __global__ void k_rho(Geom g, const void* pos, const void* mom, const long long*
     bsp<ORDER, T>(o[2], wz);
     if (DIM == 3) bsp<ORDER, T>(o[1], wy);
     const int i = cell_i(cell) - lo, j = DIM == 3 ? cell_j(cell) - lo : 0, k = cell_k(cell) - lo;
+    // skip a record whose stencil would leave the node arrays
+    if (i < 0 || k < 0 || j < 0 || i + W - 1 > g.N[0] || k + W - 1 > g.N[2] ||
+        (DIM == 3 && j + W - 1 > g.N[1]))
+      continue;
     for (int tz = 0; tz < W; ++tz)
       for (int ty = 0; ty < (DIM == 3 ? W : 1); ++ty)
         for (int tx = 0; tx < W; ++tx)

@@ -31,6 +31,10 @@ template <typename T>
 cudaError_t launch_export(const Geom&, const T*, const T*, double, void*, int, cudaStream_t);
 template <typename T>
 cudaError_t launch_import(const Geom&, const void*, int, double, T*, double*, double*, cudaStream_t);
+template <typename T>
+cudaError_t launch_push_deposit_runs(int ppt, const Geom&, const Tables&, const FieldPtrs<T>&, const SpeciesPtrs<T>&,
+                                     int prescribed, unsigned* status, unsigned long long* pushed, int nsm,
+                                     cudaStream_t);
 long long sort_scratch_words(long long ncell);
 int sort_launches(long long ncell);
 cudaError_t launch_sort(const Geom&, int pbytes, void* pos, void* mom, long long* n_dev, long long cap,
@@ -73,6 +77,8 @@ struct picpml_ctx {
   unsigned* sort_scratch = nullptr;
   std::vector<Species> sp;
   int prescribed = 0;
+  int use_runs = 1;   // order-1 fused kernel over sorted runs (else one thread per particle)
+  int ppt = 0;        // particles per thread of the run kernel (0 = default)
   long long steps_done = 0;
   long long launches = 0;
   std::string err;
@@ -158,8 +164,12 @@ int run_particles(picpml_ctx* ctx, int mode) {
     if (s.desc.immobile && mode != 0) continue;
     SpeciesPtrs<T> p = species_ptrs<T>(ctx, s);
     if (s.desc.capacity <= 0) continue;
-    CK(launch_particles<T>(mode, ctx->gd.shape_order, ctx->g, ctx->tb, fields<T>(ctx), p, ctx->prescribed,
-                           ctx->status, ctx->pushed, ctx->nsm, ctx->stream));
+    if (mode == 2 && ctx->gd.shape_order == 1 && ctx->use_runs)
+      CK(launch_push_deposit_runs<T>(ctx->ppt, ctx->g, ctx->tb, fields<T>(ctx), p, ctx->prescribed, ctx->status,
+                                     ctx->pushed, ctx->nsm, ctx->stream));
+    else
+      CK(launch_particles<T>(mode, ctx->gd.shape_order, ctx->g, ctx->tb, fields<T>(ctx), p, ctx->prescribed,
+                             ctx->status, ctx->pushed, ctx->nsm, ctx->stream));
     ctx->launches += 1;
   }
   return PIC_OK;

@@ -8,178 +8,13 @@
 // condition), so the cell index changes by at most one per axis per step and
 // the Esirkepov stencil of a move spans ORDER+2 nodes per axis starting at
 // min(old cell, new cell) - (ORDER-1)/2.
-#include "picpml_internal.cuh"
+#include "particle_common.cuh"
 
 namespace picpml {
 
 namespace {
 
-template <typename T>
-struct PIO;
-
-template <>
-struct PIO<float> {
-  __device__ static void load(const void* pos, const void* mom, long long p, float o[3], float& w,
-                              float u[3], int& cell) {
-    float4 a = reinterpret_cast<const float4*>(pos)[p];
-    float4 b = reinterpret_cast<const float4*>(mom)[p];
-    o[0] = a.x; o[1] = a.y; o[2] = a.z; w = a.w;
-    u[0] = b.x; u[1] = b.y; u[2] = b.z; cell = __float_as_int(b.w);
-  }
-  __device__ static void store(void* pos, void* mom, long long p, const float o[3], float w,
-                               const float u[3], int cell) {
-    reinterpret_cast<float4*>(pos)[p] = make_float4(o[0], o[1], o[2], w);
-    reinterpret_cast<float4*>(mom)[p] = make_float4(u[0], u[1], u[2], __int_as_float(cell));
-  }
-  __device__ static void save(void* sv, long long p, const float o[3], int cell) {
-    reinterpret_cast<float4*>(sv)[p] = make_float4(o[0], o[1], o[2], __int_as_float(cell));
-  }
-  __device__ static void restore(const void* sv, long long p, float o[3], int& cell) {
-    float4 a = reinterpret_cast<const float4*>(sv)[p];
-    o[0] = a.x; o[1] = a.y; o[2] = a.z; cell = __float_as_int(a.w);
-  }
-};
-
-template <>
-struct PIO<double> {
-  __device__ static void load(const void* pos, const void* mom, long long p, double o[3], double& w,
-                              double u[3], int& cell) {
-    dbl4 a = reinterpret_cast<const dbl4*>(pos)[p];
-    dbl4 b = reinterpret_cast<const dbl4*>(mom)[p];
-    o[0] = a.x; o[1] = a.y; o[2] = a.z; w = a.w;
-    u[0] = b.x; u[1] = b.y; u[2] = b.z; cell = (int)__double_as_longlong(b.w);
-  }
-  __device__ static void store(void* pos, void* mom, long long p, const double o[3], double w,
-                               const double u[3], int cell) {
-    dbl4 a; a.x = o[0]; a.y = o[1]; a.z = o[2]; a.w = w;
-    dbl4 b; b.x = u[0]; b.y = u[1]; b.z = u[2]; b.w = __longlong_as_double((long long)cell);
-    reinterpret_cast<dbl4*>(pos)[p] = a;
-    reinterpret_cast<dbl4*>(mom)[p] = b;
-  }
-  __device__ static void save(void* sv, long long p, const double o[3], int cell) {
-    dbl4 a; a.x = o[0]; a.y = o[1]; a.z = o[2]; a.w = __longlong_as_double((long long)cell);
-    reinterpret_cast<dbl4*>(sv)[p] = a;
-  }
-  __device__ static void restore(const void* sv, long long p, double o[3], int& cell) {
-    dbl4 a = reinterpret_cast<const dbl4*>(sv)[p];
-    o[0] = a.x; o[1] = a.y; o[2] = a.z; cell = (int)__double_as_longlong(a.w);
-  }
-};
-
-// B-spline weights of the ORDER+1 nodes around a point at offset f in [0,1)
-// from node `base` (nodes base - (ORDER==3) ... base - (ORDER==3) + ORDER).
-template <int ORDER, typename T>
-__device__ __forceinline__ void bspline(T f, T* w) {
-  if (ORDER == 1) {
-    w[0] = T(1) - f;
-    w[1] = f;
-  } else {
-    const T g = T(1) - f;
-    w[0] = g * g * g * T(1.0 / 6.0);
-    w[1] = T(2.0 / 3.0) - f * f + T(0.5) * f * f * f;
-    w[2] = T(2.0 / 3.0) - g * g + T(0.5) * g * g * g;
-    w[3] = f * f * f * T(1.0 / 6.0);
-  }
-}
-
-// Gather weights along one axis for stagger 0 (nodes) and 1/2 (centres):
-// lowest node index and ORDER+1 weights.
-template <int ORDER, typename T>
-__device__ __forceinline__ void axis_weights(int ic, T f, int& b0, T* w0, int& bh, T* wh) {
-  constexpr int lo = ORDER == 3 ? 1 : 0;
-  b0 = ic - lo;
-  bspline<ORDER, T>(f, w0);
-  if (f >= T(0.5)) {
-    bh = ic - lo;
-    bspline<ORDER, T>(f - T(0.5), wh);
-  } else {
-    bh = ic - 1 - lo;
-    bspline<ORDER, T>(f + T(0.5), wh);
-  }
-}
-
-template <int ORDER, int DIM, typename T>
-__device__ __forceinline__ T interp(const Geom& g, const T* __restrict__ F, int bx, const T* wx, int by,
-                                    const T* wy, int bz, const T* wz) {
-  constexpr int W = ORDER + 1;
-  T acc = T(0);
-#pragma unroll
-  for (int tz = 0; tz < W; ++tz) {
-#pragma unroll
-    for (int ty = 0; ty < (DIM == 3 ? W : 1); ++ty) {
-      const T wyz = (DIM == 3 ? wy[ty] : T(1)) * wz[tz];
-      const long long row = g.idx(bx, DIM == 3 ? by + ty : 0, bz + tz);
-      T racc = T(0);
-#pragma unroll
-      for (int tx = 0; tx < W; ++tx) racc += wx[tx] * __ldg(F + row + tx);
-      acc += wyz * racc;
-    }
-  }
-  return acc;
-}
-
-// B^n = (B^{n-1/2} + B^{n+1/2})/2 at the particle.
-template <int ORDER, int DIM, typename T>
-__device__ __forceinline__ T interp_avg(const Geom& g, const T* __restrict__ F1, const T* __restrict__ F2,
-                                        int bx, const T* wx, int by, const T* wy, int bz, const T* wz) {
-  return T(0.5) * (interp<ORDER, DIM, T>(g, F1, bx, wx, by, wy, bz, wz) +
-                   interp<ORDER, DIM, T>(g, F2, bx, wx, by, wy, bz, wz));
-}
-
-// Boris rotation for u = p/(mc), ke = q dt/(2 m c), fields E' and B' = cB.
-template <typename T>
-__device__ __forceinline__ void boris(T u[3], const T E[3], const T B[3], T ke) {
-  T um[3], t[3], s[3], uq[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) um[a] = u[a] + ke * E[a];
-  const T gm = sqrt(T(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
-  const T kb = ke / gm;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) t[a] = kb * B[a];
-  const T t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
-  const T f2 = T(2) / (T(1) + t2);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) s[a] = f2 * t[a];
-  uq[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);
-  uq[1] = um[1] + (um[2] * t[0] - um[0] * t[2]);
-  uq[2] = um[2] + (um[0] * t[1] - um[1] * t[0]);
-  u[0] = um[0] + (uq[1] * s[2] - uq[2] * s[1]) + ke * E[0];
-  u[1] = um[1] + (uq[2] * s[0] - uq[0] * s[2]) + ke * E[1];
-  u[2] = um[2] + (uq[0] * s[1] - uq[1] * s[0]) + ke * E[2];
-}
-
-template <typename T>
-__device__ __forceinline__ const T* al_node(const Tables& tb, int a);
-template <>
-__device__ __forceinline__ const float* al_node<float>(const Tables& tb, int a) { return tb.al_nf[a]; }
-template <>
-__device__ __forceinline__ const double* al_node<double>(const Tables& tb, int a) { return tb.al_nd[a]; }
-template <typename T>
-__device__ __forceinline__ const T* al_cent(const Tables& tb, int a);
-template <>
-__device__ __forceinline__ const float* al_cent<float>(const Tables& tb, int a) { return tb.al_cf[a]; }
-template <>
-__device__ __forceinline__ const double* al_cent<double>(const Tables& tb, int a) { return tb.al_cd[a]; }
-
-// Old (S0) and new (S1) shape values on the ORDER+2 nodes starting at
-// min(i0,i1) - (ORDER==3).
-template <int ORDER, typename T>
-__device__ __forceinline__ void esk_axis(int i0, T f0, int i1, T f1, int& lo, T* S0, T* DS) {
-  constexpr int W = ORDER + 2;
-  const int b = min(i0, i1);
-  lo = b - (ORDER == 3 ? 1 : 0);
-  T w0[ORDER + 1], w1[ORDER + 1];
-  bspline<ORDER, T>(f0, w0);
-  bspline<ORDER, T>(f1, w1);
-  const bool s0 = i0 != b, s1 = i1 != b;
-#pragma unroll
-  for (int t = 0; t < W; ++t) {
-    T a = s0 ? (t >= 1 ? w0[t - 1] : T(0)) : (t <= ORDER ? w0[t] : T(0));
-    T c = s1 ? (t >= 1 ? w1[t - 1] : T(0)) : (t <= ORDER ? w1[t] : T(0));
-    S0[t] = a;
-    DS[t] = c - a;
-  }
-}
+using namespace pc;
 
 // Esirkepov deposition of one move, damped by alpha at each component's
 // staggered location, accumulated with global atomics.
@@ -370,15 +205,17 @@ __global__ void __launch_bounds__(256) k_particles(Geom g, Tables tb, FieldPtrs<
       boris<T>(u, E, B, sp.ke);
     }
     ++pushed;
-    const T gam = sqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    const T ig = T(1) / gam;
+    const Mover<T> mv(u);
+    const T ig = mv.inv_gamma();
     int c1[3] = {c[0], c[1], c[2]};
     T o1[3] = {o[0], o[1], o[2]};
     bool out = false;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       if (DIM == 2 && a == 1) continue;
-      T x = o[a] + T(g.S[a]) * u[a] * ig;
+      const T Sh = T(g.S[a]);
+      const T Sl = T(g.S[a] - double(Sh));
+      T x = mv.advance(o[a], Sh, Sl, u[a]);
       if (x >= T(1)) {
         x -= T(1);
         c1[a] += 1;

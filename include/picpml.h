@@ -81,6 +81,9 @@ typedef struct pic_grid_desc {
   int prec;             /* pic_prec */
   int sort_every;       /* step_n sorts particles by cell every this many
                            steps (0 = never) */
+  int split_fp64;       /* PIC_FP32 only: 1 = PML split parts in IEEE FP64;
+                           0 (default) = float-float pairs (hi + lo, ~48-bit
+                           significand, 8 bytes) computed on the FP32 pipes */
 } pic_grid_desc;
 
 /* PML description: conductivity sigma(d) = coef eps0 c / Delta (d/delta)^p at

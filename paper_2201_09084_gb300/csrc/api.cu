@@ -15,9 +15,9 @@
 
 namespace picpml {
 template <typename T>
-cudaError_t launch_field_E(const Geom&, const Tables&, const FieldPtrs<T>&, cudaStream_t);
+cudaError_t launch_field_E(const Geom&, const Tables&, const FieldPtrs<T>&, int split_ff, cudaStream_t);
 template <typename T>
-cudaError_t launch_field_B(const Geom&, const Tables&, const FieldPtrs<T>&, cudaStream_t);
+cudaError_t launch_field_B(const Geom&, const Tables&, const FieldPtrs<T>&, int split_ff, cudaStream_t);
 template <typename T>
 cudaError_t launch_particles(int mode, int order, const Geom&, const Tables&, const FieldPtrs<T>&,
                              const SpeciesPtrs<T>&, int prescribed, unsigned* status, unsigned long long* pushed,
@@ -30,7 +30,7 @@ cudaError_t launch_gauss(const Geom&, const FieldPtrs<T>&, const double*, const 
 template <typename T>
 cudaError_t launch_export(const Geom&, const T*, const T*, double, void*, int, cudaStream_t);
 template <typename T>
-cudaError_t launch_import(const Geom&, const void*, int, double, T*, double*, double*, cudaStream_t);
+cudaError_t launch_import(const Geom&, const void*, int, double, T*, double*, double*, int split_ff, cudaStream_t);
 template <typename T>
 cudaError_t launch_push_deposit_runs(int ppt, const Geom&, const Tables&, const FieldPtrs<T>&, const SpeciesPtrs<T>&,
                                      int prescribed, unsigned* status, unsigned long long* pushed, int nsm,
@@ -84,6 +84,7 @@ struct picpml_ctx {
   std::string err;
   int elem() const { return gd.prec == PIC_FP64 ? 8 : 4; }
   int pbytes() const { return gd.prec == PIC_FP64 ? 32 : 16; }
+  int split_ff() const { return gd.prec != PIC_FP64 && !gd.split_fp64; }
 };
 
 namespace {
@@ -178,8 +179,8 @@ int run_particles(picpml_ctx* ctx, int mode) {
 template <typename T>
 int run_field(picpml_ctx* ctx) {
   FieldPtrs<T>& f = fields<T>(ctx);
-  CK(launch_field_E<T>(ctx->g, ctx->tb, f, ctx->stream));
-  CK(launch_field_B<T>(ctx->g, ctx->tb, f, ctx->stream));
+  CK(launch_field_E<T>(ctx->g, ctx->tb, f, ctx->split_ff(), ctx->stream));
+  CK(launch_field_B<T>(ctx->g, ctx->tb, f, ctx->split_ff(), ctx->stream));
   ctx->launches += 2;
   for (int c = 0; c < 3; ++c) std::swap(f.Bh[c], f.Bp[c]);
   return PIC_OK;
@@ -265,6 +266,7 @@ int pml_init(picpml_ctx* ctx, const pml_desc* p) {
     if (gd.dim == 2 && a == 1) {
       g.N[1] = 0; g.nn[1] = 1; g.plo[1] = 0; g.nph[1] = 0; g.rmin[1] = 0; g.rmax[1] = 1 << 30;
       g.S[1] = 0.0;
+      g.Sf[1] = g.Sfl[1] = 0.f;
       continue;
     }
     const int lo = p->ncell[2 * a], hi = p->ncell[2 * a + 1];
@@ -274,6 +276,8 @@ int pml_init(picpml_ctx* ctx, const pml_desc* p) {
     g.N[a] = gd.n[a] + lo + hi;
     g.nn[a] = g.N[a] + 1;
     g.S[a] = kC * ctx->dt / gd.d[a];
+    g.Sf[a] = (float)g.S[a];
+    g.Sfl[a] = (float)(g.S[a] - (double)g.Sf[a]);
     int rmin = margin, rmax = g.N[a] - margin;
     if (p->alpha_mode == PML_ALPHA_ZERO) {
       rmin = std::max(rmin, lo);
@@ -296,10 +300,16 @@ int pml_init(picpml_ctx* ctx, const pml_desc* p) {
   size_t total = 0;
   for (int a = 0; a < 3; ++a) total += (size_t)g.nn[a];
   host.assign(total * nt, 0.0);
-  std::vector<float> hostf(total * 2, 0.f);
+  std::vector<float> hostf(total * 4, 0.f);      // alpha (n, c), s dt (n, c) as float
+  std::vector<float2> host2(total * 4);           // ea, eb (n, c) as float-float pairs
   double* td = (double*)dev_alloc(ctx, host.size() * sizeof(double));
   float* tf = (float*)dev_alloc(ctx, hostf.size() * sizeof(float));
-  if (!td || !tf) return fail(ctx, PIC_ENOMEM, "tables");
+  float2* t2 = (float2*)dev_alloc(ctx, host2.size() * sizeof(float2));
+  if (!td || !tf || !t2) return fail(ctx, PIC_ENOMEM, "tables");
+  auto split2 = [](double v) {
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+  };
   size_t off = 0;
   for (int a = 0; a < 3; ++a) {
     const int nn = g.nn[a];
@@ -322,6 +332,9 @@ int pml_init(picpml_ctx* ctx, const pml_desc* p) {
         host[(stag * 3 + 2) * total + base] = sdt;
         host[(6 + stag) * total + base] = al;
         hostf[stag * total + base] = (float)al;
+        hostf[(2 + stag) * total + base] = (float)sdt;
+        host2[(stag * 2 + 0) * total + base] = split2(ea);
+        host2[(stag * 2 + 1) * total + base] = split2(eb);
       }
     }
     ctx->tb.ea_n[a] = td + 0 * total + off;
@@ -334,10 +347,17 @@ int pml_init(picpml_ctx* ctx, const pml_desc* p) {
     ctx->tb.al_cd[a] = td + 7 * total + off;
     ctx->tb.al_nf[a] = tf + off;
     ctx->tb.al_cf[a] = tf + total + off;
+    ctx->tb.sdtf_n[a] = tf + 2 * total + off;
+    ctx->tb.sdtf_c[a] = tf + 3 * total + off;
+    ctx->tb.ea2_n[a] = t2 + 0 * total + off;
+    ctx->tb.eb2_n[a] = t2 + 1 * total + off;
+    ctx->tb.ea2_c[a] = t2 + 2 * total + off;
+    ctx->tb.eb2_c[a] = t2 + 3 * total + off;
     off += nn;
   }
   CK(cudaMemcpyAsync(td, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(tf, hostf.data(), hostf.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(t2, host2.data(), host2.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->stream));
 
   // fields: 12 arrays of the field type + 12 FP64 split arrays, zeroed
   const size_t es = ctx->elem();
@@ -512,10 +532,10 @@ int pic_set_field(picpml_ctx* ctx, int which, const void* src, int as_double) {
   double* s1 = kind == 0 ? ctx->fd.Es[c][1] : kind == 3 ? ctx->fd.Bs[c][1] : nullptr;
   if (ctx->gd.prec == PIC_FP64) {
     double* a = kind == 0 ? ctx->fd.E[c] : kind == 3 ? ctx->fd.Bh[c] : ctx->fd.Bp[c];
-    CK(launch_import<double>(ctx->g, src, as_double, scale, a, s0, s1, ctx->stream));
+    CK(launch_import<double>(ctx->g, src, as_double, scale, a, s0, s1, 0, ctx->stream));
   } else {
     float* a = kind == 0 ? ctx->ff.E[c] : kind == 3 ? ctx->ff.Bh[c] : ctx->ff.Bp[c];
-    CK(launch_import<float>(ctx->g, src, as_double, scale, a, s0, s1, ctx->stream));
+    CK(launch_import<float>(ctx->g, src, as_double, scale, a, s0, s1, ctx->split_ff(), ctx->stream));
   }
   return PIC_OK;
 }

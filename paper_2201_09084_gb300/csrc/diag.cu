@@ -125,7 +125,7 @@ __global__ void k_export(Geom g, const T* a, const T* b, double scale, U* dst) {
 }
 
 template <typename T, typename U>
-__global__ void k_import(Geom g, const U* src, double scale, T* a, double* split0, double* split1) {
+__global__ void k_import(Geom g, const U* src, double scale, T* a, double* split0, double* split1, int ff) {
   const long long total = (long long)g.nn[0] * g.nn[1] * g.nn[2];
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
@@ -134,7 +134,11 @@ __global__ void k_import(Geom g, const U* src, double scale, T* a, double* split
     const long long id = g.idx(i, (int)(r % g.nn[1]), (int)(r / g.nn[1]));
     const double v = (double)src[t] * scale;
     a[id] = (T)v;
-    if (split0) {
+    if (split0 && ff) {  // float-float parts: (hi, lo) pairs
+      const float h = (float)v;
+      reinterpret_cast<float2*>(split0)[id] = make_float2(h, (float)(v - (double)h));
+      reinterpret_cast<float2*>(split1)[id] = make_float2(0.f, 0.f);
+    } else if (split0) {
       split0[id] = v;
       split1[id] = 0.0;
     }
@@ -180,9 +184,9 @@ cudaError_t launch_export(const Geom& g, const T* a, const T* b, double scale, v
 
 template <typename T>
 cudaError_t launch_import(const Geom& g, const void* src, int as_double, double scale, T* a, double* s0,
-                          double* s1, cudaStream_t s) {
-  if (as_double) k_import<T, double><<<1024, 256, 0, s>>>(g, (const double*)src, scale, a, s0, s1);
-  else k_import<T, float><<<1024, 256, 0, s>>>(g, (const float*)src, scale, a, s0, s1);
+                          double* s1, int ff, cudaStream_t s) {
+  if (as_double) k_import<T, double><<<1024, 256, 0, s>>>(g, (const double*)src, scale, a, s0, s1, ff);
+  else k_import<T, float><<<1024, 256, 0, s>>>(g, (const float*)src, scale, a, s0, s1, ff);
   return cudaGetLastError();
 }
 
@@ -194,7 +198,7 @@ cudaError_t launch_import(const Geom& g, const void* src, int as_double, double 
   template cudaError_t launch_export<T>(const Geom&, const T*, const T*, double, void*, int,           \
                                         cudaStream_t);                                                 \
   template cudaError_t launch_import<T>(const Geom&, const void*, int, double, T*, double*, double*,   \
-                                        cudaStream_t);
+                                        int, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -33,6 +33,8 @@ struct Geom {
   long long sz;    // stride of k
   long long size;  // elements per field array
   double S[3];     // Courant numbers c dt / d_a
+  float Sf[3];     // the same as a float-float pair (hi, lo), so kernels need no FP64
+  float Sfl[3];
   int plo[3];      // PML cells on the low face
   int nph[3];      // physical cells
   int rmin[3], rmax[3];  // a particle at X = i + f stays while rmin <= X <= rmax
@@ -52,6 +54,12 @@ struct Tables {
   const double* ea_c[3];
   const double* eb_c[3];
   const double* sdt_c[3];
+  const float* sdtf_n[3];   // s dt as float (only compared: which split part
+  const float* sdtf_c[3];   //   is damped and which takes the source)
+  const float2* ea2_n[3];   // ea, eb as float-float pairs (hi, lo) for the
+  const float2* eb2_n[3];   //   float-float split parts
+  const float2* ea2_c[3];
+  const float2* eb2_c[3];
   const float* al_nf[3];    // alpha at nodes / centres, FP32 copy
   const float* al_cf[3];
   const double* al_nd[3];   // FP64 copy

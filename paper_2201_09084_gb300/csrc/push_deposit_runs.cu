@@ -286,8 +286,8 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 2 : 1) k_pd1(Geom g, Tab
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         if (DIM == 2 && a == 1) continue;
-        const T Sh = T(g.S[a]);
-        const T Sl = T(g.S[a] - double(Sh));
+        const T Sh = sizeof(T) == 4 ? T(g.Sf[a]) : T(g.S[a]);
+        const T Sl = sizeof(T) == 4 ? T(g.Sfl[a]) : T(0);
         T x = mv.advance(o[a], Sh, Sl, u[a]);
         if (x >= T(1)) {
           x -= T(1);

@@ -34,13 +34,17 @@ def _pulse(sim_nn, pml, dim):
     return 1e6 * f
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("prec", ["fp32", "fp32-splitfp64", "fp64"])
 @pytest.mark.parametrize("dim", [3, 2])
 def test_field_step_parity(dim, prec):
+    """Yee + split PML on every face (ragged widths): float-float parts (FP32
+    default), IEEE FP64 parts with FP32 fields, and the all-FP64 form."""
     nphys = (37, 21, 45)
     pml = (6, 9, 5, 7, 8, 10)
     d = D3 if dim == 3 else D2
-    ora, gpu = make_pair(dim, nphys, pml, d, [], prec=prec)
+    split64 = prec == "fp32-splitfp64"
+    prec = "fp32" if split64 else prec
+    ora, gpu = make_pair(dim, nphys, pml, d, [], prec=prec, split_fp64=split64)
     f = _pulse(ora.nn, pml, dim)
     for s in (ora, gpu):
         s.set_field("Ey", f)

@@ -56,60 +56,75 @@ struct Acc1 {
     for (int t = 0; t < NZ; ++t) vz[t] = T(0);
   }
 
-  // 3D layout: vx[ix*9 + jy*3 + kz], vy[ix*6 + jy*3 + kz], vz[ix*6 + jy*2 + kz]
+  // 3D layout: vx[ix*9 + jy*3 + kz], vy[ix*6 + jy*3 + kz], vz[ix*6 + jy*2 + kz].
+  // Esirkepov's transverse factor S0 S0' + DS S0'/2 + S0 DS'/2 + DS DS'/3 is
+  // evaluated as M M' + DS DS'/12 with the mid-move shape M = S0 + DS/2 (the
+  // same polynomial, since 1/3 = 1/4 + 1/12); a component whose prefix sums
+  // vanish (no motion along its axis) adds nothing and is skipped.
   __device__ __forceinline__ void add(const T S0[3][3], const T DS[3][3], T w, T wvy) {
-    const T third = T(1.0 / 3.0);
+    const T c12 = T(1.0 / 12.0);
+    T M[3][3], Q[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        M[a][t] = S0[a][t] + T(0.5) * DS[a][t];
+        Q[a][t] = c12 * DS[a][t];
+      }
     if (DIM == 3) {
+      const T ax0 = w * DS[0][0], ax1 = w * (DS[0][0] + DS[0][1]);
+      if (ax0 != T(0) || ax1 != T(0)) {
 #pragma unroll
-      for (int jy = 0; jy < 3; ++jy)
+        for (int jy = 0; jy < 3; ++jy)
 #pragma unroll
-        for (int kz = 0; kz < 3; ++kz) {
-          const T Tl = w * (S0[1][jy] * S0[2][kz] + T(0.5) * DS[1][jy] * S0[2][kz] +
-                            T(0.5) * S0[1][jy] * DS[2][kz] + third * DS[1][jy] * DS[2][kz]);
-          const T a0 = DS[0][0], a1 = DS[0][0] + DS[0][1];
-          vx[0 * 9 + jy * 3 + kz] += a0 * Tl;
-          vx[1 * 9 + jy * 3 + kz] += a1 * Tl;
-        }
+          for (int kz = 0; kz < 3; ++kz) {
+            const T Tl = M[1][jy] * M[2][kz] + Q[1][jy] * DS[2][kz];
+            vx[0 * 9 + jy * 3 + kz] += ax0 * Tl;
+            vx[1 * 9 + jy * 3 + kz] += ax1 * Tl;
+          }
+      }
+      const T ay0 = w * DS[1][0], ay1 = w * (DS[1][0] + DS[1][1]);
+      if (ay0 != T(0) || ay1 != T(0)) {
 #pragma unroll
-      for (int ix = 0; ix < 3; ++ix)
+        for (int ix = 0; ix < 3; ++ix)
 #pragma unroll
-        for (int kz = 0; kz < 3; ++kz) {
-          const T Tl = w * (S0[0][ix] * S0[2][kz] + T(0.5) * DS[0][ix] * S0[2][kz] +
-                            T(0.5) * S0[0][ix] * DS[2][kz] + third * DS[0][ix] * DS[2][kz]);
-          const T a0 = DS[1][0], a1 = DS[1][0] + DS[1][1];
-          vy[ix * 6 + 0 * 3 + kz] += a0 * Tl;
-          vy[ix * 6 + 1 * 3 + kz] += a1 * Tl;
-        }
+          for (int kz = 0; kz < 3; ++kz) {
+            const T Tl = M[0][ix] * M[2][kz] + Q[0][ix] * DS[2][kz];
+            vy[ix * 6 + 0 * 3 + kz] += ay0 * Tl;
+            vy[ix * 6 + 1 * 3 + kz] += ay1 * Tl;
+          }
+      }
+      const T az0 = w * DS[2][0], az1 = w * (DS[2][0] + DS[2][1]);
+      if (az0 != T(0) || az1 != T(0)) {
 #pragma unroll
-      for (int ix = 0; ix < 3; ++ix)
+        for (int ix = 0; ix < 3; ++ix)
 #pragma unroll
-        for (int jy = 0; jy < 3; ++jy) {
-          const T Tl = w * (S0[0][ix] * S0[1][jy] + T(0.5) * DS[0][ix] * S0[1][jy] +
-                            T(0.5) * S0[0][ix] * DS[1][jy] + third * DS[0][ix] * DS[1][jy]);
-          const T a0 = DS[2][0], a1 = DS[2][0] + DS[2][1];
-          vz[ix * 6 + jy * 2 + 0] += a0 * Tl;
-          vz[ix * 6 + jy * 2 + 1] += a1 * Tl;
-        }
+          for (int jy = 0; jy < 3; ++jy) {
+            const T Tl = M[0][ix] * M[1][jy] + Q[0][ix] * DS[1][jy];
+            vz[ix * 6 + jy * 2 + 0] += az0 * Tl;
+            vz[ix * 6 + jy * 2 + 1] += az1 * Tl;
+          }
+      }
     } else {
       // 2D layout: vx[ix*3 + kz], vz[ix*2 + kz], vy[ix*3 + kz]
+      const T ax0 = w * DS[0][0], ax1 = w * (DS[0][0] + DS[0][1]);
 #pragma unroll
       for (int kz = 0; kz < 3; ++kz) {
-        const T Tl = w * (S0[2][kz] + T(0.5) * DS[2][kz]);
-        vx[0 * 3 + kz] += DS[0][0] * Tl;
-        vx[1 * 3 + kz] += (DS[0][0] + DS[0][1]) * Tl;
+        vx[0 * 3 + kz] += ax0 * M[2][kz];
+        vx[1 * 3 + kz] += ax1 * M[2][kz];
       }
+      const T az0 = w * DS[2][0], az1 = w * (DS[2][0] + DS[2][1]);
 #pragma unroll
       for (int ix = 0; ix < 3; ++ix) {
-        const T Tl = w * (S0[0][ix] + T(0.5) * DS[0][ix]);
-        vz[ix * 2 + 0] += DS[2][0] * Tl;
-        vz[ix * 2 + 1] += (DS[2][0] + DS[2][1]) * Tl;
+        vz[ix * 2 + 0] += az0 * M[0][ix];
+        vz[ix * 2 + 1] += az1 * M[0][ix];
       }
+      if (wvy != T(0)) {
 #pragma unroll
-      for (int ix = 0; ix < 3; ++ix)
+        for (int ix = 0; ix < 3; ++ix)
 #pragma unroll
-        for (int kz = 0; kz < 3; ++kz)
-          vy[ix * 3 + kz] += wvy * (S0[0][ix] * S0[2][kz] + T(0.5) * DS[0][ix] * S0[2][kz] +
-                                    T(0.5) * S0[0][ix] * DS[2][kz] + third * DS[0][ix] * DS[2][kz]);
+          for (int kz = 0; kz < 3; ++kz) vy[ix * 3 + kz] += wvy * (M[0][ix] * M[2][kz] + Q[0][ix] * DS[2][kz]);
+      }
     }
   }
 

@@ -191,3 +191,23 @@ def test_state_roundtrip_is_exact():
     gpu2.step(5)
     b = gpu2.field("Ez").cpu().numpy()
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("theta", [0.0, 25.0])
+def test_dense_beam_shared_memory_box(theta, prec):
+    """A dense beam (about 1000 particles per cell in its core): chunks of
+    cell-sorted particles span a few cells, so the order-1 kernel takes its
+    shared-memory field/current box path; the sparse tails take the global
+    path.  Whole steps with sorting, against the oracle."""
+    nphys = (20, 18, 24)
+    pml = (6,) * 6
+    center = (6 + 10.3, 6 + 9.2, 6 + 17.6)
+    parts = I.beam(3, 20000, nphys, pml, center, sigma=(0.8, 0.8, 1.3), theta_deg=theta, clip=3.0)
+    ora, gpu = make_pair(3, nphys, pml, D3, parts, order=1, prec=prec, alpha_mode="damped", sort_every=5)
+    for _ in range(3):
+        ora.step(6)
+        gpu.step(6)
+        err = max_field_err(ora, gpu)
+        assert max(err.values()) < TOL[prec], err
+    assert gpu.num_particles(0) == int(ora.particles()["alive"].sum())

@@ -210,4 +210,5 @@ def test_dense_beam_shared_memory_box(theta, prec):
         gpu.step(6)
         err = max_field_err(ora, gpu)
         assert max(err.values()) < TOL[prec], err
-    assert gpu.num_particles(0) == int(ora.particles()["alive"].sum())
+    # removed particles are marked at once and compacted at the next sort
+    assert int(gpu.particles(0)["alive"].sum()) == int(ora.particles()["alive"].sum())

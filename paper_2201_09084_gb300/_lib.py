@@ -65,6 +65,7 @@ SIGNATURES = {
     "pic_set_prescribed": (C.c_int, [VP, C.c_int]),
     "pic_num_particles": (C.c_int, [VP, C.c_int, C.POINTER(C.c_longlong)]),
     "pic_diag": (C.c_int, [VP, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "pic_diag_static": (C.c_int, [VP, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "pic_sync": (C.c_int, [VP]),
     "pic_state_size": (C.c_int, [VP, C.POINTER(C.c_longlong)]),
     "pic_get_state": (C.c_int, [VP, VP]),

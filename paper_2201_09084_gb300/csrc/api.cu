@@ -37,6 +37,7 @@ cudaError_t launch_push_deposit_runs(int ppt, const Geom&, const Tables&, const 
                                      cudaStream_t);
 long long sort_scratch_words(long long ncell);
 int sort_launches(long long ncell);
+cudaError_t static_diag_buffers(double** rho, double** out, long long* cap);
 cudaError_t launch_sort(const Geom&, int pbytes, void* pos, void* mom, long long* n_dev, long long cap,
                         unsigned* scratch, void* tmp_pos, void* tmp_mom, cudaStream_t);
 }  // namespace picpml
@@ -590,6 +591,42 @@ int pic_diag(picpml_ctx* ctx, double* gauss, double* rho_scale, double* energy) 
   else CK(launch_gauss<float>(ctx->g, ctx->ff, ctx->rho, gd.d, ctx->diag, ctx->stream));
   double h[3];
   CK(cudaMemcpyAsync(h, ctx->diag, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (gauss) *gauss = h[0];
+  if (rho_scale) *rho_scale = h[1];
+  if (energy) *energy = h[2];
+  return pic_sync(ctx);
+}
+
+int pic_diag_static(picpml_ctx* ctx, double* gauss, double* rho_scale, double* energy) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  double* rho = nullptr;
+  double* out = nullptr;
+  long long cap = 0;
+  CK(static_diag_buffers(&rho, &out, &cap));
+  if (ctx->g.size > cap)
+    return fail(ctx, PIC_EINVAL,
+                "pic_diag_static: the grid needs " + std::to_string(ctx->g.size) +
+                    " scratch nodes (x rows padded to 8); the static scratch holds " + std::to_string(cap));
+  // the shared array keeps the last call's contents: clear what accumulates
+  CK(cudaMemsetAsync(rho, 0, (size_t)ctx->g.size * sizeof(double), ctx->stream));
+  CK(cudaMemsetAsync(out, 0, 3 * sizeof(double), ctx->stream));
+  const pic_grid_desc& gd = ctx->gd;
+  const double V = gd.d[0] * gd.d[2] * (gd.dim == 3 ? gd.d[1] : 1.0);
+  for (auto& s : ctx->sp) {
+    const double qoe = s.desc.q / (kEps0 * V);
+    if (gd.prec == PIC_FP64)
+      CK(launch_rho<double>(gd.shape_order, ctx->g, s.desc.pos, s.desc.mom, s.n_dev, s.desc.capacity, qoe, rho,
+                            ctx->stream));
+    else
+      CK(launch_rho<float>(gd.shape_order, ctx->g, s.desc.pos, s.desc.mom, s.n_dev, s.desc.capacity, qoe, rho,
+                           ctx->stream));
+  }
+  if (gd.prec == PIC_FP64) CK(launch_gauss<double>(ctx->g, ctx->fd, rho, gd.d, out, ctx->stream));
+  else CK(launch_gauss<float>(ctx->g, ctx->ff, rho, gd.d, out, ctx->stream));
+  double h[3];
+  CK(cudaMemcpyAsync(h, out, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   if (gauss) *gauss = h[0];
   if (rho_scale) *rho_scale = h[1];

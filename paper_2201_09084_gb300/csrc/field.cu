@@ -105,56 +105,72 @@ __device__ __forceinline__ T courant(const Geom& g, int a) {
   return sizeof(T) == 4 ? T(g.Sf[a]) : T(g.S[a]);
 }
 
+// Nodes per thread along z (3D): a thread marches KZ nodes upward in z and
+// carries the z-neighbour values of the previous node in registers; its KZ
+// nodes' loads are independent, so more memory requests are in flight.
+constexpr int KZ = 4;
+
 template <typename T, int DIM, int SPL>
 __global__ void __launch_bounds__(256) k_field_E(Geom g, Tables tb, FieldPtrs<T> f) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = DIM == 3 ? blockIdx.y * blockDim.y + threadIdx.y : 0;
-  const int k = DIM == 3 ? blockIdx.z : blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= g.nn[0] || j >= g.nn[1] || k >= g.nn[2]) return;
-  const long long id = g.idx(i, j, k);
+  const int k0 = DIM == 3 ? blockIdx.z * KZ : (blockIdx.y * blockDim.y + threadIdx.y) * KZ;
+  if (i >= g.nn[0] || j >= g.nn[1] || k0 >= g.nn[2]) return;
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
   const T Sx = courant<T>(g, 0), Sy = courant<T>(g, 1), Sz = courant<T>(g, 2);
-  const T* Bx = f.Bh[0];
-  const T* By = f.Bh[1];
-  const T* Bz = f.Bh[2];
+  const T* __restrict__ Bx = f.Bh[0];
+  const T* __restrict__ By = f.Bh[1];
+  const T* __restrict__ Bz = f.Bh[2];
   const bool jin = DIM == 2 || (j >= 1 && j <= N1 - 1);
-  const bool kin = k >= 1 && k <= N2 - 1;
   const bool iin = i >= 1 && i <= N0 - 1;
-  // J' is consumed here: read once, zeroed where it was nonzero (most of the
-  // grid carries no current, so most threads write nothing back).
-  const T jx = f.J[0][id], jy = f.J[1][id], jz = f.J[2][id];
-  if (jx != T(0)) f.J[0][id] = T(0);
-  if (jy != T(0)) f.J[1][id] = T(0);
-  if (jz != T(0)) f.J[2][id] = T(0);
-  const float sxn = tb.sdtf_n[0][i], szn = tb.sdtf_n[2][k];
+  const float sxn = tb.sdtf_n[0][i];
   const float syn = DIM == 3 ? tb.sdtf_n[1][j] : 0.f;
-
-  // Ex(i+1/2, j, k): parts along y (sigma_y at node j) and z (sigma_z at node k)
-  if (i <= N0 - 1 && jin && kin) {
-    const T r0 = DIM == 3 ? Sy * (Bz[id] - Bz[id - g.sy]) : T(0);
-    const T r1 = -Sz * (By[id] - By[id - g.sz]);
-    if (syn > 0.f || szn > 0.f)
-      f.E[0][id] = advance<T, SPL, false>(tb, f.Es[0], id, DIM == 3 ? 1 : -1, j, 2, k, r0, r1, -jx, syn, szn);
-    else
-      f.E[0][id] += r0 + r1 - jx;
-  }
-  // Ey(i, j+1/2, k): parts along x (sigma_x at node i) and z
-  if (iin && (DIM == 2 || j <= N1 - 1) && kin) {
-    const T r0 = -Sx * (Bz[id] - Bz[id - 1]);
-    const T r1 = Sz * (Bx[id] - Bx[id - g.sz]);
-    if (sxn > 0.f || szn > 0.f)
-      f.E[1][id] = advance<T, SPL, false>(tb, f.Es[1], id, 0, i, 2, k, r0, r1, -jy, sxn, szn);
-    else
-      f.E[1][id] += r0 + r1 - jy;
-  }
-  // Ez(i, j, k+1/2): parts along x and y
-  if (iin && jin && k <= N2 - 1) {
-    const T r0 = Sx * (By[id] - By[id - 1]);
-    const T r1 = DIM == 3 ? -Sy * (Bx[id] - Bx[id - g.sy]) : T(0);
-    if (sxn > 0.f || syn > 0.f)
-      f.E[2][id] = advance<T, SPL, false>(tb, f.Es[2], id, 0, i, DIM == 3 ? 1 : -1, j, r0, r1, -jz, sxn, syn);
-    else
-      f.E[2][id] += r0 + r1 - jz;
+  long long id = g.idx(i, j, k0);
+  // values at k-1 carried from the previous node
+  T by_m = k0 >= 1 ? By[id - g.sz] : T(0);
+  T bx_m = k0 >= 1 ? Bx[id - g.sz] : T(0);
+#pragma unroll
+  for (int kk = 0; kk < KZ; ++kk, id += g.sz) {
+    const int k = k0 + kk;
+    if (k >= g.nn[2]) break;
+    const bool kin = k >= 1 && k <= N2 - 1;
+    const T by0 = By[id], bx0 = Bx[id], bz0 = Bz[id];
+    // J' is consumed here: read once, zeroed where it was nonzero (most of
+    // the grid carries no current, so most threads write nothing back).
+    const T jx = f.J[0][id], jy = f.J[1][id], jz = f.J[2][id];
+    if (jx != T(0)) f.J[0][id] = T(0);
+    if (jy != T(0)) f.J[1][id] = T(0);
+    if (jz != T(0)) f.J[2][id] = T(0);
+    const float szn = tb.sdtf_n[2][k];
+    // Ex(i+1/2, j, k): parts along y (sigma_y at node j) and z (sigma_z at node k)
+    if (i <= N0 - 1 && jin && kin) {
+      const T r0 = DIM == 3 ? Sy * (bz0 - Bz[id - g.sy]) : T(0);
+      const T r1 = -Sz * (by0 - by_m);
+      if (syn > 0.f || szn > 0.f)
+        f.E[0][id] = advance<T, SPL, false>(tb, f.Es[0], id, DIM == 3 ? 1 : -1, j, 2, k, r0, r1, -jx, syn, szn);
+      else
+        f.E[0][id] += r0 + r1 - jx;
+    }
+    // Ey(i, j+1/2, k): parts along x (sigma_x at node i) and z
+    if (iin && (DIM == 2 || j <= N1 - 1) && kin) {
+      const T r0 = -Sx * (bz0 - Bz[id - 1]);
+      const T r1 = Sz * (bx0 - bx_m);
+      if (sxn > 0.f || szn > 0.f)
+        f.E[1][id] = advance<T, SPL, false>(tb, f.Es[1], id, 0, i, 2, k, r0, r1, -jy, sxn, szn);
+      else
+        f.E[1][id] += r0 + r1 - jy;
+    }
+    // Ez(i, j, k+1/2): parts along x and y
+    if (iin && jin && k <= N2 - 1) {
+      const T r0 = Sx * (by0 - By[id - 1]);
+      const T r1 = DIM == 3 ? -Sy * (bx0 - Bx[id - g.sy]) : T(0);
+      if (sxn > 0.f || syn > 0.f)
+        f.E[2][id] = advance<T, SPL, false>(tb, f.Es[2], id, 0, i, DIM == 3 ? 1 : -1, j, r0, r1, -jz, sxn, syn);
+      else
+        f.E[2][id] += r0 + r1 - jz;
+    }
+    by_m = by0;
+    bx_m = bx0;
   }
 }
 
@@ -162,56 +178,68 @@ template <typename T, int DIM, int SPL>
 __global__ void __launch_bounds__(256) k_field_B(Geom g, Tables tb, FieldPtrs<T> f) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = DIM == 3 ? blockIdx.y * blockDim.y + threadIdx.y : 0;
-  const int k = DIM == 3 ? blockIdx.z : blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= g.nn[0] || j >= g.nn[1] || k >= g.nn[2]) return;
-  const long long id = g.idx(i, j, k);
+  const int k0 = DIM == 3 ? blockIdx.z * KZ : (blockIdx.y * blockDim.y + threadIdx.y) * KZ;
+  if (i >= g.nn[0] || j >= g.nn[1] || k0 >= g.nn[2]) return;
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
   const T Sx = courant<T>(g, 0), Sy = courant<T>(g, 1), Sz = courant<T>(g, 2);
-  const T* Ex = f.E[0];
-  const T* Ey = f.E[1];
-  const T* Ez = f.E[2];
+  const T* __restrict__ Ex = f.E[0];
+  const T* __restrict__ Ey = f.E[1];
+  const T* __restrict__ Ez = f.E[2];
   const bool jc = DIM == 2 || j <= N1 - 1;   // j is a cell-centre index
-  const bool kc = k <= N2 - 1;
   const bool ic = i <= N0 - 1;
-  const float sxc = ic ? tb.sdtf_c[0][i] : 0.f, szc = kc ? tb.sdtf_c[2][k] : 0.f;
+  const float sxc = ic ? tb.sdtf_c[0][i] : 0.f;
   const float syc = DIM == 3 && jc ? tb.sdtf_c[1][j] : 0.f;
-
-  // Bx(i, j+1/2, k+1/2): parts along y (sigma_y at centre j) and z (centre k)
-  if (jc && kc) {
-    const T r0 = DIM == 3 ? -Sy * (Ez[id + g.sy] - Ez[id]) : T(0);
-    const T r1 = Sz * (Ey[id + g.sz] - Ey[id]);
-    if (syc > 0.f || szc > 0.f)
-      f.Bp[0][id] = advance<T, SPL, true>(tb, f.Bs[0], id, DIM == 3 ? 1 : -1, j, 2, k, r0, r1, T(0), syc, szc);
-    else
-      f.Bp[0][id] = f.Bh[0][id] + (r0 + r1);
-  }
-  // By(i+1/2, j, k+1/2): parts along x (centre i) and z (centre k)
-  if (ic && kc) {
-    const T r0 = Sx * (Ez[id + 1] - Ez[id]);
-    const T r1 = -Sz * (Ex[id + g.sz] - Ex[id]);
-    if (sxc > 0.f || szc > 0.f)
-      f.Bp[1][id] = advance<T, SPL, true>(tb, f.Bs[1], id, 0, i, 2, k, r0, r1, T(0), sxc, szc);
-    else
-      f.Bp[1][id] = f.Bh[1][id] + (r0 + r1);
-  }
-  // Bz(i+1/2, j+1/2, k): parts along x (centre i) and y (centre j)
-  if (ic && jc) {
-    const T r0 = -Sx * (Ey[id + 1] - Ey[id]);
-    const T r1 = DIM == 3 ? Sy * (Ex[id + g.sy] - Ex[id]) : T(0);
-    if (sxc > 0.f || syc > 0.f)
-      f.Bp[2][id] = advance<T, SPL, true>(tb, f.Bs[2], id, 0, i, DIM == 3 ? 1 : -1, j, r0, r1, T(0), sxc, syc);
-    else
-      f.Bp[2][id] = f.Bh[2][id] + (r0 + r1);
+  long long id = g.idx(i, j, k0);
+  // values at k carried from the previous node (its k+1 neighbours)
+  T ex0 = Ex[id], ey0 = Ey[id];
+#pragma unroll
+  for (int kk = 0; kk < KZ; ++kk, id += g.sz) {
+    const int k = k0 + kk;
+    if (k >= g.nn[2]) break;
+    const bool kc = k <= N2 - 1;
+    const T ex_p = kc ? Ex[id + g.sz] : T(0);
+    const T ey_p = kc ? Ey[id + g.sz] : T(0);
+    const T ez0 = Ez[id];
+    const float szc = kc ? tb.sdtf_c[2][k] : 0.f;
+    // Bx(i, j+1/2, k+1/2): parts along y (sigma_y at centre j) and z (centre k)
+    if (jc && kc) {
+      const T r0 = DIM == 3 ? -Sy * (Ez[id + g.sy] - ez0) : T(0);
+      const T r1 = Sz * (ey_p - ey0);
+      if (syc > 0.f || szc > 0.f)
+        f.Bp[0][id] = advance<T, SPL, true>(tb, f.Bs[0], id, DIM == 3 ? 1 : -1, j, 2, k, r0, r1, T(0), syc, szc);
+      else
+        f.Bp[0][id] = f.Bh[0][id] + (r0 + r1);
+    }
+    // By(i+1/2, j, k+1/2): parts along x (centre i) and z (centre k)
+    if (ic && kc) {
+      const T r0 = Sx * (Ez[id + 1] - ez0);
+      const T r1 = -Sz * (ex_p - ex0);
+      if (sxc > 0.f || szc > 0.f)
+        f.Bp[1][id] = advance<T, SPL, true>(tb, f.Bs[1], id, 0, i, 2, k, r0, r1, T(0), sxc, szc);
+      else
+        f.Bp[1][id] = f.Bh[1][id] + (r0 + r1);
+    }
+    // Bz(i+1/2, j+1/2, k): parts along x (centre i) and y (centre j)
+    if (ic && jc) {
+      const T r0 = -Sx * (Ey[id + 1] - ey0);
+      const T r1 = DIM == 3 ? Sy * (Ex[id + g.sy] - ex0) : T(0);
+      if (sxc > 0.f || syc > 0.f)
+        f.Bp[2][id] = advance<T, SPL, true>(tb, f.Bs[2], id, 0, i, DIM == 3 ? 1 : -1, j, r0, r1, T(0), sxc, syc);
+      else
+        f.Bp[2][id] = f.Bh[2][id] + (r0 + r1);
+    }
+    ex0 = ex_p;
+    ey0 = ey_p;
   }
 }
 
 template <typename T, int SPL>
 cudaError_t launch_E(const Geom& g, const Tables& tb, const FieldPtrs<T>& f, cudaStream_t s) {
   if (g.dim == 3) {
-    dim3 blk(32, 8, 1), grd((g.nn[0] + 31) / 32, (g.nn[1] + 7) / 8, g.nn[2]);
+    dim3 blk(32, 8, 1), grd((g.nn[0] + 31) / 32, (g.nn[1] + 7) / 8, (g.nn[2] + KZ - 1) / KZ);
     k_field_E<T, 3, SPL><<<grd, blk, 0, s>>>(g, tb, f);
   } else {
-    dim3 blk(32, 8, 1), grd((g.nn[0] + 31) / 32, (g.nn[2] + 7) / 8, 1);
+    dim3 blk(32, 8, 1), grd((g.nn[0] + 31) / 32, ((g.nn[2] + KZ - 1) / KZ + 7) / 8, 1);
     k_field_E<T, 2, SPL><<<grd, blk, 0, s>>>(g, tb, f);
   }
   return cudaGetLastError();
@@ -220,10 +248,10 @@ cudaError_t launch_E(const Geom& g, const Tables& tb, const FieldPtrs<T>& f, cud
 template <typename T, int SPL>
 cudaError_t launch_B(const Geom& g, const Tables& tb, const FieldPtrs<T>& f, cudaStream_t s) {
   if (g.dim == 3) {
-    dim3 blk(32, 8, 1), grd((g.nn[0] + 31) / 32, (g.nn[1] + 7) / 8, g.nn[2]);
+    dim3 blk(32, 8, 1), grd((g.nn[0] + 31) / 32, (g.nn[1] + 7) / 8, (g.nn[2] + KZ - 1) / KZ);
     k_field_B<T, 3, SPL><<<grd, blk, 0, s>>>(g, tb, f);
   } else {
-    dim3 blk(32, 8, 1), grd((g.nn[0] + 31) / 32, (g.nn[2] + 7) / 8, 1);
+    dim3 blk(32, 8, 1), grd((g.nn[0] + 31) / 32, ((g.nn[2] + KZ - 1) / KZ + 7) / 8, 1);
     k_field_B<T, 2, SPL><<<grd, blk, 0, s>>>(g, tb, f);
   }
   return cudaGetLastError();

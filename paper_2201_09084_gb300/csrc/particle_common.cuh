@@ -120,18 +120,25 @@ __device__ __forceinline__ T interp_avg(const Geom& g, const T* __restrict__ F1,
                    interp<ORDER, DIM, T>(g, F2, bx, wx, by, wy, bz, wz));
 }
 
+__device__ __forceinline__ float inv_sqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
+
 // Boris rotation for u = p/(mc), ke = q dt/(2 m c), fields E' and B' = cB.
+// FP32 uses the hardware reciprocal square root and division (a few ulp;
+// the rotation is norm-preserving for any t, so these round-offs do not
+// accumulate systematically).
 template <typename T>
 __device__ __forceinline__ void boris(T u[3], const T E[3], const T B[3], T ke) {
   T um[3], t[3], s[3], uq[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) um[a] = u[a] + ke * E[a];
-  const T gm = sqrt(T(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
-  const T kb = ke / gm;
+  const T kb = ke * inv_sqrt(T(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
 #pragma unroll
   for (int a = 0; a < 3; ++a) t[a] = kb * B[a];
   const T t2 = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
-  const T f2 = T(2) / (T(1) + t2);
+  const T f2 = fast_div(T(2), T(1) + t2);
 #pragma unroll
   for (int a = 0; a < 3; ++a) s[a] = f2 * t[a];
   uq[0] = um[0] + (um[1] * t[2] - um[2] * t[1]);
@@ -173,19 +180,17 @@ struct Mover<float> {
       sh = t;
       sl = __fadd_rn(sl, __fadd_rn(f, e));
     }
-    // gamma = sqrt(sh + sl): one Newton correction of the FP32 root
-    const float y = sqrtf(sh);
-    float yy, yl;
-    two_prod(y, y, yy, yl);
-    const float r = __fadd_rn(__fsub_rn(__fsub_rn(sh, yy), yl), sl);
-    const float gh0 = y, gl0 = __fdiv_rn(r, __fmul_rn(2.0f, y));
-    float gh, gl;
-    two_sum(gh0, gl0, gh, gl);
-    // 1/gamma: FP32 reciprocal + one correction with the float-float residual
-    const float q = __fdiv_rn(1.0f, gh);
-    const float res = __fsub_rn(__fmaf_rn(-gh, q, 1.0f), __fmul_rn(gl, q));
-    ih = q;
-    il = __fmul_rn(q, res);
+    // 1/gamma = (sh + sl)^(-1/2): hardware estimate plus one Newton step with
+    // the residual r = 1 - s y^2 formed from exact products, so the pair
+    // (ih, il) carries about twice the FP32 precision.
+    const float y = rsqrtf(sh);
+    float y2, y2e;
+    two_prod(y, y, y2, y2e);
+    float r = __fmaf_rn(-sh, y2, 1.0f);
+    r = __fmaf_rn(-sh, y2e, r);
+    r = __fmaf_rn(-sl, y2, r);
+    ih = y;
+    il = __fmul_rn(__fmul_rn(0.5f, y), r);
   }
   // returns the displacement S u / gamma as a float-float pair
   __device__ __forceinline__ void disp(float Sh, float Sl, float ua, float& dh, float& dl) const {

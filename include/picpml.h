@@ -226,6 +226,54 @@ int pic_state_size(picpml_ctx* ctx, long long* bytes);
 int pic_get_state(picpml_ctx* ctx, void* host_dst);
 int pic_set_state(picpml_ctx* ctx, const void* host_src);
 
+/* ------------------------------------------------------------------------ */
+/* Batched independent 2D runs (the single-particle studies of Sec. III,    */
+/* swept over incidence angle and gamma): one persistent kernel launch per  */
+/* step advances every run; launches are replayed from a captured CUDA      */
+/* graph.  Runs share the cell size, time step, shape order, precision and  */
+/* PML profile; each has its own physical size, PML width (on its four      */
+/* faces) and one macroparticle.                                            */
+/* ------------------------------------------------------------------------ */
+typedef struct pic_batch pic_batch; /* opaque, library-owned */
+
+typedef struct pic_batch_desc {
+  int nruns;
+  const int* nx;        /* host arrays of nruns entries: physical cells along x, */
+  const int* nz;        /*   along z,                                             */
+  const int* npml;      /*   PML cells on each of the run's four faces            */
+  double d[2];          /* cell sizes dx, dz (m), shared by all runs */
+  double dt;            /* s; <= 0 selects cfl * Courant limit */
+  double cfl;
+  int shape_order;      /* 1 or 3 */
+  int prec;             /* PIC_FP32 (float-float PML parts) or PIC_FP64 */
+  pml_desc pml;         /* profile and alpha mode (ncell is ignored) */
+  double q, m;          /* charge and mass of the macroparticles */
+  void* pos;            /* caller-owned device arrays of nruns particle */
+  void* mom;            /*   records (layout of pic_species); record r lives in
+                           run r, its cell index relative to run r's grid */
+} pic_batch_desc;
+
+/* Validates the description, builds per-run coefficient tables (Eq.
+ * conductivity, Eq. alpha at nodes and centres), allocates and zeroes the
+ * fields of every run and records the two-step CUDA graph.  The first
+ * call on a device must not happen while that stream is being captured. */
+int pic_batch_init(pic_batch** b, const pic_batch_desc* d, void* stream);
+/* n time steps of every run (graph replay; one kernel launch per step). */
+int pic_batch_step(pic_batch* b, int n);
+/* One field component of one run into dst (device buffer of
+ * (nx+2p+1)*(nz+2p+1) elements, i fastest); which: 0-2 E^n, 3-5 B^n,
+ * 6-8 the current not yet consumed (zero after a step).  SI units. */
+int pic_batch_get_field(pic_batch* b, int run, int which, void* dst, int as_double);
+/* 1: particles keep their momentum (prescribed trajectories). */
+int pic_batch_set_prescribed(pic_batch* b, int flag);
+/* Live particles pushed so far, summed over steps (synchronises). */
+int pic_batch_particle_steps(pic_batch* b, long long* n);
+/* dt in use and the total number of cells of all runs. */
+int pic_batch_info(pic_batch* b, double* dt, long long* cells);
+int pic_batch_sync(pic_batch* b);
+const char* pic_batch_last_error(pic_batch* b);
+void pic_batch_destroy(pic_batch* b);
+
 /* Last error message of this context (or of the last failed pic_init when
  * ctx is NULL).  Valid until the next call on the context. */
 const char* pic_last_error(picpml_ctx* ctx);

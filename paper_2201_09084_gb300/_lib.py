@@ -45,6 +45,13 @@ class SpeciesDesc(C.Structure):
                 ("immobile", C.c_int)]
 
 
+class BatchDesc(C.Structure):
+    _fields_ = [("nruns", C.c_int), ("nx", C.POINTER(C.c_int)), ("nz", C.POINTER(C.c_int)),
+                ("npml", C.POINTER(C.c_int)), ("d", C.c_double * 2), ("dt", C.c_double),
+                ("cfl", C.c_double), ("shape_order", C.c_int), ("prec", C.c_int), ("pml", PmlDesc),
+                ("q", C.c_double), ("m", C.c_double), ("pos", C.c_void_p), ("mom", C.c_void_p)]
+
+
 # every symbol include/picpml.h declares, with its ctypes signature
 VP = C.c_void_p
 SIGNATURES = {
@@ -70,6 +77,15 @@ SIGNATURES = {
     "pic_state_size": (C.c_int, [VP, C.POINTER(C.c_longlong)]),
     "pic_get_state": (C.c_int, [VP, VP]),
     "pic_set_state": (C.c_int, [VP, VP]),
+    "pic_batch_init": (C.c_int, [C.POINTER(VP), C.POINTER(BatchDesc), VP]),
+    "pic_batch_step": (C.c_int, [VP, C.c_int]),
+    "pic_batch_get_field": (C.c_int, [VP, C.c_int, C.c_int, VP, C.c_int]),
+    "pic_batch_set_prescribed": (C.c_int, [VP, C.c_int]),
+    "pic_batch_particle_steps": (C.c_int, [VP, C.POINTER(C.c_longlong)]),
+    "pic_batch_info": (C.c_int, [VP, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+    "pic_batch_sync": (C.c_int, [VP]),
+    "pic_batch_last_error": (C.c_char_p, [VP]),
+    "pic_batch_destroy": (None, [VP]),
     "pic_last_error": (C.c_char_p, [VP]),
     "pic_destroy": (None, [VP]),
 }

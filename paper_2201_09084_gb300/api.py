@@ -186,3 +186,80 @@ class Sim:
     def set_state(self, buf):
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
         self._call(self.lib.pic_set_state, C.c_void_p(buf.ctypes.data))
+
+
+class Batch:
+    """Many independent 2D runs advanced together (pic_batch_* of the C ABI)."""
+
+    def __init__(self, nx, nz, npml, d, pos, mom, q, m, *, dt=0.0, cfl=0.99, order=1, prec="fp32",
+                 alpha_mode="damped", sigma_coef=4.0, delta=6.0, exponent=2.0, v_assumed=0.0, stream=None):
+        self.lib = L.load()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.n = len(nx)
+        self._nx = np.ascontiguousarray(nx, dtype=np.int32)
+        self._nz = np.ascontiguousarray(nz, dtype=np.int32)
+        self._np = np.ascontiguousarray(npml, dtype=np.int32)
+        d_ = L.BatchDesc()
+        d_.nruns = self.n
+        ip = C.POINTER(C.c_int)
+        d_.nx = self._nx.ctypes.data_as(ip)
+        d_.nz = self._nz.ctypes.data_as(ip)
+        d_.npml = self._np.ctypes.data_as(ip)
+        d_.d[0], d_.d[1] = float(d[0]), float(d[1])
+        d_.dt, d_.cfl, d_.shape_order, d_.prec = float(dt), float(cfl), int(order), L.PREC[prec]
+        d_.pml.sigma_max_coef, d_.pml.delta_cells, d_.pml.exponent = float(sigma_coef), float(delta), float(exponent)
+        d_.pml.alpha_mode = L.ALPHA[alpha_mode] if isinstance(alpha_mode, str) else int(alpha_mode)
+        d_.pml.v_assumed = float(v_assumed)
+        d_.q, d_.m = float(q), float(m)
+        want = torch.float64 if prec == "fp64" else torch.float32
+        assert pos.is_cuda and pos.dtype == want and tuple(pos.shape) == (self.n, 4)
+        d_.pos, d_.mom = pos.data_ptr(), mom.data_ptr()
+        self.pos, self.mom = pos, mom
+        h = C.c_void_p()
+        rc = self.lib.pic_batch_init(C.byref(h), C.byref(d_), C.c_void_p(self.stream.cuda_stream))
+        self.h = h
+        if rc != 0:
+            msg = self.lib.pic_batch_last_error(h).decode()
+            self.close()
+            raise L.PicError(rc, msg)
+        dtv, cells = C.c_double(), C.c_longlong()
+        self._call(self.lib.pic_batch_info, C.byref(dtv), C.byref(cells))
+        self.dt, self.cells = dtv.value, cells.value
+
+    def _call(self, fn, *args):
+        rc = fn(self.h, *args)
+        if rc != 0:
+            raise L.PicError(rc, self.lib.pic_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.pic_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        self._call(self.lib.pic_batch_step, int(n))
+
+    def sync(self):
+        self._call(self.lib.pic_batch_sync)
+
+    def set_prescribed(self, flag=True):
+        self._call(self.lib.pic_batch_set_prescribed, int(bool(flag)))
+
+    def particle_steps(self):
+        n = C.c_longlong()
+        self._call(self.lib.pic_batch_particle_steps, C.byref(n))
+        return n.value
+
+    def field(self, run, name, dtype=torch.float64):
+        nn0 = int(self._nx[run] + 2 * self._np[run] + 1)
+        nn2 = int(self._nz[run] + 2 * self._np[run] + 1)
+        out = torch.empty(nn0 * nn2, dtype=dtype, device="cuda")
+        self._call(self.lib.pic_batch_get_field, int(run), FIELDS[name], C.c_void_p(out.data_ptr()),
+                   int(dtype == torch.float64))
+        return out.view(nn2, 1, nn0)

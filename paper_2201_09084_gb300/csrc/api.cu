@@ -15,9 +15,9 @@
 
 namespace picpml {
 template <typename T>
-cudaError_t launch_field_E(const Geom&, const Tables&, const FieldPtrs<T>&, int split_ff, cudaStream_t);
+cudaError_t launch_field_E(const Geom&, const Tables&, const FieldPtrs<T>&, int split_ff, int kz, cudaStream_t);
 template <typename T>
-cudaError_t launch_field_B(const Geom&, const Tables&, const FieldPtrs<T>&, int split_ff, cudaStream_t);
+cudaError_t launch_field_B(const Geom&, const Tables&, const FieldPtrs<T>&, int split_ff, int kz, cudaStream_t);
 template <typename T>
 cudaError_t launch_particles(int mode, int order, const Geom&, const Tables&, const FieldPtrs<T>&,
                              const SpeciesPtrs<T>&, int prescribed, unsigned* status, unsigned long long* pushed,
@@ -40,6 +40,39 @@ int sort_launches(long long ncell);
 cudaError_t static_diag_buffers(double** rho, double** out, long long* cap);
 cudaError_t launch_sort(const Geom&, int pbytes, void* pos, void* mom, long long* n_dev, long long cap,
                         unsigned* scratch, void* tmp_pos, void* tmp_mom, cudaStream_t);
+}  // namespace picpml
+
+namespace picpml {
+double sigma_eps0_face(const pml_desc& p, double Delta, double dc);
+double alpha_face(const pml_desc& p, double dc);
+
+// Per-axis coefficient tables of one box at the nodes i and centres i+1/2
+// (Sec. II.B): exponential-differencing factors, s dt and alpha, from the
+// closed forms of Eq. conductivity and Eq. alpha.  plo, nph: PML cells below
+// and physical cells along the axis; `active` false for the absent y axis of
+// 2D boxes (no PML, alpha = 1).
+void build_axis_table(const pml_desc& p, double Delta, double dt, int plo, int nph, int nn, bool active,
+                      double* ea_n, double* eb_n, double* sdt_n, double* ea_c, double* eb_c, double* sdt_c,
+                      double* al_n, double* al_c) {
+  for (int i = 0; i < nn; ++i) {
+    for (int stag = 0; stag < 2; ++stag) {
+      const double x = i + 0.5 * stag;
+      double dc = 0.0;
+      if (active) {
+        const double lo = plo, hi = plo + nph;
+        dc = x < lo ? lo - x : (x > hi ? x - hi : 0.0);
+      }
+      const double sdt = sigma_eps0_face(p, Delta, dc) * dt;
+      const double ea = std::exp(-sdt);
+      const double eb = sdt > 0 ? -std::expm1(-sdt) / sdt : 1.0;
+      const double al = alpha_face(p, dc);
+      (stag ? ea_c : ea_n)[i] = ea;
+      (stag ? eb_c : eb_n)[i] = eb;
+      (stag ? sdt_c : sdt_n)[i] = sdt;
+      (stag ? al_c : al_n)[i] = al;
+    }
+  }
+}
 }  // namespace picpml
 
 using namespace picpml;
@@ -80,6 +113,7 @@ struct picpml_ctx {
   int prescribed = 0;
   int use_runs = 1;   // order-1 fused kernel over sorted runs (else one thread per particle)
   int ppt = 0;        // particles per thread of the run kernel (0 = default)
+  int kz = 1;         // nodes per thread along z in the field kernels
   long long steps_done = 0;
   long long launches = 0;
   std::string err;
@@ -119,15 +153,17 @@ double courant_limit(const pic_grid_desc& g) {
   return 1.0 / (kC * std::sqrt(s));
 }
 
+}  // namespace
+
 // sigma/eps0 at depth dc cells into a face (Eq. conductivity generalised)
-double sigma_eps0(const pml_desc& p, double Delta, double dc) {
+double picpml::sigma_eps0_face(const pml_desc& p, double Delta, double dc) {
   if (dc <= 0.0) return 0.0;
   return p.sigma_max_coef * kC / Delta * std::pow(dc / p.delta_cells, p.exponent);
 }
 
 // Eq. alpha in closed form for the power-law profile: the exponent is
 // int_0^d sigma/(eps0 v) dz = coef (c/v) delta (d/delta)^{p+1}/(p+1), d in cells.
-double alpha_of(const pml_desc& p, double dc) {
+double picpml::alpha_face(const pml_desc& p, double dc) {
   if (dc <= 0.0) return 1.0;
   if (p.alpha_mode == PML_ALPHA_ZERO) return 0.0;
   if (p.alpha_mode == PML_ALPHA_ONE) return 1.0;
@@ -136,6 +172,8 @@ double alpha_of(const pml_desc& p, double dc) {
                    std::pow(dc / p.delta_cells, p.exponent + 1.0) / (p.exponent + 1.0);
   return std::exp(-e);
 }
+
+namespace {
 
 template <typename T>
 FieldPtrs<T>& fields(picpml_ctx* c);
@@ -180,8 +218,8 @@ int run_particles(picpml_ctx* ctx, int mode) {
 template <typename T>
 int run_field(picpml_ctx* ctx) {
   FieldPtrs<T>& f = fields<T>(ctx);
-  CK(launch_field_E<T>(ctx->g, ctx->tb, f, ctx->split_ff(), ctx->stream));
-  CK(launch_field_B<T>(ctx->g, ctx->tb, f, ctx->split_ff(), ctx->stream));
+  CK(launch_field_E<T>(ctx->g, ctx->tb, f, ctx->split_ff(), ctx->kz, ctx->stream));
+  CK(launch_field_B<T>(ctx->g, ctx->tb, f, ctx->split_ff(), ctx->kz, ctx->stream));
   ctx->launches += 2;
   for (int c = 0; c < 3; ++c) std::swap(f.Bh[c], f.Bp[c]);
   return PIC_OK;
@@ -314,19 +352,14 @@ int pml_init(picpml_ctx* ctx, const pml_desc* p) {
   size_t off = 0;
   for (int a = 0; a < 3; ++a) {
     const int nn = g.nn[a];
-    const double Delta = gd.d[a];
+    std::vector<double> t8(8 * (size_t)nn);
+    double* q8 = t8.data();
+    build_axis_table(*p, gd.d[a], ctx->dt, g.plo[a], g.nph[a], nn, !(gd.dim == 2 && a == 1), q8, q8 + nn,
+                     q8 + 2 * nn, q8 + 3 * nn, q8 + 4 * nn, q8 + 5 * nn, q8 + 6 * nn, q8 + 7 * nn);
     for (int i = 0; i < nn; ++i) {
       for (int stag = 0; stag < 2; ++stag) {
-        double x = i + 0.5 * stag, dc = 0.0;
-        if (!(gd.dim == 2 && a == 1)) {
-          const double lo = g.plo[a], hi = g.plo[a] + g.nph[a];
-          dc = x < lo ? lo - x : (x > hi ? x - hi : 0.0);
-        }
-        const double s = sigma_eps0(*p, Delta, dc);
-        const double sdt = s * ctx->dt;
-        const double ea = std::exp(-sdt);
-        const double eb = sdt > 0 ? -std::expm1(-sdt) / sdt : 1.0;
-        const double al = alpha_of(*p, dc);
+        const double ea = q8[(stag * 3 + 0) * nn + i], eb = q8[(stag * 3 + 1) * nn + i];
+        const double sdt = q8[(stag * 3 + 2) * nn + i], al = q8[(6 + stag) * nn + i];
         const size_t base = off + i;
         host[(stag * 3 + 0) * total + base] = ea;
         host[(stag * 3 + 1) * total + base] = eb;

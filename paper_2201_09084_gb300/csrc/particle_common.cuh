@@ -256,5 +256,142 @@ __device__ __forceinline__ void esk_axis(int i0, T f0, int i1, T f1, int& lo, T*
   }
 }
 
+// Esirkepov deposition of one move, damped by alpha at each component's
+// staggered location, accumulated with global atomics.
+template <int ORDER, int DIM, typename T>
+__device__ __forceinline__ void deposit_one(const Geom& g, const Tables& tb, const FieldPtrs<T>& f,
+                                            const SpeciesPtrs<T>& sp, const int c0[3], const T o0[3],
+                                            const int c1[3], const T o1[3], T w, T vy) {
+  constexpr int W = ORDER + 2;
+  int lo[3];
+  T S0[3][W], DS[3][W];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (DIM == 2 && a == 1) {
+      lo[1] = 0;
+#pragma unroll
+      for (int t = 0; t < W; ++t) S0[1][t] = DS[1][t] = T(0);
+      continue;
+    }
+    esk_axis<ORDER, T>(c0[a], o0[a], c1[a], o1[a], lo[a], S0[a], DS[a]);
+  }
+  const T* anx = al_node<T>(tb, 0);
+  const T* acx = al_cent<T>(tb, 0);
+  const T* any = al_node<T>(tb, 1);
+  const T* acy = al_cent<T>(tb, 1);
+  const T* anz = al_node<T>(tb, 2);
+  const T* acz = al_cent<T>(tb, 2);
+  // transverse factor S0 S0' + DS S0'/2 + S0 DS'/2 + DS DS'/3 = M M' + Q DS'
+  // with the mid-move shape M = S0 + DS/2 and Q = DS/12 (1/3 = 1/4 + 1/12)
+  T M[3][W], Q[3][W];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int t = 0; t < W; ++t) {
+      M[a][t] = (DIM == 2 && a == 1) ? T(t == 0) : S0[a][t] + T(0.5) * DS[a][t];
+      Q[a][t] = (DIM == 2 && a == 1) ? T(0) : T(1.0 / 12.0) * DS[a][t];
+    }
+  if (DIM == 3) {
+    const T qx = sp.cj[0] * w, qy = sp.cj[1] * w, qz = sp.cj[2] * w;
+    // J_x: prefix sums along x of W_x = DSx (S0y S0z + DSy S0z/2 + S0y DSz/2 + DSy DSz/3)
+#pragma unroll
+    for (int kz = 0; kz < W; ++kz)
+#pragma unroll
+      for (int jy = 0; jy < W; ++jy) {
+        const T Tl = M[1][jy] * M[2][kz] + Q[1][jy] * DS[2][kz];
+        if (Tl == T(0)) continue;
+        const T line = qx * Tl * any[lo[1] + jy] * anz[lo[2] + kz];
+        const long long row = g.idx(lo[0], lo[1] + jy, lo[2] + kz);
+        T acc = T(0);
+#pragma unroll
+        for (int ix = 0; ix < W - 1; ++ix) {
+          acc += DS[0][ix];
+          if (acc != T(0)) atomicAdd(f.J[0] + row + ix, line * acc * acx[lo[0] + ix]);
+        }
+      }
+    // J_y
+#pragma unroll
+    for (int kz = 0; kz < W; ++kz)
+#pragma unroll
+      for (int ix = 0; ix < W; ++ix) {
+        const T Tl = M[0][ix] * M[2][kz] + Q[0][ix] * DS[2][kz];
+        if (Tl == T(0)) continue;
+        const T line = qy * Tl * anx[lo[0] + ix] * anz[lo[2] + kz];
+        T acc = T(0);
+#pragma unroll
+        for (int jy = 0; jy < W - 1; ++jy) {
+          acc += DS[1][jy];
+          if (acc != T(0))
+            atomicAdd(f.J[1] + g.idx(lo[0] + ix, lo[1] + jy, lo[2] + kz), line * acc * acy[lo[1] + jy]);
+        }
+      }
+    // J_z
+#pragma unroll
+    for (int jy = 0; jy < W; ++jy)
+#pragma unroll
+      for (int ix = 0; ix < W; ++ix) {
+        const T Tl = M[0][ix] * M[1][jy] + Q[0][ix] * DS[1][jy];
+        if (Tl == T(0)) continue;
+        const T line = qz * Tl * anx[lo[0] + ix] * any[lo[1] + jy];
+        T acc = T(0);
+#pragma unroll
+        for (int kz = 0; kz < W - 1; ++kz) {
+          acc += DS[2][kz];
+          if (acc != T(0))
+            atomicAdd(f.J[2] + g.idx(lo[0] + ix, lo[1] + jy, lo[2] + kz), line * acc * acz[lo[2] + kz]);
+        }
+      }
+  } else {
+    const T qx = sp.cj[0] * w, qz = sp.cj[2] * w, qy = sp.cjy2d * w * vy;
+    // J_x: prefix along x of W_x = DSx (S0z + DSz/2)
+#pragma unroll
+    for (int kz = 0; kz < W; ++kz) {
+      const T Tl = M[2][kz];
+      if (Tl == T(0)) continue;
+      const T line = qx * Tl * anz[lo[2] + kz];
+      const long long row = g.idx(lo[0], 0, lo[2] + kz);
+      T acc = T(0);
+#pragma unroll
+      for (int ix = 0; ix < W - 1; ++ix) {
+        acc += DS[0][ix];
+        if (acc != T(0)) atomicAdd(f.J[0] + row + ix, line * acc * acx[lo[0] + ix]);
+      }
+    }
+    // J_z: prefix along z of W_z = DSz (S0x + DSx/2)
+#pragma unroll
+    for (int ix = 0; ix < W; ++ix) {
+      const T Tl = M[0][ix];
+      if (Tl == T(0)) continue;
+      const T line = qz * Tl * anx[lo[0] + ix];
+      T acc = T(0);
+#pragma unroll
+      for (int kz = 0; kz < W - 1; ++kz) {
+        acc += DS[2][kz];
+        if (acc != T(0)) atomicAdd(f.J[2] + g.idx(lo[0] + ix, 0, lo[2] + kz), line * acc * acz[lo[2] + kz]);
+      }
+    }
+    // J_y (out of plane): v_y times the time-averaged shape
+    if (qy != T(0)) {
+#pragma unroll
+      for (int kz = 0; kz < W; ++kz)
+#pragma unroll
+        for (int ix = 0; ix < W; ++ix) {
+          const T Wy = M[0][ix] * M[2][kz] + Q[0][ix] * DS[2][kz];
+          if (Wy != T(0))
+            atomicAdd(f.J[1] + g.idx(lo[0] + ix, 0, lo[2] + kz), qy * Wy * anx[lo[0] + ix] * anz[lo[2] + kz]);
+        }
+    }
+  }
+}
+
+
+// Deposit of one 2D particle of a batched run (same arithmetic).
+template <int ORDER, typename T>
+__device__ __forceinline__ void deposit_run_particle(const Geom& g, const Tables& tb, const FieldPtrs<T>& f,
+                                                     const SpeciesPtrs<T>& sp, const int c0[3], const T o0[3],
+                                                     const int c1[3], const T o1[3], T w, T vy) {
+  deposit_one<ORDER, 2, T>(g, tb, f, sp, c0, o0, c1, o1, w, vy);
+}
+
 }  // namespace pc
 }  // namespace picpml

@@ -16,127 +16,6 @@ namespace {
 
 using namespace pc;
 
-// Esirkepov deposition of one move, damped by alpha at each component's
-// staggered location, accumulated with global atomics.
-template <int ORDER, int DIM, typename T>
-__device__ __forceinline__ void deposit_one(const Geom& g, const Tables& tb, const FieldPtrs<T>& f,
-                                            const SpeciesPtrs<T>& sp, const int c0[3], const T o0[3],
-                                            const int c1[3], const T o1[3], T w, T vy) {
-  constexpr int W = ORDER + 2;
-  int lo[3];
-  T S0[3][W], DS[3][W];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (DIM == 2 && a == 1) {
-      lo[1] = 0;
-      continue;
-    }
-    esk_axis<ORDER, T>(c0[a], o0[a], c1[a], o1[a], lo[a], S0[a], DS[a]);
-  }
-  const T* anx = al_node<T>(tb, 0);
-  const T* acx = al_cent<T>(tb, 0);
-  const T* any = al_node<T>(tb, 1);
-  const T* acy = al_cent<T>(tb, 1);
-  const T* anz = al_node<T>(tb, 2);
-  const T* acz = al_cent<T>(tb, 2);
-  const T third = T(1.0 / 3.0);
-  if (DIM == 3) {
-    const T qx = sp.cj[0] * w, qy = sp.cj[1] * w, qz = sp.cj[2] * w;
-    // J_x: prefix sums along x of W_x = DSx (S0y S0z + DSy S0z/2 + S0y DSz/2 + DSy DSz/3)
-#pragma unroll
-    for (int kz = 0; kz < W; ++kz)
-#pragma unroll
-      for (int jy = 0; jy < W; ++jy) {
-        const T Tl = S0[1][jy] * S0[2][kz] + T(0.5) * DS[1][jy] * S0[2][kz] +
-                     T(0.5) * S0[1][jy] * DS[2][kz] + third * DS[1][jy] * DS[2][kz];
-        if (Tl == T(0)) continue;
-        const T line = qx * Tl * any[lo[1] + jy] * anz[lo[2] + kz];
-        const long long row = g.idx(lo[0], lo[1] + jy, lo[2] + kz);
-        T acc = T(0);
-#pragma unroll
-        for (int ix = 0; ix < W - 1; ++ix) {
-          acc += DS[0][ix];
-          if (acc != T(0)) atomicAdd(f.J[0] + row + ix, line * acc * acx[lo[0] + ix]);
-        }
-      }
-    // J_y
-#pragma unroll
-    for (int kz = 0; kz < W; ++kz)
-#pragma unroll
-      for (int ix = 0; ix < W; ++ix) {
-        const T Tl = S0[0][ix] * S0[2][kz] + T(0.5) * DS[0][ix] * S0[2][kz] +
-                     T(0.5) * S0[0][ix] * DS[2][kz] + third * DS[0][ix] * DS[2][kz];
-        if (Tl == T(0)) continue;
-        const T line = qy * Tl * anx[lo[0] + ix] * anz[lo[2] + kz];
-        T acc = T(0);
-#pragma unroll
-        for (int jy = 0; jy < W - 1; ++jy) {
-          acc += DS[1][jy];
-          if (acc != T(0))
-            atomicAdd(f.J[1] + g.idx(lo[0] + ix, lo[1] + jy, lo[2] + kz), line * acc * acy[lo[1] + jy]);
-        }
-      }
-    // J_z
-#pragma unroll
-    for (int jy = 0; jy < W; ++jy)
-#pragma unroll
-      for (int ix = 0; ix < W; ++ix) {
-        const T Tl = S0[0][ix] * S0[1][jy] + T(0.5) * DS[0][ix] * S0[1][jy] +
-                     T(0.5) * S0[0][ix] * DS[1][jy] + third * DS[0][ix] * DS[1][jy];
-        if (Tl == T(0)) continue;
-        const T line = qz * Tl * anx[lo[0] + ix] * any[lo[1] + jy];
-        T acc = T(0);
-#pragma unroll
-        for (int kz = 0; kz < W - 1; ++kz) {
-          acc += DS[2][kz];
-          if (acc != T(0))
-            atomicAdd(f.J[2] + g.idx(lo[0] + ix, lo[1] + jy, lo[2] + kz), line * acc * acz[lo[2] + kz]);
-        }
-      }
-  } else {
-    const T qx = sp.cj[0] * w, qz = sp.cj[2] * w, qy = sp.cjy2d * w * vy;
-    // J_x: prefix along x of W_x = DSx (S0z + DSz/2)
-#pragma unroll
-    for (int kz = 0; kz < W; ++kz) {
-      const T Tl = S0[2][kz] + T(0.5) * DS[2][kz];
-      if (Tl == T(0)) continue;
-      const T line = qx * Tl * anz[lo[2] + kz];
-      const long long row = g.idx(lo[0], 0, lo[2] + kz);
-      T acc = T(0);
-#pragma unroll
-      for (int ix = 0; ix < W - 1; ++ix) {
-        acc += DS[0][ix];
-        if (acc != T(0)) atomicAdd(f.J[0] + row + ix, line * acc * acx[lo[0] + ix]);
-      }
-    }
-    // J_z: prefix along z of W_z = DSz (S0x + DSx/2)
-#pragma unroll
-    for (int ix = 0; ix < W; ++ix) {
-      const T Tl = S0[0][ix] + T(0.5) * DS[0][ix];
-      if (Tl == T(0)) continue;
-      const T line = qz * Tl * anx[lo[0] + ix];
-      T acc = T(0);
-#pragma unroll
-      for (int kz = 0; kz < W - 1; ++kz) {
-        acc += DS[2][kz];
-        if (acc != T(0)) atomicAdd(f.J[2] + g.idx(lo[0] + ix, 0, lo[2] + kz), line * acc * acz[lo[2] + kz]);
-      }
-    }
-    // J_y (out of plane): v_y times the time-averaged shape
-    if (qy != T(0)) {
-#pragma unroll
-      for (int kz = 0; kz < W; ++kz)
-#pragma unroll
-        for (int ix = 0; ix < W; ++ix) {
-          const T Wy = S0[0][ix] * S0[2][kz] + T(0.5) * DS[0][ix] * S0[2][kz] +
-                       T(0.5) * S0[0][ix] * DS[2][kz] + third * DS[0][ix] * DS[2][kz];
-          if (Wy != T(0))
-            atomicAdd(f.J[1] + g.idx(lo[0] + ix, 0, lo[2] + kz), qy * Wy * anx[lo[0] + ix] * anz[lo[2] + kz]);
-        }
-    }
-  }
-}
-
 // MODE 0: push only (saves x^n); MODE 1: deposit only (from saved x^n);
 // MODE 2: fused push + deposit.
 template <int ORDER, int DIM, typename T, int MODE>

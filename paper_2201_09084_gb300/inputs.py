@@ -107,3 +107,25 @@ def random_particles(dim, n_particles, lo, hi, u_rms=0.5, seed=SEED_BASE + 7, q=
     u = rng.normal(0.0, u_rms, (n_particles, 3))
     out = _pack(X, u, np.full(n_particles, w), dim)
     return [dict(out, q=q, m=m, immobile=False)]
+
+
+def batched_runs(nruns, size_range=(64, 256), pml_range=(8, 24), theta_max_deg=80.0,
+                 gamma_range=(1.1, 100.0), seed=SEED_BASE + 5, q=-Q_E, m=M_E):
+    """Independent 2D single-particle runs (the angle / gamma sweeps of the
+    paper's single-particle studies): physical sizes nx, nz ~ U{lo..hi},
+    PML width ~ U{lo..hi}, one electron at the box centre moving at an angle
+    ~ U[0, theta_max] from +z with gamma log-uniform in gamma_range.
+    Particle cells are relative to each run's own grid."""
+    rng = np.random.default_rng(seed)
+    nx = rng.integers(size_range[0], size_range[1] + 1, nruns)
+    nz = rng.integers(size_range[0], size_range[1] + 1, nruns)
+    npml = rng.integers(pml_range[0], pml_range[1] + 1, nruns)
+    theta = rng.uniform(0.0, theta_max_deg, nruns)
+    gamma = np.exp(rng.uniform(np.log(gamma_range[0]), np.log(gamma_range[1]), nruns))
+    X = np.stack([npml + 0.5 * nx + rng.uniform(0.1, 0.9, nruns), np.zeros(nruns),
+                  npml + 0.5 * nz + rng.uniform(0.1, 0.9, nruns)], axis=1)
+    u = np.sqrt(gamma ** 2 - 1.0)
+    th = np.radians(theta)
+    U = np.stack([u * np.sin(th), np.zeros(nruns), u * np.cos(th)], axis=1)
+    out = _pack(X, U, np.ones(nruns), 2)
+    return dict(out, nx=nx, nz=nz, npml=npml, theta=theta, gamma=gamma, q=q, m=m)

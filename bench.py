@@ -262,6 +262,51 @@ def run_gpu(args, rank, world):
 
 
 # ----------------------------------------------------------------------------
+def run_batch(steps, warmup, prec, nruns=4096, order=3):
+    """Batched independent 2D runs: nruns single-particle boxes with sizes
+    U{64..256} x U{64..256}, PML U{8..24} cells, angle U[0, 80] deg from +z,
+    gamma log-uniform in [1.1, 100]; one persistent launch per step replayed
+    from a CUDA graph.  Returns a dict of rates and the roofline of the step
+    kernel (algorithmic bytes: 60 B per interior cell, 164 B per PML cell in
+    FP32 (8 split parts read and written); 120 / 248 B in FP64)."""
+    import torch
+    from paper_2201_09084_gb300 import inputs as I
+    from paper_2201_09084_gb300.api import Batch, pack_particles
+    r = I.batched_runs(nruns)
+    pos, mom = pack_particles(r["cell"], r["off"], r["u"], r["w"], prec)
+    b = Batch(r["nx"], r["nz"], r["npml"], (D[0], D[2]), pos, mom, r["q"], r["m"], cfl=0.99, order=order,
+              prec=prec, alpha_mode="damped")
+    stream = torch.cuda.current_stream()
+    b.step(warmup)
+    b.sync()
+    p0 = b.particle_steps()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ps = b.particle_steps() - p0
+    nx, nz, npml = r["nx"].astype(np.int64), r["nz"].astype(np.int64), r["npml"].astype(np.int64)
+    cells = int(np.sum((nx + 2 * npml) * (nz + 2 * npml)))
+    interior = int(np.sum(nx * nz))
+    e = 8 if prec == "fp64" else 4
+    byts = 15 * e * interior + (128 + 9 * e) * (cells - interior)
+    peak, kind = measured_peak()
+    achieved = byts / (ms / steps / 1e3) / 1e9
+    b.close()
+    return {"workload": f"{nruns} independent 2D runs, 64-256 cells per side, PML 8-24, one electron each, "
+                        f"angle 0-80 deg, gamma 1.1-100, order {order}, {prec}",
+            "steps": steps, "ms_per_step": ms / steps, "cell_updates_per_s": cells * steps / (ms / 1e3),
+            "particle_steps_per_s": ps / (ms / 1e3), "cells": cells,
+            "roofline": {"bound": "hbm", "kernel": "k_batch_step", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{kind} (copy)",
+                         "algorithmic_bytes_per_launch": byts},
+            "launches_per_step": 1, "graph": "two steps per captured graph"}
+
+
 def cpu_sample(order, theta, sample, steps):
     """The oracle on a bounded sample of the workload: the full 160^3 grid,
     `sample` beam particles (weights scaled to the same charge), `steps` time
@@ -321,6 +366,7 @@ def main():
     ap.add_argument("--theta", type=float, default=0.0)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched 2D runs measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -334,6 +380,11 @@ def main():
         out = run_reference(args, rank, world)
     else:
         out = run_gpu(args, rank, world)
+        if not args.no_batch:
+            nb = min(args.steps, 200)
+            out["batch2d"] = {"fp32": run_batch(nb, 3, "fp32"), "fp64": run_batch(nb, 3, "fp64")}
+            out["batch2d"]["fp32_over_fp64_particle_steps"] = (
+                out["batch2d"]["fp32"]["particle_steps_per_s"] / out["batch2d"]["fp64"]["particle_steps_per_s"])
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             v, desc, _ = cpu_sample(args.order, args.theta, 65536, 8)
             out["cpu_baseline"] = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",

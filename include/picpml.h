@@ -194,6 +194,19 @@ int pic_num_particles(picpml_ctx* ctx, int sid, long long* n);
  * (eps0 E^2 + B^2/mu0)/2 over the whole grid (J per m in 2D). */
 int pic_diag(picpml_ctx* ctx, double* gauss, double* rho_scale, double* energy);
 
+/* Autotuner: times the fused particle kernel for each particles-per-thread
+ * choice (order 1, FP32) and the field kernels for each z-nodes-per-thread
+ * choice, `steps` steps per candidate, each from the same state (a device
+ * snapshot, restored afterwards; the call allocates that snapshot), keeps
+ * the fastest and returns the choices.  Results do not depend on the choice
+ * beyond the summation order of the current. */
+int pic_autotune(picpml_ctx* ctx, int steps, int* particles_per_thread, int* z_nodes_per_thread);
+
+/* Sets the launch shapes directly (e.g. the result of pic_autotune in
+ * another context): particles per thread 0 (default), 4 or 8; z nodes per
+ * thread 1, 2 or 4. */
+int pic_set_tuning(picpml_ctx* ctx, int particles_per_thread, int z_nodes_per_thread);
+
 /* Particle-steps done so far: the number of live particles each push has
  * moved, summed over all pushes since pml_init (synchronises the stream). */
 int pic_particle_steps(picpml_ctx* ctx, long long* n);
@@ -255,7 +268,9 @@ typedef struct pic_batch_desc {
 
 /* Validates the description, builds per-run coefficient tables (Eq.
  * conductivity, Eq. alpha at nodes and centres), allocates and zeroes the
- * fields of every run and records the two-step CUDA graph.  The first
+ * fields of every run, autotunes the kernel's block shape by timing a few
+ * steps of every candidate from the initial state (then restored), and
+ * records the two-step CUDA graph.  The first
  * call on a device must not happen while that stream is being captured. */
 int pic_batch_init(pic_batch** b, const pic_batch_desc* d, void* stream);
 /* n time steps of every run (graph replay; one kernel launch per step). */
@@ -268,6 +283,11 @@ int pic_batch_get_field(pic_batch* b, int run, int which, void* dst, int as_doub
 int pic_batch_set_prescribed(pic_batch* b, int flag);
 /* Live particles pushed so far, summed over steps (synchronises). */
 int pic_batch_particle_steps(pic_batch* b, long long* n);
+/* Block shape the batch autotuner chose at pic_batch_init (threads per
+ * block, minimum resident blocks per SM) and the measured ms per step of the
+ * ncand candidates (threads, min blocks) = (512,1), (256,2), (512,2),
+ * (1024,1). */
+int pic_batch_tuning(pic_batch* b, int* threads, int* min_blocks, float* ms_per_step, int ncand);
 /* dt in use and the total number of cells of all runs. */
 int pic_batch_info(pic_batch* b, double* dt, long long* cells);
 int pic_batch_sync(pic_batch* b);

@@ -65,6 +65,8 @@ SIGNATURES = {
     "push_deposit": (C.c_int, [VP]),
     "pic_launch_count": (C.c_int, [VP, C.POINTER(C.c_longlong)]),
     "pic_particle_steps": (C.c_int, [VP, C.POINTER(C.c_longlong)]),
+    "pic_autotune": (C.c_int, [VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "pic_set_tuning": (C.c_int, [VP, C.c_int, C.c_int]),
     "pic_sort": (C.c_int, [VP]),
     "pic_grid_info": (C.c_int, [VP, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "pic_get_field": (C.c_int, [VP, C.c_int, VP, C.c_int]),
@@ -83,6 +85,7 @@ SIGNATURES = {
     "pic_batch_set_prescribed": (C.c_int, [VP, C.c_int]),
     "pic_batch_particle_steps": (C.c_int, [VP, C.POINTER(C.c_longlong)]),
     "pic_batch_info": (C.c_int, [VP, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+    "pic_batch_tuning": (C.c_int, [VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float), C.c_int]),
     "pic_batch_sync": (C.c_int, [VP]),
     "pic_batch_last_error": (C.c_char_p, [VP]),
     "pic_batch_destroy": (None, [VP]),

@@ -150,6 +150,14 @@ class Sim:
         self._call(self.lib.pic_particle_steps, C.byref(n))
         return n.value
 
+    def autotune(self, steps=3):
+        p, k = C.c_int(), C.c_int()
+        self._call(self.lib.pic_autotune, int(steps), C.byref(p), C.byref(k))
+        return {"particles_per_thread": p.value, "z_nodes_per_thread": k.value}
+
+    def set_tuning(self, particles_per_thread=0, z_nodes_per_thread=1):
+        self._call(self.lib.pic_set_tuning, int(particles_per_thread), int(z_nodes_per_thread))
+
     def step(self, n=1):
         self._call(self.lib.step_n, int(n))
 
@@ -255,6 +263,12 @@ class Batch:
         n = C.c_longlong()
         self._call(self.lib.pic_batch_particle_steps, C.byref(n))
         return n.value
+
+    def tuning(self):
+        t, mb = C.c_int(), C.c_int()
+        ms = (C.c_float * 4)()
+        self._call(self.lib.pic_batch_tuning, C.byref(t), C.byref(mb), ms, 4)
+        return {"threads": t.value, "min_blocks_per_sm": mb.value, "candidate_ms_per_step": list(ms)}
 
     def field(self, run, name, dtype=torch.float64):
         nn0 = int(self._nx[run] + 2 * self._np[run] + 1)

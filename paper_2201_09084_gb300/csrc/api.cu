@@ -503,6 +503,117 @@ int pic_particle_steps(picpml_ctx* ctx, long long* n) {
   return PIC_OK;
 }
 
+namespace {
+struct Snapshot {
+  std::vector<std::pair<void*, size_t>> items;   // (source, bytes)
+  std::vector<void*> copies;
+};
+}  // namespace
+
+// Times the particle kernel for each particles-per-thread choice and the field
+// kernels for each z-nodes-per-thread choice over `steps` steps each, starting
+// every candidate from the same state (a device-side snapshot of the fields,
+// the particle records and the counters, restored afterwards), and keeps the
+// fastest.  The result does not depend on the choice beyond round-off order.
+int pic_autotune(picpml_ctx* ctx, int steps, int* ppt, int* kz) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (steps < 1) steps = 3;
+  const bool f64 = ctx->gd.prec == PIC_FP64;
+  Snapshot sn;
+  const size_t es = ctx->elem();
+  void* fm = f64 ? (void*)ctx->fd.E[0] : (void*)ctx->ff.E[0];
+  sn.items.push_back({fm, (size_t)ctx->g.size * (12 * es + 12 * 8)});
+  for (auto& s : ctx->sp) {
+    sn.items.push_back({s.desc.pos, (size_t)s.desc.capacity * ctx->pbytes()});
+    sn.items.push_back({s.desc.mom, (size_t)s.desc.capacity * ctx->pbytes()});
+    sn.items.push_back({s.n_dev, sizeof(long long)});
+  }
+  sn.items.push_back({ctx->status, 64});
+  for (auto& it : sn.items) {
+    void* c = nullptr;
+    if (cudaMalloc(&c, it.second) != cudaSuccess) {
+      for (void* q : sn.copies) cudaFree(q);
+      return fail(ctx, PIC_ENOMEM, "autotune snapshot");
+    }
+    sn.copies.push_back(c);
+    CK(cudaMemcpyAsync(c, it.first, it.second, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  auto restore = [&]() -> cudaError_t {
+    for (size_t t = 0; t < sn.items.size(); ++t) {
+      cudaError_t e = cudaMemcpyAsync(sn.items[t].first, sn.copies[t], sn.items[t].second,
+                                      cudaMemcpyDeviceToDevice, ctx->stream);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  // the field kernels write B into the "previous" buffer: keep the pointer order
+  FieldPtrs<float> ff0 = ctx->ff;
+  FieldPtrs<double> fd0 = ctx->fd;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto time_it = [&](bool particles, float* ms) -> int {
+    int rr = 0;
+    // warm-up launch, then the timed ones
+    for (int t = 0; t <= steps; ++t) {
+      if (t == 1) CK(cudaEventRecord(e0, ctx->stream));
+      rr = particles ? (f64 ? run_particles<double>(ctx, 2) : run_particles<float>(ctx, 2))
+                     : (f64 ? run_field<double>(ctx) : run_field<float>(ctx));
+      if (rr) return rr;
+    }
+    CK(cudaEventRecord(e1, ctx->stream));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(ms, e0, e1));
+    *ms /= steps;
+    CK(restore());
+    ctx->ff = ff0;
+    ctx->fd = fd0;
+    return PIC_OK;
+  };
+  const long long launches0 = ctx->launches;
+  int best_p = ctx->ppt, best_k = ctx->kz;
+  if (ctx->gd.shape_order == 1 && !f64) {
+    float best = 1e30f;
+    for (int p : {4, 8}) {
+      ctx->ppt = p;
+      float ms = 0;
+      r = time_it(true, &ms);
+      if (r) return r;
+      if (ms < best) { best = ms; best_p = p; }
+    }
+  }
+  {
+    float best = 1e30f;
+    for (int k : {1, 2, 4}) {
+      ctx->kz = k;
+      float ms = 0;
+      r = time_it(false, &ms);
+      if (r) return r;
+      if (ms < best) { best = ms; best_k = k; }
+    }
+  }
+  ctx->ppt = best_p;
+  ctx->kz = best_k;
+  ctx->launches = launches0;
+  CK(cudaStreamSynchronize(ctx->stream));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (void* q : sn.copies) cudaFree(q);
+  if (ppt) *ppt = ctx->ppt;
+  if (kz) *kz = ctx->kz;
+  return PIC_OK;
+}
+
+int pic_set_tuning(picpml_ctx* ctx, int ppt, int kz) {
+  if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
+  if (!(ppt == 0 || ppt == 4 || ppt == 8) || !(kz == 1 || kz == 2 || kz == 4))
+    return fail(ctx, PIC_EINVAL, "particles per thread must be 0, 4 or 8; z nodes per thread 1, 2 or 4");
+  ctx->ppt = ppt;
+  ctx->kz = kz;
+  return PIC_OK;
+}
+
 int pic_launch_count(picpml_ctx* ctx, long long* n) {
   if (!ctx || !n) return fail(ctx, PIC_EINVAL, "null argument");
   *n = ctx->launches;

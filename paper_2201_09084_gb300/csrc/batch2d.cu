@@ -96,8 +96,8 @@ __device__ __forceinline__ Tables run_tables(const BatchArgs<T>& a, const RunInf
   return t;
 }
 
-template <typename T, int ORDER, int SPL>
-__global__ void __launch_bounds__(512) k_batch_step(BatchArgs<T> a, int parity) {
+template <typename T, int ORDER, int SPL, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_batch_step(BatchArgs<T> a, int parity) {
   __shared__ int s_run;
   for (;;) {
     __syncthreads();
@@ -249,6 +249,8 @@ struct pic_batch {
   cudaStream_t stream = nullptr;      // caller's stream
   cudaStream_t capture = nullptr;     // private stream used only to record the graph
   int nsm = 148, blocks = 0;
+  int cfg = 0;                         // block shape chosen by the autotuner (index into kShapes)
+  std::vector<float> tune_ms;          // measured ms per step of every candidate
   std::vector<RunInfo> runs;
   std::vector<void*> allocs;
   BatchArgs<float> af{};
@@ -285,20 +287,41 @@ BatchArgs<float>& args<float>(pic_batch* b) { return b->af; }
 template <>
 BatchArgs<double>& args<double>(pic_batch* b) { return b->ad; }
 
+// Block shapes the autotuner chooses from: (threads, minimum blocks per SM).
+constexpr int kShapes[4][2] = {{512, 1}, {256, 2}, {512, 2}, {1024, 1}};
+
+template <typename T, int ORDER, int SPL, int NT, int MINB>
+cudaError_t launch_shape(pic_batch* b, BatchArgs<T>& a, int parity, cudaStream_t s) {
+  static int per_sm = 0;   // resident blocks per SM of this instance (queried once)
+  if (per_sm == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_step<T, ORDER, SPL, NT, MINB>, NT, 0) !=
+            cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+  }
+  const int blocks = std::max(1, std::min(b->nsm * per_sm, b->d.nruns));
+  k_batch_step<T, ORDER, SPL, NT, MINB><<<blocks, NT, 0, s>>>(a, parity);
+  return cudaGetLastError();
+}
+
+template <typename T, int ORDER, int SPL>
+cudaError_t launch_cfg(pic_batch* b, BatchArgs<T>& a, int parity, cudaStream_t s) {
+  switch (b->cfg) {
+    case 1: return launch_shape<T, ORDER, SPL, 256, 2>(b, a, parity, s);
+    case 2: return launch_shape<T, ORDER, SPL, 512, 2>(b, a, parity, s);
+    case 3: return launch_shape<T, ORDER, SPL, 1024, 1>(b, a, parity, s);
+    default: return launch_shape<T, ORDER, SPL, 512, 1>(b, a, parity, s);
+  }
+}
+
 template <typename T>
 cudaError_t launch_step(pic_batch* b, int parity, cudaStream_t s) {
   BatchArgs<T>& a = args<T>(b);
   cudaError_t e = cudaMemsetAsync(a.queue, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   const bool ff = sizeof(T) == 4;
-  if (b->order == 1) {
-    if (ff) k_batch_step<T, 1, 1><<<b->blocks, 512, 0, s>>>(a, parity);
-    else k_batch_step<T, 1, 0><<<b->blocks, 512, 0, s>>>(a, parity);
-  } else {
-    if (ff) k_batch_step<T, 3, 1><<<b->blocks, 512, 0, s>>>(a, parity);
-    else k_batch_step<T, 3, 0><<<b->blocks, 512, 0, s>>>(a, parity);
-  }
-  return cudaGetLastError();
+  if (b->order == 1) return ff ? launch_cfg<T, 1, 1>(b, a, parity, s) : launch_cfg<T, 1, 0>(b, a, parity, s);
+  return ff ? launch_cfg<T, 3, 1>(b, a, parity, s) : launch_cfg<T, 3, 0>(b, a, parity, s);
 }
 
 cudaError_t launch_any(pic_batch* b, int parity, cudaStream_t s) {
@@ -486,18 +509,45 @@ int pic_batch_init(pic_batch** out, const pic_batch_desc* d, void* stream) {
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
-  int per_sm = 1;
-  cudaError_t e;
-  if (b->prec == PIC_FP64)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, b->order == 1 ? (const void*)k_batch_step<double, 1, 0> : (const void*)k_batch_step<double, 3, 0>,
-        512, 0);
-  else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &per_sm, b->order == 1 ? (const void*)k_batch_step<float, 1, 1> : (const void*)k_batch_step<float, 3, 1>,
-        512, 0);
-  if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-  b->blocks = std::min(b->nsm * per_sm, n);
+  // autotune the block shape: a few steps per candidate from the initial
+  // state, which is then restored (fields zeroed, particle records copied back)
+  {
+    const size_t pb = (size_t)n * (b->prec == PIC_FP64 ? 32 : 16);
+    void* save = balloc(b, 2 * pb);
+    if (!save) return bfail(b, PIC_ENOMEM, "autotune scratch");
+    BCK(cudaMemcpyAsync(save, d->pos, pb, cudaMemcpyDeviceToDevice, b->stream));
+    BCK(cudaMemcpyAsync((char*)save + pb, d->mom, pb, cudaMemcpyDeviceToDevice, b->stream));
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_cfg = 0;
+    for (int c = 0; c < 4; ++c) {
+      b->cfg = c;
+      BCK(launch_any(b, 0, b->stream));   // warm-up (first launch of this shape)
+      BCK(cudaEventRecord(e0, b->stream));
+      for (int t = 0; t < 3; ++t) BCK(launch_any(b, (t + 1) & 1, b->stream));
+      BCK(cudaEventRecord(e1, b->stream));
+      BCK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      BCK(cudaEventElapsedTime(&ms, e0, e1));
+      b->tune_ms.push_back(ms / 3);
+      if (ms < best) {
+        best = ms;
+        best_cfg = c;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->cfg = best_cfg;
+    // restore the initial state
+    const size_t es = b->prec == PIC_FP64 ? 8 : 4;
+    char* fm = b->prec == PIC_FP64 ? (char*)b->ad.E[0] : (char*)b->af.E[0];
+    BCK(cudaMemsetAsync(fm, 0, (size_t)total * (12 * es + 12 * 8), b->stream));
+    BCK(cudaMemcpyAsync(d->pos, save, pb, cudaMemcpyDeviceToDevice, b->stream));
+    BCK(cudaMemcpyAsync(d->mom, (char*)save + pb, pb, cudaMemcpyDeviceToDevice, b->stream));
+    BCK(cudaMemsetAsync(misc, 0, 256, b->stream));
+  }
   // record the two-step graph on a private stream (no work runs during capture)
   BCK(cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking));
   cudaGraph_t graph = nullptr;
@@ -593,6 +643,14 @@ int pic_batch_sync(pic_batch* b) {
   unsigned st = 0;
   BCK(cudaMemcpy(&st, b->prec == PIC_FP64 ? b->ad.status : b->af.status, sizeof(st), cudaMemcpyDeviceToHost));
   if (st & ST_BAD_PARTICLE) return bfail(b, PIC_EPARTICLE, "a particle was outside its allowed cells (removed)");
+  return PIC_OK;
+}
+
+int pic_batch_tuning(pic_batch* b, int* threads, int* min_blocks, float* ms_per_step, int ncand) {
+  if (!b || !b->pair) return bfail(b, PIC_ESTATE, "batch not initialised");
+  if (threads) *threads = kShapes[b->cfg][0];
+  if (min_blocks) *min_blocks = kShapes[b->cfg][1];
+  for (int c = 0; c < ncand && c < (int)b->tune_ms.size(); ++c) ms_per_step[c] = b->tune_ms[c];
   return PIC_OK;
 }
 

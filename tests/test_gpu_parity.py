@@ -212,3 +212,23 @@ def test_dense_beam_shared_memory_box(theta, prec):
         assert max(err.values()) < TOL[prec], err
     # removed particles are marked at once and compacted at the next sort
     assert int(gpu.particles(0)["alive"].sum()) == int(ora.particles()["alive"].sum())
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_autotune_restores_state(prec):
+    """pic_autotune runs candidate kernels from a snapshot and restores it:
+    afterwards the run continues exactly as if no tuning had happened."""
+    nphys = (20, 18, 24)
+    pml = (6,) * 6
+    center = (6 + 10.3, 6 + 9.2, 6 + 17.6)
+    parts = I.beam(3, 20000, nphys, pml, center, sigma=(0.8, 0.8, 1.3), theta_deg=10.0, clip=3.0)
+    ora, gpu = make_pair(3, nphys, pml, D3, parts, order=1, prec=prec, alpha_mode="damped", sort_every=5)
+    ora.step(4)
+    gpu.step(4)
+    choice = gpu.autotune(steps=2)
+    assert choice["z_nodes_per_thread"] in (1, 2, 4)
+    assert choice["particles_per_thread"] in (0, 4, 8)
+    ora.step(8)
+    gpu.step(8)
+    err = max_field_err(ora, gpu)
+    assert max(err.values()) < TOL[prec], err

@@ -299,11 +299,12 @@ def run_batch(steps, warmup, prec, nruns=4096, order=3):
     byts = 15 * e * interior + (128 + 9 * e) * (cells - interior)
     peak, kind = measured_peak()
     achieved = byts / (ms / steps / 1e3) / 1e9
+    tuning = b.tuning()
     b.close()
     return {"workload": f"{nruns} independent 2D runs, 64-256 cells per side, PML 8-24, one electron each, "
                         f"angle 0-80 deg, gamma 1.1-100, order {order}, {prec}",
             "steps": steps, "ms_per_step": ms / steps, "cell_updates_per_s": cells * steps / (ms / 1e3),
-            "particle_steps_per_s": ps / (ms / 1e3), "cells": cells, "autotune": b.tuning(),
+            "particle_steps_per_s": ps / (ms / 1e3), "cells": cells, "autotune": tuning,
             "roofline": {"bound": "hbm", "kernel": "k_batch_step", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{kind} (copy)",
                          "algorithmic_bytes_per_launch": byts},

@@ -371,6 +371,7 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 2D runs measurement")
+    ap.add_argument("--batch-runs", type=int, default=4096, help="number of batched 2D runs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -386,7 +387,8 @@ def main():
         out = run_gpu(args, rank, world)
         if not args.no_batch:
             nb = min(args.steps, 200)
-            out["batch2d"] = {"fp32": run_batch(nb, 3, "fp32"), "fp64": run_batch(nb, 3, "fp64")}
+            out["batch2d"] = {"fp32": run_batch(nb, 3, "fp32", nruns=args.batch_runs),
+                              "fp64": run_batch(nb, 3, "fp64", nruns=args.batch_runs)}
             out["batch2d"]["fp32_over_fp64_particle_steps"] = (
                 out["batch2d"]["fp32"]["particle_steps_per_s"] / out["batch2d"]["fp64"]["particle_steps_per_s"])
         if rank == 0 and world == 1 and not args.no_cpu_baseline:

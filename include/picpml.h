@@ -161,8 +161,9 @@ int push_deposit(picpml_ctx* ctx);
  * then field_step; particles are sorted by cell every sort_every steps. */
 int step_n(picpml_ctx* ctx, int n);
 
-/* Sorts every species by cell index (stable counting sort) and drops removed
- * particles; the live count is updated on the device. */
+/* Sorts every species by cell (counting sort on a tile-major key: 4x4x4-cell
+ * tiles, then the cell inside the tile; the order within a cell is not kept)
+ * and drops removed particles; the live count is updated on the device. */
 int pic_sort(picpml_ctx* ctx);
 
 /* Node counts of the field arrays (nx, ny, nz): N+1 per axis (ny = 1 in 2D),

@@ -37,6 +37,7 @@ cudaError_t launch_push_deposit_runs(int ppt, const Geom&, const Tables&, const 
                                      cudaStream_t);
 long long sort_scratch_words(long long ncell);
 int sort_launches(long long ncell);
+long long sort_keys(const Geom& g);
 cudaError_t static_diag_buffers(double** rho, double** out, long long* cap);
 cudaError_t launch_sort(const Geom&, int pbytes, void* pos, void* mom, long long* n_dev, long long cap,
                         unsigned* scratch, void* tmp_pos, void* tmp_mom, cudaStream_t);
@@ -233,7 +234,7 @@ int check_ready(picpml_ctx* ctx) {
 
 template <typename T>
 int do_sort(picpml_ctx* ctx) {
-  const long long ncell = (long long)ctx->g.N[0] * (ctx->g.dim == 3 ? ctx->g.N[1] : 1) * ctx->g.N[2];
+  const long long ncell = sort_keys(ctx->g);
   if (!ctx->sort_scratch) {
     ctx->sort_scratch = (unsigned*)dev_alloc(ctx, sort_scratch_words(ncell) * sizeof(unsigned));
     if (!ctx->sort_scratch) return fail(ctx, PIC_ENOMEM, "sort scratch");

@@ -1,6 +1,8 @@
-// Counting sort of one species by cell index, dropping removed particles.
-// Consecutive particles then share their cell, so the gather hits the same
-// field lines and the deposit hits the same current lines (L1/L2 locality).
+// Counting sort of one species by cell, dropping removed particles.  The key
+// is tile-major: 4x4x4-cell tiles in x,y,z order, then the cell inside the
+// tile.  Consecutive particles then share their cell, and any run of them
+// covers a compact 3D block of cells, which keeps the shared-memory field
+// and current box of the particle kernel small.
 //   1. histogram of the linear cell index (atomics),
 //   2. exclusive scan of the histogram (block scans + recursive carry),
 //   3. scatter into scratch arrays (order within a cell is not kept),
@@ -11,8 +13,13 @@ namespace picpml {
 
 namespace {
 
+// Tile-major key; tiles per axis tx, ty (2D: one tile layer in y).
 __device__ __forceinline__ long long lin_cell(const Geom& g, int cell) {
-  return (long long)cell_i(cell) + (long long)g.N[0] * ((long long)cell_j(cell) + (long long)(g.dim == 3 ? g.N[1] : 1) * cell_k(cell));
+  const int i = cell_i(cell), j = cell_j(cell), k = cell_k(cell);
+  const long long tx = (g.N[0] + 3) >> 2, ty = g.dim == 3 ? (g.N[1] + 3) >> 2 : 1;
+  const long long tile = (i >> 2) + tx * ((j >> 2) + ty * (k >> 2));
+  const int in_tile = g.dim == 3 ? (i & 3) + 4 * ((j & 3) + 4 * (k & 3)) : (i & 3) + 4 * (k & 3);
+  return tile * (g.dim == 3 ? 64 : 16) + in_tile;
 }
 
 template <int PB>
@@ -137,9 +144,15 @@ int sort_launches(long long ncell) {
 // Scratch needed: hist (ncell+1) + scan carries (< ncell/512) unsigned.
 long long sort_scratch_words(long long ncell) { return ncell + 1 + ncell / 512 + 64; }
 
+// Number of sort keys (cells padded to whole tiles).
+long long sort_keys(const Geom& g) {
+  const long long tx = (g.N[0] + 3) >> 2, ty = g.dim == 3 ? (g.N[1] + 3) >> 2 : 1, tz = (g.N[2] + 3) >> 2;
+  return tx * ty * tz * (g.dim == 3 ? 64 : 16);
+}
+
 cudaError_t launch_sort(const Geom& g, int pbytes, void* pos, void* mom, long long* n_dev, long long cap,
                         unsigned* scratch, void* tmp_pos, void* tmp_mom, cudaStream_t s) {
-  const long long ncell = (long long)g.N[0] * (g.dim == 3 ? g.N[1] : 1) * g.N[2];
+  const long long ncell = sort_keys(g);
   unsigned* hist = scratch;
   unsigned* carry = scratch + ncell + 1;
   cudaError_t e = cudaMemsetAsync(hist, 0, (ncell + 1) * sizeof(unsigned), s);

@@ -154,8 +154,11 @@ def test_sort_keeps_particles_and_drops_removed():
     assert n == int((~kill).sum())
     after = pos[:n].cpu().numpy()
     c = mom.view(torch.int32)[:n, 3].cpu().numpy().astype(np.int64)
-    lin = (c & 1023) + 38 * (((c >> 10) & 1023) + 28 * ((c >> 20) & 2047))
-    assert np.all(np.diff(lin) >= 0)
+    i, j, k = c & 1023, (c >> 10) & 1023, (c >> 20) & 2047
+    # tile-major order: 4x4x4-cell tiles, then the cell inside the tile
+    tx, ty = (38 + 3) // 4, (28 + 3) // 4
+    key = ((i >> 2) + tx * ((j >> 2) + ty * (k >> 2))) * 64 + (i & 3) + 4 * ((j & 3) + 4 * (k & 3))
+    assert np.all(np.diff(key) >= 0)
     key = lambda a: np.lexsort(a.T[::-1])
     assert np.array_equal(before[key(before)], after[key(after)])
 

@@ -85,6 +85,13 @@ def lib():
             L.ora_boris.argtypes = [dp, dp, dp, C.c_double, C.c_double, C.c_double]
             L.ora_esirkepov.argtypes = [C.c_void_p, dp, dp, C.c_double, C.c_double]
             L.ora_gather.argtypes = [C.c_void_p, dp, dp, dp]
+            ip_ = C.POINTER(C.c_int)
+            fp_ = C.POINTER(C.c_float)
+            lp_ = C.POINTER(C.c_longlong)
+            L.ora_fixed_deposit3d.argtypes = [C.c_int, C.c_longlong, ip_, fp_, ip_, fp_, fp_, C.c_double,
+                                              C.c_int, C.c_longlong, C.c_longlong, C.c_longlong, lp_, lp_, lp_]
+            L.ora_fixed_rho3d.argtypes = [C.c_int, C.c_longlong, ip_, fp_,
+                                          C.c_longlong, C.c_longlong, C.c_longlong, lp_]
             _lib = L
     return _lib
 
@@ -119,6 +126,41 @@ def boris(u, E, B, q, m, dt):
     u = _f64(u).copy()
     lib().ora_boris(_dp(u), _dp(_f64(E)), _dp(_f64(B)), q, m, dt)
     return u
+
+
+FIXED_SHAPE_BITS = 20
+FIXED_UNIT = 6.0 * 2.0 ** 24   # integer current units per elementary charge crossing a face
+
+
+def fixed_deposit3d(order, cell0, off0, cell1, off1, w, qn, nn, raw=False):
+    """Integer currents of the deterministic deposition mode (3D) for the
+    given moves: returns (Jx, Jy, Jz) int64 arrays indexed [k, j, i]; see
+    ``ora_fixed_deposit3d`` for the arithmetic and units.  cell*: (n, 3) int
+    cells (i, j, k); off*: (n, 3) float32 offsets; w: (n,) float32 weights;
+    qn: charge in units of the elementary charge."""
+    c0 = np.ascontiguousarray(cell0, dtype=np.int32).reshape(-1)
+    c1 = np.ascontiguousarray(cell1, dtype=np.int32).reshape(-1)
+    f0 = np.ascontiguousarray(off0, dtype=np.float32).reshape(-1)
+    f1 = np.ascontiguousarray(off1, dtype=np.float32).reshape(-1)
+    wf = np.ascontiguousarray(w, dtype=np.float32).reshape(-1)
+    out = [np.zeros(nn[0] * nn[1] * nn[2], dtype=np.int64) for _ in range(3)]
+    ip, fp, lp = C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_longlong)
+    lib().ora_fixed_deposit3d(int(order), len(wf), c0.ctypes.data_as(ip), f0.ctypes.data_as(fp),
+                              c1.ctypes.data_as(ip), f1.ctypes.data_as(fp), wf.ctypes.data_as(fp),
+                              float(qn), int(bool(raw)), nn[0], nn[1], nn[2],
+                              *[o.ctypes.data_as(lp) for o in out])
+    return [o.reshape(nn[2], nn[1], nn[0]) for o in out]
+
+
+def fixed_rho3d(order, cell, off, nn):
+    """Integer node charge 6 S S S (units 2^-60 of a particle's charge)."""
+    c = np.ascontiguousarray(cell, dtype=np.int32).reshape(-1)
+    f = np.ascontiguousarray(off, dtype=np.float32).reshape(-1)
+    out = np.zeros(nn[0] * nn[1] * nn[2], dtype=np.int64)
+    ip, fp, lp = C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_longlong)
+    lib().ora_fixed_rho3d(int(order), len(c) // 3, c.ctypes.data_as(ip), f.ctypes.data_as(fp),
+                          nn[0], nn[1], nn[2], out.ctypes.data_as(lp))
+    return out.reshape(nn[2], nn[1], nn[0])
 
 
 def yee_dt(d, cfl, dim):

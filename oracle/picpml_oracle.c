@@ -705,3 +705,125 @@ void ora_get_table(const ora_sim* s, int which, int axis, double* out) {
 }
 
 void ora_dims(const ora_sim* s, long* nn) { nn[0] = s->nn[0]; nn[1] = s->nn[1]; nn[2] = s->nn[2]; }
+
+/* ------------------------------------------------------------------------- */
+/* Deterministic (int64 fixed-point) deposition, 3D                         */
+/* ------------------------------------------------------------------------- */
+/* The deterministic mode takes its only floating-point decisions per
+ * particle, in a fixed order, so the integers it adds are independent of the
+ * order in which particles reach the grid:
+ *   1. the B-spline shape values of the old and new offsets, in FP32 with the
+ *      operation order below (this file is compiled without contraction), are
+ *      quantised S_int = rint(S * 2^20), except one node per axis that takes
+ *      2^20 minus the others (the node at offset f for order 1, the second
+ *      node for order 3), so every quantised shape sums to 2^20 exactly and
+ *      the decomposition conserves the integer charge exactly;
+ *   2. Esirkepov's decomposition (the charge-conserving W of Esirkepov 2001,
+ *      App. A) is then exact integer arithmetic.  Scaled by 6 so the 1/2 and
+ *      1/3 weights stay integral, for the x component
+ *        6 W_x = DSx (6 S0y S0z + 3 DSy S0z + 3 S0y DSz + 2 DSy DSz),
+ *      and acc_x(i) = sum_{i' <= i} 6 W_x(i') (likewise y, z), in units of
+ *      2^-60 of the macroparticle's charge; sum_c 6 W_c = 6 (S1 S1 S1 - S0 S0 S0)
+ *      holds exactly;
+ *   3. each nonzero acc becomes one integer contribution
+ *        val = rint( (double(acc) * (double(w) * qn)) * 2^-36 ),
+ *      qn = q / e (the charge in units of the elementary charge), i.e. units of
+ *      e / (6 * 2^24) per cell face; the sum over particles is exact.
+ * The physical current is J_x = -(e / (dy dz dt)) val_x / (6 * 2^24) before
+ * the PML damping (likewise for y, z).  raw != 0 skips step 3 and adds acc
+ * itself (for the continuity check; weights and qn are ignored).
+ * Moves: cell0/cell1 (i, j, k) and FP32 offsets off0/off1 in [0,1) per axis,
+ * three per particle; the cell changes by at most one per axis.  Output:
+ * int64 sums (+=) in the node layout i + nx (j + ny k); nodes outside the
+ * arrays are skipped. */
+
+#define FIX_QB 20
+
+static void fixed_shape(int order, float f, long long* w) {
+  const float scale = (float)(1 << FIX_QB);
+  const long long one = 1LL << FIX_QB;
+  if (order == 1) {
+    w[1] = (long long)nearbyintf(f * scale);
+    w[0] = one - w[1];
+    return;
+  }
+  const float g = 1.0f - f;
+  const float sixth = (float)(1.0 / 6.0), twothird = (float)(2.0 / 3.0);
+  const float s0 = ((g * g) * g) * sixth;
+  const float s2 = (twothird - (g * g)) + (((0.5f * g) * g) * g);
+  const float s3 = ((f * f) * f) * sixth;
+  w[0] = (long long)nearbyintf(s0 * scale);
+  w[2] = (long long)nearbyintf(s2 * scale);
+  w[3] = (long long)nearbyintf(s3 * scale);
+  w[1] = one - w[0] - w[2] - w[3];
+}
+
+/* Old shape S0 and change DS on the order+2 nodes starting at
+ * min(c0, c1) - (order == 3); returns that first node. */
+static int fixed_axis(int order, int c0, float f0, int c1, float f1, long long* S0, long long* DS) {
+  const int b = c0 < c1 ? c0 : c1;
+  long long w0[4], w1[4], S1[5] = {0, 0, 0, 0, 0};
+  fixed_shape(order, f0, w0);
+  fixed_shape(order, f1, w1);
+  for (int t = 0; t < order + 2; ++t) S0[t] = 0;
+  for (int t = 0; t <= order; ++t) {
+    S0[c0 - b + t] = w0[t];
+    S1[c1 - b + t] = w1[t];
+  }
+  for (int t = 0; t < order + 2; ++t) DS[t] = S1[t] - S0[t];
+  return b - (order == 3 ? 1 : 0);
+}
+
+void ora_fixed_deposit3d(int order, long long n, const int* cell0, const float* off0, const int* cell1,
+                         const float* off1, const float* w, double qn, int raw, long long nx, long long ny,
+                         long long nz, long long* Jx, long long* Jy, long long* Jz) {
+  const int W = order + 2;
+  const double down = ldexp(1.0, -36);
+  for (long long p = 0; p < n; ++p) {
+    long long S0[3][5], DS[3][5];
+    int lo[3];
+    for (int a = 0; a < 3; ++a)
+      lo[a] = fixed_axis(order, cell0[3 * p + a], off0[3 * p + a], cell1[3 * p + a], off1[3 * p + a], S0[a], DS[a]);
+    const double wq = (double)w[p] * qn;
+    for (int c = 0; c < 3; ++c) {
+      /* component c: prefix sums along axis c; the two transverse axes b < d */
+      const int b = c == 0 ? 1 : 0, d = c == 2 ? 1 : 2;
+      long long* J = c == 0 ? Jx : (c == 1 ? Jy : Jz);
+      for (int tb = 0; tb < W; ++tb)
+        for (int td = 0; td < W; ++td) {
+          const long long T = 6 * S0[b][tb] * S0[d][td] + 3 * DS[b][tb] * S0[d][td] +
+                              3 * S0[b][tb] * DS[d][td] + 2 * DS[b][tb] * DS[d][td];
+          long long acc = 0;
+          for (int ta = 0; ta < W - 1; ++ta) {
+            acc += DS[c][ta] * T;
+            if (acc == 0) continue;
+            long long idx[3];
+            idx[c] = lo[c] + ta;
+            idx[b] = lo[b] + tb;
+            idx[d] = lo[d] + td;
+            if (idx[0] < 0 || idx[0] >= nx || idx[1] < 0 || idx[1] >= ny || idx[2] < 0 || idx[2] >= nz) continue;
+            const long long v = raw ? acc : llrint(((double)acc * wq) * down);
+            J[idx[0] + nx * (idx[1] + ny * idx[2])] += v;
+          }
+        }
+    }
+  }
+}
+
+/* Integer node charge 6 S_int,x S_int,y S_int,z (units 2^-60 of the particle
+ * charge): the quantity whose change the raw integer currents carry exactly. */
+void ora_fixed_rho3d(int order, long long n, const int* cell, const float* off, long long nx, long long ny,
+                     long long nz, long long* rho) {
+  const int lo = order == 3 ? 1 : 0;
+  for (long long p = 0; p < n; ++p) {
+    long long w[3][4];
+    for (int a = 0; a < 3; ++a) fixed_shape(order, off[3 * p + a], w[a]);
+    for (int tk = 0; tk <= order; ++tk)
+      for (int tj = 0; tj <= order; ++tj)
+        for (int ti = 0; ti <= order; ++ti) {
+          const long long i = cell[3 * p] - lo + ti, j = cell[3 * p + 1] - lo + tj, k = cell[3 * p + 2] - lo + tk;
+          if (i < 0 || i >= nx || j < 0 || j >= ny || k < 0 || k >= nz) continue;
+          rho[i + nx * (j + ny * k)] += 6 * w[0][ti] * w[1][tj] * w[2][tk];
+        }
+  }
+}

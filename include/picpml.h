@@ -58,7 +58,8 @@ typedef enum {
   PIC_FP32 = 0,         /* FP32 fields, momenta and offsets; FP64 PML splits */
   PIC_FP64 = 1,         /* everything FP64 (the plain FP64 form) */
   PIC_FP32_FIXED64 = 2  /* as PIC_FP32, current accumulated in int64 fixed
-                           point: deterministic, bit-identical J */
+                           point: deterministic, bit-identical J (3D only;
+                           see pic_get_current_fixed) */
 } pic_prec;
 
 typedef enum {
@@ -145,6 +146,33 @@ int push(picpml_ctx* ctx);
  * (Eq. MaxwellE source term, Eq. alpha).  Accumulates into J, which the next
  * field_step() consumes and zeroes. */
 int deposit(picpml_ctx* ctx);
+
+/* Sets x^n, the positions deposit() moves from (what push() saves), for a
+ * species: src is a caller-owned device buffer of `capacity` records, float4
+ * (ox, oy, oz, cell bits) (PIC_FP64: four doubles, cell as int64 bits; a cell
+ * of -1 deposits nothing).  With it, deposit() deposits any prescribed moves
+ * from src to the species' current positions (each move shorter than one
+ * cell per axis). */
+int pic_set_old_positions(picpml_ctx* ctx, int sid, const void* src);
+
+/* PIC_FP32_FIXED64 only (else PIC_ESTATE): copies the int64 current sums of
+ * the last deposit() / push_deposit() / step into dst (caller-owned device
+ * buffer of nx*ny*nz int64, index i + nx (j + ny k)), before the PML damping.
+ * Deterministic mode, per particle and in a fixed operation order:
+ *   shape values of the old and new offsets (B-spline of Sec. II.A's PIC,
+ *   order 1 or 3) in FP32, quantised to 2^-20, one node per axis taking the
+ *   remainder so every shape sums to 1 exactly;
+ *   Esirkepov's decomposition (App. A) in exact integers, scaled by 6:
+ *   6 W_x = DSx (6 S0y S0z + 3 DSy S0z + 3 S0y DSz + 2 DSy DSz), prefix sums
+ *   along x (y, z likewise), so continuity holds exactly in integers;
+ *   per node one rounding, rint(acc * (w q/e) * 2^-36), added with int64
+ *   atomics (order-independent).
+ * Units: one integer is e / (6 * 2^24) of charge crossing the component's
+ * cell face, i.e. J_x = -(e / (dy dz dt)) Jq_x / (6 * 2^24) in A/m^2 before
+ * damping.  The deposit then writes J = alpha_c * that (Eq. alpha) over the
+ * whole grid (replacing, not adding to, J).  Limits: |w q/e| <= 2^32 per
+ * particle and |Jq| <= 2^62 per node, else PIC_EOVERFLOW at pic_sync. */
+int pic_get_current_fixed(picpml_ctx* ctx, int comp, long long* dst);
 
 /* Field update: E^{n+1} = E^n + dt (c^2 curl B^{n+1/2} - J/eps0), then
  * B^{n+3/2} = B^{n+1/2} - dt curl E^{n+1}; split-field PML components in

@@ -72,6 +72,8 @@ SIGNATURES = {
     "pic_get_field": (C.c_int, [VP, C.c_int, VP, C.c_int]),
     "pic_set_field": (C.c_int, [VP, C.c_int, VP, C.c_int]),
     "pic_set_prescribed": (C.c_int, [VP, C.c_int]),
+    "pic_set_old_positions": (C.c_int, [VP, C.c_int, VP]),
+    "pic_get_current_fixed": (C.c_int, [VP, C.c_int, VP]),
     "pic_num_particles": (C.c_int, [VP, C.c_int, C.POINTER(C.c_longlong)]),
     "pic_diag": (C.c_int, [VP, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "pic_diag_static": (C.c_int, [VP, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),

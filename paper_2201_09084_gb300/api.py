@@ -127,6 +127,35 @@ class Sim:
     def set_prescribed(self, flag=True):
         self._call(self.lib.pic_set_prescribed, int(bool(flag)))
 
+    def set_old_positions(self, sid, cell, off):
+        """Sets x^n (what push() saves) of species sid from host (n, 3) cells
+        and offsets, so deposit() deposits the moves to the current positions.
+        Returns the device buffer, which must live until the deposit ran."""
+        pos, _ = self.species[sid]
+        cap = pos.shape[0]
+        dt = torch.float64 if self.prec == "fp64" else torch.float32
+        n = len(off)
+        cell = np.asarray(cell, dtype=np.int64)
+        packed = np.full(cap, -1, dtype=np.int64)
+        packed[:n] = cell[:, 0] | (cell[:, 1] << 10) | (cell[:, 2] << 20)
+        buf = torch.zeros((cap, 4), dtype=dt)
+        buf[:n, :3] = torch.from_numpy(np.asarray(off)).to(dt)
+        if dt == torch.float32:
+            buf.view(torch.int32)[:, 3] = torch.from_numpy(packed.astype(np.int32))
+        else:
+            buf.view(torch.int64)[:, 3] = torch.from_numpy(packed)
+        buf = buf.to("cuda")
+        self._call(self.lib.pic_set_old_positions, int(sid), C.c_void_p(buf.data_ptr()))
+        self._keep = buf
+        return buf
+
+    def current_fixed(self, comp):
+        """int64 current sums of the last deposit (fixed64 contexts), as a
+        device tensor indexed [k, j, i]."""
+        out = torch.empty(self.nn[2] * self.nn[1] * self.nn[0], dtype=torch.int64, device="cuda")
+        self._call(self.lib.pic_get_current_fixed, int(comp), C.c_void_p(out.data_ptr()))
+        return out.view(self.nn[2], self.nn[1], self.nn[0])
+
     # stepping ---------------------------------------------------------
     def push(self):
         self._call(self.lib.push)

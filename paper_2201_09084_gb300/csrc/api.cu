@@ -35,6 +35,8 @@ template <typename T>
 cudaError_t launch_push_deposit_runs(int ppt, const Geom&, const Tables&, const FieldPtrs<T>&, const SpeciesPtrs<T>&,
                                      int prescribed, unsigned* status, unsigned long long* pushed, int nsm,
                                      cudaStream_t);
+cudaError_t launch_fixed_flush(const Geom&, const Tables&, const FieldPtrs<float>&, const double K[3], unsigned*,
+                               cudaStream_t);
 long long sort_scratch_words(long long ncell);
 int sort_launches(long long ncell);
 long long sort_keys(const Geom& g);
@@ -87,6 +89,7 @@ struct Species {
   void* tmp_pos = nullptr;   // sort scratch, allocated at the first sort
   void* tmp_mom = nullptr;
   double ke = 0, cj[3] = {0, 0, 0}, cjy2d = 0;
+  double qn = 0;             // charge in elementary charges (deterministic mode)
 };
 
 thread_local std::string g_init_error;
@@ -121,6 +124,7 @@ struct picpml_ctx {
   int elem() const { return gd.prec == PIC_FP64 ? 8 : 4; }
   int pbytes() const { return gd.prec == PIC_FP64 ? 32 : 16; }
   int split_ff() const { return gd.prec != PIC_FP64 && !gd.split_fp64; }
+  bool fixed() const { return gd.prec == PIC_FP32_FIXED64; }
 };
 
 namespace {
@@ -194,6 +198,7 @@ SpeciesPtrs<T> species_ptrs(picpml_ctx* ctx, Species& s) {
   for (int a = 0; a < 3; ++a) p.cj[a] = (T)s.cj[a];
   p.cjy2d = (T)s.cjy2d;
   p.immobile = s.desc.immobile;
+  p.qn = s.qn;
   p.save_pos = reinterpret_cast<float4*>(s.save);
   p.save_mom = nullptr;
   return p;
@@ -201,16 +206,29 @@ SpeciesPtrs<T> species_ptrs(picpml_ctx* ctx, Species& s) {
 
 template <typename T>
 int run_particles(picpml_ctx* ctx, int mode) {
+  const bool fixed = ctx->fixed() && mode != 0;
+  if (fixed) {
+    // the integer sums of the previous deposit stay readable until here
+    const size_t jb = (size_t)ctx->g.size * sizeof(long long);
+    for (int c = 0; c < 3; ++c) CK(cudaMemsetAsync(ctx->ff.Jq[c], 0, jb, ctx->stream));
+  }
   for (auto& s : ctx->sp) {
     if (s.desc.immobile && mode != 0) continue;
     SpeciesPtrs<T> p = species_ptrs<T>(ctx, s);
     if (s.desc.capacity <= 0) continue;
-    if (mode == 2 && ctx->gd.shape_order == 1 && ctx->use_runs)
+    if (mode == 2 && ctx->gd.shape_order == 1 && ctx->use_runs && !ctx->fixed())
       CK(launch_push_deposit_runs<T>(ctx->ppt, ctx->g, ctx->tb, fields<T>(ctx), p, ctx->prescribed, ctx->status,
                                      ctx->pushed, ctx->nsm, ctx->stream));
     else
       CK(launch_particles<T>(mode, ctx->gd.shape_order, ctx->g, ctx->tb, fields<T>(ctx), p, ctx->prescribed,
                              ctx->status, ctx->pushed, ctx->nsm, ctx->stream));
+    ctx->launches += 1;
+  }
+  if (fixed) {
+    const double* d = ctx->gd.d;
+    const double K[3] = {-kQe / (kEps0 * d[1] * d[2]) / kFixUnit, -kQe / (kEps0 * d[0] * d[2]) / kFixUnit,
+                         -kQe / (kEps0 * d[0] * d[1]) / kFixUnit};
+    CK(launch_fixed_flush(ctx->g, ctx->tb, ctx->ff, K, ctx->status, ctx->stream));
     ctx->launches += 1;
   }
   return PIC_OK;
@@ -263,7 +281,8 @@ int pic_init(picpml_ctx** out, const pic_grid_desc* g, void* stream) {
   if (g->shape_order != 1 && g->shape_order != 3) return fail(nullptr, PIC_EINVAL, "shape_order must be 1 or 3");
   if (g->prec != PIC_FP32 && g->prec != PIC_FP64 && g->prec != PIC_FP32_FIXED64)
     return fail(nullptr, PIC_EINVAL, "bad prec");
-  if (g->prec == PIC_FP32_FIXED64) return fail(nullptr, PIC_ENOTIMPL, "fixed-point deposition is not built yet");
+  if (g->prec == PIC_FP32_FIXED64 && g->dim != 3)
+    return fail(nullptr, PIC_ENOTIMPL, "fixed-point deposition is built for 3D grids only");
   for (int a = 0; a < 3; ++a) {
     if (g->dim == 2 && a == 1) continue;
     if (g->n[a] < 1 || !(g->d[a] > 0)) return fail(nullptr, PIC_EINVAL, "cells and cell sizes must be positive");
@@ -419,6 +438,12 @@ int pml_init(picpml_ctx* ctx, const pml_desc* p) {
       ctx->ff.Es[c][h] = ctx->fd.Es[c][h] = e;
       ctx->ff.Bs[c][h] = ctx->fd.Bs[c][h] = b;
     }
+  if (ctx->fixed()) {
+    long long* jq = (long long*)dev_alloc(ctx, (size_t)g.size * 3 * sizeof(long long));
+    if (!jq) return fail(ctx, PIC_ENOMEM, "fixed-point current");
+    CK(cudaMemsetAsync(jq, 0, (size_t)g.size * 3 * sizeof(long long), ctx->stream));
+    for (int c = 0; c < 3; ++c) ctx->ff.Jq[c] = jq + (size_t)c * g.size;
+  }
   ctx->status = (unsigned*)dev_alloc(ctx, 64);
   ctx->pushed = (unsigned long long*)(ctx->status + 8);
   ctx->diag = (double*)dev_alloc(ctx, 8 * sizeof(double));
@@ -447,6 +472,7 @@ int pic_add_species(picpml_ctx* ctx, const pic_species* s, int* sid) {
   const pic_grid_desc& gd = ctx->gd;
   const double q = s->q, dt = ctx->dt;
   sp.ke = q * dt / (2.0 * s->m * kC);
+  sp.qn = q / kQe;
   if (gd.dim == 3) {
     sp.cj[0] = -q / (kEps0 * gd.d[1] * gd.d[2]);
     sp.cj[1] = -q / (kEps0 * gd.d[0] * gd.d[2]);
@@ -574,7 +600,7 @@ int pic_autotune(picpml_ctx* ctx, int steps, int* ppt, int* kz) {
   };
   const long long launches0 = ctx->launches;
   int best_p = ctx->ppt, best_k = ctx->kz;
-  if (ctx->gd.shape_order == 1 && !f64) {
+  if (ctx->gd.shape_order == 1 && !f64 && !ctx->fixed()) {
     float best = 1e30f;
     for (int p : {4, 8}) {
       ctx->ppt = p;
@@ -637,6 +663,29 @@ int step_n(picpml_ctx* ctx, int n) {
     if (r) return r;
     ctx->steps_done++;
   }
+  return PIC_OK;
+}
+
+int pic_set_old_positions(picpml_ctx* ctx, int sid, const void* src) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (sid < 0 || sid >= (int)ctx->sp.size() || !src) return fail(ctx, PIC_EINVAL, "bad species id or source");
+  Species& s = ctx->sp[sid];
+  if (s.desc.capacity > 0)
+    CK(cudaMemcpyAsync(s.save, src, (size_t)s.desc.capacity * ctx->pbytes(), cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+  return PIC_OK;
+}
+
+int pic_get_current_fixed(picpml_ctx* ctx, int comp, long long* dst) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (!ctx->fixed()) return fail(ctx, PIC_ESTATE, "the context does not use fixed-point deposition");
+  if (comp < 0 || comp > 2 || !dst) return fail(ctx, PIC_EINVAL, "bad component or destination");
+  const Geom& g = ctx->g;
+  CK(cudaMemcpy2DAsync(dst, (size_t)g.nn[0] * sizeof(long long), ctx->ff.Jq[comp], (size_t)g.px * sizeof(long long),
+                       (size_t)g.nn[0] * sizeof(long long), (size_t)g.nn[1] * g.nn[2], cudaMemcpyDeviceToDevice,
+                       ctx->stream));
   return PIC_OK;
 }
 

@@ -385,6 +385,101 @@ __device__ __forceinline__ void deposit_one(const Geom& g, const Tables& tb, con
 }
 
 
+// ---------------------------------------------------------------------------
+// Deterministic deposition (3D): the only floating-point decisions are per
+// particle and in a fixed operation order (explicitly rounded intrinsics, no
+// contraction), so the int64 sums do not depend on the order in which
+// particles reach the grid.
+//   1. Shape values of the old and new offsets in FP32, quantised to
+//      2^-20: S = rint(s 2^20); one node per axis (the node at offset f for
+//      order 1, the second node for order 3) takes 2^20 minus the others so
+//      every shape sums to 2^20 exactly.
+//   2. Esirkepov's decomposition in exact integers, scaled by 6:
+//      6 W_x = DSx (6 S0y S0z + 3 DSy S0z + 3 S0y DSz + 2 DSy DSz), prefix
+//      sums along x (likewise y, z); the continuity equation then holds
+//      exactly in integers.
+//   3. One rounding per node: val = rint((double(acc) * (w q/e)) 2^-36),
+//      added with an int64 atomic.
+// ---------------------------------------------------------------------------
+template <int ORDER>
+__device__ __forceinline__ void fixed_shape(float f, long long* w) {
+  const float scale = (float)(1 << kFixShapeBits);
+  const long long one = 1LL << kFixShapeBits;
+  if (ORDER == 1) {
+    w[1] = __float2ll_rn(__fmul_rn(f, scale));
+    w[0] = one - w[1];
+  } else {
+    const float g = __fsub_rn(1.0f, f);
+    const float sixth = (float)(1.0 / 6.0), twothird = (float)(2.0 / 3.0);
+    const float s0 = __fmul_rn(__fmul_rn(__fmul_rn(g, g), g), sixth);
+    const float s2 = __fadd_rn(__fsub_rn(twothird, __fmul_rn(g, g)), __fmul_rn(__fmul_rn(__fmul_rn(0.5f, g), g), g));
+    const float s3 = __fmul_rn(__fmul_rn(__fmul_rn(f, f), f), sixth);
+    w[0] = __float2ll_rn(__fmul_rn(s0, scale));
+    w[2] = __float2ll_rn(__fmul_rn(s2, scale));
+    w[3] = __float2ll_rn(__fmul_rn(s3, scale));
+    w[1] = one - w[0] - w[2] - w[3];
+  }
+}
+
+template <int ORDER>
+__device__ __forceinline__ int fixed_axis(int c0, float f0, int c1, float f1, long long* S0, long long* DS) {
+  constexpr int W = ORDER + 2;
+  const int b = min(c0, c1);
+  long long w0[ORDER + 1], w1[ORDER + 1];
+  fixed_shape<ORDER>(f0, w0);
+  fixed_shape<ORDER>(f1, w1);
+  const bool s0 = c0 != b, s1 = c1 != b;
+#pragma unroll
+  for (int t = 0; t < W; ++t) {
+    const long long a = s0 ? (t >= 1 ? w0[t - 1] : 0) : (t <= ORDER ? w0[t] : 0);
+    const long long c = s1 ? (t >= 1 ? w1[t - 1] : 0) : (t <= ORDER ? w1[t] : 0);
+    S0[t] = a;
+    DS[t] = c - a;
+  }
+  return b - (ORDER == 3 ? 1 : 0);
+}
+
+template <int ORDER>
+__device__ __forceinline__ void deposit_fixed(const Geom& g, const FieldPtrs<float>& f, double qn, const int c0[3],
+                                              const float o0[3], const int c1[3], const float o1[3], float w,
+                                              unsigned* status) {
+  constexpr int W = ORDER + 2;
+  long long S0[3][W], DS[3][W];
+  int lo[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) lo[a] = fixed_axis<ORDER>(c0[a], o0[a], c1[a], o1[a], S0[a], DS[a]);
+  const double wq = __dmul_rn((double)w, qn);
+  if (!(fabs(wq) <= kFixMaxWq)) {
+    atomicOr(status, ST_FIXED_OVERFLOW);
+    return;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int b = c == 0 ? 1 : 0, d = c == 2 ? 1 : 2;   // transverse axes, b < d
+#pragma unroll
+    for (int tb = 0; tb < W; ++tb)
+#pragma unroll
+      for (int td = 0; td < W; ++td) {
+        const long long T = 6 * S0[b][tb] * S0[d][td] + 3 * DS[b][tb] * S0[d][td] + 3 * S0[b][tb] * DS[d][td] +
+                            2 * DS[b][tb] * DS[d][td];
+        if (T == 0) continue;
+        long long acc = 0;
+#pragma unroll
+        for (int ta = 0; ta < W - 1; ++ta) {
+          acc += DS[c][ta] * T;
+          if (acc == 0) continue;
+          int idx[3];
+          idx[c] = lo[c] + ta;
+          idx[b] = lo[b] + tb;
+          idx[d] = lo[d] + td;
+          const long long v = __double2ll_rn(__dmul_rn(__dmul_rn(__ll2double_rn(acc), wq), kFixDown));
+          atomicAdd(reinterpret_cast<unsigned long long*>(f.Jq[c] + g.idx(idx[0], idx[1], idx[2])),
+                    static_cast<unsigned long long>(v));
+        }
+      }
+  }
+}
+
 // Deposit of one 2D particle of a batched run (same arithmetic).
 template <int ORDER, typename T>
 __device__ __forceinline__ void deposit_run_particle(const Geom& g, const Tables& tb, const FieldPtrs<T>& f,

@@ -17,8 +17,9 @@ namespace {
 using namespace pc;
 
 // MODE 0: push only (saves x^n); MODE 1: deposit only (from saved x^n);
-// MODE 2: fused push + deposit.
-template <int ORDER, int DIM, typename T, int MODE>
+// MODE 2: fused push + deposit.  FIX: deterministic int64 deposition (3D
+// FP32 only) instead of the floating-point one.
+template <int ORDER, int DIM, typename T, int MODE, bool FIX = false>
 __global__ void __launch_bounds__(256) k_particles(Geom g, Tables tb, FieldPtrs<T> f, SpeciesPtrs<T> sp,
                                                    int prescribed, unsigned* status,
                                                    unsigned long long* pushed_total) {
@@ -36,8 +37,12 @@ __global__ void __launch_bounds__(256) k_particles(Geom g, Tables tb, FieldPtrs<
       if (cell < 0 || cell0 < 0) continue;
       const int c0[3] = {cell_i(cell0), cell_j(cell0), cell_k(cell0)};
       const int c1[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
-      const T g2 = sqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-      deposit_one<ORDER, DIM, T>(g, tb, f, sp, c0, o0, c1, o, w, u[1] / g2);
+      if constexpr (FIX) {
+        deposit_fixed<ORDER>(g, f, sp.qn, c0, o0, c1, o, w, status);
+      } else {
+        const T g2 = sqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        deposit_one<ORDER, DIM, T>(g, tb, f, sp, c0, o0, c1, o, w, u[1] / g2);
+      }
       continue;
     }
     if (cell < 0) {
@@ -112,7 +117,11 @@ __global__ void __launch_bounds__(256) k_particles(Geom g, Tables tb, FieldPtrs<
     const int cell1 = out ? -1 : pack_cell(c1[0], c1[1], c1[2]);
     if (MODE == 0) PIO<T>::save(sp.save_pos, p, o, out ? -1 : cell);
     PIO<T>::store(sp.pos, sp.mom, p, out ? o : o1, w, u, cell1);
-    if (MODE == 2 && !out) deposit_one<ORDER, DIM, T>(g, tb, f, sp, c, o, c1, o1, w, u[1] * ig);
+    if constexpr (MODE == 2 && FIX) {
+      if (!out) deposit_fixed<ORDER>(g, f, sp.qn, c, o, c1, o1, w, status);
+    } else if (MODE == 2 && !out) {
+      deposit_one<ORDER, DIM, T>(g, tb, f, sp, c, o, c1, o1, w, u[1] * ig);
+    }
   }
   // particles pushed this launch: warp sum, one atomic per warp
   if (MODE != 1 && pushed_total) {
@@ -121,7 +130,7 @@ __global__ void __launch_bounds__(256) k_particles(Geom g, Tables tb, FieldPtrs<
   }
 }
 
-template <int ORDER, int DIM, typename T>
+template <int ORDER, int DIM, typename T, bool FIX = false>
 cudaError_t launch_mode(int mode, const Geom& g, const Tables& tb, const FieldPtrs<T>& f,
                         const SpeciesPtrs<T>& sp, int prescribed, unsigned* status,
                         unsigned long long* pushed, int nsm, cudaStream_t s) {
@@ -135,10 +144,37 @@ cudaError_t launch_mode(int mode, const Geom& g, const Tables& tb, const FieldPt
   if (mode == 0)
     k_particles<ORDER, DIM, T, 0><<<blocks, threads, 0, s>>>(g, tb, f, sp, prescribed, status, pushed);
   else if (mode == 1)
-    k_particles<ORDER, DIM, T, 1><<<blocks, threads, 0, s>>>(g, tb, f, sp, prescribed, status, pushed);
+    k_particles<ORDER, DIM, T, 1, FIX><<<blocks, threads, 0, s>>>(g, tb, f, sp, prescribed, status, pushed);
   else
-    k_particles<ORDER, DIM, T, 2><<<blocks, threads, 0, s>>>(g, tb, f, sp, prescribed, status, pushed);
+    k_particles<ORDER, DIM, T, 2, FIX><<<blocks, threads, 0, s>>>(g, tb, f, sp, prescribed, status, pushed);
   return cudaGetLastError();
+}
+
+// Deterministic mode, after all species have deposited: the damped current
+// J'_c = alpha_c K_c Jq_c with K_c = -e / (eps0 d_a d_b) / (6 2^24) (a, b the
+// axes transverse to c) and alpha_c at the component's staggered location
+// (Eq. alpha, Sec. II.B), one thread per node; J' is overwritten, the integer
+// sums are kept until the next deposit clears them.  |Jq| above 2^62 is
+// reported as an overflow.
+__global__ void __launch_bounds__(256) k_fixed_flush(Geom g, Tables tb, FieldPtrs<float> f, double K0, double K1,
+                                                     double K2, unsigned* status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y, k = blockIdx.z;
+  if (i >= g.nn[0]) return;
+  const long long id = g.idx(i, j, k);
+  const double anx = tb.al_nd[0][i], acx = tb.al_cd[0][i];
+  const double any = tb.al_nd[1][j], acy = tb.al_cd[1][j];
+  const double anz = tb.al_nd[2][k], acz = tb.al_cd[2][k];
+  const double al[3] = {acx * any * anz, anx * acy * anz, anx * any * acz};
+  const double K[3] = {K0, K1, K2};
+  bool big = false;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const long long v = f.Jq[c][id];
+    big |= v > (1LL << 62) || v < -(1LL << 62);
+    f.J[c][id] = (float)(((double)v * K[c]) * al[c]);
+  }
+  if (big) atomicOr(status, ST_FIXED_OVERFLOW);
 }
 
 }  // namespace
@@ -147,12 +183,25 @@ template <typename T>
 cudaError_t launch_particles(int mode, int order, const Geom& g, const Tables& tb, const FieldPtrs<T>& f,
                              const SpeciesPtrs<T>& sp, int prescribed, unsigned* status,
                              unsigned long long* pushed, int nsm, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (f.Jq[0] && g.dim == 3)
+      return order == 1 ? launch_mode<1, 3, T, true>(mode, g, tb, f, sp, prescribed, status, pushed, nsm, s)
+                        : launch_mode<3, 3, T, true>(mode, g, tb, f, sp, prescribed, status, pushed, nsm, s);
+  }
   if (order == 1) {
     return g.dim == 3 ? launch_mode<1, 3, T>(mode, g, tb, f, sp, prescribed, status, pushed, nsm, s)
                       : launch_mode<1, 2, T>(mode, g, tb, f, sp, prescribed, status, pushed, nsm, s);
   }
   return g.dim == 3 ? launch_mode<3, 3, T>(mode, g, tb, f, sp, prescribed, status, pushed, nsm, s)
                     : launch_mode<3, 2, T>(mode, g, tb, f, sp, prescribed, status, pushed, nsm, s);
+}
+
+cudaError_t launch_fixed_flush(const Geom& g, const Tables& tb, const FieldPtrs<float>& f, const double K[3],
+                               unsigned* status, cudaStream_t s) {
+  if (g.dim != 3 || !f.Jq[0]) return cudaErrorInvalidValue;
+  dim3 blk(128, 1, 1), grd((g.nn[0] + 127) / 128, g.nn[1], g.nn[2]);
+  k_fixed_flush<<<grd, blk, 0, s>>>(g, tb, f, K[0], K[1], K[2], status);
+  return cudaGetLastError();
 }
 
 template cudaError_t launch_particles<float>(int, int, const Geom&, const Tables&, const FieldPtrs<float>&,

@@ -74,6 +74,7 @@ struct FieldPtrs {
   T* J[3];    // J' (dt/eps0 units)
   double* Es[3][2];
   double* Bs[3][2];
+  long long* Jq[3];   // deterministic mode: int64 current sums (else null)
 };
 
 // Particle data of one species for a kernel.
@@ -87,6 +88,7 @@ struct SpeciesPtrs {
   T cj[3];                  // J' per unit weight: -q/(eps0 d_b d_c) (3D)
   T cjy2d;                  // 2D out-of-plane: q dt c /(eps0 dx dz Ly)
   int immobile;
+  double qn;                // charge in elementary charges (deterministic mode)
   float4* save_pos;         // scratch of push(): x^n (FP32 layout)
   float4* save_mom;
 };
@@ -95,6 +97,16 @@ struct SpeciesPtrs {
 struct __align__(32) dbl4 {
   double x, y, z, w;
 };
+
+// Deterministic deposition: shape quantum 2^-kFixShapeBits; one integer
+// current unit is e / (6 * 2^24) of charge crossing a cell face, reached from
+// the exact integer Esirkepov sums (units 2^-60 of the particle charge, times
+// 6) by the factor w q/e 2^-36.
+constexpr int kFixShapeBits = 20;
+constexpr double kFixDown = 1.0 / 68719476736.0;   // 2^-36
+constexpr double kFixUnit = 6.0 * 16777216.0;      // 6 * 2^24
+constexpr double kFixMaxWq = 4294967296.0;         // |w q/e| above 2^32 is refused
+constexpr double kQe = 1.602176634e-19;
 
 // Device status word bits.
 enum : unsigned { ST_BAD_PARTICLE = 1u, ST_FIXED_OVERFLOW = 2u };

@@ -109,6 +109,22 @@ def random_particles(dim, n_particles, lo, hi, u_rms=0.5, seed=SEED_BASE + 7, q=
     return [dict(out, q=q, m=m, immobile=False)]
 
 
+def random_moves(n, lo, hi, max_step=0.95, seed=SEED_BASE + 9, w_range=(0.5, 4.0)):
+    """Prescribed one-step moves for depositing in isolation: start positions
+    uniform in [lo, hi) (cells, 3D), displacements uniform in +-max_step per
+    axis, weights uniform in w_range.  Returns (cell0, off0, cell1, off1, w)
+    with int32 cells and FP32 offsets / weights."""
+    rng = np.random.default_rng(seed)
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    X0 = lo + rng.random((n, 3)) * (hi - lo)
+    c0, f0 = split_position(X0)
+    X1 = absolute(c0, f0) + rng.uniform(-max_step, max_step, (n, 3))
+    c1, f1 = split_position(X1)
+    w = rng.uniform(w_range[0], w_range[1], n).astype(np.float32)
+    return c0, f0, c1, f1, w
+
+
 def batched_runs(nruns, size_range=(64, 256), pml_range=(8, 24), theta_max_deg=80.0,
                  gamma_range=(1.1, 100.0), seed=SEED_BASE + 5, q=-Q_E, m=M_E):
     """Independent 2D single-particle runs (the angle / gamma sweeps of the

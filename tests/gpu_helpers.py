@@ -10,8 +10,10 @@ from paper_2201_09084_gb300 import inputs as I
 # the oracle (E and cB share units; Eq. error weighs them the same way), and
 # for the currents by max |J| over the three components.  FP32 kernels: 1e-5
 # (the target accuracy of the FP32 form against the FP64 oracle); FP64
-# kernels: 1e-11 (only summation orders differ from the oracle).
-TOL = {"fp32": 1e-5, "fp64": 1e-11}
+# kernels: 1e-11 (only summation orders differ from the oracle).  The
+# deterministic int64 deposition carries the FP32 target (its shape quantum
+# 2^-20 moves a current by about 1e-6 of its scale).
+TOL = {"fp32": 1e-5, "fp64": 1e-11, "fixed64": 1e-5}
 
 
 def make_pair(dim, nphys, pml, d, parts, order=1, prec="fp32", alpha_mode="damped", cfl=0.99,

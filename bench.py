@@ -44,10 +44,10 @@ def beam_center():
     return (PML[0] + NPHYS[0] / 2 + 0.3, PML[2] + NPHYS[1] / 2 + 0.1, PML[4] + NPHYS[2] - 24 + 0.2)
 
 
-def workload(order, theta, prec):
-    return {"workload": f"3D beam exiting +z PML: {NPHYS[0]}^3 + {PML[0]}-cell PML, {NPART} macroparticles, "
+def workload(order, theta, prec, npart=NPART):
+    return {"workload": f"3D beam exiting +z PML: {NPHYS[0]}^3 + {PML[0]}-cell PML, {npart} macroparticles, "
                         f"order {order}, theta {theta} deg, {prec} fields + fp64 PML splits",
-            "grid": [n + 2 * p for n, p in zip(NPHYS, PML[::2])], "particles": NPART,
+            "grid": [n + 2 * p for n, p in zip(NPHYS, PML[::2])], "particles": npart,
             "shape_order": order, "theta_deg": theta, "alpha": "damped (Eq. alpha, v=c)",
             "sort_every": SORT_EVERY, "l2": "working set > L2 (particles 134 MB + fields ~550 MB)",
             "data": "synthetic"}
@@ -146,15 +146,21 @@ def run_gpu(args, rank, world):
         B.build()
     if world > 1:
         torch.distributed.barrier()
-    parts = I.beam(3, NPART, NPHYS, PML, beam_center(), theta_deg=args.theta)[0]
+    npart = args.particles
+    parts = I.beam(3, npart, NPHYS, PML, beam_center(), theta_deg=args.theta)[0]
     stream = torch.cuda.current_stream()
     sim = Sim(3, NPHYS, D, PML, cfl=0.99, order=args.order, prec=args.prec, alpha_mode="damped",
               sort_every=0, stream=stream)
     pos, mom = pack_particles(parts["cell"], parts["off"], parts["u"], parts["w"], args.prec)
-    sim.add_species(pos, mom, NPART, parts["q"], parts["m"])
+    sim.add_species(pos, mom, npart, parts["q"], parts["m"])
     pos0, mom0 = pos.clone(), mom.clone()
     sim.sort()
-    tuning = sim.autotune(steps=3)   # launch shapes, from a restored snapshot
+    if args.tuning:
+        p_, k_ = (int(x) for x in args.tuning.split(","))
+        sim.set_tuning(p_, k_)
+        tuning = {"particles_per_thread": p_, "z_nodes_per_thread": k_, "source": "--tuning"}
+    else:
+        tuning = sim.autotune(steps=3)   # launch shapes, from a restored snapshot
 
     def one_step(i, ev=None):
         if i % SORT_EVERY == 0:
@@ -204,10 +210,10 @@ def run_gpu(args, rank, world):
     hmom = mom0.cpu().pin_memory()
     sim2 = Sim(3, NPHYS, D, PML, cfl=0.99, order=args.order, prec=args.prec, alpha_mode="damped",
                sort_every=SORT_EVERY, stream=stream)
-    sim2.set_tuning(**tuning)   # the launch shapes chosen for the timed run
+    sim2.set_tuning(tuning["particles_per_thread"], tuning["z_nodes_per_thread"])
     dpos = torch.empty_like(pos0)
     dmom = torch.empty_like(mom0)
-    sim2.add_species(dpos, dmom, NPART, parts["q"], parts["m"])
+    sim2.add_species(dpos, dmom, npart, parts["q"], parts["m"])
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -246,14 +252,14 @@ def run_gpu(args, rank, world):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.prec == "fp32" else "f64",
         "data": "synthetic",
-        "config": dict(workload(args.order, args.theta, args.prec), parallelism=f"replicas x{world}"),
+        "config": dict(workload(args.order, args.theta, args.prec, npart), parallelism=f"replicas x{world}"),
         "cell_updates_per_s": cell_updates,
         "kernel_ms": {"push_deposit": t_pd, "field_step": t_f},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": f"{peak_kind} (copy)", "traffic": None,
                      "algorithmic_bytes_per_launch": b_dom},
         "e2e": {"value": ps_e2e / (ms_e2e / 1e3), "unit": "particle-steps/s",
-                "h2d_bytes_per_step": 2 * NPART * (32 if args.prec == "fp64" else 16) / nsteps_e2e,
+                "h2d_bytes_per_step": 2 * npart * (32 if args.prec == "fp64" else 16) / nsteps_e2e,
                 "d2h_bytes_per_step": 8 / nsteps_e2e,
                 "note": f"pinned host particles copied in once per run of {nsteps_e2e} steps "
                         "(step_n with sorting), particle-step count read back; bytes are per step"},
@@ -372,6 +378,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 2D runs measurement")
     ap.add_argument("--batch-runs", type=int, default=4096, help="number of batched 2D runs")
+    ap.add_argument("--particles", type=int, default=NPART,
+                    help="beam macroparticles (default 4194304; smaller only for profiling captures)")
+    ap.add_argument("--tuning", default=None,
+                    help="P,KZ launch shapes instead of the autotuner (profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

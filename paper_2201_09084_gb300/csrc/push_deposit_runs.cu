@@ -1,22 +1,28 @@
 // Fused gather + Boris + move + Esirkepov deposit + alpha-damped flush for
-// shape order 1, over particles sorted by cell.
+// shape order 1, over particles sorted by tile.
 //
-// A block takes a chunk of 256*P consecutive particles.  The chunk is loaded
-// into shared memory with coalesced 16-byte loads (structure of arrays, rows
-// padded to P+1 words so the strided per-thread reads are bank-conflict
-// free), every thread then processes its own run of P consecutive particles,
-// and the updated records go back with coalesced stores.
-//
-// Deposit: consecutive particles of a sorted run mostly share the Esirkepov
-// stencil anchor (per-axis min(old cell, new cell)); the order-1 current of a
-// move spans 3 nodes per axis, i.e. 2x3x3 prefix values per component, 54 in
-// all.  A thread accumulates them in registers while the anchor stays the same
-// and flushes only when it changes.  Because alpha (Eq. alpha) and the charge
-// factor depend only on the node, they are applied once per flush, which is
-// the "damping fused into the flush to the grid" of Eq. MaxwellE's source
-// term.  At the end of a run the lanes of a warp that share one anchor sum
-// their accumulators with shuffles, so a dense beam core costs one set of
-// global atomics per warp instead of one per particle.
+// A block takes a chunk of 128*P consecutive particles and works in phases,
+// all from shared memory:
+//   1. stage the chunk with coalesced 16-byte loads (structure of arrays, rows
+//      padded to P+1 words so a thread's strided reads are bank-conflict free)
+//      and find the bounding box of its cells;
+//   2. load E and the time-averaged B of that box (+ guard nodes);
+//   A. push: every thread gathers, rotates and moves its own P particles and
+//      keeps old and new positions in the stage;
+//   B. counting-sort the chunk by Esirkepov anchor (the per-axis minimum of
+//      old and new cell, where the order-1 current stencil of the move
+//      starts); the E/B box is dead now and becomes the current box;
+//   C. deposit: each thread takes P consecutive particles of the anchor order,
+//      so a run mostly shares one anchor, and accumulates the 2x3x3 prefix
+//      values of each component (54 in 3D) in registers; at the end, for each
+//      anchor present in a warp, the warp sums its lanes' values with a
+//      reduce-scatter of shuffles (each lane ends with two sums) and adds them
+//      to the box with two shared-memory atomics per lane;
+//   D. add the box to the grid with the charge factor and alpha (Eq. alpha,
+//      at each component's staggered location): the damping of Eq. MaxwellE's
+//      source term applied once per node in the flush; write the chunk back.
+// A chunk whose box does not fit in shared memory (sparse particles) takes a
+// per-particle path with global loads and atomics.
 #include "particle_common.cuh"
 
 namespace picpml {
@@ -38,25 +44,24 @@ __device__ __forceinline__ int bits_to_cell<float>(float v) { return __float_as_
 template <>
 __device__ __forceinline__ int bits_to_cell<double>(double v) { return (int)__double_as_longlong(v); }
 
-// Register accumulator of the order-1 current of a run (values are
-// w * (shape factor) sums; the charge factor and alpha are applied at flush).
+// Register accumulator of the order-1 current of a run: w * (Esirkepov shape
+// factor) prefix sums; the charge factor and alpha are applied at the flush.
+// Flat layout, 3D: Jx [ix*9 + jy*3 + kz] (ix < 2), Jy 18 + [ix*6 + jy*3 + kz]
+// (jy < 2), Jz 36 + [ix*6 + jy*2 + kz] (kz < 2); 2D: Jx [ix*3 + kz],
+// Jy (out of plane) 6 + [ix*3 + kz], Jz 15 + [ix*2 + kz].
 template <typename T, int DIM>
 struct Acc1 {
-  static constexpr int NX = DIM == 3 ? 18 : 6;   // Jx: 2 x 3 (x 3)
-  static constexpr int NY = DIM == 3 ? 18 : 9;   // Jy: 3 x 2 x 3 (3D) / 3 x 3 (2D, out of plane)
-  static constexpr int NZ = DIM == 3 ? 18 : 6;
-  T vx[NX], vy[NY], vz[NZ];
+  static constexpr int NX = DIM == 3 ? 18 : 6;
+  static constexpr int NY = DIM == 3 ? 18 : 9;
+  static constexpr int NV = DIM == 3 ? 54 : 21;
+  static constexpr int NVP = DIM == 3 ? 64 : 32;   // padded to 32 * 2^k for the reduce-scatter
+  T v[NV];
 
   __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int t = 0; t < NX; ++t) vx[t] = T(0);
-#pragma unroll
-    for (int t = 0; t < NY; ++t) vy[t] = T(0);
-#pragma unroll
-    for (int t = 0; t < NZ; ++t) vz[t] = T(0);
+    for (int t = 0; t < NV; ++t) v[t] = T(0);
   }
 
-  // 3D layout: vx[ix*9 + jy*3 + kz], vy[ix*6 + jy*3 + kz], vz[ix*6 + jy*2 + kz].
   // Esirkepov's transverse factor S0 S0' + DS S0'/2 + S0 DS'/2 + DS DS'/3 is
   // evaluated as M M' + DS DS'/12 with the mid-move shape M = S0 + DS/2 (the
   // same polynomial, since 1/3 = 1/4 + 1/12); a component whose prefix sums
@@ -79,8 +84,8 @@ struct Acc1 {
 #pragma unroll
           for (int kz = 0; kz < 3; ++kz) {
             const T Tl = M[1][jy] * M[2][kz] + Q[1][jy] * DS[2][kz];
-            vx[0 * 9 + jy * 3 + kz] += ax0 * Tl;
-            vx[1 * 9 + jy * 3 + kz] += ax1 * Tl;
+            v[0 * 9 + jy * 3 + kz] += ax0 * Tl;
+            v[1 * 9 + jy * 3 + kz] += ax1 * Tl;
           }
       }
       const T ay0 = w * DS[1][0], ay1 = w * (DS[1][0] + DS[1][1]);
@@ -90,8 +95,8 @@ struct Acc1 {
 #pragma unroll
           for (int kz = 0; kz < 3; ++kz) {
             const T Tl = M[0][ix] * M[2][kz] + Q[0][ix] * DS[2][kz];
-            vy[ix * 6 + 0 * 3 + kz] += ay0 * Tl;
-            vy[ix * 6 + 1 * 3 + kz] += ay1 * Tl;
+            v[NX + ix * 6 + 0 * 3 + kz] += ay0 * Tl;
+            v[NX + ix * 6 + 1 * 3 + kz] += ay1 * Tl;
           }
       }
       const T az0 = w * DS[2][0], az1 = w * (DS[2][0] + DS[2][1]);
@@ -101,212 +106,132 @@ struct Acc1 {
 #pragma unroll
           for (int jy = 0; jy < 3; ++jy) {
             const T Tl = M[0][ix] * M[1][jy] + Q[0][ix] * DS[1][jy];
-            vz[ix * 6 + jy * 2 + 0] += az0 * Tl;
-            vz[ix * 6 + jy * 2 + 1] += az1 * Tl;
+            v[NX + NY + ix * 6 + jy * 2 + 0] += az0 * Tl;
+            v[NX + NY + ix * 6 + jy * 2 + 1] += az1 * Tl;
           }
       }
     } else {
-      // 2D layout: vx[ix*3 + kz], vz[ix*2 + kz], vy[ix*3 + kz]
       const T ax0 = w * DS[0][0], ax1 = w * (DS[0][0] + DS[0][1]);
 #pragma unroll
       for (int kz = 0; kz < 3; ++kz) {
-        vx[0 * 3 + kz] += ax0 * M[2][kz];
-        vx[1 * 3 + kz] += ax1 * M[2][kz];
+        v[0 * 3 + kz] += ax0 * M[2][kz];
+        v[1 * 3 + kz] += ax1 * M[2][kz];
       }
       const T az0 = w * DS[2][0], az1 = w * (DS[2][0] + DS[2][1]);
 #pragma unroll
       for (int ix = 0; ix < 3; ++ix) {
-        vz[ix * 2 + 0] += az0 * M[0][ix];
-        vz[ix * 2 + 1] += az1 * M[0][ix];
+        v[NX + NY + ix * 2 + 0] += az0 * M[0][ix];
+        v[NX + NY + ix * 2 + 1] += az1 * M[0][ix];
       }
       if (wvy != T(0)) {
 #pragma unroll
         for (int ix = 0; ix < 3; ++ix)
 #pragma unroll
-          for (int kz = 0; kz < 3; ++kz) vy[ix * 3 + kz] += wvy * (M[0][ix] * M[2][kz] + Q[0][ix] * DS[2][kz]);
+          for (int kz = 0; kz < 3; ++kz) v[NX + ix * 3 + kz] += wvy * (M[0][ix] * M[2][kz] + Q[0][ix] * DS[2][kz]);
       }
     }
   }
 
-  __device__ __forceinline__ void warp_sum() {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-#pragma unroll
-      for (int t = 0; t < NX; ++t) vx[t] += __shfl_xor_sync(0xffffffffu, vx[t], off);
-#pragma unroll
-      for (int t = 0; t < NY; ++t) vy[t] += __shfl_xor_sync(0xffffffffu, vy[t], off);
-#pragma unroll
-      for (int t = 0; t < NZ; ++t) vz[t] += __shfl_xor_sync(0xffffffffu, vz[t], off);
-    }
-  }
-
-  // Sums the accumulators of each contiguous run of lanes with equal segment
-  // id towards the run's first lane (shuffle-down segmented reduction).
-  __device__ __forceinline__ void seg_sum(int segid, int lane) {
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int so = __shfl_down_sync(0xffffffffu, segid, off);
-      const bool take = lane + off < 32 && so == segid;
-#pragma unroll
-      for (int t = 0; t < NX; ++t) {
-        const T o = __shfl_down_sync(0xffffffffu, vx[t], off);
-        if (take) vx[t] += o;
-      }
-#pragma unroll
-      for (int t = 0; t < NY; ++t) {
-        const T o = __shfl_down_sync(0xffffffffu, vy[t], off);
-        if (take) vy[t] += o;
-      }
-#pragma unroll
-      for (int t = 0; t < NZ; ++t) {
-        const T o = __shfl_down_sync(0xffffffffu, vz[t], off);
-        if (take) vz[t] += o;
-      }
-    }
-  }
-
-  // Adds the run's sums into the shared-memory current box (local anchor
-  // (ax, ay, az), box row lengths bx, by; arrays J0, J1, J2).
-  __device__ __forceinline__ void flush_box(T* J0, T* J1, T* J2, int ax, int ay, int az, int bx, int bxy) const {
+  // Component and node offsets of flat index idx.
+  __device__ __forceinline__ static void node_of(int idx, int& comp, int& ix, int& jy, int& kz) {
     if (DIM == 3) {
-#pragma unroll
-      for (int ix = 0; ix < 2; ++ix)
-#pragma unroll
-        for (int jy = 0; jy < 3; ++jy)
-#pragma unroll
-          for (int kz = 0; kz < 3; ++kz) {
-            const T v = vx[ix * 9 + jy * 3 + kz];
-            if (v != T(0)) atomicAdd(J0 + (ax + ix) + bx * (ay + jy) + bxy * (az + kz), v);
-          }
-#pragma unroll
-      for (int ix = 0; ix < 3; ++ix)
-#pragma unroll
-        for (int jy = 0; jy < 2; ++jy)
-#pragma unroll
-          for (int kz = 0; kz < 3; ++kz) {
-            const T v = vy[ix * 6 + jy * 3 + kz];
-            if (v != T(0)) atomicAdd(J1 + (ax + ix) + bx * (ay + jy) + bxy * (az + kz), v);
-          }
-#pragma unroll
-      for (int ix = 0; ix < 3; ++ix)
-#pragma unroll
-        for (int jy = 0; jy < 3; ++jy)
-#pragma unroll
-          for (int kz = 0; kz < 2; ++kz) {
-            const T v = vz[ix * 6 + jy * 2 + kz];
-            if (v != T(0)) atomicAdd(J2 + (ax + ix) + bx * (ay + jy) + bxy * (az + kz), v);
-          }
+      if (idx < 18) {
+        comp = 0; ix = idx / 9; jy = (idx / 3) % 3; kz = idx % 3;
+      } else if (idx < 36) {
+        const int t = idx - 18;
+        comp = 1; ix = t / 6; jy = (t / 3) % 2; kz = t % 3;
+      } else {
+        const int t = idx - 36;
+        comp = 2; ix = t / 6; jy = (t / 2) % 3; kz = t % 2;
+      }
     } else {
-#pragma unroll
-      for (int ix = 0; ix < 2; ++ix)
-#pragma unroll
-        for (int kz = 0; kz < 3; ++kz) {
-          const T v = vx[ix * 3 + kz];
-          if (v != T(0)) atomicAdd(J0 + (ax + ix) + bxy * (az + kz), v);
-        }
-#pragma unroll
-      for (int ix = 0; ix < 3; ++ix)
-#pragma unroll
-        for (int kz = 0; kz < 2; ++kz) {
-          const T v = vz[ix * 2 + kz];
-          if (v != T(0)) atomicAdd(J2 + (ax + ix) + bxy * (az + kz), v);
-        }
-#pragma unroll
-      for (int ix = 0; ix < 3; ++ix)
-#pragma unroll
-        for (int kz = 0; kz < 3; ++kz) {
-          const T v = vy[ix * 3 + kz];
-          if (v != T(0)) atomicAdd(J1 + (ax + ix) + bxy * (az + kz), v);
-        }
+      jy = 0;
+      if (idx < 6) {
+        comp = 0; ix = idx / 3; kz = idx % 3;
+      } else if (idx < 15) {
+        const int t = idx - 6;
+        comp = 1; ix = t / 3; kz = t % 3;
+      } else {
+        const int t = idx - 15;
+        comp = 2; ix = t / 2; kz = t % 2;
+      }
     }
   }
 
-  // Adds the run's current, times the charge factors and alpha, to the grid.
-  __device__ __forceinline__ void flush(const Geom& g, const Tables& tb, const FieldPtrs<T>& f,
-                                        const SpeciesPtrs<T>& sp, int key) const {
-    const int ax = cell_i(key), ay = DIM == 3 ? cell_j(key) : 0, az = cell_k(key);
-    const T* anx = al_node<T>(tb, 0);
-    const T* acx = al_cent<T>(tb, 0);
-    const T* any = al_node<T>(tb, 1);
-    const T* acy = al_cent<T>(tb, 1);
-    const T* anz = al_node<T>(tb, 2);
-    const T* acz = al_cent<T>(tb, 2);
-    if (DIM == 3) {
+  // Adds this thread's sums into the shared-memory current box at the local
+  // anchor (ax, ay, az); bx, bxy: box row and plane lengths.
+  __device__ __forceinline__ void flush_box(T* J, int NBS, int ax, int ay, int az, int bx, int bxy) const {
 #pragma unroll
-      for (int ix = 0; ix < 2; ++ix)
+    for (int t = 0; t < NV; ++t) {
+      const T val = v[t];
+      if (val == T(0)) continue;
+      int comp, ix, jy, kz;
+      node_of(t, comp, ix, jy, kz);
+      atomicAdd(J + comp * NBS + (ax + ix) + bx * (ay + jy) + bxy * (az + kz), val);
+    }
+  }
+
+  // Sums the accumulators of the lanes with member == true (one anchor) by a
+  // reduce-scatter of shuffles into a scratch array: after five halving steps
+  // lane L holds the group's sums of flat indices K L .. K L + K - 1
+  // (K = NVP / 32), which it adds to the box.  Every lane takes part (lanes
+  // outside the group contribute zeros and carry partial sums) and keeps its
+  // own accumulators for its own group.
+  __device__ __forceinline__ void group_flush(bool member, int lane, T* J, int NBS, int ax, int ay, int az, int bx,
+                                              int bxy) const {
+    constexpr int H = NVP / 2;
+    T t[H];
+    {
+      const bool up = (lane & 16) != 0;
 #pragma unroll
-        for (int jy = 0; jy < 3; ++jy)
+      for (int i = 0; i < H; ++i) {
+        const T lo = (i < NV && member) ? v[i < NV ? i : 0] : T(0);
+        const T hi = (i + H < NV && member) ? v[i + H < NV ? i + H : 0] : T(0);
+        t[i] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, 16);
+      }
+    }
 #pragma unroll
-          for (int kz = 0; kz < 3; ++kz) {
-            const T v = vx[ix * 9 + jy * 3 + kz];
-            if (v != T(0))
-              atomicAdd(f.J[0] + g.idx(ax + ix, ay + jy, az + kz),
-                        sp.cj[0] * v * acx[ax + ix] * any[ay + jy] * anz[az + kz]);
-          }
+    for (int lev = 1; lev < 5; ++lev) {
+      const int o = 16 >> lev;
+      const int h = H >> lev;
+      const bool up = (lane & o) != 0;
 #pragma unroll
-      for (int ix = 0; ix < 3; ++ix)
+      for (int i = 0; i < h; ++i) {
+        const T lo = t[i], hi = t[i + h];
+        t[i] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, o);
+      }
+    }
+    constexpr int K = NVP / 32;
 #pragma unroll
-        for (int jy = 0; jy < 2; ++jy)
-#pragma unroll
-          for (int kz = 0; kz < 3; ++kz) {
-            const T v = vy[ix * 6 + jy * 3 + kz];
-            if (v != T(0))
-              atomicAdd(f.J[1] + g.idx(ax + ix, ay + jy, az + kz),
-                        sp.cj[1] * v * anx[ax + ix] * acy[ay + jy] * anz[az + kz]);
-          }
-#pragma unroll
-      for (int ix = 0; ix < 3; ++ix)
-#pragma unroll
-        for (int jy = 0; jy < 3; ++jy)
-#pragma unroll
-          for (int kz = 0; kz < 2; ++kz) {
-            const T v = vz[ix * 6 + jy * 2 + kz];
-            if (v != T(0))
-              atomicAdd(f.J[2] + g.idx(ax + ix, ay + jy, az + kz),
-                        sp.cj[2] * v * anx[ax + ix] * any[ay + jy] * acz[az + kz]);
-          }
-    } else {
-#pragma unroll
-      for (int ix = 0; ix < 2; ++ix)
-#pragma unroll
-        for (int kz = 0; kz < 3; ++kz) {
-          const T v = vx[ix * 3 + kz];
-          if (v != T(0))
-            atomicAdd(f.J[0] + g.idx(ax + ix, 0, az + kz), sp.cj[0] * v * acx[ax + ix] * anz[az + kz]);
-        }
-#pragma unroll
-      for (int ix = 0; ix < 3; ++ix)
-#pragma unroll
-        for (int kz = 0; kz < 2; ++kz) {
-          const T v = vz[ix * 2 + kz];
-          if (v != T(0))
-            atomicAdd(f.J[2] + g.idx(ax + ix, 0, az + kz), sp.cj[2] * v * anx[ax + ix] * acz[az + kz]);
-        }
-#pragma unroll
-      for (int ix = 0; ix < 3; ++ix)
-#pragma unroll
-        for (int kz = 0; kz < 3; ++kz) {
-          const T v = vy[ix * 3 + kz];
-          if (v != T(0))
-            atomicAdd(f.J[1] + g.idx(ax + ix, 0, az + kz), sp.cjy2d * v * anx[ax + ix] * anz[az + kz]);
-        }
+    for (int k = 0; k < K; ++k) {
+      const int idx = k + K * lane;
+      const T val = t[k];
+      if (idx < NV && val != T(0)) {
+        int comp, ix, jy, kz;
+        node_of(idx, comp, ix, jy, kz);
+        atomicAdd(J + comp * NBS + (ax + ix) + bx * (ay + jy) + bxy * (az + kz), val);
+      }
     }
   }
 };
 
 constexpr int kNT = 128;
 
-// Shared memory of one block: the staged chunk (8 words per particle, rows
-// padded to P+1), the field/current box (E, time-averaged B, J: 9 arrays of
-// NBMAX nodes), the per-cell counters and the permutation of the chunk sort.
-template <typename T, int P>
+// Shared memory of one block: the staged chunk (NW words per particle, rows
+// padded to P+1), the field box (E and time-averaged B, 6 arrays of NBMAX
+// nodes; its first 3 arrays are the current box after the push), the
+// counters and the permutation of the anchor sort.
+// Stage words: 0-2 old offsets, 3 weight, 4-6 u, 7 old cell, 8-10 new
+// offsets, 11 new cell (-1: removed or deposits nothing), 12 (2D) w v_y/c.
+template <typename T, int DIM, int P>
 struct Plan {
   static constexpr int PP = P + 1;
   static constexpr int ROW = kNT * PP;
   static constexpr int C = kNT * P;
-  static constexpr int NBMAX = sizeof(T) == 4 ? 768 : 384;
-  static constexpr size_t stage = (size_t)8 * ROW * sizeof(T);
-  static constexpr size_t box = (size_t)9 * NBMAX * sizeof(T);
+  static constexpr int NW = DIM == 3 ? 12 : 13;
+  static constexpr int NBMAX = sizeof(T) == 4 ? (P >= 8 ? 512 : 768) : 384;
+  static constexpr size_t stage = (size_t)NW * ROW * sizeof(T);
+  static constexpr size_t box = (size_t)6 * NBMAX * sizeof(T);
   static constexpr size_t cnt = (size_t)(NBMAX + 1) * sizeof(int);
   static constexpr size_t perm = (size_t)C * sizeof(unsigned short);
   static constexpr size_t total = stage + box + cnt + perm;
@@ -338,11 +263,98 @@ __device__ __forceinline__ int warp_max(int v) {
   return v;
 }
 
+// Boris push and move of one particle with fields E, B; returns false when
+// the particle leaves its allowed cells.  c1, o1: new cell and offsets.
+template <int DIM, typename T>
+__device__ __forceinline__ bool move_particle(const Geom& g, const T o[3], const int c[3], T u[3], int c1[3],
+                                              T o1[3], T& inv_gamma) {
+  const Mover<T> mv(u);
+  inv_gamma = mv.inv_gamma();
+  bool out = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    c1[a] = c[a];
+    o1[a] = o[a];
+    if (DIM == 2 && a == 1) continue;
+    const T Sh = sizeof(T) == 4 ? T(g.Sf[a]) : T(g.S[a]);
+    const T Sl = sizeof(T) == 4 ? T(g.Sfl[a]) : T(0);
+    T x = mv.advance(o[a], Sh, Sl, u[a]);
+    if (x >= T(1)) {
+      x -= T(1);
+      c1[a] += 1;
+    } else if (x < T(0)) {
+      x += T(1);
+      c1[a] -= 1;
+      if (x >= T(1)) {  // x was a tiny negative number: stay on the node
+        x = T(0);
+        c1[a] += 1;
+      }
+    }
+    o1[a] = x;
+    if (c1[a] < g.rmin[a] || c1[a] > g.rmax[a] || (c1[a] == g.rmax[a] && x > T(0))) out = true;
+  }
+  return !out;
+}
+
+// The whole step of one particle from global memory (chunks whose box does
+// not fit in shared memory): gather, push, move, deposit with global atomics
+// (charge factor and alpha per contribution).  Reads and writes the stage.
+template <typename T, int DIM>
+__device__ __noinline__ unsigned particle_global(const Geom& g, const Tables& tb, const FieldPtrs<T>& f,
+                                                 const SpeciesPtrs<T>& sp, int prescribed, T* stg, int slot, int ROW) {
+  const int cell = bits_to_cell<T>(stg[7 * ROW + slot]);
+  T o[3] = {stg[0 * ROW + slot], stg[1 * ROW + slot], stg[2 * ROW + slot]};
+  stg[8 * ROW + slot] = o[0];
+  stg[9 * ROW + slot] = o[1];
+  stg[10 * ROW + slot] = o[2];
+  stg[11 * ROW + slot] = cell_to_bits<T>(-1);
+  if (cell < 0) return 0;
+  const T w = stg[3 * ROW + slot];
+  T u[3] = {stg[4 * ROW + slot], stg[5 * ROW + slot], stg[6 * ROW + slot]};
+  const int c[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
+  if (!prescribed) {
+    int b0[3], bh[3];
+    T w0[3][2], wh[3][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (DIM == 2 && a == 1) {
+        b0[1] = bh[1] = 0;
+        w0[1][0] = wh[1][0] = T(1);
+        w0[1][1] = wh[1][1] = T(0);
+        continue;
+      }
+      axis_weights<1, T>(c[a], o[a], b0[a], w0[a], bh[a], wh[a]);
+    }
+    T E[3], B[3];
+    E[0] = interp<1, DIM, T>(g, f.E[0], bh[0], wh[0], b0[1], w0[1], b0[2], w0[2]);
+    E[1] = interp<1, DIM, T>(g, f.E[1], b0[0], w0[0], bh[1], wh[1], b0[2], w0[2]);
+    E[2] = interp<1, DIM, T>(g, f.E[2], b0[0], w0[0], b0[1], w0[1], bh[2], wh[2]);
+    B[0] = interp_avg<1, DIM, T>(g, f.Bh[0], f.Bp[0], b0[0], w0[0], bh[1], wh[1], bh[2], wh[2]);
+    B[1] = interp_avg<1, DIM, T>(g, f.Bh[1], f.Bp[1], bh[0], wh[0], b0[1], w0[1], bh[2], wh[2]);
+    B[2] = interp_avg<1, DIM, T>(g, f.Bh[2], f.Bp[2], bh[0], wh[0], bh[1], wh[1], b0[2], w0[2]);
+    boris<T>(u, E, B, sp.ke);
+  }
+  stg[4 * ROW + slot] = u[0];
+  stg[5 * ROW + slot] = u[1];
+  stg[6 * ROW + slot] = u[2];
+  int c1[3];
+  T o1[3], ig;
+  if (!move_particle<DIM, T>(g, o, c, u, c1, o1, ig)) return 1;
+  stg[8 * ROW + slot] = o1[0];
+  stg[9 * ROW + slot] = o1[1];
+  stg[10 * ROW + slot] = o1[2];
+  stg[11 * ROW + slot] = cell_to_bits<T>(pack_cell(c1[0], c1[1], c1[2]));
+  deposit_one<1, DIM, T>(g, tb, f, sp, c, o, c1, o1, w, u[1] * ig);
+  return 1;
+}
+
 template <typename T, int DIM, int P>
-__global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 3 : 2)
-    k_pd1(Geom g, Tables tb, FieldPtrs<T> f, SpeciesPtrs<T> sp, int prescribed, unsigned* status,
+__global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
+    k_pd1(const __grid_constant__ Geom g, const __grid_constant__ Tables tb, const __grid_constant__ FieldPtrs<T> f,
+          const __grid_constant__ SpeciesPtrs<T> sp, int prescribed, unsigned* status,
           unsigned long long* pushed_total) {
-  using PL = Plan<T, P>;
+  using PL = Plan<T, DIM, P>;
+  using AC = Acc1<T, DIM>;
   constexpr int PP = PL::PP, ROW = PL::ROW, C = PL::C, NBMAX = PL::NBMAX;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* stg = reinterpret_cast<T*>(smraw);
@@ -350,13 +362,14 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 3 : 2)
   int* cnt = reinterpret_cast<int*>(smraw + PL::stage + PL::box);
   unsigned short* perm = reinterpret_cast<unsigned short*>(smraw + PL::stage + PL::box + PL::cnt);
   __shared__ int s_red[6][kNT / 32];
-  __shared__ int s_geo[8];   // origin x,y,z; box dims x, y, z; cells per row x, y (of the sort key)
+  __shared__ int s_geo[8];   // box origin x, y, z and dims x, y, z
   __shared__ int s_use_box;
   __shared__ int s_scan[kNT / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long n = *sp.n_dev;
   const long long nchunks = (n + C - 1) / C;
   unsigned pushed = 0;
+  if (sp.immobile) return;
 
   for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const long long base = ch * C;
@@ -382,7 +395,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 3 : 2)
       }
     }
     __syncthreads();
-    // ---- 2. validate, bounding box of the current cells ----
+    // validate, bounding box of the current cells
     int mn[3] = {1 << 30, 1 << 30, 1 << 30}, mx[3] = {-1, -1, -1};
     for (int i = 0; i < P; ++i) {
       const int slot = tid * PP + i;
@@ -396,11 +409,9 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 3 : 2)
         const T o = stg[a * ROW + slot];
         if (c[a] < g.rmin[a] || c[a] > g.rmax[a] || !(o >= T(0) && o < T(1))) bad = true;
       }
-      if (bad || (sp.immobile)) {
-        if (bad) {
-          atomicOr(status, ST_BAD_PARTICLE);
-          stg[7 * ROW + slot] = cell_to_bits<T>(-1);  // removed
-        }
+      if (bad) {
+        atomicOr(status, ST_BAD_PARTICLE);
+        stg[7 * ROW + slot] = cell_to_bits<T>(-1);  // removed
         continue;
       }
 #pragma unroll
@@ -427,6 +438,9 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 3 : 2)
         }
       int use = hi[0] >= 0;
       if (DIM == 2) lo[1] = hi[1] = 0;
+      // nodes lo-1 .. hi+2 per axis: the gather reads from the cell's lower
+      // node minus one (half-staggered components) to its upper node, the
+      // deposit stencil of a move spans min(old, new cell) .. + 2
       const int dx = hi[0] - lo[0] + 4, dy = DIM == 3 ? hi[1] - lo[1] + 4 : 1, dz = hi[2] - lo[2] + 4;
       if (use && (long long)dx * dy * dz > NBMAX) use = 0;
       s_use_box = use;
@@ -439,47 +453,99 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 3 : 2)
     }
     __syncthreads();
     const int use_box = s_use_box;
-    const int ox = s_geo[0], oy = s_geo[1], oz = s_geo[2];
-    const int bdx = s_geo[3], bdy = s_geo[4], bdz = s_geo[5];
-    const int bxy = bdx * bdy;
-    const int NB = bdx * bdy * bdz;
-    T* const BE0 = bx_;
-    T* const BE1 = bx_ + NBMAX;
-    T* const BE2 = bx_ + 2 * NBMAX;
-    T* const BB0 = bx_ + 3 * NBMAX;
-    T* const BB1 = bx_ + 4 * NBMAX;
-    T* const BB2 = bx_ + 5 * NBMAX;
-    T* const BJ0 = bx_ + 6 * NBMAX;
-    T* const BJ1 = bx_ + 7 * NBMAX;
-    T* const BJ2 = bx_ + 8 * NBMAX;
-    // the sort key is the box-local node of the particle's cell
+
     if (use_box) {
-      // ---- 3. load E and the time-averaged B of the box, zero the J box ----
+      const int ox = s_geo[0], oy = s_geo[1], oz = s_geo[2];
+      const int bdx = s_geo[3], bdy = s_geo[4], bdz = s_geo[5];
+      const int bxy = bdx * bdy;
+      const int NB = bdx * bdy * bdz;
+      // ---- 2. E and the time-averaged B of the box ----
       for (int t = tid; t < NB; t += kNT) {
         const int li = t % bdx, r = t / bdx, lj = r % bdy, lk = r / bdy;
         const long long gi = g.idx(ox + li, oy + lj, oz + lk);
-        BE0[t] = f.E[0][gi];
-        BE1[t] = f.E[1][gi];
-        BE2[t] = f.E[2][gi];
-        BB0[t] = T(0.5) * (f.Bh[0][gi] + f.Bp[0][gi]);
-        BB1[t] = T(0.5) * (f.Bh[1][gi] + f.Bp[1][gi]);
-        BB2[t] = T(0.5) * (f.Bh[2][gi] + f.Bp[2][gi]);
-        BJ0[t] = BJ1[t] = BJ2[t] = T(0);
+        bx_[0 * NBMAX + t] = f.E[0][gi];
+        bx_[1 * NBMAX + t] = f.E[1][gi];
+        bx_[2 * NBMAX + t] = f.E[2][gi];
+        bx_[3 * NBMAX + t] = T(0.5) * (f.Bh[0][gi] + f.Bp[0][gi]);
+        bx_[4 * NBMAX + t] = T(0.5) * (f.Bh[1][gi] + f.Bp[1][gi]);
+        bx_[5 * NBMAX + t] = T(0.5) * (f.Bh[2][gi] + f.Bp[2][gi]);
       }
+      __syncthreads();
+      // ---- A. gather, push and move this thread's P particles ----
+      for (int i = 0; i < P; ++i) {
+        const int slot = tid * PP + i;
+        const int cell = bits_to_cell<T>(stg[7 * ROW + slot]);
+        T o[3] = {stg[0 * ROW + slot], stg[1 * ROW + slot], stg[2 * ROW + slot]};
+        if (cell < 0) {
+          stg[8 * ROW + slot] = o[0];
+          stg[9 * ROW + slot] = o[1];
+          stg[10 * ROW + slot] = o[2];
+          stg[11 * ROW + slot] = cell_to_bits<T>(-1);
+          continue;
+        }
+        T u[3] = {stg[4 * ROW + slot], stg[5 * ROW + slot], stg[6 * ROW + slot]};
+        const int c[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
+        if (!prescribed) {
+          int b0[3], bh[3];
+          T w0[3][2], wh[3][2];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            if (DIM == 2 && a == 1) {
+              b0[1] = bh[1] = 0;
+              w0[1][0] = wh[1][0] = T(1);
+              w0[1][1] = wh[1][1] = T(0);
+              continue;
+            }
+            axis_weights<1, T>(c[a], o[a], b0[a], w0[a], bh[a], wh[a]);
+          }
+          const int l0x = b0[0] - ox, lhx = bh[0] - ox, l0y = b0[1] - oy, lhy = bh[1] - oy, l0z = b0[2] - oz,
+                    lhz = bh[2] - oz;
+          T E[3], B[3];
+          E[0] = interp_box<DIM, T>(bx_ + 0 * NBMAX, bdx, bxy, lhx, wh[0], l0y, w0[1], l0z, w0[2]);
+          E[1] = interp_box<DIM, T>(bx_ + 1 * NBMAX, bdx, bxy, l0x, w0[0], lhy, wh[1], l0z, w0[2]);
+          E[2] = interp_box<DIM, T>(bx_ + 2 * NBMAX, bdx, bxy, l0x, w0[0], l0y, w0[1], lhz, wh[2]);
+          B[0] = interp_box<DIM, T>(bx_ + 3 * NBMAX, bdx, bxy, l0x, w0[0], lhy, wh[1], lhz, wh[2]);
+          B[1] = interp_box<DIM, T>(bx_ + 4 * NBMAX, bdx, bxy, lhx, wh[0], l0y, w0[1], lhz, wh[2]);
+          B[2] = interp_box<DIM, T>(bx_ + 5 * NBMAX, bdx, bxy, lhx, wh[0], lhy, wh[1], l0z, w0[2]);
+          boris<T>(u, E, B, sp.ke);
+        }
+        ++pushed;
+        stg[4 * ROW + slot] = u[0];
+        stg[5 * ROW + slot] = u[1];
+        stg[6 * ROW + slot] = u[2];
+        int c1[3];
+        T o1[3], ig;
+        const bool in = move_particle<DIM, T>(g, o, c, u, c1, o1, ig);
+        stg[8 * ROW + slot] = in ? o1[0] : o[0];
+        stg[9 * ROW + slot] = in ? o1[1] : o[1];
+        stg[10 * ROW + slot] = in ? o1[2] : o[2];
+        stg[11 * ROW + slot] = cell_to_bits<T>(in ? pack_cell(c1[0], c1[1], c1[2]) : -1);
+        if constexpr (DIM == 2) stg[12 * ROW + slot] = stg[3 * ROW + slot] * u[1] * ig;
+      }
+      __syncthreads();
+      // ---- B. counting sort of the chunk by box-local anchor ----
+      // (the E/B box is dead: its first three arrays become the current box)
+      T* const BJ = bx_;
+      for (int t = tid; t < 3 * NBMAX; t += kNT) BJ[t] = T(0);
       for (int t = tid; t <= NB; t += kNT) cnt[t] = 0;
       __syncthreads();
-      // ---- 4. counting sort of the chunk by box-local cell (warp-aggregated) ----
+      auto anchor_key = [&](int slot) -> int {
+        const int c0 = bits_to_cell<T>(stg[7 * ROW + slot]);
+        const int c1 = bits_to_cell<T>(stg[11 * ROW + slot]);
+        if (c0 < 0 || c1 < 0) return NB;
+        const int ax = min(cell_i(c0), cell_i(c1)) - ox;
+        const int ay = DIM == 3 ? min(cell_j(c0), cell_j(c1)) - oy : 0;
+        const int az = min(cell_k(c0), cell_k(c1)) - oz;
+        return ax + bdx * (ay + bdy * az);
+      };
       for (int k = 0; k < P; ++k) {
         const int q = tid + k * kNT;
-        const int slot = (q / P) * PP + (q % P);
-        const int cell = bits_to_cell<T>(stg[7 * ROW + slot]);
-        const int key = cell < 0 ? NB : (cell_i(cell) - ox) + bdx * ((DIM == 3 ? cell_j(cell) - oy : 0) + bdy * (cell_k(cell) - oz));
+        const int key = anchor_key((q / P) * PP + (q % P));
         const unsigned m = __match_any_sync(0xffffffffu, key);
         if (lane == __ffs(m) - 1) atomicAdd(cnt + key, __popc(m));
       }
       __syncthreads();
-      // exclusive scan of cnt[0..NB]
-      {
+      {  // exclusive scan of cnt[0..NB]
         const int per = (NB + 1 + kNT - 1) / kNT;
         const int b0 = tid * per;
         int loc = 0;
@@ -507,8 +573,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 3 : 2)
       for (int k = 0; k < P; ++k) {
         const int q = tid + k * kNT;
         const int slot = (q / P) * PP + (q % P);
-        const int cell = bits_to_cell<T>(stg[7 * ROW + slot]);
-        const int key = cell < 0 ? NB : (cell_i(cell) - ox) + bdx * ((DIM == 3 ? cell_j(cell) - oy : 0) + bdy * (cell_k(cell) - oz));
+        const int key = anchor_key(slot);
         const unsigned m = __match_any_sync(0xffffffffu, key);
         const int leader = __ffs(m) - 1;
         int b = 0;
@@ -517,138 +582,50 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 3 : 2)
         perm[b + __popc(m & ((1u << lane) - 1u))] = (unsigned short)slot;
       }
       __syncthreads();
-    }
-
-    // ---- 5. push and deposit one run of P particles per thread ----
-    Acc1<T, DIM> acc;
-    acc.zero();
-    int key = -1;
-    for (int i = 0; i < P; ++i) {
-      const int slot = use_box ? (int)perm[tid * P + i] : tid * PP + i;
-      const int cell = bits_to_cell<T>(stg[7 * ROW + slot]);
-      if (cell < 0 || sp.immobile) continue;
-      T o[3] = {stg[0 * ROW + slot], stg[1 * ROW + slot], stg[2 * ROW + slot]};
-      const T w = stg[3 * ROW + slot];
-      T u[3] = {stg[4 * ROW + slot], stg[5 * ROW + slot], stg[6 * ROW + slot]};
-      int c[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
-      if (!prescribed) {
-        int b0[3], bh[3];
-        T w0[3][2], wh[3][2];
+      // ---- C. deposit runs of P consecutive particles in anchor order ----
+      AC acc;
+      acc.zero();
+      int key = -1;
+      for (int i = 0; i < P; ++i) {
+        const int slot = perm[tid * P + i];
+        const int cell1 = bits_to_cell<T>(stg[11 * ROW + slot]);
+        const int cell0 = bits_to_cell<T>(stg[7 * ROW + slot]);
+        if (cell1 < 0 || cell0 < 0) continue;
+        const int c0[3] = {cell_i(cell0), cell_j(cell0), cell_k(cell0)};
+        const int c1[3] = {cell_i(cell1), cell_j(cell1), cell_k(cell1)};
+        int lo[3] = {0, 0, 0};
+        T S0[3][3], DS[3][3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           if (DIM == 2 && a == 1) {
-            b0[1] = bh[1] = 0;
-            w0[1][0] = wh[1][0] = T(1);
-            w0[1][1] = wh[1][1] = T(0);
+            S0[1][0] = T(1);
+            S0[1][1] = S0[1][2] = T(0);
+            DS[1][0] = DS[1][1] = DS[1][2] = T(0);
             continue;
           }
-          axis_weights<1, T>(c[a], o[a], b0[a], w0[a], bh[a], wh[a]);
+          esk_axis<1, T>(c0[a], stg[a * ROW + slot], c1[a], stg[(8 + a) * ROW + slot], lo[a], S0[a], DS[a]);
         }
-        T E[3], B[3];
-        if (use_box) {
-          const int l0x = b0[0] - ox, lhx = bh[0] - ox, l0y = b0[1] - oy, lhy = bh[1] - oy, l0z = b0[2] - oz,
-                    lhz = bh[2] - oz;
-          E[0] = interp_box<DIM, T>(BE0, bdx, bxy, lhx, wh[0], l0y, w0[1], l0z, w0[2]);
-          E[1] = interp_box<DIM, T>(BE1, bdx, bxy, l0x, w0[0], lhy, wh[1], l0z, w0[2]);
-          E[2] = interp_box<DIM, T>(BE2, bdx, bxy, l0x, w0[0], l0y, w0[1], lhz, wh[2]);
-          B[0] = interp_box<DIM, T>(BB0, bdx, bxy, l0x, w0[0], lhy, wh[1], lhz, wh[2]);
-          B[1] = interp_box<DIM, T>(BB1, bdx, bxy, lhx, wh[0], l0y, w0[1], lhz, wh[2]);
-          B[2] = interp_box<DIM, T>(BB2, bdx, bxy, lhx, wh[0], lhy, wh[1], l0z, w0[2]);
-        } else {
-          E[0] = interp<1, DIM, T>(g, f.E[0], bh[0], wh[0], b0[1], w0[1], b0[2], w0[2]);
-          E[1] = interp<1, DIM, T>(g, f.E[1], b0[0], w0[0], bh[1], wh[1], b0[2], w0[2]);
-          E[2] = interp<1, DIM, T>(g, f.E[2], b0[0], w0[0], b0[1], w0[1], bh[2], wh[2]);
-          B[0] = interp_avg<1, DIM, T>(g, f.Bh[0], f.Bp[0], b0[0], w0[0], bh[1], wh[1], bh[2], wh[2]);
-          B[1] = interp_avg<1, DIM, T>(g, f.Bh[1], f.Bp[1], bh[0], wh[0], b0[1], w0[1], bh[2], wh[2]);
-          B[2] = interp_avg<1, DIM, T>(g, f.Bh[2], f.Bp[2], bh[0], wh[0], bh[1], wh[1], b0[2], w0[2]);
+        const int k = pack_cell(lo[0] - ox, DIM == 3 ? lo[1] - oy : 0, lo[2] - oz);
+        if (k != key) {
+          if (key >= 0) acc.flush_box(BJ, NBMAX, cell_i(key), cell_j(key), cell_k(key), bdx, bxy);
+          acc.zero();
+          key = k;
         }
-        boris<T>(u, E, B, sp.ke);
+        T wvy = T(0);
+        if constexpr (DIM == 2) wvy = stg[12 * ROW + slot];
+        acc.add(S0, DS, stg[3 * ROW + slot], wvy);
       }
-      ++pushed;
-      const Mover<T> mv(u);
-      int c1[3] = {c[0], c[1], c[2]};
-      T o1[3] = {o[0], o[1], o[2]};
-      bool out = false;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (DIM == 2 && a == 1) continue;
-        const T Sh = sizeof(T) == 4 ? T(g.Sf[a]) : T(g.S[a]);
-        const T Sl = sizeof(T) == 4 ? T(g.Sfl[a]) : T(0);
-        T x = mv.advance(o[a], Sh, Sl, u[a]);
-        if (x >= T(1)) {
-          x -= T(1);
-          c1[a] += 1;
-        } else if (x < T(0)) {
-          x += T(1);
-          c1[a] -= 1;
-          if (x >= T(1)) {
-            x = T(0);
-            c1[a] += 1;
-          }
-        }
-        o1[a] = x;
-        if (c1[a] < g.rmin[a] || c1[a] > g.rmax[a] || (c1[a] == g.rmax[a] && x > T(0))) out = true;
+      // lanes that share an anchor sum their runs; one group at a time
+      unsigned pend = __ballot_sync(0xffffffffu, key >= 0);
+      while (pend) {
+        const int leader = __ffs(pend) - 1;
+        const int gk = __shfl_sync(0xffffffffu, key, leader);
+        const bool mem = key == gk;
+        pend &= ~__ballot_sync(0xffffffffu, mem);
+        acc.group_flush(mem, lane, BJ, NBMAX, cell_i(gk), cell_j(gk), cell_k(gk), bdx, bxy);
       }
-      stg[4 * ROW + slot] = u[0];
-      stg[5 * ROW + slot] = u[1];
-      stg[6 * ROW + slot] = u[2];
-      if (out) {
-        stg[7 * ROW + slot] = cell_to_bits<T>(-1);
-        continue;
-      }
-      stg[0 * ROW + slot] = o1[0];
-      stg[1 * ROW + slot] = o1[1];
-      stg[2 * ROW + slot] = o1[2];
-      stg[7 * ROW + slot] = cell_to_bits<T>(pack_cell(c1[0], c1[1], c1[2]));
-      int lo[3] = {0, 0, 0};
-      T S0[3][3], DS[3][3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (DIM == 2 && a == 1) {
-          S0[1][0] = T(1);
-          S0[1][1] = S0[1][2] = T(0);
-          DS[1][0] = DS[1][1] = DS[1][2] = T(0);
-          continue;
-        }
-        esk_axis<1, T>(c[a], o[a], c1[a], o1[a], lo[a], S0[a], DS[a]);
-      }
-      // anchor key: box-local in the box path, global otherwise
-      const int k = use_box ? pack_cell(lo[0] - ox, DIM == 3 ? lo[1] - oy : 0, lo[2] - oz)
-                            : pack_cell(lo[0], lo[1], lo[2]);
-      if (k != key) {
-        if (key >= 0) {
-          if (use_box)
-            acc.flush_box(BJ0, BJ1, BJ2, cell_i(key), cell_j(key), cell_k(key), bdx, bxy);
-          else
-            acc.flush(g, tb, f, sp, key);
-        }
-        acc.zero();
-        key = k;
-      }
-      acc.add(S0, DS, w, w * u[1] * mv.inv_gamma());
-    }
-    // ---- 6. end of the runs: warp-level reduction, flush ----
-    if (use_box) {
-      const int up = __shfl_up_sync(0xffffffffu, key, 1);
-      const bool head = lane == 0 || up != key;
-      const unsigned hm = __ballot_sync(0xffffffffu, head);
-      const int segid = __popc(hm & ((2u << lane) - 1u));
-      acc.seg_sum(segid, lane);
-      if (head && key >= 0) acc.flush_box(BJ0, BJ1, BJ2, cell_i(key), cell_j(key), cell_k(key), bdx, bxy);
-    } else {
-      const unsigned same = __match_any_sync(0xffffffffu, key);
-      if (same == 0xffffffffu) {
-        if (key >= 0) {
-          acc.warp_sum();
-          if (lane == 0) acc.flush(g, tb, f, sp, key);
-        }
-      } else if (key >= 0) {
-        acc.flush(g, tb, f, sp, key);
-      }
-    }
-    __syncthreads();
-    // ---- 7. flush the J box to the grid with the charge factor and alpha ----
-    if (use_box) {
+      __syncthreads();
+      // ---- D. add the current box to the grid with the charge factor and alpha ----
       const T* anx = al_node<T>(tb, 0);
       const T* acx = al_cent<T>(tb, 0);
       const T* any = al_node<T>(tb, 1);
@@ -657,7 +634,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 3 : 2)
       const T* acz = al_cent<T>(tb, 2);
       const T qy = DIM == 3 ? sp.cj[1] : sp.cjy2d;
       for (int t = tid; t < NB; t += kNT) {
-        const T j0 = BJ0[t], j1 = BJ1[t], j2 = BJ2[t];
+        const T j0 = BJ[t], j1 = BJ[NBMAX + t], j2 = BJ[2 * NBMAX + t];
         if (j0 == T(0) && j1 == T(0) && j2 == T(0)) continue;
         const int li = t % bdx, r = t / bdx, lj = r % bdy, lk = r / bdy;
         const int gi = ox + li, gj = oy + lj, gk = oz + lk;
@@ -667,15 +644,20 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 3 : 2)
         if (j1 != T(0)) atomicAdd(f.J[1] + id, qy * j1 * anx[gi] * ay_c * anz[gk]);
         if (j2 != T(0)) atomicAdd(f.J[2] + id, sp.cj[2] * j2 * anx[gi] * ay_n * acz[gk]);
       }
+    } else {
+      // sparse chunk: one particle at a time from global memory
+      for (int i = 0; i < P; ++i)
+        pushed += particle_global<T, DIM>(g, tb, f, sp, prescribed, stg, tid * PP + i, ROW);
     }
-    // ---- 8. write the chunk back (coalesced) ----
+    __syncthreads();
+    // ---- write the chunk back (coalesced) ----
     for (int q = tid; q < C; q += kNT) {
       const long long gp = base + q;
       if (gp >= n) break;
       const int slot = (q / P) * PP + (q % P);
-      const T o[3] = {stg[0 * ROW + slot], stg[1 * ROW + slot], stg[2 * ROW + slot]};
+      const T o[3] = {stg[8 * ROW + slot], stg[9 * ROW + slot], stg[10 * ROW + slot]};
       const T u[3] = {stg[4 * ROW + slot], stg[5 * ROW + slot], stg[6 * ROW + slot]};
-      PIO<T>::store(sp.pos, sp.mom, gp, o, stg[3 * ROW + slot], u, bits_to_cell<T>(stg[7 * ROW + slot]));
+      PIO<T>::store(sp.pos, sp.mom, gp, o, stg[3 * ROW + slot], u, bits_to_cell<T>(stg[11 * ROW + slot]));
     }
   }
   if (pushed_total) {
@@ -688,7 +670,7 @@ template <typename T, int DIM, int P>
 cudaError_t launch_pd1_p(const Geom& g, const Tables& tb, const FieldPtrs<T>& f, const SpeciesPtrs<T>& sp,
                          int prescribed, unsigned* status, unsigned long long* pushed, int nsm, int blocks_per_sm,
                          cudaStream_t s) {
-  const size_t smem = Plan<T, P>::total;
+  const size_t smem = Plan<T, DIM, P>::total;
   static bool configured = false;  // per template instance, once per process
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(k_pd1<T, DIM, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -713,15 +695,16 @@ cudaError_t launch_push_deposit_runs(int ppt, const Geom& g, const Tables& tb, c
                                      unsigned long long* pushed, int nsm, cudaStream_t s) {
   if (sp.capacity <= 0) return cudaSuccess;
   const bool d3 = g.dim == 3;
-  if (sizeof(T) == 8) {
+  if constexpr (sizeof(T) == 8) {
     return d3 ? launch_pd1_p<T, 3, 4>(g, tb, f, sp, prescribed, status, pushed, nsm, 2, s)
               : launch_pd1_p<T, 2, 4>(g, tb, f, sp, prescribed, status, pushed, nsm, 2, s);
+  } else {
+    if (ppt == 4)
+      return d3 ? launch_pd1_p<T, 3, 4>(g, tb, f, sp, prescribed, status, pushed, nsm, 4, s)
+                : launch_pd1_p<T, 2, 4>(g, tb, f, sp, prescribed, status, pushed, nsm, 4, s);
+    return d3 ? launch_pd1_p<T, 3, 8>(g, tb, f, sp, prescribed, status, pushed, nsm, 3, s)
+              : launch_pd1_p<T, 2, 8>(g, tb, f, sp, prescribed, status, pushed, nsm, 3, s);
   }
-  if (ppt == 4)
-    return d3 ? launch_pd1_p<T, 3, 4>(g, tb, f, sp, prescribed, status, pushed, nsm, 4, s)
-              : launch_pd1_p<T, 2, 4>(g, tb, f, sp, prescribed, status, pushed, nsm, 4, s);
-  return d3 ? launch_pd1_p<T, 3, 8>(g, tb, f, sp, prescribed, status, pushed, nsm, 3, s)
-            : launch_pd1_p<T, 2, 8>(g, tb, f, sp, prescribed, status, pushed, nsm, 3, s);
 }
 
 template cudaError_t launch_push_deposit_runs<float>(int, const Geom&, const Tables&, const FieldPtrs<float>&,

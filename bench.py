@@ -134,6 +134,20 @@ def count_cells():
     return total, interior, total - interior
 
 
+def combine_ranks(ms, psteps, ms_e2e, ps_e2e, world, device):
+    """Whole-job figures of N replicas: the slowest rank's times (max over
+    ranks) and the particle-steps of all ranks (sum)."""
+    if world == 1:
+        return ms, psteps, ms_e2e, ps_e2e
+    import torch
+    vals = torch.tensor([ms, psteps, ms_e2e, ps_e2e], dtype=torch.float64, device=device)
+    mx = vals.clone()
+    torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
+    sm = vals.clone()
+    torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1]), float(mx[2]), float(sm[3])
+
+
 def run_gpu(args, rank, world):
     import torch
     from paper_2201_09084_gb300 import inputs as I
@@ -228,14 +242,7 @@ def run_gpu(args, rank, world):
     nsteps_e2e = args.warmup + args.steps
 
     # ---- reductions over ranks ----
-    vals = torch.tensor([ms, psteps, ms_e2e, ps_e2e], dtype=torch.float64, device="cuda")
-    if world > 1:
-        mx = vals.clone()
-        torch.distributed.all_reduce(mx, op=torch.distributed.ReduceOp.MAX)
-        sm = vals.clone()
-        torch.distributed.all_reduce(sm, op=torch.distributed.ReduceOp.SUM)
-        ms, ms_e2e = float(mx[0]), float(mx[2])
-        psteps, ps_e2e = float(sm[1]), float(sm[3])
+    ms, psteps, ms_e2e, ps_e2e = combine_ranks(ms, psteps, ms_e2e, ps_e2e, world, "cuda")
     value = psteps / (ms / 1e3)
     total_cells, n_int, n_pml = count_cells()
     cell_updates = world * total_cells * args.steps / (ms / 1e3)

@@ -1,0 +1,61 @@
+"""Multi-rank host logic of bench.py on CPU: world size 2 over gloo.
+
+The replicas' figures combine as the slowest rank's time and the sum of the
+particle-steps; under --impl reference only rank 0 works and prints."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _rank_main(rank, world, port, out):
+    import torch.distributed as dist
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms, ps, ms2, ps2 = [(10.0, 100.0, 20.0, 110.0), (12.0, 90.0, 19.0, 95.0)][rank]
+    r = bench.combine_ranks(ms, ps, ms2, ps2, world, "cpu")
+    dist.barrier()
+    dist.destroy_process_group()
+    out.put((rank, r))
+
+
+def test_combine_ranks_gloo_world2():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r in range(2):
+        assert res[r] == (12.0, 190.0, 20.0, 205.0)
+
+
+def test_reference_arm_other_ranks_do_no_work():
+    import argparse
+    import bench
+    args = argparse.Namespace(steps=1, warmup=3, order=1, theta=0.0)
+    assert bench.run_reference(args, rank=1, world=2) is None
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench.combine_ranks(1.0, 2.0, 3.0, 4.0, 1, "cpu") == (1.0, 2.0, 3.0, 4.0)

@@ -158,35 +158,43 @@ struct Acc1 {
     }
   }
 
+  // Box offset of flat index idx (component array comp * NBOX + node offset)
+  // in a box with row length BX and plane size BXY.
+  template <int BX, int BXY, int NBOX>
+  __device__ __forceinline__ static int box_offset(int idx) {
+    int comp, ix, jy, kz;
+    node_of(idx, comp, ix, jy, kz);
+    return comp * NBOX + ix + BX * jy + BXY * kz;
+  }
+
   // Adds this thread's sums into the shared-memory current box at the local
-  // anchor (ax, ay, az); bx, bxy: box row and plane lengths.
-  __device__ __forceinline__ void flush_box(T* J, int NBS, int ax, int ay, int az, int bx, int bxy) const {
+  // anchor node a (linear box index).
+  template <int BX, int BXY, int NBOX>
+  __device__ __forceinline__ void flush_box(T* J, int a) const {
 #pragma unroll
     for (int t = 0; t < NV; ++t) {
       const T val = v[t];
-      if (val == T(0)) continue;
-      int comp, ix, jy, kz;
-      node_of(t, comp, ix, jy, kz);
-      atomicAdd(J + comp * NBS + (ax + ix) + bx * (ay + jy) + bxy * (az + kz), val);
+      if (val != T(0)) atomicAdd(J + a + box_offset<BX, BXY, NBOX>(t), val);
     }
   }
 
   // Sums the accumulators of the lanes with member == true (one anchor) by a
   // reduce-scatter of shuffles into a scratch array: after five halving steps
   // lane L holds the group's sums of flat indices K L .. K L + K - 1
-  // (K = NVP / 32), which it adds to the box.  Every lane takes part (lanes
-  // outside the group contribute zeros and carry partial sums) and keeps its
-  // own accumulators for its own group.
-  __device__ __forceinline__ void group_flush(bool member, int lane, T* J, int NBS, int ax, int ay, int az, int bx,
-                                              int bxy) const {
+  // (K = NVP / 32), which it adds to the box at offsets goff (precomputed per
+  // lane, -1 past the last index).  Every lane takes part (lanes outside the
+  // group contribute zeros and carry partial sums) and keeps its own
+  // accumulators for its own group.
+  template <bool ALL>
+  __device__ __forceinline__ void group_flush(bool member, int lane, T* J, int a, const int* goff) const {
     constexpr int H = NVP / 2;
     T t[H];
     {
       const bool up = (lane & 16) != 0;
 #pragma unroll
       for (int i = 0; i < H; ++i) {
-        const T lo = (i < NV && member) ? v[i < NV ? i : 0] : T(0);
-        const T hi = (i + H < NV && member) ? v[i + H < NV ? i + H : 0] : T(0);
+        const T lo = (i < NV && (ALL || member)) ? v[i < NV ? i : 0] : T(0);
+        const T hi = (i + H < NV && (ALL || member)) ? v[i + H < NV ? i + H : 0] : T(0);
         t[i] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, 16);
       }
     }
@@ -203,24 +211,20 @@ struct Acc1 {
     }
     constexpr int K = NVP / 32;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      const int idx = k + K * lane;
-      const T val = t[k];
-      if (idx < NV && val != T(0)) {
-        int comp, ix, jy, kz;
-        node_of(idx, comp, ix, jy, kz);
-        atomicAdd(J + comp * NBS + (ax + ix) + bx * (ay + jy) + bxy * (az + kz), val);
-      }
-    }
+    for (int k = 0; k < K; ++k)
+      if (goff[k] >= 0 && t[k] != T(0)) atomicAdd(J + a + goff[k], t[k]);
   }
 };
 
 constexpr int kNT = 128;
 
 // Shared memory of one block: the staged chunk (NW words per particle, rows
-// padded to P+1), the field box (E and time-averaged B, 6 arrays of NBMAX
-// nodes; its first 3 arrays are the current box after the push), the
-// counters and the permutation of the anchor sort.
+// padded to P+1), the field box (E and time-averaged B, 6 arrays of NBOX
+// nodes with fixed strides BX, BX*BY, so every gather and deposit offset is a
+// compile-time constant; its first 3 arrays are the current box after the
+// push), the counters and the permutation of the anchor sort.  The box holds
+// nodes lo-1 .. hi+2 of a chunk whose cells span lo .. hi: up to 9 cells
+// along x (two x-adjacent 4-cell sort tiles) and 5 along y and z.
 // Stage words: 0-2 old offsets, 3 weight, 4-6 u, 7 old cell, 8-10 new
 // offsets, 11 new cell (-1: removed or deposits nothing), 12 (2D) w v_y/c.
 template <typename T, int DIM, int P>
@@ -229,24 +233,26 @@ struct Plan {
   static constexpr int ROW = kNT * PP;
   static constexpr int C = kNT * P;
   static constexpr int NW = DIM == 3 ? 12 : 13;
-  static constexpr int NBMAX = sizeof(T) == 4 ? (P >= 8 ? 512 : 768) : 384;
+  static constexpr int BX = 12, BY = DIM == 3 ? 8 : 1, BZ = 8;
+  static constexpr int BXY = BX * BY;
+  static constexpr int NBOX = BXY * BZ;
   static constexpr size_t stage = (size_t)NW * ROW * sizeof(T);
-  static constexpr size_t box = (size_t)6 * NBMAX * sizeof(T);
-  static constexpr size_t cnt = (size_t)(NBMAX + 1) * sizeof(int);
+  static constexpr size_t box = (size_t)6 * NBOX * sizeof(T);
+  static constexpr size_t cnt = (size_t)(NBOX + 1) * sizeof(int);
   static constexpr size_t perm = (size_t)C * sizeof(unsigned short);
   static constexpr size_t total = stage + box + cnt + perm;
 };
 
-// Order-1 interpolation from a shared-memory box (local base indices).
-template <int DIM, typename T>
-__device__ __forceinline__ T interp_box(const T* F, int bx, int bxy, int li, const T* wx, int lj, const T* wy, int lk,
-                                        const T* wz) {
+// Order-1 interpolation from a shared-memory box with fixed strides; b is
+// the box index of the lowest of the 8 (4 in 2D) nodes.
+template <int DIM, int BX, int BXY, typename T>
+__device__ __forceinline__ T interp_box(const T* F, int b, const T* wx, const T* wy, const T* wz) {
   T acc = T(0);
 #pragma unroll
   for (int tz = 0; tz < 2; ++tz)
 #pragma unroll
     for (int ty = 0; ty < (DIM == 3 ? 2 : 1); ++ty) {
-      const T* row = F + li + bx * (lj + ty) + bxy * (lk + tz);
+      const T* row = F + b + BX * ty + BXY * tz;
       acc += (DIM == 3 ? wy[ty] : T(1)) * wz[tz] * (wx[0] * row[0] + wx[1] * row[1]);
     }
   return acc;
@@ -355,7 +361,9 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
           unsigned long long* pushed_total) {
   using PL = Plan<T, DIM, P>;
   using AC = Acc1<T, DIM>;
-  constexpr int PP = PL::PP, ROW = PL::ROW, C = PL::C, NBMAX = PL::NBMAX;
+  constexpr int PP = PL::PP, ROW = PL::ROW, C = PL::C;
+  constexpr int BX = PL::BX, BY = PL::BY, BZ = PL::BZ, BXY = PL::BXY, NBOX = PL::NBOX;
+  constexpr int K = AC::NVP / 32;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* stg = reinterpret_cast<T*>(smraw);
   T* bx_ = reinterpret_cast<T*>(smraw + PL::stage);
@@ -370,6 +378,13 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
   const long long nchunks = (n + C - 1) / C;
   unsigned pushed = 0;
   if (sp.immobile) return;
+  // box offsets of the two (2D: one) reduce-scatter results this lane adds
+  int goff[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int idx = k + K * lane;
+    goff[k] = idx < AC::NV ? AC::template box_offset<BX, BXY, NBOX>(idx) : -1;
+  }
 
   for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const long long base = ch * C;
@@ -442,7 +457,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
       // node minus one (half-staggered components) to its upper node, the
       // deposit stencil of a move spans min(old, new cell) .. + 2
       const int dx = hi[0] - lo[0] + 4, dy = DIM == 3 ? hi[1] - lo[1] + 4 : 1, dz = hi[2] - lo[2] + 4;
-      if (use && (long long)dx * dy * dz > NBMAX) use = 0;
+      if (use && (dx > BX || dy > BY || dz > BZ)) use = 0;
       s_use_box = use;
       s_geo[0] = lo[0] - 1;
       s_geo[1] = DIM == 3 ? lo[1] - 1 : 0;
@@ -457,18 +472,18 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
     if (use_box) {
       const int ox = s_geo[0], oy = s_geo[1], oz = s_geo[2];
       const int bdx = s_geo[3], bdy = s_geo[4], bdz = s_geo[5];
-      const int bxy = bdx * bdy;
-      const int NB = bdx * bdy * bdz;
+      const int NB = bdx * bdy * bdz;   // nodes of the chunk's region (row length bdx)
       // ---- 2. E and the time-averaged B of the box ----
       for (int t = tid; t < NB; t += kNT) {
         const int li = t % bdx, r = t / bdx, lj = r % bdy, lk = r / bdy;
         const long long gi = g.idx(ox + li, oy + lj, oz + lk);
-        bx_[0 * NBMAX + t] = f.E[0][gi];
-        bx_[1 * NBMAX + t] = f.E[1][gi];
-        bx_[2 * NBMAX + t] = f.E[2][gi];
-        bx_[3 * NBMAX + t] = T(0.5) * (f.Bh[0][gi] + f.Bp[0][gi]);
-        bx_[4 * NBMAX + t] = T(0.5) * (f.Bh[1][gi] + f.Bp[1][gi]);
-        bx_[5 * NBMAX + t] = T(0.5) * (f.Bh[2][gi] + f.Bp[2][gi]);
+        const int bi = li + BX * lj + BXY * lk;
+        bx_[0 * NBOX + bi] = f.E[0][gi];
+        bx_[1 * NBOX + bi] = f.E[1][gi];
+        bx_[2 * NBOX + bi] = f.E[2][gi];
+        bx_[3 * NBOX + bi] = T(0.5) * (f.Bh[0][gi] + f.Bp[0][gi]);
+        bx_[4 * NBOX + bi] = T(0.5) * (f.Bh[1][gi] + f.Bp[1][gi]);
+        bx_[5 * NBOX + bi] = T(0.5) * (f.Bh[2][gi] + f.Bp[2][gi]);
       }
       __syncthreads();
       // ---- A. gather, push and move this thread's P particles ----
@@ -501,12 +516,14 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
           const int l0x = b0[0] - ox, lhx = bh[0] - ox, l0y = b0[1] - oy, lhy = bh[1] - oy, l0z = b0[2] - oz,
                     lhz = bh[2] - oz;
           T E[3], B[3];
-          E[0] = interp_box<DIM, T>(bx_ + 0 * NBMAX, bdx, bxy, lhx, wh[0], l0y, w0[1], l0z, w0[2]);
-          E[1] = interp_box<DIM, T>(bx_ + 1 * NBMAX, bdx, bxy, l0x, w0[0], lhy, wh[1], l0z, w0[2]);
-          E[2] = interp_box<DIM, T>(bx_ + 2 * NBMAX, bdx, bxy, l0x, w0[0], l0y, w0[1], lhz, wh[2]);
-          B[0] = interp_box<DIM, T>(bx_ + 3 * NBMAX, bdx, bxy, l0x, w0[0], lhy, wh[1], lhz, wh[2]);
-          B[1] = interp_box<DIM, T>(bx_ + 4 * NBMAX, bdx, bxy, lhx, wh[0], l0y, w0[1], lhz, wh[2]);
-          B[2] = interp_box<DIM, T>(bx_ + 5 * NBMAX, bdx, bxy, lhx, wh[0], lhy, wh[1], l0z, w0[2]);
+          // box index of the lowest node per (x, y, z) stagger combination
+          const int sx0 = l0x, sxh = lhx, sy0 = BX * l0y, syh = BX * lhy, sz0 = BXY * l0z, szh = BXY * lhz;
+          E[0] = interp_box<DIM, BX, BXY, T>(bx_ + 0 * NBOX, sxh + sy0 + sz0, wh[0], w0[1], w0[2]);
+          E[1] = interp_box<DIM, BX, BXY, T>(bx_ + 1 * NBOX, sx0 + syh + sz0, w0[0], wh[1], w0[2]);
+          E[2] = interp_box<DIM, BX, BXY, T>(bx_ + 2 * NBOX, sx0 + sy0 + szh, w0[0], w0[1], wh[2]);
+          B[0] = interp_box<DIM, BX, BXY, T>(bx_ + 3 * NBOX, sx0 + syh + szh, w0[0], wh[1], wh[2]);
+          B[1] = interp_box<DIM, BX, BXY, T>(bx_ + 4 * NBOX, sxh + sy0 + szh, wh[0], w0[1], wh[2]);
+          B[2] = interp_box<DIM, BX, BXY, T>(bx_ + 5 * NBOX, sxh + syh + sz0, wh[0], wh[1], w0[2]);
           boris<T>(u, E, B, sp.ke);
         }
         ++pushed;
@@ -526,17 +543,17 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
       // ---- B. counting sort of the chunk by box-local anchor ----
       // (the E/B box is dead: its first three arrays become the current box)
       T* const BJ = bx_;
-      for (int t = tid; t < 3 * NBMAX; t += kNT) BJ[t] = T(0);
-      for (int t = tid; t <= NB; t += kNT) cnt[t] = 0;
+      for (int t = tid; t < 3 * NBOX; t += kNT) BJ[t] = T(0);
+      for (int t = tid; t <= NBOX; t += kNT) cnt[t] = 0;
       __syncthreads();
       auto anchor_key = [&](int slot) -> int {
         const int c0 = bits_to_cell<T>(stg[7 * ROW + slot]);
         const int c1 = bits_to_cell<T>(stg[11 * ROW + slot]);
-        if (c0 < 0 || c1 < 0) return NB;
+        if (c0 < 0 || c1 < 0) return NBOX;
         const int ax = min(cell_i(c0), cell_i(c1)) - ox;
         const int ay = DIM == 3 ? min(cell_j(c0), cell_j(c1)) - oy : 0;
         const int az = min(cell_k(c0), cell_k(c1)) - oz;
-        return ax + bdx * (ay + bdy * az);
+        return ax + BX * ay + BXY * az;
       };
       for (int k = 0; k < P; ++k) {
         const int q = tid + k * kNT;
@@ -545,12 +562,12 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
         if (lane == __ffs(m) - 1) atomicAdd(cnt + key, __popc(m));
       }
       __syncthreads();
-      {  // exclusive scan of cnt[0..NB]
-        const int per = (NB + 1 + kNT - 1) / kNT;
+      {  // exclusive scan of cnt[0..NBOX]
+        const int per = (NBOX + 1 + kNT - 1) / kNT;
         const int b0 = tid * per;
         int loc = 0;
         for (int t = 0; t < per; ++t)
-          if (b0 + t <= NB) loc += cnt[b0 + t];
+          if (b0 + t <= NBOX) loc += cnt[b0 + t];
         int inc = loc;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -563,7 +580,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
         for (int w8 = 0; w8 < warp; ++w8) wofs += s_scan[w8];
         int run = wofs + inc - loc;
         for (int t = 0; t < per; ++t)
-          if (b0 + t <= NB) {
+          if (b0 + t <= NBOX) {
             const int c0 = cnt[b0 + t];
             cnt[b0 + t] = run;
             run += c0;
@@ -605,9 +622,9 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
           }
           esk_axis<1, T>(c0[a], stg[a * ROW + slot], c1[a], stg[(8 + a) * ROW + slot], lo[a], S0[a], DS[a]);
         }
-        const int k = pack_cell(lo[0] - ox, DIM == 3 ? lo[1] - oy : 0, lo[2] - oz);
+        const int k = (lo[0] - ox) + BX * (DIM == 3 ? lo[1] - oy : 0) + BXY * (lo[2] - oz);
         if (k != key) {
-          if (key >= 0) acc.flush_box(BJ, NBMAX, cell_i(key), cell_j(key), cell_k(key), bdx, bxy);
+          if (key >= 0) acc.template flush_box<BX, BXY, NBOX>(BJ, key);
           acc.zero();
           key = k;
         }
@@ -622,7 +639,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
         const int gk = __shfl_sync(0xffffffffu, key, leader);
         const bool mem = key == gk;
         pend &= ~__ballot_sync(0xffffffffu, mem);
-        acc.group_flush(mem, lane, BJ, NBMAX, cell_i(gk), cell_j(gk), cell_k(gk), bdx, bxy);
+        acc.template group_flush<false>(mem, lane, BJ, gk, goff);
       }
       __syncthreads();
       // ---- D. add the current box to the grid with the charge factor and alpha ----
@@ -634,9 +651,10 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
       const T* acz = al_cent<T>(tb, 2);
       const T qy = DIM == 3 ? sp.cj[1] : sp.cjy2d;
       for (int t = tid; t < NB; t += kNT) {
-        const T j0 = BJ[t], j1 = BJ[NBMAX + t], j2 = BJ[2 * NBMAX + t];
-        if (j0 == T(0) && j1 == T(0) && j2 == T(0)) continue;
         const int li = t % bdx, r = t / bdx, lj = r % bdy, lk = r / bdy;
+        const int bi = li + BX * lj + BXY * lk;
+        const T j0 = BJ[bi], j1 = BJ[NBOX + bi], j2 = BJ[2 * NBOX + bi];
+        if (j0 == T(0) && j1 == T(0) && j2 == T(0)) continue;
         const int gi = ox + li, gj = oy + lj, gk = oz + lk;
         const long long id = g.idx(gi, gj, gk);
         const T ay_n = DIM == 3 ? any[gj] : T(1), ay_c = DIM == 3 ? acy[gj] : T(1);

@@ -20,7 +20,10 @@
 //      to the box with two shared-memory atomics per lane;
 //   D. add the box to the grid with the charge factor and alpha (Eq. alpha,
 //      at each component's staggered location): the damping of Eq. MaxwellE's
-//      source term applied once per node in the flush; write the chunk back.
+//      source term applied once per node in the flush.
+// The pushed records are written back from phase A directly (a thread's P
+// particles are consecutive, so a warp's stores cover whole lines over its P
+// iterations and merge in L2).
 // A chunk whose box does not fit in shared memory (sparse particles) takes a
 // per-particle path with global loads and atomics.
 #include "particle_common.cuh"
@@ -225,14 +228,15 @@ constexpr int kNT = 128;
 // push), the counters and the permutation of the anchor sort.  The box holds
 // nodes lo-1 .. hi+2 of a chunk whose cells span lo .. hi: up to 9 cells
 // along x (two x-adjacent 4-cell sort tiles) and 5 along y and z.
-// Stage words: 0-2 old offsets, 3 weight, 4-6 u, 7 old cell, 8-10 new
-// offsets, 11 new cell (-1: removed or deposits nothing), 12 (2D) w v_y/c.
+// Stage words: 0-2 old offsets, 3 weight, 4-6 u (replaced by the new offsets
+// once the particle is pushed and its record written back), 7 old cell,
+// 8 new cell (-1: removed or deposits nothing), 9 (2D) w v_y/c.
 template <typename T, int DIM, int P>
 struct Plan {
   static constexpr int PP = P + 1;
   static constexpr int ROW = kNT * PP;
   static constexpr int C = kNT * P;
-  static constexpr int NW = DIM == 3 ? 12 : 13;
+  static constexpr int NW = DIM == 3 ? 9 : 10;
   static constexpr int BX = 12, BY = DIM == 3 ? 8 : 1, BZ = 8;
   static constexpr int BXY = BX * BY;
   static constexpr int NBOX = BXY * BZ;
@@ -304,19 +308,20 @@ __device__ __forceinline__ bool move_particle(const Geom& g, const T o[3], const
 
 // The whole step of one particle from global memory (chunks whose box does
 // not fit in shared memory): gather, push, move, deposit with global atomics
-// (charge factor and alpha per contribution).  Reads and writes the stage.
+// (charge factor and alpha per contribution), and the particle's record is
+// written back.  Returns 1 if the particle was pushed.
 template <typename T, int DIM>
 __device__ __noinline__ unsigned particle_global(const Geom& g, const Tables& tb, const FieldPtrs<T>& f,
-                                                 const SpeciesPtrs<T>& sp, int prescribed, T* stg, int slot, int ROW) {
+                                                 const SpeciesPtrs<T>& sp, int prescribed, const T* stg, int slot,
+                                                 int ROW, long long gp) {
   const int cell = bits_to_cell<T>(stg[7 * ROW + slot]);
-  T o[3] = {stg[0 * ROW + slot], stg[1 * ROW + slot], stg[2 * ROW + slot]};
-  stg[8 * ROW + slot] = o[0];
-  stg[9 * ROW + slot] = o[1];
-  stg[10 * ROW + slot] = o[2];
-  stg[11 * ROW + slot] = cell_to_bits<T>(-1);
-  if (cell < 0) return 0;
+  const T o[3] = {stg[0 * ROW + slot], stg[1 * ROW + slot], stg[2 * ROW + slot]};
   const T w = stg[3 * ROW + slot];
   T u[3] = {stg[4 * ROW + slot], stg[5 * ROW + slot], stg[6 * ROW + slot]};
+  if (cell < 0) {
+    PIO<T>::store(sp.pos, sp.mom, gp, o, w, u, -1);
+    return 0;
+  }
   const int c[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
   if (!prescribed) {
     int b0[3], bh[3];
@@ -340,17 +345,11 @@ __device__ __noinline__ unsigned particle_global(const Geom& g, const Tables& tb
     B[2] = interp_avg<1, DIM, T>(g, f.Bh[2], f.Bp[2], bh[0], wh[0], bh[1], wh[1], b0[2], w0[2]);
     boris<T>(u, E, B, sp.ke);
   }
-  stg[4 * ROW + slot] = u[0];
-  stg[5 * ROW + slot] = u[1];
-  stg[6 * ROW + slot] = u[2];
   int c1[3];
   T o1[3], ig;
-  if (!move_particle<DIM, T>(g, o, c, u, c1, o1, ig)) return 1;
-  stg[8 * ROW + slot] = o1[0];
-  stg[9 * ROW + slot] = o1[1];
-  stg[10 * ROW + slot] = o1[2];
-  stg[11 * ROW + slot] = cell_to_bits<T>(pack_cell(c1[0], c1[1], c1[2]));
-  deposit_one<1, DIM, T>(g, tb, f, sp, c, o, c1, o1, w, u[1] * ig);
+  const bool in = move_particle<DIM, T>(g, o, c, u, c1, o1, ig);
+  PIO<T>::store(sp.pos, sp.mom, gp, in ? o1 : o, w, u, in ? pack_cell(c1[0], c1[1], c1[2]) : -1);
+  if (in) deposit_one<1, DIM, T>(g, tb, f, sp, c, o, c1, o1, w, u[1] * ig);
   return 1;
 }
 
@@ -486,19 +485,20 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
         bx_[5 * NBOX + bi] = T(0.5) * (f.Bh[2][gi] + f.Bp[2][gi]);
       }
       __syncthreads();
-      // ---- A. gather, push and move this thread's P particles ----
+      // ---- A. gather, push and move this thread's P particles; the new
+      //      records go straight back to global memory ----
       for (int i = 0; i < P; ++i) {
         const int slot = tid * PP + i;
+        const long long gp = base + tid * P + i;
         const int cell = bits_to_cell<T>(stg[7 * ROW + slot]);
-        T o[3] = {stg[0 * ROW + slot], stg[1 * ROW + slot], stg[2 * ROW + slot]};
+        const T o[3] = {stg[0 * ROW + slot], stg[1 * ROW + slot], stg[2 * ROW + slot]};
+        const T w = stg[3 * ROW + slot];
+        T u[3] = {stg[4 * ROW + slot], stg[5 * ROW + slot], stg[6 * ROW + slot]};
         if (cell < 0) {
-          stg[8 * ROW + slot] = o[0];
-          stg[9 * ROW + slot] = o[1];
-          stg[10 * ROW + slot] = o[2];
-          stg[11 * ROW + slot] = cell_to_bits<T>(-1);
+          stg[8 * ROW + slot] = cell_to_bits<T>(-1);
+          if (gp < n) PIO<T>::store(sp.pos, sp.mom, gp, o, w, u, -1);
           continue;
         }
-        T u[3] = {stg[4 * ROW + slot], stg[5 * ROW + slot], stg[6 * ROW + slot]};
         const int c[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
         if (!prescribed) {
           int b0[3], bh[3];
@@ -527,17 +527,16 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
           boris<T>(u, E, B, sp.ke);
         }
         ++pushed;
-        stg[4 * ROW + slot] = u[0];
-        stg[5 * ROW + slot] = u[1];
-        stg[6 * ROW + slot] = u[2];
         int c1[3];
         T o1[3], ig;
         const bool in = move_particle<DIM, T>(g, o, c, u, c1, o1, ig);
-        stg[8 * ROW + slot] = in ? o1[0] : o[0];
-        stg[9 * ROW + slot] = in ? o1[1] : o[1];
-        stg[10 * ROW + slot] = in ? o1[2] : o[2];
-        stg[11 * ROW + slot] = cell_to_bits<T>(in ? pack_cell(c1[0], c1[1], c1[2]) : -1);
-        if constexpr (DIM == 2) stg[12 * ROW + slot] = stg[3 * ROW + slot] * u[1] * ig;
+        const int cell1 = in ? pack_cell(c1[0], c1[1], c1[2]) : -1;
+        PIO<T>::store(sp.pos, sp.mom, gp, in ? o1 : o, w, u, cell1);
+        stg[4 * ROW + slot] = o1[0];
+        stg[5 * ROW + slot] = o1[1];
+        stg[6 * ROW + slot] = o1[2];
+        stg[8 * ROW + slot] = cell_to_bits<T>(cell1);
+        if constexpr (DIM == 2) stg[9 * ROW + slot] = w * u[1] * ig;
       }
       __syncthreads();
       // ---- B. counting sort of the chunk by box-local anchor ----
@@ -548,7 +547,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
       __syncthreads();
       auto anchor_key = [&](int slot) -> int {
         const int c0 = bits_to_cell<T>(stg[7 * ROW + slot]);
-        const int c1 = bits_to_cell<T>(stg[11 * ROW + slot]);
+        const int c1 = bits_to_cell<T>(stg[8 * ROW + slot]);
         if (c0 < 0 || c1 < 0) return NBOX;
         const int ax = min(cell_i(c0), cell_i(c1)) - ox;
         const int ay = DIM == 3 ? min(cell_j(c0), cell_j(c1)) - oy : 0;
@@ -605,7 +604,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
       int key = -1;
       for (int i = 0; i < P; ++i) {
         const int slot = perm[tid * P + i];
-        const int cell1 = bits_to_cell<T>(stg[11 * ROW + slot]);
+        const int cell1 = bits_to_cell<T>(stg[8 * ROW + slot]);
         const int cell0 = bits_to_cell<T>(stg[7 * ROW + slot]);
         if (cell1 < 0 || cell0 < 0) continue;
         const int c0[3] = {cell_i(cell0), cell_j(cell0), cell_k(cell0)};
@@ -620,7 +619,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
             DS[1][0] = DS[1][1] = DS[1][2] = T(0);
             continue;
           }
-          esk_axis<1, T>(c0[a], stg[a * ROW + slot], c1[a], stg[(8 + a) * ROW + slot], lo[a], S0[a], DS[a]);
+          esk_axis<1, T>(c0[a], stg[a * ROW + slot], c1[a], stg[(4 + a) * ROW + slot], lo[a], S0[a], DS[a]);
         }
         const int k = (lo[0] - ox) + BX * (DIM == 3 ? lo[1] - oy : 0) + BXY * (lo[2] - oz);
         if (k != key) {
@@ -629,7 +628,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
           key = k;
         }
         T wvy = T(0);
-        if constexpr (DIM == 2) wvy = stg[12 * ROW + slot];
+        if constexpr (DIM == 2) wvy = stg[9 * ROW + slot];
         acc.add(S0, DS, stg[3 * ROW + slot], wvy);
       }
       // lanes that share an anchor sum their runs; one group at a time
@@ -664,18 +663,10 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
       }
     } else {
       // sparse chunk: one particle at a time from global memory
-      for (int i = 0; i < P; ++i)
-        pushed += particle_global<T, DIM>(g, tb, f, sp, prescribed, stg, tid * PP + i, ROW);
-    }
-    __syncthreads();
-    // ---- write the chunk back (coalesced) ----
-    for (int q = tid; q < C; q += kNT) {
-      const long long gp = base + q;
-      if (gp >= n) break;
-      const int slot = (q / P) * PP + (q % P);
-      const T o[3] = {stg[8 * ROW + slot], stg[9 * ROW + slot], stg[10 * ROW + slot]};
-      const T u[3] = {stg[4 * ROW + slot], stg[5 * ROW + slot], stg[6 * ROW + slot]};
-      PIO<T>::store(sp.pos, sp.mom, gp, o, stg[3 * ROW + slot], u, bits_to_cell<T>(stg[11 * ROW + slot]));
+      for (int i = 0; i < P; ++i) {
+        const long long gp = base + tid * P + i;
+        if (gp < n) pushed += particle_global<T, DIM>(g, tb, f, sp, prescribed, stg, tid * PP + i, ROW, gp);
+      }
     }
   }
   if (pushed_total) {

@@ -242,7 +242,10 @@ struct Plan {
   static constexpr int NBOX = BXY * BZ;
   static constexpr size_t stage = (size_t)NW * ROW * sizeof(T);
   static constexpr size_t box = (size_t)6 * NBOX * sizeof(T);
-  static constexpr size_t cnt = (size_t)(NBOX + 1) * sizeof(int);
+  // anchor counters; reused as the list of deferred particles (up to C)
+  static constexpr size_t cnt = (size_t)(NBOX + 1) * sizeof(int) > (size_t)C * sizeof(unsigned short)
+                                    ? (size_t)(NBOX + 1) * sizeof(int)
+                                    : (size_t)C * sizeof(unsigned short);
   static constexpr size_t perm = (size_t)C * sizeof(unsigned short);
   static constexpr size_t total = stage + box + cnt + perm;
 };
@@ -372,6 +375,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
   __shared__ int s_geo[8];   // box origin x, y, z and dims x, y, z
   __shared__ int s_use_box;
   __shared__ int s_scan[kNT / 32];
+  __shared__ int s_ndefer;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long n = *sp.n_dev;
   const long long nchunks = (n + C - 1) / C;
@@ -544,6 +548,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
       T* const BJ = bx_;
       for (int t = tid; t < 3 * NBOX; t += kNT) BJ[t] = T(0);
       for (int t = tid; t <= NBOX; t += kNT) cnt[t] = 0;
+      if (tid == 0) s_ndefer = 0;
       __syncthreads();
       auto anchor_key = [&](int slot) -> int {
         const int c0 = bits_to_cell<T>(stg[7 * ROW + slot]);
@@ -599,18 +604,15 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
       }
       __syncthreads();
       // ---- C. deposit runs of P consecutive particles in anchor order ----
-      AC acc;
-      acc.zero();
-      int key = -1;
-      for (int i = 0; i < P; ++i) {
-        const int slot = perm[tid * P + i];
+      // Shape factors of a slot's move; returns the box-local anchor, or -1
+      // for a particle that deposits nothing.
+      auto prepare = [&](int slot, T (&S0)[3][3], T (&DS)[3][3]) -> int {
         const int cell1 = bits_to_cell<T>(stg[8 * ROW + slot]);
         const int cell0 = bits_to_cell<T>(stg[7 * ROW + slot]);
-        if (cell1 < 0 || cell0 < 0) continue;
+        if (cell1 < 0 || cell0 < 0) return -1;
         const int c0[3] = {cell_i(cell0), cell_j(cell0), cell_k(cell0)};
         const int c1[3] = {cell_i(cell1), cell_j(cell1), cell_k(cell1)};
         int lo[3] = {0, 0, 0};
-        T S0[3][3], DS[3][3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           if (DIM == 2 && a == 1) {
@@ -621,15 +623,32 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
           }
           esk_axis<1, T>(c0[a], stg[a * ROW + slot], c1[a], stg[(4 + a) * ROW + slot], lo[a], S0[a], DS[a]);
         }
-        const int k = (lo[0] - ox) + BX * (DIM == 3 ? lo[1] - oy : 0) + BXY * (lo[2] - oz);
-        if (k != key) {
-          if (key >= 0) acc.template flush_box<BX, BXY, NBOX>(BJ, key);
-          acc.zero();
+        return (lo[0] - ox) + BX * (DIM == 3 ? lo[1] - oy : 0) + BXY * (lo[2] - oz);
+      };
+      auto wvy_of = [&](int slot) -> T {
+        if constexpr (DIM == 2) return stg[9 * ROW + slot];
+        return T(0);
+      };
+      // A run keeps the anchor of its first particle; a particle with another
+      // anchor (a run that straddles two anchors after the sort) is deferred
+      // to a list deposited one particle per thread below, so no warp ever
+      // diverges into a flush inside the loop.
+      unsigned short* defer = reinterpret_cast<unsigned short*>(cnt);  // the counters are dead now
+      AC acc;
+      acc.zero();
+      int key = -1;
+      for (int i = 0; i < P; ++i) {
+        const int slot = perm[tid * P + i];
+        T S0[3][3], DS[3][3];
+        const int k = prepare(slot, S0, DS);
+        if (k < 0) continue;
+        if (key < 0) {
           key = k;
+        } else if (k != key) {
+          defer[atomicAdd(&s_ndefer, 1)] = (unsigned short)slot;
+          continue;
         }
-        T wvy = T(0);
-        if constexpr (DIM == 2) wvy = stg[9 * ROW + slot];
-        acc.add(S0, DS, stg[3 * ROW + slot], wvy);
+        acc.add(S0, DS, stg[3 * ROW + slot], wvy_of(slot));
       }
       // lanes that share an anchor sum their runs; one group at a time
       unsigned pend = __ballot_sync(0xffffffffu, key >= 0);
@@ -639,6 +658,16 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
         const bool mem = key == gk;
         pend &= ~__ballot_sync(0xffffffffu, mem);
         acc.template group_flush<false>(mem, lane, BJ, gk, goff);
+      }
+      __syncthreads();
+      const int nd = s_ndefer;
+      for (int e = tid; e < nd; e += kNT) {
+        const int slot = defer[e];
+        T S0[3][3], DS[3][3];
+        const int k = prepare(slot, S0, DS);
+        acc.zero();
+        acc.add(S0, DS, stg[3 * ROW + slot], wvy_of(slot));
+        acc.template flush_box<BX, BXY, NBOX>(BJ, k);
       }
       __syncthreads();
       // ---- D. add the current box to the grid with the charge factor and alpha ----

@@ -134,6 +134,13 @@ def count_cells():
     return total, interior, total - interior
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu
+# capture of the full workload) of the fused order-1 kernel with 4 particles
+# per thread, FP32, theta 0; keyed by (order, particles per thread, prec,
+# theta, particles).  Reset to {} whenever that kernel changes.
+NCU_TRAFFIC = {(1, 4, "fp32", 0.0, NPART): 217743872}
+
+
 def combine_ranks(ms, psteps, ms_e2e, ps_e2e, world, device):
     """Whole-job figures of N replicas: the slowest rank's times (max over
     ranks) and the particle-steps of all ranks (sum)."""
@@ -249,8 +256,12 @@ def run_gpu(args, rank, world):
     n_live_avg = (psteps / world) / args.steps
     b_part, b_field = algorithmic_bytes(n_live_avg, occ, n_int, n_pml, args.prec)
     peak, peak_kind = measured_peak()
+    traffic = None
     if t_pd >= t_f:
-        dom, t_dom, b_dom = "push_deposit (k_particles fused)", t_pd, b_part
+        name = ("k_pd1 (fused order-1 gather/push/move/deposit/damp)" if args.order == 1
+                else "k_particles (fused gather/push/move/deposit/damp)")
+        dom, t_dom, b_dom = name, t_pd, b_part
+        traffic = NCU_TRAFFIC.get((args.order, tuning["particles_per_thread"], args.prec, args.theta, npart))
     else:
         dom, t_dom, b_dom = "field_step (k_field_E + k_field_B)", t_f, b_field
     achieved = b_dom / (t_dom / 1e3) / 1e9
@@ -263,7 +274,7 @@ def run_gpu(args, rank, world):
         "cell_updates_per_s": cell_updates,
         "kernel_ms": {"push_deposit": t_pd, "field_step": t_f},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": f"{peak_kind} (copy)", "traffic": None,
+                     "frac": achieved / peak, "peak_kind": f"{peak_kind} (copy)", "traffic": traffic,
                      "algorithmic_bytes_per_launch": b_dom},
         "e2e": {"value": ps_e2e / (ms_e2e / 1e3), "unit": "particle-steps/s",
                 "h2d_bytes_per_step": 2 * npart * (32 if args.prec == "fp64" else 16) / nsteps_e2e,

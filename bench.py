@@ -138,7 +138,7 @@ def count_cells():
 # capture of the full workload) of the fused order-1 kernel with 4 particles
 # per thread, FP32, theta 0; keyed by (order, particles per thread, prec,
 # theta, particles).  Reset to {} whenever that kernel changes.
-NCU_TRAFFIC = {(1, 4, "fp32", 0.0, NPART): 217743872}
+NCU_TRAFFIC = {}
 
 
 def combine_ranks(ms, psteps, ms_e2e, ps_e2e, world, device):
@@ -384,6 +384,100 @@ def run_reference(args, rank, world):
     return out
 
 
+def run_precision_study(args):
+    """Precision study on the plasma + beam workload (128 x 128 x 256 cells +
+    16-cell PML, electrons and protons 8 per cell, Maxwellian u_th = 0.01,
+    drifting beam at u_z = 5, order 1, sort every 20 steps): the FP32 forms
+    (float-float PML parts, IEEE FP64 parts, int64 deterministic deposition)
+    against the plain FP64 form on the GPU at full size, with each form's
+    throughput; and every form against the FP64 CPU oracle on the same
+    workload reduced to 24 x 24 x 48 + 8 cells for 20 steps (the plasma is
+    chaotic, so forms separate physically after a few tens of steps)."""
+    import torch
+    import oracle as O
+    from paper_2201_09084_gb300 import inputs as I
+    from paper_2201_09084_gb300.api import Sim, pack_particles
+    from paper_2201_09084_gb300 import build as B
+    B.build()
+    names = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
+    forms = [("fp64", "fp64", False), ("fp32", "fp32", False), ("fp32-splitfp64", "fp32", True),
+             ("fixed64", "fixed64", False)]
+
+    def run(nphys, pml, parts, prec, split, steps, marks, dt):
+        sim = Sim(3, nphys, D, pml, dt=dt, order=1, prec=prec, alpha_mode="damped", sort_every=20,
+                  split_fp64=split)
+        keep = []
+        for sp in parts:
+            pos, mom = pack_particles(sp["cell"], sp["off"], sp["u"], sp["w"], prec)
+            sim.add_species(pos, mom, len(sp["w"]), sp["q"], sp["m"], sp["immobile"])
+            keep.append((pos, mom))
+        snaps, done, t = {}, 0, 0.0
+        for m in marks:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sim.step(m - done)
+            e1.record()
+            torch.cuda.synchronize()
+            t += e0.elapsed_time(e1)
+            done = m
+            snaps[m] = {k: sim.field(k).cpu().numpy() for k in names}
+            dg = sim.diag()
+            snaps[m]["gauss"] = dg["gauss"] / dg["rho_scale"] if dg["rho_scale"] > 0 else None
+        ps = sim.particle_steps()
+        sim.close()
+        del keep
+        torch.cuda.empty_cache()
+        return snaps, ps / (t / 1e3)
+
+    def err(a, b):
+        scale = max(max(np.abs(b[k]).max() * (C if k[0] == "B" else 1.0) for k in names), 1e-300)
+        return max(np.abs(a[k] - b[k]).max() * (C if k[0] == "B" else 1.0) for k in names) / scale
+
+    C = 299792458.0
+    out = {"metric": "max relative field error vs FP64", "unit": "1", "higher_is_better": False,
+           "data": "synthetic", "config": {"workload": "precision study: plasma + drifting beam, "
+                                            "128x128x256 + 16-cell PML, 8 ppc e- and p+, u_th 0.01, "
+                                            "beam u_z 5, order 1"}}
+    # full size, GPU forms against the GPU FP64 form
+    nphys, pml = (128, 128, 256), (16,) * 6
+    parts = I.plasma(nphys, pml, D[0])
+    dt = None
+    import oracle as _O
+    dt = _O.yee_dt(D, 0.99, 3)
+    marks = (20, args.steps if args.steps > 20 else 50)
+    res = {}
+    ref = None
+    for label, prec, split in forms:
+        snaps, rate = run(nphys, pml, parts, prec, split, marks[-1], marks, dt)
+        if label == "fp64":
+            ref = snaps
+        res[label] = {"particle_steps_per_s": rate,
+                      "gauss_rel": {str(m): snaps[m]["gauss"] for m in marks},
+                      "err_vs_fp64": {str(m): (err(snaps[m], ref[m]) if ref is not None else 0.0) for m in marks}}
+    out["full_size"] = {"steps": list(marks), "particles": int(sum(len(p["w"]) for p in parts)), "forms": res}
+    # reduced size, every form against the oracle
+    nphys_s, pml_s = (24, 24, 48), (8,) * 6
+    parts_s = I.plasma(nphys_s, pml_s, D[0], beam_radius=4.0, beam_length=12.0)
+    ora = O.OracleSim(3, nphys_s, pml_s, D, dt, order=1, alpha_mode="damped")
+    for sp in parts_s:
+        X = I.absolute(sp["cell"], sp["off"])
+        u = sp["u"].astype(np.float64)
+        ora.add_particles(X[:, 0], X[:, 1], X[:, 2], u[:, 0], u[:, 1], u[:, 2], sp["w"].astype(np.float64),
+                          sp["q"], sp["m"], sp["immobile"])
+    oref = {}
+    for m in (10, 20):
+        ora.step(10)
+        oref[m] = {k: ora.field(k) for k in names}
+    small = {}
+    for label, prec, split in forms:
+        snaps, _ = run(nphys_s, pml_s, parts_s, prec, split, 20, (10, 20), dt)
+        small[label] = {"err_vs_oracle": {str(m): err(snaps[m], oref[m]) for m in (10, 20)},
+                        "gauss_rel": {str(m): snaps[m]["gauss"] for m in (10, 20)}}
+    out["vs_oracle_reduced"] = {"grid": "24x24x48 + 8-cell PML", "steps": [10, 20], "forms": small}
+    out["value"] = small["fp32"]["err_vs_oracle"]["20"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -398,6 +492,8 @@ def main():
     ap.add_argument("--batch-runs", type=int, default=4096, help="number of batched 2D runs")
     ap.add_argument("--particles", type=int, default=NPART,
                     help="beam macroparticles (default 4194304; smaller only for profiling captures)")
+    ap.add_argument("--precision-study", action="store_true",
+                    help="FP32 forms vs FP64 on the plasma + beam workload (prints its own JSON line)")
     ap.add_argument("--tuning", default=None,
                     help="P,KZ launch shapes instead of the autotuner (profiling captures)")
     args = ap.parse_args()
@@ -409,7 +505,9 @@ def main():
         import torch
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         torch.distributed.init_process_group("nccl" if args.impl == "gb300" else "gloo")
-    if args.impl == "reference":
+    if args.precision_study:
+        out = run_precision_study(args) if rank == 0 else None
+    elif args.impl == "reference":
         out = run_reference(args, rank, world)
     else:
         out = run_gpu(args, rank, world)

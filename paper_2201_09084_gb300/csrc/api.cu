@@ -115,8 +115,8 @@ struct picpml_ctx {
   unsigned* sort_scratch = nullptr;
   std::vector<Species> sp;
   int prescribed = 0;
-  int use_runs = 1;   // order-1 fused kernel over sorted runs (else one thread per particle)
-  int ppt = 0;        // particles per thread of the run kernel (0 = default)
+  int ppt = 0;        // order 1: particles per thread of the shared-memory run kernel (4 or 8;
+                      // 0 = default 4), or 1 = one thread per particle with global atomics
   int kz = 1;         // nodes per thread along z in the field kernels
   long long steps_done = 0;
   long long launches = 0;
@@ -216,7 +216,7 @@ int run_particles(picpml_ctx* ctx, int mode) {
     if (s.desc.immobile && mode != 0) continue;
     SpeciesPtrs<T> p = species_ptrs<T>(ctx, s);
     if (s.desc.capacity <= 0) continue;
-    if (mode == 2 && ctx->gd.shape_order == 1 && ctx->use_runs && !ctx->fixed())
+    if (mode == 2 && ctx->gd.shape_order == 1 && ctx->ppt != 1 && !ctx->fixed())
       CK(launch_push_deposit_runs<T>(ctx->ppt, ctx->g, ctx->tb, fields<T>(ctx), p, ctx->prescribed, ctx->status,
                                      ctx->pushed, ctx->nsm, ctx->stream));
     else
@@ -600,9 +600,10 @@ int pic_autotune(picpml_ctx* ctx, int steps, int* ppt, int* kz) {
   };
   const long long launches0 = ctx->launches;
   int best_p = ctx->ppt, best_k = ctx->kz;
-  if (ctx->gd.shape_order == 1 && !f64 && !ctx->fixed()) {
+  if (ctx->gd.shape_order == 1 && !ctx->fixed()) {
     float best = 1e30f;
-    for (int p : {4, 8}) {
+    for (int p : {1, 4, 8}) {
+      if (f64 && p == 8) continue;
       ctx->ppt = p;
       float ms = 0;
       r = time_it(true, &ms);
@@ -634,8 +635,8 @@ int pic_autotune(picpml_ctx* ctx, int steps, int* ppt, int* kz) {
 
 int pic_set_tuning(picpml_ctx* ctx, int ppt, int kz) {
   if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
-  if (!(ppt == 0 || ppt == 4 || ppt == 8) || !(kz == 1 || kz == 2 || kz == 4))
-    return fail(ctx, PIC_EINVAL, "particles per thread must be 0, 4 or 8; z nodes per thread 1, 2 or 4");
+  if (!(ppt == 0 || ppt == 1 || ppt == 4 || ppt == 8) || !(kz == 1 || kz == 2 || kz == 4))
+    return fail(ctx, PIC_EINVAL, "particles per thread must be 0, 1, 4 or 8; z nodes per thread 1, 2 or 4");
   ctx->ppt = ppt;
   ctx->kz = kz;
   return PIC_OK;

@@ -15,9 +15,10 @@
 //   C. deposit: each thread takes P consecutive particles of the anchor order,
 //      so a run mostly shares one anchor, and accumulates the 2x3x3 prefix
 //      values of each component (54 in 3D) in registers; at the end, for each
-//      anchor present in a warp, the warp sums its lanes' values with a
-//      reduce-scatter of shuffles (each lane ends with two sums) and adds them
-//      to the box with two shared-memory atomics per lane;
+//      anchor present in a warp (up to three), the warp sums its lanes' values
+//      with a reduce-scatter of shuffles (each lane ends with two sums) and
+//      adds them to the box with two shared-memory atomics per lane; a warp
+//      holding more anchors (sparse particles) adds each lane's run directly;
 //   D. add the box to the grid with the charge factor and alpha (Eq. alpha,
 //      at each component's staggered location): the damping of Eq. MaxwellE's
 //      source term applied once per node in the flush.
@@ -220,6 +221,9 @@ struct Acc1 {
 };
 
 constexpr int kNT = 128;
+// Most anchors a warp sums by reduce-scatter (about 330 instructions each);
+// above this each lane adds its own run to the current box.
+constexpr int kMaxGroups = 3;
 
 // Shared memory of one block: the staged chunk (NW words per particle, rows
 // padded to P+1), the field box (E and time-averaged B, 6 arrays of NBOX
@@ -650,14 +654,24 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
         }
         acc.add(S0, DS, stg[3 * ROW + slot], wvy_of(slot));
       }
-      // lanes that share an anchor sum their runs; one group at a time
-      unsigned pend = __ballot_sync(0xffffffffu, key >= 0);
-      while (pend) {
-        const int leader = __ffs(pend) - 1;
-        const int gk = __shfl_sync(0xffffffffu, key, leader);
-        const bool mem = key == gk;
-        pend &= ~__ballot_sync(0xffffffffu, mem);
-        acc.template group_flush<false>(mem, lane, BJ, gk, goff);
+      // Lanes that share an anchor sum their runs, one reduce-scatter per
+      // anchor, when the warp holds few anchors (dense particles).  With
+      // many anchors (a few particles per cell) the groups are small, so
+      // each lane adds its own run to the box: few lanes meet on an address.
+      {
+        const int up = __shfl_up_sync(0xffffffffu, key, 1);
+        const bool head = key >= 0 && (lane == 0 || up != key);
+        unsigned pend = __ballot_sync(0xffffffffu, head);
+        if (__popc(pend) <= kMaxGroups) {
+          while (pend) {
+            const int leader = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const int gk = __shfl_sync(0xffffffffu, key, leader);
+            acc.template group_flush<false>(key == gk, lane, BJ, gk, goff);
+          }
+        } else if (key >= 0) {
+          acc.template flush_box<BX, BXY, NBOX>(BJ, key);
+        }
       }
       __syncthreads();
       const int nd = s_ndefer;
@@ -726,7 +740,7 @@ cudaError_t launch_pd1_p(const Geom& g, const Tables& tb, const FieldPtrs<T>& f,
 
 }  // namespace
 
-// Particles per thread P of the run kernel; 0 selects the default.
+// Particles per thread P of the run kernel: 8, else 4 (FP64: always 4).
 template <typename T>
 cudaError_t launch_push_deposit_runs(int ppt, const Geom& g, const Tables& tb, const FieldPtrs<T>& f,
                                      const SpeciesPtrs<T>& sp, int prescribed, unsigned* status,
@@ -737,11 +751,11 @@ cudaError_t launch_push_deposit_runs(int ppt, const Geom& g, const Tables& tb, c
     return d3 ? launch_pd1_p<T, 3, 4>(g, tb, f, sp, prescribed, status, pushed, nsm, 2, s)
               : launch_pd1_p<T, 2, 4>(g, tb, f, sp, prescribed, status, pushed, nsm, 2, s);
   } else {
-    if (ppt == 4)
-      return d3 ? launch_pd1_p<T, 3, 4>(g, tb, f, sp, prescribed, status, pushed, nsm, 4, s)
-                : launch_pd1_p<T, 2, 4>(g, tb, f, sp, prescribed, status, pushed, nsm, 4, s);
-    return d3 ? launch_pd1_p<T, 3, 8>(g, tb, f, sp, prescribed, status, pushed, nsm, 3, s)
-              : launch_pd1_p<T, 2, 8>(g, tb, f, sp, prescribed, status, pushed, nsm, 3, s);
+    if (ppt == 8)
+      return d3 ? launch_pd1_p<T, 3, 8>(g, tb, f, sp, prescribed, status, pushed, nsm, 3, s)
+                : launch_pd1_p<T, 2, 8>(g, tb, f, sp, prescribed, status, pushed, nsm, 3, s);
+    return d3 ? launch_pd1_p<T, 3, 4>(g, tb, f, sp, prescribed, status, pushed, nsm, 4, s)
+              : launch_pd1_p<T, 2, 4>(g, tb, f, sp, prescribed, status, pushed, nsm, 4, s);
   }
 }
 

@@ -109,6 +109,64 @@ def random_particles(dim, n_particles, lo, hi, u_rms=0.5, seed=SEED_BASE + 7, q=
     return [dict(out, q=q, m=m, immobile=False)]
 
 
+EPS0 = 8.8541878128e-12
+C_LIGHT = 299792458.0
+
+
+def plasma_density(u_th, d):
+    """Density n0 whose Debye length u_th c / omega_p equals the cell size d:
+    omega_p = u_th c / d, n0 = eps0 m_e omega_p^2 / e^2."""
+    wp = u_th * C_LIGHT / d
+    return EPS0 * M_E * wp * wp / (Q_E * Q_E)
+
+
+def plasma(nphys, pml, d, ppc=8, u_th=0.01, beam_uz=5.0, beam_radius=16.0, beam_length=64.0,
+           beam_density=0.1, seed=SEED_BASE + 3, box=None):
+    """Neutral electron-proton plasma filling the physical box (3D), ppc
+    macroparticles per cell and species, uniform in each cell; every proton
+    starts at its electron's position (zero charge density at t = 0).
+    Momenta are Maxwellian with u_th (as p/(mc)) for both species.  Density
+    n0 with Debye length = cell size; weight n0 d^3 / ppc.  Plus a drifting
+    electron beam (cylinder of radius beam_radius and length beam_length
+    cells along z, density beam_density n0, u_z = beam_uz) whose front sits
+    beam_length cells before the +z interface, with immobile neutralising
+    ions at the beam electrons' starting positions (so the charge density is
+    zero at t = 0 and Gauss's law holds from the start).  box: optional
+    (lo, hi) absolute cell range the plasma is restricted to (default: the
+    physical box).  Returns [electrons, protons, beam, beam ions] species."""
+    rng = np.random.default_rng(seed)
+    lo = np.array([pml[0], pml[2], pml[4]], dtype=np.float64)
+    hi = lo + np.array(nphys, dtype=np.float64)
+    if box is not None:
+        lo, hi = np.asarray(box[0], dtype=np.float64), np.asarray(box[1], dtype=np.float64)
+    ncell = np.round(hi - lo).astype(np.int64)
+    n0 = plasma_density(u_th, d)
+    w = n0 * d ** 3 / ppc
+    cells = np.stack(np.meshgrid(np.arange(ncell[0]), np.arange(ncell[1]), np.arange(ncell[2]),
+                                 indexing="ij"), -1).reshape(-1, 3)
+    cells = np.repeat(cells, ppc, axis=0)
+    X = lo + cells + rng.random(cells.shape)
+    n = len(X)
+    ue = rng.normal(0.0, u_th, (n, 3))
+    up = rng.normal(0.0, u_th, (n, 3))
+    el = _pack(X, ue, np.full(n, w), 3)
+    pr = _pack(X, up, np.full(n, w), 3)
+    # drifting beam: cylinder along z, front beam_length before the +z interface
+    zf = lo[2] + ncell[2] - beam_length
+    cx, cy = lo[0] + ncell[0] / 2, lo[1] + ncell[1] / 2
+    vol = np.pi * beam_radius ** 2 * beam_length
+    nb = int(round(vol * ppc * beam_density))
+    r = beam_radius * np.sqrt(rng.random(nb))
+    ph = 2 * np.pi * rng.random(nb)
+    Xb = np.stack([cx + r * np.cos(ph), cy + r * np.sin(ph), zf - beam_length * rng.random(nb)], 1)
+    ub = np.zeros((nb, 3))
+    ub[:, 2] = beam_uz
+    bm = _pack(Xb, ub, np.full(nb, w), 3)
+    bi = _pack(Xb, np.zeros((nb, 3)), np.full(nb, w), 3)
+    return [dict(el, q=-Q_E, m=M_E, immobile=False), dict(pr, q=Q_E, m=M_P, immobile=False),
+            dict(bm, q=-Q_E, m=M_E, immobile=False), dict(bi, q=Q_E, m=M_P, immobile=True)]
+
+
 def random_moves(n, lo, hi, max_step=0.95, seed=SEED_BASE + 9, w_range=(0.5, 4.0)):
     """Prescribed one-step moves for depositing in isolation: start positions
     uniform in [lo, hi) (cells, 3D), displacements uniform in +-max_step per

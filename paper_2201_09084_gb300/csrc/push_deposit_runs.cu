@@ -15,10 +15,10 @@
 //   C. deposit: each thread takes P consecutive particles of the anchor order,
 //      so a run mostly shares one anchor, and accumulates the 2x3x3 prefix
 //      values of each component (54 in 3D) in registers; at the end, for each
-//      anchor present in a warp (up to three), the warp sums its lanes' values
-//      with a reduce-scatter of shuffles (each lane ends with two sums) and
-//      adds them to the box with two shared-memory atomics per lane; a warp
-//      holding more anchors (sparse particles) adds each lane's run directly;
+//      anchor held by at least three lanes of a warp, the warp sums those
+//      lanes' values with a reduce-scatter of shuffles (each lane ends with two
+//      sums) and adds them to the box with two shared-memory atomics per lane;
+//      lanes of smaller groups (sparse particles) add their runs directly;
 //   D. add the box to the grid with the charge factor and alpha (Eq. alpha,
 //      at each component's staggered location): the damping of Eq. MaxwellE's
 //      source term applied once per node in the flush.
@@ -221,9 +221,9 @@ struct Acc1 {
 };
 
 constexpr int kNT = 128;
-// Most anchors a warp sums by reduce-scatter (about 330 instructions each);
-// above this each lane adds its own run to the current box.
-constexpr int kMaxGroups = 3;
+// Fewest lanes of one anchor that a warp sums by reduce-scatter (about 330
+// instructions per anchor); smaller groups add their runs lane by lane.
+constexpr int kMinGroupLanes = 3;
 
 // Shared memory of one block: the staged chunk (NW words per particle, rows
 // padded to P+1), the field box (E and time-averaged B, 6 arrays of NBOX
@@ -380,6 +380,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
   __shared__ int s_use_box;
   __shared__ int s_scan[kNT / 32];
   __shared__ int s_ndefer;
+  __shared__ int s_nanchor;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long n = *sp.n_dev;
   const long long nchunks = (n + C - 1) / C;
@@ -552,7 +553,10 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
       T* const BJ = bx_;
       for (int t = tid; t < 3 * NBOX; t += kNT) BJ[t] = T(0);
       for (int t = tid; t <= NBOX; t += kNT) cnt[t] = 0;
-      if (tid == 0) s_ndefer = 0;
+      if (tid == 0) {
+        s_ndefer = 0;
+        s_nanchor = 0;
+      }
       __syncthreads();
       auto anchor_key = [&](int slot) -> int {
         const int c0 = bits_to_cell<T>(stg[7 * ROW + slot]);
@@ -573,9 +577,16 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
       {  // exclusive scan of cnt[0..NBOX]
         const int per = (NBOX + 1 + kNT - 1) / kNT;
         const int b0 = tid * per;
-        int loc = 0;
+        int loc = 0, nz = 0;
         for (int t = 0; t < per; ++t)
-          if (b0 + t <= NBOX) loc += cnt[b0 + t];
+          if (b0 + t < NBOX) {
+            loc += cnt[b0 + t];
+            nz += cnt[b0 + t] != 0;
+          } else if (b0 + t == NBOX) {
+            loc += cnt[b0 + t];
+          }
+        nz = __reduce_add_sync(0xffffffffu, nz);
+        if (lane == 0 && nz) atomicAdd(&s_nanchor, nz);
         int inc = loc;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -637,7 +648,11 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
       // anchor (a run that straddles two anchors after the sort) is deferred
       // to a list deposited one particle per thread below, so no warp ever
       // diverges into a flush inside the loop.
+      // A chunk with fewer than 2P particles per anchor (sparse particles)
+      // has straddling runs everywhere: there a run flushes and restarts at
+      // each new anchor instead.
       unsigned short* defer = reinterpret_cast<unsigned short*>(cnt);  // the counters are dead now
+      const bool sparse = s_nanchor * (2 * P) > C;
       AC acc;
       acc.zero();
       int key = -1;
@@ -649,29 +664,39 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
         if (key < 0) {
           key = k;
         } else if (k != key) {
-          defer[atomicAdd(&s_ndefer, 1)] = (unsigned short)slot;
-          continue;
+          if (!sparse) {
+            defer[atomicAdd(&s_ndefer, 1)] = (unsigned short)slot;
+            continue;
+          }
+          acc.template flush_box<BX, BXY, NBOX>(BJ, key);
+          acc.zero();
+          key = k;
         }
         acc.add(S0, DS, stg[3 * ROW + slot], wvy_of(slot));
       }
-      // Lanes that share an anchor sum their runs, one reduce-scatter per
-      // anchor, when the warp holds few anchors (dense particles).  With
-      // many anchors (a few particles per cell) the groups are small, so
-      // each lane adds its own run to the box: few lanes meet on an address.
+      // Lanes that share an anchor hold contiguous runs (anchor order).  A
+      // group of at least kMinGroupLanes lanes sums its runs with one
+      // reduce-scatter; the lanes of smaller groups (a few particles per
+      // cell) add their own runs to the box, where few lanes meet on an
+      // address.
       {
         const int up = __shfl_up_sync(0xffffffffu, key, 1);
         const bool head = key >= 0 && (lane == 0 || up != key);
-        unsigned pend = __ballot_sync(0xffffffffu, head);
-        if (__popc(pend) <= kMaxGroups) {
-          while (pend) {
-            const int leader = __ffs(pend) - 1;
-            pend &= pend - 1;
-            const int gk = __shfl_sync(0xffffffffu, key, leader);
-            acc.template group_flush<false>(key == gk, lane, BJ, gk, goff);
-          }
-        } else if (key >= 0) {
-          acc.template flush_box<BX, BXY, NBOX>(BJ, key);
+        const unsigned heads = __ballot_sync(0xffffffffu, head);
+        const unsigned live = __ballot_sync(0xffffffffu, key >= 0);
+        const unsigned below = heads & ((2u << lane) - 1u);     // heads at or before this lane
+        const unsigned above = (heads | ~live) & ~((2u << lane) - 1u);
+        const int first = below ? 31 - __clz(below) : 0;
+        const int next = above ? __ffs(above) - 1 : 32;
+        const bool big = key >= 0 && next - first >= kMinGroupLanes;
+        unsigned pend = __ballot_sync(0xffffffffu, head && big);
+        while (pend) {
+          const int leader = __ffs(pend) - 1;
+          pend &= pend - 1;
+          const int gk = __shfl_sync(0xffffffffu, key, leader);
+          acc.template group_flush<false>(key == gk, lane, BJ, gk, goff);
         }
+        if (key >= 0 && !big) acc.template flush_box<BX, BXY, NBOX>(BJ, key);
       }
       __syncthreads();
       const int nd = s_ndefer;

@@ -224,7 +224,8 @@ int pic_num_particles(picpml_ctx* ctx, int sid, long long* n);
 int pic_diag(picpml_ctx* ctx, double* gauss, double* rho_scale, double* energy);
 
 /* Autotuner: times the fused particle kernel for each particles-per-thread
- * choice (order 1: 1, 4, 8; FP64: 1, 4) and the field kernels for each
+ * choice (order 1, and order 3 in 3D: 1, 4, 8; FP64: 1, 4) and the field
+ * kernels for each
  * z-nodes-per-thread choice, `steps` steps per candidate, each from the same
  * state (a device snapshot, restored afterwards; the call allocates that
  * snapshot), keeps the fastest and returns the choices.  Results do not
@@ -232,8 +233,8 @@ int pic_diag(picpml_ctx* ctx, double* gauss, double* rho_scale, double* energy);
 int pic_autotune(picpml_ctx* ctx, int steps, int* particles_per_thread, int* z_nodes_per_thread);
 
 /* Sets the launch shapes directly (e.g. the result of pic_autotune in
- * another context).  Particles per thread (order 1): 4 or 8 = the
- * shared-memory kernel over sorted runs of that many particles per thread
+ * another context).  Particles per thread (order 1; order 3 in 3D): 4 or 8
+ * = the shared-memory chunk kernel with that many particles per thread
  * (dense particles), 1 = one thread per particle with global atomics (a few
  * particles per cell), 0 = default (4; FP64 uses 4 for 8).  z nodes per
  * thread of the field kernels: 1, 2 or 4. */

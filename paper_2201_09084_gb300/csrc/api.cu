@@ -37,6 +37,10 @@ cudaError_t launch_push_deposit_runs(int ppt, const Geom&, const Tables&, const 
                                      cudaStream_t);
 cudaError_t launch_fixed_flush(const Geom&, const Tables&, const FieldPtrs<float>&, const double K[3], unsigned*,
                                cudaStream_t);
+template <typename T>
+cudaError_t launch_push_deposit_o3(int ppt, const Geom&, const Tables&, const FieldPtrs<T>&, const SpeciesPtrs<T>&,
+                                   int prescribed, unsigned* status, unsigned long long* pushed, int nsm,
+                                   cudaStream_t);
 long long sort_scratch_words(long long ncell);
 int sort_launches(long long ncell);
 long long sort_keys(const Geom& g);
@@ -115,8 +119,9 @@ struct picpml_ctx {
   unsigned* sort_scratch = nullptr;
   std::vector<Species> sp;
   int prescribed = 0;
-  int ppt = 0;        // order 1: particles per thread of the shared-memory run kernel (4 or 8;
-                      // 0 = default 4), or 1 = one thread per particle with global atomics
+  int ppt = 0;        // particles per thread of the shared-memory chunk kernels (order 1; order 3
+                      // in 3D): 4 or 8 (0 = default 4), or 1 = one thread per particle with
+                      // global atomics
   int kz = 1;         // nodes per thread along z in the field kernels
   long long steps_done = 0;
   long long launches = 0;
@@ -219,6 +224,9 @@ int run_particles(picpml_ctx* ctx, int mode) {
     if (mode == 2 && ctx->gd.shape_order == 1 && ctx->ppt != 1 && !ctx->fixed())
       CK(launch_push_deposit_runs<T>(ctx->ppt, ctx->g, ctx->tb, fields<T>(ctx), p, ctx->prescribed, ctx->status,
                                      ctx->pushed, ctx->nsm, ctx->stream));
+    else if (mode == 2 && ctx->gd.shape_order == 3 && ctx->gd.dim == 3 && ctx->ppt != 1 && !ctx->fixed())
+      CK(launch_push_deposit_o3<T>(ctx->ppt, ctx->g, ctx->tb, fields<T>(ctx), p, ctx->prescribed, ctx->status,
+                                   ctx->pushed, ctx->nsm, ctx->stream));
     else
       CK(launch_particles<T>(mode, ctx->gd.shape_order, ctx->g, ctx->tb, fields<T>(ctx), p, ctx->prescribed,
                              ctx->status, ctx->pushed, ctx->nsm, ctx->stream));
@@ -600,7 +608,7 @@ int pic_autotune(picpml_ctx* ctx, int steps, int* ppt, int* kz) {
   };
   const long long launches0 = ctx->launches;
   int best_p = ctx->ppt, best_k = ctx->kz;
-  if (ctx->gd.shape_order == 1 && !ctx->fixed()) {
+  if ((ctx->gd.shape_order == 1 || ctx->gd.dim == 3) && !ctx->fixed()) {
     float best = 1e30f;
     for (int p : {1, 4, 8}) {
       if (f64 && p == 8) continue;

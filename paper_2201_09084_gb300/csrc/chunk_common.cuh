@@ -1,0 +1,152 @@
+// Pieces shared by the chunked particle kernels (order 1 and order 3): a
+// block stages a chunk of consecutive particles in shared memory, finds the
+// bounding box of their cells, pushes them against a shared-memory field box
+// and deposits through a shared-memory current box.
+#pragma once
+
+#include "particle_common.cuh"
+
+namespace picpml {
+namespace chunk {
+
+using namespace pc;
+
+template <typename T>
+__device__ __forceinline__ T cell_to_bits(int c);
+template <>
+__device__ __forceinline__ float cell_to_bits<float>(int c) { return __int_as_float(c); }
+template <>
+__device__ __forceinline__ double cell_to_bits<double>(int c) { return __longlong_as_double((long long)c); }
+template <typename T>
+__device__ __forceinline__ int bits_to_cell(T v);
+template <>
+__device__ __forceinline__ int bits_to_cell<float>(float v) { return __float_as_int(v); }
+template <>
+__device__ __forceinline__ int bits_to_cell<double>(double v) { return (int)__double_as_longlong(v); }
+
+__device__ __forceinline__ int warp_min(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Move of one particle with its new u; returns false when the particle leaves
+// its allowed cells.  c1, o1: new cell and offsets.
+template <int DIM, typename T>
+__device__ __forceinline__ bool move_particle(const Geom& g, const T o[3], const int c[3], const T u[3], int c1[3],
+                                              T o1[3], T& inv_gamma) {
+  const Mover<T> mv(u);
+  inv_gamma = mv.inv_gamma();
+  bool out = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    c1[a] = c[a];
+    o1[a] = o[a];
+    if (DIM == 2 && a == 1) continue;
+    const T Sh = sizeof(T) == 4 ? T(g.Sf[a]) : T(g.S[a]);
+    const T Sl = sizeof(T) == 4 ? T(g.Sfl[a]) : T(0);
+    T x = mv.advance(o[a], Sh, Sl, u[a]);
+    if (x >= T(1)) {
+      x -= T(1);
+      c1[a] += 1;
+    } else if (x < T(0)) {
+      x += T(1);
+      c1[a] -= 1;
+      if (x >= T(1)) {  // x was a tiny negative number: stay on the node
+        x = T(0);
+        c1[a] += 1;
+      }
+    }
+    o1[a] = x;
+    if (c1[a] < g.rmin[a] || c1[a] > g.rmax[a] || (c1[a] == g.rmax[a] && x > T(0))) out = true;
+  }
+  return !out;
+}
+
+// Stages particles [base, base + NT*P) with coalesced loads into the stage
+// (words 0-2 offsets, 3 weight, 4-6 u, 7 cell; row length ROW, particle q at
+// slot (q / P) * (P + 1) + q % P), removes and reports particles outside
+// their allowed cells, and leaves the bounding box of the live particles'
+// cells in s_lo / s_hi (s_hi[0] < 0: no live particle).  Ends with a barrier.
+template <typename T, int DIM, int P, int NT>
+__device__ __forceinline__ void stage_chunk(const Geom& g, const SpeciesPtrs<T>& sp, long long base, long long n,
+                                            T* stg, int ROW, unsigned* status, int (*s_red)[NT / 32], int* s_lo,
+                                            int* s_hi) {
+  constexpr int PP = P + 1, C = NT * P;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int q = tid; q < C; q += NT) {
+    const long long gp = base + q;
+    const int slot = (q / P) * PP + (q % P);
+    if (gp < n) {
+      T o[3], u[3], w;
+      int cell;
+      PIO<T>::load(sp.pos, sp.mom, gp, o, w, u, cell);
+      stg[0 * ROW + slot] = o[0];
+      stg[1 * ROW + slot] = o[1];
+      stg[2 * ROW + slot] = o[2];
+      stg[3 * ROW + slot] = w;
+      stg[4 * ROW + slot] = u[0];
+      stg[5 * ROW + slot] = u[1];
+      stg[6 * ROW + slot] = u[2];
+      stg[7 * ROW + slot] = cell_to_bits<T>(cell);
+    } else {
+      stg[7 * ROW + slot] = cell_to_bits<T>(-1);
+    }
+  }
+  __syncthreads();
+  int mn[3] = {1 << 30, 1 << 30, 1 << 30}, mx[3] = {-1, -1, -1};
+  for (int i = 0; i < P; ++i) {
+    const int slot = tid * PP + i;
+    const int cell = bits_to_cell<T>(stg[7 * ROW + slot]);
+    if (cell < 0) continue;
+    const int c[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (DIM == 2 && a == 1) continue;
+      const T o = stg[a * ROW + slot];
+      if (c[a] < g.rmin[a] || c[a] > g.rmax[a] || !(o >= T(0) && o < T(1))) bad = true;
+    }
+    if (bad) {
+      atomicOr(status, ST_BAD_PARTICLE);
+      stg[7 * ROW + slot] = cell_to_bits<T>(-1);  // removed
+      continue;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      mn[a] = min(mn[a], c[a]);
+      mx[a] = max(mx[a], c[a]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int lo = warp_min(mn[a]), hi = warp_max(mx[a]);
+    if (lane == 0) {
+      s_red[a][warp] = lo;
+      s_red[3 + a][warp] = hi;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int a = 0; a < 3; ++a) {
+      int lo = 1 << 30, hi = -1;
+      for (int w8 = 0; w8 < NT / 32; ++w8) {
+        lo = min(lo, s_red[a][w8]);
+        hi = max(hi, s_red[3 + a][w8]);
+      }
+      if (DIM == 2 && a == 1) lo = hi = 0;
+      s_lo[a] = lo;
+      s_hi[a] = hi;
+    }
+    if (s_hi[0] < 0) s_hi[0] = -1;
+  }
+  __syncthreads();
+}
+
+}  // namespace chunk
+}  // namespace picpml

@@ -27,26 +27,14 @@
 // iterations and merge in L2).
 // A chunk whose box does not fit in shared memory (sparse particles) takes a
 // per-particle path with global loads and atomics.
-#include "particle_common.cuh"
+#include "chunk_common.cuh"
 
 namespace picpml {
 
 namespace {
 
 using namespace pc;
-
-template <typename T>
-__device__ __forceinline__ T cell_to_bits(int c);
-template <>
-__device__ __forceinline__ float cell_to_bits<float>(int c) { return __int_as_float(c); }
-template <>
-__device__ __forceinline__ double cell_to_bits<double>(int c) { return __longlong_as_double((long long)c); }
-template <typename T>
-__device__ __forceinline__ int bits_to_cell(T v);
-template <>
-__device__ __forceinline__ int bits_to_cell<float>(float v) { return __float_as_int(v); }
-template <>
-__device__ __forceinline__ int bits_to_cell<double>(double v) { return (int)__double_as_longlong(v); }
+using namespace chunk;
 
 // Register accumulator of the order-1 current of a run: w * (Esirkepov shape
 // factor) prefix sums; the charge factor and alpha are applied at the flush.
@@ -269,50 +257,6 @@ __device__ __forceinline__ T interp_box(const T* F, int b, const T* wx, const T*
   return acc;
 }
 
-__device__ __forceinline__ int warp_min(int v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-__device__ __forceinline__ int warp_max(int v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-// Boris push and move of one particle with fields E, B; returns false when
-// the particle leaves its allowed cells.  c1, o1: new cell and offsets.
-template <int DIM, typename T>
-__device__ __forceinline__ bool move_particle(const Geom& g, const T o[3], const int c[3], T u[3], int c1[3],
-                                              T o1[3], T& inv_gamma) {
-  const Mover<T> mv(u);
-  inv_gamma = mv.inv_gamma();
-  bool out = false;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    c1[a] = c[a];
-    o1[a] = o[a];
-    if (DIM == 2 && a == 1) continue;
-    const T Sh = sizeof(T) == 4 ? T(g.Sf[a]) : T(g.S[a]);
-    const T Sl = sizeof(T) == 4 ? T(g.Sfl[a]) : T(0);
-    T x = mv.advance(o[a], Sh, Sl, u[a]);
-    if (x >= T(1)) {
-      x -= T(1);
-      c1[a] += 1;
-    } else if (x < T(0)) {
-      x += T(1);
-      c1[a] -= 1;
-      if (x >= T(1)) {  // x was a tiny negative number: stay on the node
-        x = T(0);
-        c1[a] += 1;
-      }
-    }
-    o1[a] = x;
-    if (c1[a] < g.rmin[a] || c1[a] > g.rmax[a] || (c1[a] == g.rmax[a] && x > T(0))) out = true;
-  }
-  return !out;
-}
-
 // The whole step of one particle from global memory (chunks whose box does
 // not fit in shared memory): gather, push, move, deposit with global atomics
 // (charge factor and alpha per contribution), and the particle's record is
@@ -377,6 +321,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
   unsigned short* perm = reinterpret_cast<unsigned short*>(smraw + PL::stage + PL::box + PL::cnt);
   __shared__ int s_red[6][kNT / 32];
   __shared__ int s_geo[8];   // box origin x, y, z and dims x, y, z
+  __shared__ int s_lo[3], s_hi[3];
   __shared__ int s_use_box;
   __shared__ int s_scan[kNT / 32];
   __shared__ int s_ndefer;
@@ -397,79 +342,17 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
   for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const long long base = ch * C;
     __syncthreads();
-    // ---- 1. stage the chunk (coalesced), mark empty slots ----
-    for (int q = tid; q < C; q += kNT) {
-      const long long gp = base + q;
-      const int slot = (q / P) * PP + (q % P);
-      if (gp < n) {
-        T o[3], u[3], w;
-        int cell;
-        PIO<T>::load(sp.pos, sp.mom, gp, o, w, u, cell);
-        stg[0 * ROW + slot] = o[0];
-        stg[1 * ROW + slot] = o[1];
-        stg[2 * ROW + slot] = o[2];
-        stg[3 * ROW + slot] = w;
-        stg[4 * ROW + slot] = u[0];
-        stg[5 * ROW + slot] = u[1];
-        stg[6 * ROW + slot] = u[2];
-        stg[7 * ROW + slot] = cell_to_bits<T>(cell);
-      } else {
-        stg[7 * ROW + slot] = cell_to_bits<T>(-1);
-      }
-    }
-    __syncthreads();
-    // validate, bounding box of the current cells
-    int mn[3] = {1 << 30, 1 << 30, 1 << 30}, mx[3] = {-1, -1, -1};
-    for (int i = 0; i < P; ++i) {
-      const int slot = tid * PP + i;
-      const int cell = bits_to_cell<T>(stg[7 * ROW + slot]);
-      if (cell < 0) continue;
-      const int c[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
-      bool bad = false;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        if (DIM == 2 && a == 1) continue;
-        const T o = stg[a * ROW + slot];
-        if (c[a] < g.rmin[a] || c[a] > g.rmax[a] || !(o >= T(0) && o < T(1))) bad = true;
-      }
-      if (bad) {
-        atomicOr(status, ST_BAD_PARTICLE);
-        stg[7 * ROW + slot] = cell_to_bits<T>(-1);  // removed
-        continue;
-      }
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        mn[a] = min(mn[a], c[a]);
-        mx[a] = max(mx[a], c[a]);
-      }
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const int lo = warp_min(mn[a]), hi = warp_max(mx[a]);
-      if (lane == 0) {
-        s_red[a][warp] = lo;
-        s_red[3 + a][warp] = hi;
-      }
-    }
-    __syncthreads();
+    // ---- 1. stage the chunk, bounding box of its cells ----
+    stage_chunk<T, DIM, P, kNT>(g, sp, base, n, stg, ROW, status, s_red, s_lo, s_hi);
     if (tid == 0) {
-      int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-1, -1, -1};
-      for (int w8 = 0; w8 < kNT / 32; ++w8)
-        for (int a = 0; a < 3; ++a) {
-          lo[a] = min(lo[a], s_red[a][w8]);
-          hi[a] = max(hi[a], s_red[3 + a][w8]);
-        }
-      int use = hi[0] >= 0;
-      if (DIM == 2) lo[1] = hi[1] = 0;
       // nodes lo-1 .. hi+2 per axis: the gather reads from the cell's lower
       // node minus one (half-staggered components) to its upper node, the
       // deposit stencil of a move spans min(old, new cell) .. + 2
-      const int dx = hi[0] - lo[0] + 4, dy = DIM == 3 ? hi[1] - lo[1] + 4 : 1, dz = hi[2] - lo[2] + 4;
-      if (use && (dx > BX || dy > BY || dz > BZ)) use = 0;
-      s_use_box = use;
-      s_geo[0] = lo[0] - 1;
-      s_geo[1] = DIM == 3 ? lo[1] - 1 : 0;
-      s_geo[2] = lo[2] - 1;
+      const int dx = s_hi[0] - s_lo[0] + 4, dy = DIM == 3 ? s_hi[1] - s_lo[1] + 4 : 1, dz = s_hi[2] - s_lo[2] + 4;
+      s_use_box = s_hi[0] >= 0 && dx <= BX && dy <= BY && dz <= BZ;
+      s_geo[0] = s_lo[0] - 1;
+      s_geo[1] = DIM == 3 ? s_lo[1] - 1 : 0;
+      s_geo[2] = s_lo[2] - 1;
       s_geo[3] = dx;
       s_geo[4] = dy;
       s_geo[5] = dz;

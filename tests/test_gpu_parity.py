@@ -196,18 +196,23 @@ def test_state_roundtrip_is_exact():
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("ppt", [4, 8])
+@pytest.mark.parametrize("order", [1, 3])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("theta", [0.0, 25.0])
-def test_dense_beam_shared_memory_box(theta, prec):
+def test_dense_beam_shared_memory_box(theta, prec, order, ppt):
     """A dense beam (about 1000 particles per cell in its core): chunks of
-    cell-sorted particles span a few cells, so the order-1 kernel takes its
-    shared-memory field/current box path; the sparse tails take the global
-    path.  Whole steps with sorting, against the oracle."""
+    tile-sorted particles span a few cells, so the chunk kernels (order 1:
+    anchor runs and warp reductions; order 3: private current copies) take
+    their shared-memory field/current box path; the sparse tails take the
+    global path.  Whole steps with sorting, against the oracle, for both
+    particles-per-thread shapes."""
     nphys = (20, 18, 24)
     pml = (6,) * 6
     center = (6 + 10.3, 6 + 9.2, 6 + 17.6)
     parts = I.beam(3, 20000, nphys, pml, center, sigma=(0.8, 0.8, 1.3), theta_deg=theta, clip=3.0)
-    ora, gpu = make_pair(3, nphys, pml, D3, parts, order=1, prec=prec, alpha_mode="damped", sort_every=5)
+    ora, gpu = make_pair(3, nphys, pml, D3, parts, order=order, prec=prec, alpha_mode="damped", sort_every=5)
+    gpu.set_tuning(ppt, 1)
     for _ in range(3):
         ora.step(6)
         gpu.step(6)

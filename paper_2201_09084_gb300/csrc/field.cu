@@ -2,10 +2,11 @@
 // MaxwellSum), in the normalised units of picpml_internal.cuh.
 //
 // One thread per node (i,j,k) updates the three components staggered from
-// that node; threads are laid out along x so every array access of a warp is
-// one contiguous run (coalesced).  A component location is "split" when the
-// conductivity of either axis it is split along is nonzero there; its two
-// parts then advance by exponential differencing,
+// that node; threads are laid out along x (then y) so every array access of a
+// warp is one contiguous run (coalesced).  A component location is "split"
+// when it lies in the PML along either axis it is split along (decided from
+// the box geometry, so the parts' loads do not wait for a table load); its
+// two parts then advance by exponential differencing,
 //   F <- e^{-s dt} F + (1 - e^{-s dt})/(s dt) (R dt),
 // and their sum is written to the field array.  The source -alpha j goes to the
 // part with the larger conductivity (first axis on ties), which for a pure
@@ -18,8 +19,10 @@
 //            a small fraction of its FP32 rate, and with FP64 parts the E pass
 //            was FP64-pipe bound; the pairs keep the accumulation precision at
 //            FP32 instruction cost and the same 8 bytes per part.
-// Conductivity tests and Courant numbers use float copies, so FP32 fields need
-// no FP64 instruction outside the FP64 parts.
+// Conductivity comparisons and Courant numbers use float copies, so FP32
+// fields need no FP64 instruction outside the FP64 parts.  Launch bounds ask
+// for 6 blocks of 256 per SM (one node per thread) to keep more loads in
+// flight; the passes are memory-latency bound.
 #include "field_node.cuh"
 
 namespace picpml {
@@ -29,12 +32,31 @@ namespace {
 // KZ: nodes per thread along z.  A thread marches KZ nodes upward in z and
 // carries the z-neighbour values of the previous node in registers (fewer
 // loads, fewer resident warps); chosen by the autotuner, 1 by default.
+// Threads cover the (x, y) node plane as one flat range (x fastest), so no
+// thread idles in a partial row block; blockIdx.y walks z in steps of KZ (in
+// 2D the flat range is the (x, z/KZ) plane).
+template <int DIM>
+__device__ __forceinline__ bool node_of_thread(const Geom& g, int KZ, int& i, int& j, int& k0) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (DIM == 3) {
+    if (t >= g.nn[0] * g.nn[1]) return false;
+    i = t % g.nn[0];
+    j = t / g.nn[0];
+    k0 = blockIdx.y * KZ;
+  } else {  // 2D: the (x, z/KZ) plane is the flat range
+    const int nk = (g.nn[2] + KZ - 1) / KZ;
+    if (t >= g.nn[0] * nk) return false;
+    i = t % g.nn[0];
+    j = 0;
+    k0 = (t / g.nn[0]) * KZ;
+  }
+  return k0 < g.nn[2];
+}
+
 template <typename T, int DIM, int SPL, int KZ>
-__global__ void __launch_bounds__(256) k_field_E(Geom g, Tables tb, FieldPtrs<T> f) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = DIM == 3 ? blockIdx.y * blockDim.y + threadIdx.y : 0;
-  const int k0 = DIM == 3 ? blockIdx.z * KZ : (blockIdx.y * blockDim.y + threadIdx.y) * KZ;
-  if (i >= g.nn[0] || j >= g.nn[1] || k0 >= g.nn[2]) return;
+__global__ void __launch_bounds__(256, KZ == 1 ? 6 : 4) k_field_E(Geom g, Tables tb, FieldPtrs<T> f) {
+  int i, j, k0;
+  if (!node_of_thread<DIM>(g, KZ, i, j, k0)) return;
   long long id = g.idx(i, j, k0);
   T by_m = k0 >= 1 ? f.Bh[1][id - g.sz] : T(0);
   T bx_m = k0 >= 1 ? f.Bh[0][id - g.sz] : T(0);
@@ -43,18 +65,16 @@ __global__ void __launch_bounds__(256) k_field_E(Geom g, Tables tb, FieldPtrs<T>
     const int k = k0 + kk;
     if (k >= g.nn[2]) break;
     const T by0 = f.Bh[1][id], bx0 = f.Bh[0][id], bz0 = f.Bh[2][id];
-    fn::e_update<T, DIM, SPL>(g, tb, f, i, j, k, id, by_m, bx_m, by0, bx0, bz0);
+    fn::e_update<T, DIM, SPL, true>(g, tb, f, i, j, k, id, by_m, bx_m, by0, bx0, bz0);
     by_m = by0;
     bx_m = bx0;
   }
 }
 
 template <typename T, int DIM, int SPL, int KZ>
-__global__ void __launch_bounds__(256) k_field_B(Geom g, Tables tb, FieldPtrs<T> f) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = DIM == 3 ? blockIdx.y * blockDim.y + threadIdx.y : 0;
-  const int k0 = DIM == 3 ? blockIdx.z * KZ : (blockIdx.y * blockDim.y + threadIdx.y) * KZ;
-  if (i >= g.nn[0] || j >= g.nn[1] || k0 >= g.nn[2]) return;
+__global__ void __launch_bounds__(256, KZ == 1 ? 6 : 4) k_field_B(Geom g, Tables tb, FieldPtrs<T> f) {
+  int i, j, k0;
+  if (!node_of_thread<DIM>(g, KZ, i, j, k0)) return;
   long long id = g.idx(i, j, k0);
   T ex0 = f.E[0][id], ey0 = f.E[1][id];
 #pragma unroll
@@ -64,33 +84,33 @@ __global__ void __launch_bounds__(256) k_field_B(Geom g, Tables tb, FieldPtrs<T>
     const bool kc = k <= g.N[2] - 1;
     const T ex_p = kc ? f.E[0][id + g.sz] : T(0);
     const T ey_p = kc ? f.E[1][id + g.sz] : T(0);
-    fn::b_update<T, DIM, SPL>(g, tb, f, i, j, k, id, ex_p, ey_p, ex0, ey0, f.E[2][id]);
+    fn::b_update<T, DIM, SPL, true>(g, tb, f, i, j, k, id, ex_p, ey_p, ex0, ey0, f.E[2][id]);
     ex0 = ex_p;
     ey0 = ey_p;
   }
 }
 
+inline dim3 field_grid(const Geom& g, int KZ) {
+  const long long nk = (g.nn[2] + KZ - 1) / KZ;
+  if (g.dim == 3) return dim3((unsigned)(((long long)g.nn[0] * g.nn[1] + 255) / 256), (unsigned)nk, 1);
+  return dim3((unsigned)(((long long)g.nn[0] * nk + 255) / 256), 1, 1);
+}
+
 template <typename T, int SPL, int KZ>
 cudaError_t launch_E(const Geom& g, const Tables& tb, const FieldPtrs<T>& f, cudaStream_t s) {
-  if (g.dim == 3) {
-    dim3 blk(32, 8, 1), grd((g.nn[0] + 31) / 32, (g.nn[1] + 7) / 8, (g.nn[2] + KZ - 1) / KZ);
-    k_field_E<T, 3, SPL, KZ><<<grd, blk, 0, s>>>(g, tb, f);
-  } else {
-    dim3 blk(32, 8, 1), grd((g.nn[0] + 31) / 32, ((g.nn[2] + KZ - 1) / KZ + 7) / 8, 1);
-    k_field_E<T, 2, SPL, KZ><<<grd, blk, 0, s>>>(g, tb, f);
-  }
+  if (g.dim == 3)
+    k_field_E<T, 3, SPL, KZ><<<field_grid(g, KZ), 256, 0, s>>>(g, tb, f);
+  else
+    k_field_E<T, 2, SPL, KZ><<<field_grid(g, KZ), 256, 0, s>>>(g, tb, f);
   return cudaGetLastError();
 }
 
 template <typename T, int SPL, int KZ>
 cudaError_t launch_B(const Geom& g, const Tables& tb, const FieldPtrs<T>& f, cudaStream_t s) {
-  if (g.dim == 3) {
-    dim3 blk(32, 8, 1), grd((g.nn[0] + 31) / 32, (g.nn[1] + 7) / 8, (g.nn[2] + KZ - 1) / KZ);
-    k_field_B<T, 3, SPL, KZ><<<grd, blk, 0, s>>>(g, tb, f);
-  } else {
-    dim3 blk(32, 8, 1), grd((g.nn[0] + 31) / 32, ((g.nn[2] + KZ - 1) / KZ + 7) / 8, 1);
-    k_field_B<T, 2, SPL, KZ><<<grd, blk, 0, s>>>(g, tb, f);
-  }
+  if (g.dim == 3)
+    k_field_B<T, 3, SPL, KZ><<<field_grid(g, KZ), 256, 0, s>>>(g, tb, f);
+  else
+    k_field_B<T, 2, SPL, KZ><<<field_grid(g, KZ), 256, 0, s>>>(g, tb, f);
   return cudaGetLastError();
 }
 

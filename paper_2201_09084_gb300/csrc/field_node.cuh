@@ -51,8 +51,21 @@ __device__ __forceinline__ T courant(const Geom& g, int a) {
 }
 
 
-// E^{n+1} at node (i,j,k).  by_m, bx_m: By, Bx at (i,j,k-1).
-template <typename T, int DIM, int SPL>
+// Whether a node (centre: the point i + 1/2) lies in the PML along axis a,
+// from the box geometry: there sigma > 0 whenever the profile's coefficient
+// is (Eq. conductivity vanishes only at depth 0).
+__device__ __forceinline__ bool pml_node(const Geom& g, int a, int i) {
+  return i < g.plo[a] || i > g.plo[a] + g.nph[a];
+}
+__device__ __forceinline__ bool pml_cent(const Geom& g, int a, int i) {
+  return i < g.plo[a] || i >= g.plo[a] + g.nph[a];
+}
+
+// E^{n+1} at node (i,j,k).  by_m, bx_m: By, Bx at (i,j,k-1).  GEO: decide
+// the split locations from the box geometry (single boxes), so the split
+// parts' loads need not wait for the conductivity tables; else from the
+// tables (batched runs).
+template <typename T, int DIM, int SPL, bool GEO = false>
 __device__ __forceinline__ void e_update(const Geom& g, const Tables& tb, const FieldPtrs<T>& f, int i, int j, int k,
                                          long long id, T by_m, T bx_m, T by0, T bx0, T bz0) {
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
@@ -63,6 +76,9 @@ __device__ __forceinline__ void e_update(const Geom& g, const Tables& tb, const 
   const float sxn = tb.sdtf_n[0][i];
   const float syn = DIM == 3 ? tb.sdtf_n[1][j] : 0.f;
   const float szn = tb.sdtf_n[2][k];
+  const bool px = GEO ? pml_node(g, 0, i) : sxn > 0.f;
+  const bool py = DIM == 3 && (GEO ? pml_node(g, 1, j) : syn > 0.f);
+  const bool pz = GEO ? pml_node(g, 2, k) : szn > 0.f;
   // J' is consumed here: read once, zeroed where it was nonzero (most of the
   // grid carries no current, so most threads write nothing back).
   const T jx = f.J[0][id], jy = f.J[1][id], jz = f.J[2][id];
@@ -76,7 +92,7 @@ __device__ __forceinline__ void e_update(const Geom& g, const Tables& tb, const 
   if (i <= N0 - 1 && jin && kin) {
     const T r0 = DIM == 3 ? Sy * (bz0 - Bz[id - g.sy]) : T(0);
     const T r1 = -Sz * (by0 - by_m);
-    if (syn > 0.f || szn > 0.f)
+    if (py || pz)
       f.E[0][id] = advance<T, SPL, false>(tb, f.Es[0], id, DIM == 3 ? 1 : -1, j, 2, k, r0, r1, -jx, syn, szn);
     else
       f.E[0][id] += r0 + r1 - jx;
@@ -85,7 +101,7 @@ __device__ __forceinline__ void e_update(const Geom& g, const Tables& tb, const 
   if (iin && (DIM == 2 || j <= N1 - 1) && kin) {
     const T r0 = -Sx * (bz0 - Bz[id - 1]);
     const T r1 = Sz * (bx0 - bx_m);
-    if (sxn > 0.f || szn > 0.f)
+    if (px || pz)
       f.E[1][id] = advance<T, SPL, false>(tb, f.Es[1], id, 0, i, 2, k, r0, r1, -jy, sxn, szn);
     else
       f.E[1][id] += r0 + r1 - jy;
@@ -94,7 +110,7 @@ __device__ __forceinline__ void e_update(const Geom& g, const Tables& tb, const 
   if (iin && jin && k <= N2 - 1) {
     const T r0 = Sx * (by0 - By[id - 1]);
     const T r1 = DIM == 3 ? -Sy * (bx0 - Bx[id - g.sy]) : T(0);
-    if (sxn > 0.f || syn > 0.f)
+    if (px || py)
       f.E[2][id] = advance<T, SPL, false>(tb, f.Es[2], id, 0, i, DIM == 3 ? 1 : -1, j, r0, r1, -jz, sxn, syn);
     else
       f.E[2][id] += r0 + r1 - jz;
@@ -103,7 +119,7 @@ __device__ __forceinline__ void e_update(const Geom& g, const Tables& tb, const 
 
 // B^{n+3/2} at node (i,j,k) into Bp.  ex_p, ey_p: Ex, Ey at (i,j,k+1) (any
 // value when k = N2); ex0, ey0, ez0: values at (i,j,k).
-template <typename T, int DIM, int SPL>
+template <typename T, int DIM, int SPL, bool GEO = false>
 __device__ __forceinline__ void b_update(const Geom& g, const Tables& tb, const FieldPtrs<T>& f, int i, int j, int k,
                                          long long id, T ex_p, T ey_p, T ex0, T ey0, T ez0) {
   const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
@@ -117,11 +133,14 @@ __device__ __forceinline__ void b_update(const Geom& g, const Tables& tb, const 
   const float sxc = ic ? tb.sdtf_c[0][i] : 0.f;
   const float syc = DIM == 3 && jc ? tb.sdtf_c[1][j] : 0.f;
   const float szc = kc ? tb.sdtf_c[2][k] : 0.f;
+  const bool px = GEO ? (ic && pml_cent(g, 0, i)) : sxc > 0.f;
+  const bool py = DIM == 3 && (GEO ? (jc && pml_cent(g, 1, j)) : syc > 0.f);
+  const bool pz = GEO ? (kc && pml_cent(g, 2, k)) : szc > 0.f;
   // Bx(i, j+1/2, k+1/2): parts along y (sigma_y at centre j) and z (centre k)
   if (jc && kc) {
     const T r0 = DIM == 3 ? -Sy * (Ez[id + g.sy] - ez0) : T(0);
     const T r1 = Sz * (ey_p - ey0);
-    if (syc > 0.f || szc > 0.f)
+    if (py || pz)
       f.Bp[0][id] = advance<T, SPL, true>(tb, f.Bs[0], id, DIM == 3 ? 1 : -1, j, 2, k, r0, r1, T(0), syc, szc);
     else
       f.Bp[0][id] = f.Bh[0][id] + (r0 + r1);
@@ -130,7 +149,7 @@ __device__ __forceinline__ void b_update(const Geom& g, const Tables& tb, const 
   if (ic && kc) {
     const T r0 = Sx * (Ez[id + 1] - ez0);
     const T r1 = -Sz * (ex_p - ex0);
-    if (sxc > 0.f || szc > 0.f)
+    if (px || pz)
       f.Bp[1][id] = advance<T, SPL, true>(tb, f.Bs[1], id, 0, i, 2, k, r0, r1, T(0), sxc, szc);
     else
       f.Bp[1][id] = f.Bh[1][id] + (r0 + r1);
@@ -139,7 +158,7 @@ __device__ __forceinline__ void b_update(const Geom& g, const Tables& tb, const 
   if (ic && jc) {
     const T r0 = -Sx * (Ey[id + 1] - ey0);
     const T r1 = DIM == 3 ? Sy * (Ex[id + g.sy] - ex0) : T(0);
-    if (sxc > 0.f || syc > 0.f)
+    if (px || py)
       f.Bp[2][id] = advance<T, SPL, true>(tb, f.Bs[2], id, 0, i, DIM == 3 ? 1 : -1, j, r0, r1, T(0), sxc, syc);
     else
       f.Bp[2][id] = f.Bh[2][id] + (r0 + r1);

@@ -36,6 +36,7 @@ struct RunInfo {
   int N0, N2;          // total cells along x and z
   int nn0, nn2;        // nodes
   int rmin0, rmax0, rmin2, rmax2;
+  int p, nx, nz;       // PML cells on each face, physical cells along x and z
   long long off;       // first element of this run in every field array
   int tx, tz;          // first entry of this run's x and z tables
 };
@@ -119,9 +120,10 @@ __global__ void __launch_bounds__(NT, MINB) k_batch_step(BatchArgs<T> a, int par
       g.S[ax] = a.S[ax];
       g.Sf[ax] = a.Sf[ax];
       g.Sfl[ax] = a.Sfl[ax];
-      g.plo[ax] = 0;
-      g.nph[ax] = 0;
     }
+    g.plo[0] = ri.p; g.nph[0] = ri.nx;
+    g.plo[1] = 0; g.nph[1] = 0;
+    g.plo[2] = ri.p; g.nph[2] = ri.nz;
     g.rmin[0] = ri.rmin0; g.rmax[0] = ri.rmax0;
     g.rmin[1] = 0; g.rmax[1] = 1 << 30;
     g.rmin[2] = ri.rmin2; g.rmax[2] = ri.rmax2;
@@ -211,7 +213,7 @@ __global__ void __launch_bounds__(NT, MINB) k_batch_step(BatchArgs<T> a, int par
       const long long id = t;
       const T by_m = k >= 1 ? f.Bh[1][id - g.sz] : T(0);
       const T bx_m = k >= 1 ? f.Bh[0][id - g.sz] : T(0);
-      fn::e_update<T, 2, SPL>(g, tb, f, i, 0, k, id, by_m, bx_m, f.Bh[1][id], f.Bh[0][id], f.Bh[2][id]);
+      fn::e_update<T, 2, SPL, true>(g, tb, f, i, 0, k, id, by_m, bx_m, f.Bh[1][id], f.Bh[0][id], f.Bh[2][id]);
     }
     __syncthreads();
     // ---- B pass ----
@@ -221,7 +223,7 @@ __global__ void __launch_bounds__(NT, MINB) k_batch_step(BatchArgs<T> a, int par
       const bool kc = k <= g.N[2] - 1;
       const T ex_p = kc ? f.E[0][id + g.sz] : T(0);
       const T ey_p = kc ? f.E[1][id + g.sz] : T(0);
-      fn::b_update<T, 2, SPL>(g, tb, f, i, 0, k, id, ex_p, ey_p, f.E[0][id], f.E[1][id], f.E[2][id]);
+      fn::b_update<T, 2, SPL, true>(g, tb, f, i, 0, k, id, ex_p, ey_p, f.E[0][id], f.E[1][id], f.E[2][id]);
     }
   }
 }
@@ -288,7 +290,11 @@ template <>
 BatchArgs<double>& args<double>(pic_batch* b) { return b->ad; }
 
 // Block shapes the autotuner chooses from: (threads, minimum blocks per SM).
-constexpr int kShapes[4][2] = {{512, 1}, {256, 2}, {512, 2}, {1024, 1}};
+// The last two cap registers (42 and 32 per thread) for more resident warps
+// in the field passes; the particle stage of a run, one thread's work, may
+// then spill.
+constexpr int kNumShapes = 6;
+constexpr int kShapes[kNumShapes][2] = {{512, 1}, {256, 2}, {512, 2}, {1024, 1}, {256, 6}, {256, 8}};
 
 template <typename T, int ORDER, int SPL, int NT, int MINB>
 cudaError_t launch_shape(pic_batch* b, BatchArgs<T>& a, int parity, cudaStream_t s) {
@@ -310,6 +316,8 @@ cudaError_t launch_cfg(pic_batch* b, BatchArgs<T>& a, int parity, cudaStream_t s
     case 1: return launch_shape<T, ORDER, SPL, 256, 2>(b, a, parity, s);
     case 2: return launch_shape<T, ORDER, SPL, 512, 2>(b, a, parity, s);
     case 3: return launch_shape<T, ORDER, SPL, 1024, 1>(b, a, parity, s);
+    case 4: return launch_shape<T, ORDER, SPL, 256, 6>(b, a, parity, s);
+    case 5: return launch_shape<T, ORDER, SPL, 256, 8>(b, a, parity, s);
     default: return launch_shape<T, ORDER, SPL, 512, 1>(b, a, parity, s);
   }
 }
@@ -446,6 +454,7 @@ int pic_batch_init(pic_batch** out, const pic_batch_desc* d, void* stream) {
     }
     if (r1 <= r0 || z1 <= z0) return bfail(b, PIC_EINVAL, "run " + std::to_string(r) + ": too small for the shape");
     ri.rmin0 = r0; ri.rmax0 = r1; ri.rmin2 = z0; ri.rmax2 = z1;
+    ri.p = p; ri.nx = nx; ri.nz = nz;
     ri.off = total;
     total += ((long long)ri.nn0 * ri.nn2 + 31) / 32 * 32;
     ri.tx = (int)ntab;
@@ -522,7 +531,7 @@ int pic_batch_init(pic_batch** out, const pic_batch_desc* d, void* stream) {
     BCK(cudaEventCreate(&e1));
     float best = 1e30f;
     int best_cfg = 0;
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < kNumShapes; ++c) {
       b->cfg = c;
       BCK(launch_any(b, 0, b->stream));   // warm-up (first launch of this shape)
       BCK(cudaEventRecord(e0, b->stream));

@@ -11,10 +11,11 @@
 //      below the cell, the deposit stencil of a move three above);
 //   A. push every particle (64-point gather per component from the box),
 //      write its record back and keep old and new positions in the stage;
-//   C. the field box is dead: it becomes K private copies of a compact
-//      current box over the chunk's nodes, and every thread adds its P
-//      particles' Esirkepov values into copy (lane mod K) with shared-memory
-//      atomics, so lanes of a dense cell collide K times less often;
+//   C. every thread takes its P particles' moves into registers; the stage
+//      and the dead field box become K private copies of a compact current
+//      box over the chunk's nodes, and every thread adds its particles'
+//      Esirkepov values into copy (lane mod K) with shared-memory atomics, so
+//      lanes of a dense cell collide K times less often;
 //   D. sum the copies and add them to the grid with the charge factor and
 //      alpha at each component's staggered location (Eq. alpha, Sec. II.B),
 //      once per node: the damping of Eq. MaxwellE's source in the flush.
@@ -233,28 +234,44 @@ __global__ void __launch_bounds__(kNT3, sizeof(T) == 4 ? 3 : 2)
       }
       __syncthreads();
       // ---- C. private current copies over the chunk's nodes (compact strides) ----
+      // Each thread keeps its own P particles' moves in registers, so the
+      // stage and the dead field box together hold the copies.
+      int mc0[P], mc1[P];
+      T mo0[P][3], mo1[P][3], mw[P];
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        const int slot = tid * PP + i;
+        mc0[i] = bits_to_cell<T>(stg[7 * ROW + slot]);
+        mc1[i] = bits_to_cell<T>(stg[8 * ROW + slot]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          mo0[i][a] = stg[a * ROW + slot];
+          mo1[i][a] = stg[(4 + a) * ROW + slot];
+        }
+        mw[i] = stg[3 * ROW + slot];
+      }
+      __syncthreads();
+      constexpr int kRoom = (int)((PL::stage + PL::box) / sizeof(T));
       int K = 1;
-      while (K < PL::KMAX && 2 * K * 3 * NB <= 6 * NBOX) K *= 2;
-      T* const BJ = bx_;
+      while (K < PL::KMAX && 2 * K * 3 * NB <= kRoom) K *= 2;
+      T* const BJ = stg;
       for (int t = tid; t < K * 3 * NB; t += kNT3) BJ[t] = T(0);
       __syncthreads();
       T* const Jmine = BJ + (lane & (K - 1)) * 3 * NB;
+#pragma unroll 1
       for (int i = 0; i < P; ++i) {
-        const int slot = tid * PP + i;
-        const int cell1 = bits_to_cell<T>(stg[8 * ROW + slot]);
-        const int cell0 = bits_to_cell<T>(stg[7 * ROW + slot]);
-        if (cell1 < 0 || cell0 < 0) continue;
-        const int c0[3] = {cell_i(cell0), cell_j(cell0), cell_k(cell0)};
-        const int c1[3] = {cell_i(cell1), cell_j(cell1), cell_k(cell1)};
+        if (mc1[i] < 0 || mc0[i] < 0) continue;
+        const int c0[3] = {cell_i(mc0[i]), cell_j(mc0[i]), cell_k(mc0[i])};
+        const int c1[3] = {cell_i(mc1[i]), cell_j(mc1[i]), cell_k(mc1[i])};
         const int org[3] = {ox, oy, oz};
         int lo[3];
         T S0[3][5], DS[3][5];
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          esk_axis<3, T>(c0[a], stg[a * ROW + slot], c1[a], stg[(4 + a) * ROW + slot], lo[a], S0[a], DS[a]);
+          esk_axis<3, T>(c0[a], mo0[i][a], c1[a], mo1[i][a], lo[a], S0[a], DS[a]);
           lo[a] -= org[a];
         }
-        deposit3_box<T>(Jmine, NB, bdx, bdx * bdy, lo, S0, DS, stg[3 * ROW + slot]);
+        deposit3_box<T>(Jmine, NB, bdx, bdx * bdy, lo, S0, DS, mw[i]);
       }
       __syncthreads();
       // ---- D. sum the copies, add to the grid with the charge factor and alpha ----

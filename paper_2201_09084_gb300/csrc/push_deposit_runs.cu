@@ -450,11 +450,18 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
         const int az = min(cell_k(c0), cell_k(c1)) - oz;
         return ax + BX * ay + BXY * az;
       };
+      // count pass: each particle's key and its rank among the chunk's
+      // particles of that key (warp-aggregated counter increments)
+      int keys[P], ranks[P];
+#pragma unroll
       for (int k = 0; k < P; ++k) {
         const int q = tid + k * kNT;
-        const int key = anchor_key((q / P) * PP + (q % P));
-        const unsigned m = __match_any_sync(0xffffffffu, key);
-        if (lane == __ffs(m) - 1) atomicAdd(cnt + key, __popc(m));
+        keys[k] = anchor_key((q / P) * PP + (q % P));
+        const unsigned m = __match_any_sync(0xffffffffu, keys[k]);
+        const int leader = __ffs(m) - 1;
+        int b = 0;
+        if (lane == leader) b = atomicAdd(cnt + keys[k], __popc(m));
+        ranks[k] = __shfl_sync(0xffffffffu, b, leader) + __popc(m & ((1u << lane) - 1u));
       }
       __syncthreads();
       {  // exclusive scan of cnt[0..NBOX]
@@ -489,16 +496,11 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
           }
       }
       __syncthreads();
+      // scatter pass: the scan turned the counters into each key's start
+#pragma unroll
       for (int k = 0; k < P; ++k) {
         const int q = tid + k * kNT;
-        const int slot = (q / P) * PP + (q % P);
-        const int key = anchor_key(slot);
-        const unsigned m = __match_any_sync(0xffffffffu, key);
-        const int leader = __ffs(m) - 1;
-        int b = 0;
-        if (lane == leader) b = atomicAdd(cnt + key, __popc(m));
-        b = __shfl_sync(0xffffffffu, b, leader);
-        perm[b + __popc(m & ((1u << lane) - 1u))] = (unsigned short)slot;
+        perm[cnt[keys[k]] + ranks[k]] = (unsigned short)((q / P) * PP + (q % P));
       }
       __syncthreads();
       // ---- C. deposit runs of P consecutive particles in anchor order ----
@@ -572,14 +574,19 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
         const int first = below ? 31 - __clz(below) : 0;
         const int next = above ? __ffs(above) - 1 : 32;
         const bool big = key >= 0 && next - first >= kMinGroupLanes;
-        unsigned pend = __ballot_sync(0xffffffffu, head && big);
-        while (pend) {
-          const int leader = __ffs(pend) - 1;
-          pend &= pend - 1;
-          const int gk = __shfl_sync(0xffffffffu, key, leader);
-          acc.template group_flush<false>(key == gk, lane, BJ, gk, goff);
+        if (heads == 1u && live == 0xffffffffu) {
+          // the whole warp holds one anchor: no membership masks
+          acc.template group_flush<true>(true, lane, BJ, key, goff);
+        } else {
+          unsigned pend = __ballot_sync(0xffffffffu, head && big);
+          while (pend) {
+            const int leader = __ffs(pend) - 1;
+            pend &= pend - 1;
+            const int gk = __shfl_sync(0xffffffffu, key, leader);
+            acc.template group_flush<false>(key == gk, lane, BJ, gk, goff);
+          }
+          if (key >= 0 && !big) acc.template flush_box<BX, BXY, NBOX>(BJ, key);
         }
-        if (key >= 0 && !big) acc.template flush_box<BX, BXY, NBOX>(BJ, key);
       }
       __syncthreads();
       const int nd = s_ndefer;

@@ -64,6 +64,9 @@ def lib():
             L.ora_num_particles.restype = C.c_long
             L.ora_num_particles.argtypes = [C.c_void_p]
             L.ora_get_particles.argtypes = [C.c_void_p] + [dp] * 6 + [ip]
+            L.ora_get_weights.argtypes = [C.c_void_p, dp]
+            L.ora_weight_integral.restype = C.c_double
+            L.ora_weight_integral.argtypes = [C.c_void_p, dp, dp]
             for f in ("ora_push", "ora_deposit", "ora_deposit_raw", "ora_damp_J", "ora_zero_J",
                       "ora_field_E", "ora_field_B"):
                 getattr(L, f).argtypes = [C.c_void_p]
@@ -104,7 +107,7 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-ALPHA_MODES = {"zero": 0, "one": 1, "damped": 2}
+ALPHA_MODES = {"zero": 0, "one": 1, "damped": 2, "weight": 3}
 
 
 def alpha(dcells, coef=4.0, delta=6.0, p=2.0, v=C_LIGHT, mode="damped"):
@@ -222,8 +225,14 @@ class OracleSim:
         alive = np.zeros(n, dtype=np.int32)
         lib().ora_get_particles(self._h, *[_dp(a) for a in out],
                                 alive.ctypes.data_as(C.POINTER(C.c_int)))
+        w = np.zeros(n)
+        lib().ora_get_weights(self._h, _dp(w))
         return dict(X=out[0], Y=out[1], Z=out[2], ux=out[3], uy=out[4], uz=out[5],
-                    alive=alive.astype(bool))
+                    alive=alive.astype(bool), w=w)
+
+    def weight_integral(self, X0, X1):
+        """The step's damping exponent int sigma/eps0 dt (weight mode)."""
+        return lib().ora_weight_integral(self._h, _dp(_f64(X0)), _dp(_f64(X1)))
 
     # stepping ------------------------------------------------------------
     def step(self, n=1):

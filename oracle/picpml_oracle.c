@@ -93,12 +93,13 @@ double ora_sigma_over_eps0(double dcells, double Delta, double coef, double delt
  * form for the power-law profile:  int_0^d (coef c/Delta)(z/delta)^p dz' (z in
  * metres, z = zc Delta) = coef c delta (d/delta)^{p+1}/(p+1) with d, delta in
  * cells.  mode 0: alpha = 0 inside the PML (Berenger, no source); mode 1:
- * alpha = 1 (undamped deposition); mode 2: Eq. alpha. */
+ * alpha = 1 (undamped deposition); mode 2: Eq. alpha; mode 3: alpha = 1, the
+ * macroparticle weights are damped instead (ora_weight_integral). */
 double ora_alpha(double dcells, double coef, double delta, double p, double v,
                  int mode) {
   if (dcells <= 0.0) return 1.0;
   if (mode == 0) return 0.0;
-  if (mode == 1) return 1.0;
+  if (mode == 1 || mode == 3) return 1.0;
   double integral = coef * (ORA_C / v) * delta * pow(dcells / delta, p + 1.0) / (p + 1.0);
   return exp(-integral);
 }
@@ -245,6 +246,10 @@ void ora_get_particles(const ora_sim* s, double* X, double* Y, double* Z,
     ux[p] = s->u[0][p]; uy[p] = s->u[1][p]; uz[p] = s->u[2][p];
     alive[p] = s->alive[p];
   }
+}
+
+void ora_get_weights(const ora_sim* s, double* w) {
+  for (long p = 0; p < s->np; ++p) w[p] = s->w[p];
 }
 
 /* ------------------------------------------------------------------------- */
@@ -463,7 +468,29 @@ void ora_zero_J(ora_sim* s) {
   for (int c = 0; c < 3; ++c) memset(s->J[c], 0, s->ntot * sizeof(double));
 }
 
-/* Step 3 of the time step: J^{n+1/2} of every particle moved by ora_push. */
+/* Weight damping (alpha mode 3; the scheme of the paper's discussion of
+ * limitations, Sec. II): alpha = 1 in the deposit and each macroparticle's
+ * weight decays as w' = w exp(-int sigma(x(t'))/eps0 dt') along its own path,
+ * so the damping matches every particle's actual velocity.  In corners and
+ * edges the exponent is the sum over the faces (the product of the per-face
+ * factors, as for alpha).  Over one step the integral is taken by the
+ * trapezoid rule on the straight move:
+ *   I = dt (s(X0) + s(X1)) / 2,  s(X) = sum_a sigma_a(depth_a(X)) / eps0,
+ * sigma from Eq. conductivity at the particle's position.  The step's
+ * current uses the mid-step weight w exp(-I/2); the weight then becomes
+ * w exp(-I). */
+double ora_weight_integral(const ora_sim* s, const double* X0, const double* X1) {
+  double sum = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    if (s->dim == 2 && a == 1) continue;
+    sum += ora_sigma_over_eps0(depth_of(s, a, X0[a]), s->d[a], s->sig_coef, s->delta, s->sig_exp);
+    sum += ora_sigma_over_eps0(depth_of(s, a, X1[a]), s->d[a], s->sig_coef, s->delta, s->sig_exp);
+  }
+  return 0.5 * s->dt * sum;
+}
+
+/* Step 3 of the time step: J^{n+1/2} of every particle moved by ora_push
+ * (with weight damping: at the mid-step weight, then the weight decays). */
 void ora_deposit_raw(ora_sim* s) {
   ora_zero_J(s);
   for (long p = 0; p < s->np; ++p) {
@@ -472,7 +499,14 @@ void ora_deposit_raw(ora_sim* s) {
     double X1[3] = {s->X[0][p], s->X[1][p], s->X[2][p]};
     double g = sqrt(1.0 + s->u[0][p] * s->u[0][p] + s->u[1][p] * s->u[1][p] + s->u[2][p] * s->u[2][p]);
     double vy = ORA_C * s->u[1][p] / g;
-    ora_esirkepov(s, X0, X1, s->q[p] * s->w[p], vy);
+    double wd = s->w[p];
+    double I = 0.0;
+    if (s->alpha_mode == 3) {
+      I = ora_weight_integral(s, X0, X1);
+      wd *= exp(-0.5 * I);
+    }
+    ora_esirkepov(s, X0, X1, s->q[p] * wd, vy);
+    if (s->alpha_mode == 3) s->w[p] *= exp(-I);
   }
 }
 

@@ -1,0 +1,109 @@
+"""Pins of the oracle's weight-damping mode (the alternative scheme of the
+paper's discussion of limitations: alpha = 1 in the deposit, each
+macroparticle's weight damped by exp(-int sigma(x(t))/eps0 dt) along its own
+path, trapezoid rule per step).
+
+- Uniform conductivity (profile exponent 0) around a particle at rest inside
+  the PML: the weight decays exactly as exp(-n dt sigma/eps0).
+- Linear profile (exponent 1) and a particle moving at constant velocity
+  inside a PML corner: the trapezoid rule is exact for the linear integrand,
+  so after n steps the weight equals the closed form
+  exp(-sum_a coef c/(d_a delta) (x_a t + v_a t^2 / (2 d_a))), summed over
+  the two faces.
+- The deposited current uses the mid-step weight: one step's total J_z equals
+  that of an undamped deposit times exp(-I/2).
+- The point of the scheme: for a particle slower than the v assumed by
+  Eq. alpha, weight damping leaves a smaller Eq. error than the damped
+  current with v = c (2D, cubic shapes, exit through the +z PML).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+C = O.C_LIGHT
+D2 = (1e-6, 1e-6, 1e-6)
+
+
+def _sim(dim, n, pml, mode, coef=4.0, delta=6.0, p=2.0, order=1, d=(1e-6, 1.2e-6, 0.9e-6)):
+    dt = O.yee_dt(d, 0.9, dim)
+    return O.OracleSim(dim, n, pml, d, dt, order=order, alpha_mode=mode, sig_coef=coef, delta=delta,
+                       sig_exp=p), d, dt
+
+
+def test_weight_uniform_sigma_at_rest():
+    s, d, dt = _sim(3, (10, 10, 10), (8,) * 6, "weight", coef=2.5, p=0.0)
+    X = [8 + 5.3, 8 + 5.1, 8 + 10 + 3.4]          # 3.4 cells deep in the +z PML only
+    s.add_particles([X[0]], [X[1]], [X[2]], [0.0], [0.0], [0.0], [3.0], -O.Q_E, O.M_E)
+    s.set_prescribed(True)
+    n = 25
+    s.step(n)
+    w = s.particles()["w"][0]
+    sig = 2.5 * C / d[2]
+    assert w == pytest.approx(3.0 * np.exp(-n * dt * sig), rel=1e-13)
+
+
+def test_weight_linear_profile_corner_closed_form():
+    coef, delta = 3.0, 5.0
+    s, d, dt = _sim(3, (10, 10, 10), (8,) * 6, "weight", coef=coef, delta=delta, p=1.0)
+    X0 = np.array([8 + 10 + 1.25, 8 + 4.6, 8 + 10 + 0.75])   # inside the +x and +z PMLs
+    u = np.array([0.8, 0.0, 1.1])
+    s.add_particles([X0[0]], [X0[1]], [X0[2]], [u[0]], [u[1]], [u[2]], [2.0], -O.Q_E, O.M_E)
+    s.set_prescribed(True)
+    n = 12
+    s.step(n)
+    g = np.sqrt(1 + u @ u)
+    t = n * dt
+    expo = 0.0
+    for a in (0, 2):
+        x0 = X0[a] - 18.0                     # depth (cells) at t = 0
+        v = C * u[a] / g                      # m/s
+        # int_0^t coef c / d_a (x0 + v t' / d_a) / delta dt'
+        expo += coef * C / (d[a] * delta) * (x0 * t + v * t * t / (2 * d[a]))
+    w = s.particles()["w"][0]
+    assert w == pytest.approx(2.0 * np.exp(-expo), rel=1e-12)
+    assert s.particles()["alive"][0]
+
+
+def test_weight_deposit_uses_mid_step_weight():
+    common = dict(coef=4.0, delta=6.0, p=2.0, order=3)
+    X0, X1 = np.array([8 + 4.3, 8 + 5.2, 8 + 10 + 2.1]), np.array([8 + 4.6, 8 + 5.0, 8 + 10 + 2.8])
+    qw = -O.Q_E * 2.0
+    a, _, _ = _sim(3, (10, 10, 10), (8,) * 6, "weight", **common)
+    b, _, _ = _sim(3, (10, 10, 10), (8,) * 6, "one", **common)
+    b.esirkepov(X0, X1, qw)
+    I = a.weight_integral(X0, X1)
+    assert I > 0
+    a.esirkepov(X0, X1, qw * np.exp(-0.5 * I))
+    for c in "xyz":
+        assert np.allclose(a.field("J" + c), b.field("J" + c) * np.exp(-0.5 * I), rtol=1e-13, atol=0)
+
+
+def _exit_2d(mode, steps, gamma, ref=False, v_assumed=C, n=48, npml=16, m=90):
+    dt = O.yee_dt(D2, 0.99, 2)
+    if ref:
+        s = O.OracleSim(2, (n + 2 * m, 0, n + 2 * m), (0,) * 6, D2, dt, order=3, alpha_mode="one")
+        off = m
+    else:
+        s = O.OracleSim(2, (n, 0, n), (npml, npml, 0, 0, npml, npml), D2, dt, order=3, alpha_mode=mode,
+                        v_assumed=v_assumed)
+        off = npml
+    X = [off + n / 2 + 0.3, 0.0, off + n / 2 + 0.2]
+    u = np.sqrt(gamma ** 2 - 1)
+    s.add_particles([X[0]], [X[1]], [X[2]], [0.0], [0.0], [u], [1.0], -O.Q_E, O.M_E)
+    s.add_particles([X[0]], [X[1]], [X[2]], [0.0], [0.0], [0.0], [1.0], O.Q_E, O.M_E, True)
+    s.set_prescribed(True)
+    s.step(steps)
+    return s, off
+
+
+def test_weight_damping_lifts_the_velocity_limit():
+    gamma = 1.25                                   # v = 0.6 c; Eq. alpha assumes v = c
+    steps = 130                                    # reaches the PML at ~57, absorbed afterwards
+    ref, off_r = _exit_2d(None, steps, gamma, ref=True)
+    offset = (off_r - 16, 0, off_r - 16)
+    e = {mode: O.rel_error(_exit_2d(mode, steps, gamma)[0], ref, offset) for mode in ("one", "damped", "weight")}
+    assert e["weight"] < e["damped"] < e["one"], e
+    # with the particle's own velocity in Eq. alpha the damped current does about as well
+    e_matched = O.rel_error(_exit_2d("damped", steps, gamma, v_assumed=0.6 * C)[0], ref, offset)
+    assert e["weight"] < 2.0 * e_matched, (e, e_matched)

@@ -66,7 +66,15 @@ typedef enum {
   PML_ALPHA_ZERO = 0,   /* alpha = 0 in the PML: Berenger's PML, particles
                            removed on entering it (Sec. I, Eq. MaxwellE) */
   PML_ALPHA_ONE = 1,    /* alpha = 1: undamped deposition in the PML */
-  PML_ALPHA_DAMPED = 2  /* alpha of Eq. alpha (the paper's scheme) */
+  PML_ALPHA_DAMPED = 2, /* alpha of Eq. alpha (the paper's scheme) */
+  PML_ALPHA_WEIGHT = 3  /* alpha = 1 in the deposit; instead each
+                           macroparticle's weight decays as
+                           w exp(-int sigma(x(t))/eps0 dt) along its own path
+                           (the alternative scheme of the paper's discussion
+                           of limitations, Sec. II): per step the trapezoid
+                           rule I = dt (s(x^n) + s(x^{n+1}))/2, s summed over
+                           the faces; the step's current uses w exp(-I/2) and
+                           the stored weight becomes w exp(-I) */
 } pml_alpha_mode;
 
 /* Grid description.  n[] counts PHYSICAL cells (the PML cells of pml_desc

@@ -176,7 +176,7 @@ double picpml::sigma_eps0_face(const pml_desc& p, double Delta, double dc) {
 double picpml::alpha_face(const pml_desc& p, double dc) {
   if (dc <= 0.0) return 1.0;
   if (p.alpha_mode == PML_ALPHA_ZERO) return 0.0;
-  if (p.alpha_mode == PML_ALPHA_ONE) return 1.0;
+  if (p.alpha_mode == PML_ALPHA_ONE || p.alpha_mode == PML_ALPHA_WEIGHT) return 1.0;
   const double v = p.v_assumed > 0 ? p.v_assumed : kC;
   const double e = p.sigma_max_coef * (kC / v) * p.delta_cells *
                    std::pow(dc / p.delta_cells, p.exponent + 1.0) / (p.exponent + 1.0);
@@ -321,7 +321,7 @@ int pic_init(picpml_ctx** out, const pic_grid_desc* g, void* stream) {
 int pml_init(picpml_ctx* ctx, const pml_desc* p) {
   if (!ctx || !p) return fail(ctx, PIC_EINVAL, "null argument");
   if (ctx->ready) return fail(ctx, PIC_ESTATE, "pml_init called twice");
-  if (p->alpha_mode < 0 || p->alpha_mode > 2) return fail(ctx, PIC_EINVAL, "bad alpha_mode");
+  if (p->alpha_mode < 0 || p->alpha_mode > 3) return fail(ctx, PIC_EINVAL, "bad alpha_mode");
   if (p->sigma_max_coef < 0 || !(p->delta_cells > 0) || p->exponent < 0)
     return fail(ctx, PIC_EINVAL, "bad conductivity profile");
   const pic_grid_desc& gd = ctx->gd;
@@ -356,6 +356,10 @@ int pml_init(picpml_ctx* ctx, const pml_desc* p) {
   }
   if (g.N[0] > 1023 || g.N[1] > 1023 || g.N[2] > 2047)
     return fail(ctx, PIC_EINVAL, "grid too large for the packed cell index (1023 x 1023 x 2047 cells)");
+  g.wdamp = p->alpha_mode == PML_ALPHA_WEIGHT ? 1 : 0;
+  for (int a = 0; a < 3; ++a) g.wk[a] = (gd.dim == 2 && a == 1) ? 0.0 : p->sigma_max_coef * g.S[a];
+  g.winv_delta = 1.0 / p->delta_cells;
+  g.wexp = p->exponent;
   g.px = (g.nn[0] + 7) / 8 * 8;
   g.sy = g.px;
   g.sz = (long long)g.px * g.nn[1];

@@ -69,6 +69,8 @@ struct BatchArgs {
   T ke, cjx, cjz, cjy;
   double S[3];
   float Sf[3], Sfl[3];
+  int wdamp;                 // weight damping (PML_ALPHA_WEIGHT): see Geom
+  double wk[3], winv_delta, wexp;
   unsigned* status;
   unsigned long long* pushed;
   int prescribed;
@@ -121,6 +123,10 @@ __global__ void __launch_bounds__(NT, MINB) k_batch_step(BatchArgs<T> a, int par
       g.Sf[ax] = a.Sf[ax];
       g.Sfl[ax] = a.Sfl[ax];
     }
+    g.wdamp = a.wdamp;
+    for (int ax = 0; ax < 3; ++ax) g.wk[ax] = a.wk[ax];
+    g.winv_delta = a.winv_delta;
+    g.wexp = a.wexp;
     g.plo[0] = ri.p; g.nph[0] = ri.nx;
     g.plo[1] = 0; g.nph[1] = 0;
     g.plo[2] = ri.p; g.nph[2] = ri.nz;
@@ -193,14 +199,20 @@ __global__ void __launch_bounds__(NT, MINB) k_batch_step(BatchArgs<T> a, int par
             o1[ax] = x;
             if (c1[ax] < g.rmin[ax] || c1[ax] > g.rmax[ax] || (c1[ax] == g.rmax[ax] && x > T(0))) out = true;
           }
-          PIO<T>::store(a.pos, a.mom, run, out ? o : o1, w, u, out ? -1 : pack_cell(c1[0], 0, c1[2]));
+          const int cc0[3] = {c[0], 0, c[2]};
+          T wd = w, wn = w;
+          if (g.wdamp && !out) {  // weight damping: mid-step weight for the current, then decay
+            const T I = weight_exponent<T>(g, cc0, o, c1, o1);
+            wd = w * exp(T(-0.5) * I);
+            wn = w * exp(-I);
+          }
+          PIO<T>::store(a.pos, a.mom, run, out ? o : o1, wn, u, out ? -1 : pack_cell(c1[0], 0, c1[2]));
           if (!out) {
             SpeciesPtrs<T> sp{};
             sp.cj[0] = a.cjx;
             sp.cj[2] = a.cjz;
             sp.cjy2d = a.cjy;
-            const int cc0[3] = {c[0], 0, c[2]};
-            deposit_run_particle<ORDER, T>(g, tb, f, sp, cc0, o, c1, o1, w, u[1] * mv.inv_gamma());
+            deposit_run_particle<ORDER, T>(g, tb, f, sp, cc0, o, c1, o1, wd, u[1] * mv.inv_gamma());
           }
         }
       }
@@ -402,6 +414,10 @@ void set_constants(pic_batch* b, const RunInfo* runs_dev, const int* order_dev, 
   a.status = status;
   a.pushed = pushed;
   a.prescribed = 0;
+  a.wdamp = b->d.pml.alpha_mode == PML_ALPHA_WEIGHT ? 1 : 0;
+  for (int ax = 0; ax < 3; ++ax) a.wk[ax] = b->d.pml.sigma_max_coef * S[ax];
+  a.winv_delta = 1.0 / b->d.pml.delta_cells;
+  a.wexp = b->d.pml.exponent;
 }
 
 }  // namespace
@@ -423,7 +439,7 @@ int pic_batch_init(pic_batch** out, const pic_batch_desc* d, void* stream) {
   if (d->prec != PIC_FP32 && d->prec != PIC_FP64) return bfail(b, PIC_EINVAL, "prec must be PIC_FP32 or PIC_FP64");
   if (!(d->d[0] > 0 && d->d[1] > 0) || !(d->m > 0) || !d->pos || !d->mom)
     return bfail(b, PIC_EINVAL, "cell sizes, mass and particle arrays");
-  if (d->pml.alpha_mode < 0 || d->pml.alpha_mode > 2 || !(d->pml.delta_cells > 0))
+  if (d->pml.alpha_mode < 0 || d->pml.alpha_mode > 3 || !(d->pml.delta_cells > 0))
     return bfail(b, PIC_EINVAL, "PML profile");
   const double lim = 1.0 / (kC * std::sqrt(1.0 / (d->d[0] * d->d[0]) + 1.0 / (d->d[1] * d->d[1])));
   double dt = d->dt;

@@ -236,6 +236,40 @@ __device__ __forceinline__ const float* al_cent<float>(const Tables& tb, int a) 
 template <>
 __device__ __forceinline__ const double* al_cent<double>(const Tables& tb, int a) { return tb.al_cd[a]; }
 
+// Weight damping (the alternative scheme of the paper's discussion of
+// limitations): alpha = 1 in the deposit, and a macroparticle's weight decays
+// as w exp(-int sigma(x(t))/eps0 dt) along its own path, summed over the
+// faces.  Per step the integral is the trapezoid rule on the straight move,
+// I = (dt s(x0) + dt s(x1)) / 2; the step's current uses w exp(-I/2), the
+// weight then becomes w exp(-I).  Depths in cells from cell index + offset.
+template <typename T>
+__device__ __forceinline__ T pml_depth(const Geom& g, int a, int c, T o) {
+  const int lo = g.plo[a], hi = g.plo[a] + g.nph[a];
+  if (c < lo) return T(lo - c) - o;
+  if (c >= hi) return T(c - hi) + o;
+  return T(0);
+}
+template <typename T>
+__device__ __forceinline__ T sdt_at_depth(const Geom& g, int a, T d) {
+  if (!(d > T(0))) return T(0);
+  const T x = d * T(g.winv_delta);
+  const T p = T(g.wexp);
+  const T xp = p == T(2) ? x * x : (p == T(1) ? x : (p == T(0) ? T(1) : pow(x, p)));
+  return T(g.wk[a]) * xp;
+}
+template <typename T>
+__device__ __forceinline__ T weight_exponent(const Geom& g, const int c0[3], const T o0[3], const int c1[3],
+                                             const T o1[3]) {
+  T sum = T(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (g.dim == 2 && a == 1) continue;
+    sum += sdt_at_depth<T>(g, a, pml_depth<T>(g, a, c0[a], o0[a]));
+    sum += sdt_at_depth<T>(g, a, pml_depth<T>(g, a, c1[a], o1[a]));
+  }
+  return T(0.5) * sum;
+}
+
 // Old (S0) and new (S1) shape values on the ORDER+2 nodes starting at
 // min(i0,i1) - (ORDER==3).
 template <int ORDER, typename T>

@@ -37,11 +37,17 @@ __global__ void __launch_bounds__(256) k_particles(Geom g, Tables tb, FieldPtrs<
       if (cell < 0 || cell0 < 0) continue;
       const int c0[3] = {cell_i(cell0), cell_j(cell0), cell_k(cell0)};
       const int c1[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
+      T wd = w;
+      if (g.wdamp) {  // weight damping: mid-step weight for the current, then decay
+        const T I = weight_exponent<T>(g, c0, o0, c1, o);
+        wd = w * exp(T(-0.5) * I);
+        PIO<T>::store(sp.pos, sp.mom, p, o, w * exp(-I), u, cell);
+      }
       if constexpr (FIX) {
-        deposit_fixed<ORDER>(g, f, sp.qn, c0, o0, c1, o, w, status);
+        deposit_fixed<ORDER>(g, f, sp.qn, c0, o0, c1, o, wd, status);
       } else {
         const T g2 = sqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-        deposit_one<ORDER, DIM, T>(g, tb, f, sp, c0, o0, c1, o, w, u[1] / g2);
+        deposit_one<ORDER, DIM, T>(g, tb, f, sp, c0, o0, c1, o, wd, u[1] / g2);
       }
       continue;
     }
@@ -116,11 +122,18 @@ __global__ void __launch_bounds__(256) k_particles(Geom g, Tables tb, FieldPtrs<
     }
     const int cell1 = out ? -1 : pack_cell(c1[0], c1[1], c1[2]);
     if (MODE == 0) PIO<T>::save(sp.save_pos, p, o, out ? -1 : cell);
-    PIO<T>::store(sp.pos, sp.mom, p, out ? o : o1, w, u, cell1);
+    // weight damping (fused step only; the stage call deposit() applies it)
+    T wd = w, wn = w;
+    if (MODE == 2 && g.wdamp && !out) {
+      const T I = weight_exponent<T>(g, c, o, c1, o1);
+      wd = w * exp(T(-0.5) * I);
+      wn = w * exp(-I);
+    }
+    PIO<T>::store(sp.pos, sp.mom, p, out ? o : o1, wn, u, cell1);
     if constexpr (MODE == 2 && FIX) {
-      if (!out) deposit_fixed<ORDER>(g, f, sp.qn, c, o, c1, o1, w, status);
+      if (!out) deposit_fixed<ORDER>(g, f, sp.qn, c, o, c1, o1, wd, status);
     } else if (MODE == 2 && !out) {
-      deposit_one<ORDER, DIM, T>(g, tb, f, sp, c, o, c1, o1, w, u[1] * ig);
+      deposit_one<ORDER, DIM, T>(g, tb, f, sp, c, o, c1, o1, wd, u[1] * ig);
     }
   }
   // particles pushed this launch: warp sum, one atomic per warp

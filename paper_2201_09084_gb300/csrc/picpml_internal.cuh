@@ -38,6 +38,11 @@ struct Geom {
   int plo[3];      // PML cells on the low face
   int nph[3];      // physical cells
   int rmin[3], rmax[3];  // a particle at X = i + f stays while rmin <= X <= rmax
+  // weight damping (alpha mode PML_ALPHA_WEIGHT): dt sigma/eps0 at depth d
+  // cells into a face is wk[a] (d / delta)^wexp, wk[a] = coef c dt / d_a
+  int wdamp;
+  double wk[3];
+  double winv_delta, wexp;
   __host__ __device__ long long idx(int i, int j, int k) const {
     return (long long)i + sy * j + sz * k;
   }

@@ -133,8 +133,14 @@ __device__ __noinline__ unsigned particle3_global(const Geom& g, const Tables& t
   int c1[3];
   T o1[3], ig;
   const bool in = move_particle<3, T>(g, o, c, u, c1, o1, ig);
-  PIO<T>::store(sp.pos, sp.mom, gp, in ? o1 : o, w, u, in ? pack_cell(c1[0], c1[1], c1[2]) : -1);
-  if (in) deposit_one<3, 3, T>(g, tb, f, sp, c, o, c1, o1, w, T(0));
+  T wd = w, wn = w;
+  if (g.wdamp && in) {
+    const T I = weight_exponent<T>(g, c, o, c1, o1);
+    wd = w * exp(T(-0.5) * I);
+    wn = w * exp(-I);
+  }
+  PIO<T>::store(sp.pos, sp.mom, gp, in ? o1 : o, wn, u, in ? pack_cell(c1[0], c1[1], c1[2]) : -1);
+  if (in) deposit_one<3, 3, T>(g, tb, f, sp, c, o, c1, o1, wd, T(0));
   return 1;
 }
 
@@ -226,7 +232,13 @@ __global__ void __launch_bounds__(kNT3, sizeof(T) == 4 ? 3 : 2)
         T o1[3], ig;
         const bool in = move_particle<3, T>(g, o, c, u, c1, o1, ig);
         const int cell1 = in ? pack_cell(c1[0], c1[1], c1[2]) : -1;
-        PIO<T>::store(sp.pos, sp.mom, gp, in ? o1 : o, w, u, cell1);
+        T wn = w;
+        if (g.wdamp && in) {  // weight damping: mid-step weight for this step's current
+          const T I = weight_exponent<T>(g, c, o, c1, o1);
+          stg[3 * ROW + slot] = w * exp(T(-0.5) * I);
+          wn = w * exp(-I);
+        }
+        PIO<T>::store(sp.pos, sp.mom, gp, in ? o1 : o, wn, u, cell1);
         stg[4 * ROW + slot] = o1[0];
         stg[5 * ROW + slot] = o1[1];
         stg[6 * ROW + slot] = o1[2];

@@ -299,8 +299,14 @@ __device__ __noinline__ unsigned particle_global(const Geom& g, const Tables& tb
   int c1[3];
   T o1[3], ig;
   const bool in = move_particle<DIM, T>(g, o, c, u, c1, o1, ig);
-  PIO<T>::store(sp.pos, sp.mom, gp, in ? o1 : o, w, u, in ? pack_cell(c1[0], c1[1], c1[2]) : -1);
-  if (in) deposit_one<1, DIM, T>(g, tb, f, sp, c, o, c1, o1, w, u[1] * ig);
+  T wd = w, wn = w;
+  if (g.wdamp && in) {
+    const T I = weight_exponent<T>(g, c, o, c1, o1);
+    wd = w * exp(T(-0.5) * I);
+    wn = w * exp(-I);
+  }
+  PIO<T>::store(sp.pos, sp.mom, gp, in ? o1 : o, wn, u, in ? pack_cell(c1[0], c1[1], c1[2]) : -1);
+  if (in) deposit_one<1, DIM, T>(g, tb, f, sp, c, o, c1, o1, wd, u[1] * ig);
   return 1;
 }
 
@@ -423,12 +429,18 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
         T o1[3], ig;
         const bool in = move_particle<DIM, T>(g, o, c, u, c1, o1, ig);
         const int cell1 = in ? pack_cell(c1[0], c1[1], c1[2]) : -1;
-        PIO<T>::store(sp.pos, sp.mom, gp, in ? o1 : o, w, u, cell1);
+        T wn = w;
+        if (g.wdamp && in) {  // weight damping: mid-step weight for this step's current
+          const T I = weight_exponent<T>(g, c, o, c1, o1);
+          stg[3 * ROW + slot] = w * exp(T(-0.5) * I);
+          wn = w * exp(-I);
+        }
+        PIO<T>::store(sp.pos, sp.mom, gp, in ? o1 : o, wn, u, cell1);
         stg[4 * ROW + slot] = o1[0];
         stg[5 * ROW + slot] = o1[1];
         stg[6 * ROW + slot] = o1[2];
         stg[8 * ROW + slot] = cell_to_bits<T>(cell1);
-        if constexpr (DIM == 2) stg[9 * ROW + slot] = w * u[1] * ig;
+        if constexpr (DIM == 2) stg[9 * ROW + slot] = stg[3 * ROW + slot] * u[1] * ig;
       }
       __syncthreads();
       // ---- B. counting sort of the chunk by box-local anchor ----

@@ -18,21 +18,22 @@ def _runs(n, seed):
     return I.batched_runs(n, size_range=(20, 44), pml_range=(6, 12), gamma_range=(1.5, 30.0), seed=seed)
 
 
+@pytest.mark.parametrize("mode", ["damped", "weight"])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("order", [1, 3])
-def test_batched_runs_match_single_oracle_boxes(order, prec):
+def test_batched_runs_match_single_oracle_boxes(order, prec, mode):
     import torch
     from paper_2201_09084_gb300.api import Batch, pack_particles
     r = _runs(7, seed=31 + order)
     dt = O.yee_dt(D2, 0.99, 2)
     pos, mom = pack_particles(r["cell"], r["off"], r["u"], r["w"], prec)
     b = Batch(r["nx"], r["nz"], r["npml"], (D2[0], D2[2]), pos, mom, r["q"], r["m"], dt=dt, order=order,
-              prec=prec, alpha_mode="damped")
+              prec=prec, alpha_mode=mode)
     oras = []
     for k in range(7):
         p = int(r["npml"][k])
         s = O.OracleSim(2, (int(r["nx"][k]), 0, int(r["nz"][k])), (p, p, 0, 0, p, p), D2, dt, order=order,
-                        alpha_mode="damped")
+                        alpha_mode=mode)
         X = I.absolute(r["cell"][k:k + 1], r["off"][k:k + 1])
         u = r["u"][k].astype(np.float64)
         s.add_particles(X[:, 0], X[:, 1], X[:, 2], [u[0]], [u[1]], [u[2]], [1.0], r["q"], r["m"])

@@ -57,10 +57,11 @@ def test_field_step_parity(dim, prec):
     assert max(err.values()) < TOL[prec], err
 
 
+@pytest.mark.parametrize("mode", ["damped", "weight"])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("order", [1, 3])
 @pytest.mark.parametrize("dim", [3, 2])
-def test_push_deposit_stage_parity(dim, order, prec):
+def test_push_deposit_stage_parity(dim, order, prec, mode):
     """One push and one deposit in smooth nonzero fields: positions, momenta
     and the damped current agree; particles straddle the PML interface."""
     nphys = (20, 18, 22)
@@ -69,7 +70,7 @@ def test_push_deposit_stage_parity(dim, order, prec):
     lo = [4, 4 if dim == 3 else 0, 4]
     hi = [6 + 20 + 2, (6 + 18 + 2) if dim == 3 else 1, 6 + 22 + 2]
     parts = I.random_particles(dim, 3000, lo, hi, u_rms=2.0, seed=11 + order)
-    ora, gpu = make_pair(dim, nphys, pml, d, parts, order=order, prec=prec)
+    ora, gpu = make_pair(dim, nphys, pml, d, parts, order=order, prec=prec, alpha_mode=mode)
     f = _pulse(ora.nn, pml, dim)
     for s in (ora, gpu):
         s.set_field("Ex", 3e11 * f / 1e6)
@@ -97,7 +98,7 @@ def test_push_deposit_stage_parity(dim, order, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-@pytest.mark.parametrize("mode", ["zero", "one", "damped"])
+@pytest.mark.parametrize("mode", ["zero", "one", "damped", "weight"])
 @pytest.mark.parametrize("order", [1, 3])
 def test_single_particle_exit_2d(order, mode, prec):
     """A gamma = 10 electron and its motionless partner (App. A); the electron
@@ -114,6 +115,10 @@ def test_single_particle_exit_2d(order, mode, prec):
     Xg, ug, alive = gpu_positions(gpu, 0)
     Xo = ora.particles()
     assert alive[0] == Xo["alive"][0]
+    if mode == "weight" and alive[0]:
+        wg = float(gpu.particles(0)["w"][0])
+        assert wg < 1.0
+        assert abs(wg - Xo["w"][0]) <= (2e-6 if prec == "fp32" else 1e-12) * Xo["w"][0]
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
@@ -134,6 +139,33 @@ def test_beam_exit_3d(theta, order, prec):
         assert max(err.values()) < TOL[prec], err
     Xg, ug, alive = gpu_positions(gpu, 0)
     assert np.array_equal(alive, ora.particles()["alive"])
+
+
+@pytest.mark.parametrize("ppt", [1, 4])
+@pytest.mark.parametrize("order", [1, 3])
+def test_beam_exit_3d_weight_damping(order, ppt):
+    """The beam of test_beam_exit_3d, slower (u_z ~ N(2, 0.1)) so it is still
+    inside the PML with damped weights at the end, with per-particle weight
+    damping instead of the damped current: the chunk kernel and the
+    one-thread-per-particle kernel, fields and weights against the oracle."""
+    nphys = (22, 19, 26)
+    pml = (6, 6, 6, 6, 6, 6)
+    center = (6 + 11.3, 6 + 9.6, 6 + 19.0)
+    parts = I.beam(3, 2000, nphys, pml, center, sigma=(1.5, 1.5, 2.5), theta_deg=15.0, clip=3.0,
+                   uz_mean=2.0, uz_rms=0.1)
+    ora, gpu = make_pair(3, nphys, pml, D3, parts, order=order, prec="fp32", alpha_mode="weight")
+    gpu.set_tuning(ppt, 1)
+    for _ in range(2):
+        ora.step(10)
+        gpu.step(10)
+        err = max_field_err(ora, gpu)
+        assert max(err.values()) < TOL["fp32"], err
+    po, pg = ora.particles(), gpu.particles(0)
+    assert np.array_equal(pg["alive"], po["alive"])
+    a = pg["alive"]
+    damped = po["w"][a] < po["w"][a].max() * (1 - 1e-6)
+    assert damped.sum() > 100
+    assert np.abs(pg["w"][a] - po["w"][a]).max() <= 2e-6 * po["w"][a].max()
 
 
 def test_sort_keeps_particles_and_drops_removed():

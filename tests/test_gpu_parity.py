@@ -118,8 +118,8 @@ def test_single_particle_exit_2d(order, mode, prec):
     if mode == "weight" and alive[0]:
         wg = float(gpu.particles(0)["w"][0])
         assert wg < 1.0
-        # FP32: one multiply by an FP32 exponential per step, about 4 ulp each
-        assert abs(wg - Xo["w"][0]) <= (120 * 4 * 6e-8 if prec == "fp32" else 1e-12) * Xo["w"][0]
+        # FP32: the per-step factor is rounded and follows the FP32 trajectory
+        assert abs(wg - Xo["w"][0]) <= (TOL["fp32"] if prec == "fp32" else 1e-12) * Xo["w"][0]
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
@@ -166,9 +166,10 @@ def test_beam_exit_3d_weight_damping(order, ppt):
     a = pg["alive"]
     damped = po["w"][a] < po["w"][a].max() * (1 - 1e-6)
     assert damped.sum() > 100
-    # the FP32 weight takes one multiply by an FP32 exponential per step:
-    # about 4 ulp (6e-8 each) per step over 20 steps
-    assert np.all(np.abs(pg["w"][a] - po["w"][a]) <= 20 * 4 * 6e-8 * po["w"][a])
+    # FP32 weights: each step's factor exp(-I) is rounded (a few ulp) and I
+    # follows the FP32 trajectory (positions within ~1e-6 cell of the oracle's,
+    # times an accumulated exponent of a few): the FP32 tolerance, 1e-5 relative
+    assert np.all(np.abs(pg["w"][a] - po["w"][a]) <= TOL["fp32"] * po["w"][a])
 
 
 def test_sort_keeps_particles_and_drops_removed():

@@ -33,17 +33,4 @@ __device__ __forceinline__ ff ff_mul(float2 a, ff b) {
 }
 
 
-// One split-part pair advance with float-float storage: each part
-// F <- ea F + eb (r + source); returns the rounded total of both parts.
-__device__ __forceinline__ float advff(float2* p0, float2* p1, long long id, float r0, float r1, float src, float2 ea0,
-                                       float2 eb0, float2 ea1, float2 eb1, bool into1) {
-  const float2 a = p0[id], b = p1[id];
-  ff e0 = ff_add(ff_mul(ea0, ff{a.x, a.y}), ff_mul(eb0, ff_two_sum(r0, into1 ? 0.f : src)));
-  ff e1 = ff_add(ff_mul(ea1, ff{b.x, b.y}), ff_mul(eb1, ff_two_sum(r1, into1 ? src : 0.f)));
-  p0[id] = make_float2(e0.h, e0.l);
-  p1[id] = make_float2(e1.h, e1.l);
-  const ff t = ff_add(e0, e1);
-  return __fadd_rn(t.h, t.l);
-}
-
 }  // namespace picpml

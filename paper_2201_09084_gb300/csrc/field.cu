@@ -21,8 +21,9 @@
 //            FP32 instruction cost and the same 8 bytes per part.
 // Conductivity comparisons and Courant numbers use float copies, so FP32
 // fields need no FP64 instruction outside the FP64 parts.  Launch bounds ask
-// for 6 blocks of 256 per SM (one node per thread) to keep more loads in
-// flight; the passes are memory-latency bound.
+// for 6 blocks of 256 per SM for FP32 (one node per thread) to keep more
+// loads in flight (the passes are memory-latency bound), 4 for FP64, whose
+// node update needs more registers.
 #include "field_node.cuh"
 
 namespace picpml {
@@ -54,7 +55,7 @@ __device__ __forceinline__ bool node_of_thread(const Geom& g, int KZ, int& i, in
 }
 
 template <typename T, int DIM, int SPL, int KZ>
-__global__ void __launch_bounds__(256, KZ == 1 ? 6 : 4) k_field_E(Geom g, Tables tb, FieldPtrs<T> f) {
+__global__ void __launch_bounds__(256, KZ == 1 && sizeof(T) == 4 ? 6 : 4) k_field_E(Geom g, Tables tb, FieldPtrs<T> f) {
   int i, j, k0;
   if (!node_of_thread<DIM>(g, KZ, i, j, k0)) return;
   long long id = g.idx(i, j, k0);
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(256, KZ == 1 ? 6 : 4) k_field_E(Geom g, Tables
 }
 
 template <typename T, int DIM, int SPL, int KZ>
-__global__ void __launch_bounds__(256, KZ == 1 ? 6 : 4) k_field_B(Geom g, Tables tb, FieldPtrs<T> f) {
+__global__ void __launch_bounds__(256, KZ == 1 && sizeof(T) == 4 ? 6 : 4) k_field_B(Geom g, Tables tb, FieldPtrs<T> f) {
   int i, j, k0;
   if (!node_of_thread<DIM>(g, KZ, i, j, k0)) return;
   long long id = g.idx(i, j, k0);

@@ -10,38 +10,69 @@
 namespace picpml {
 namespace fn {
 
-// ---- split-part advance, FP64 parts ----
-template <typename T>
-__device__ __forceinline__ T adv64(double* p0, double* p1, long long id, T r0, T r1, T src, double ea0, double eb0,
-                                   double ea1, double eb1, bool into1) {
-  double e0 = p0[id], e1 = p1[id];
-  e0 = ea0 * e0 + eb0 * ((double)r0 + (into1 ? 0.0 : (double)src));
-  e1 = ea1 * e1 + eb1 * ((double)r1 + (into1 ? (double)src : 0.0));
-  p0[id] = e0;
-  p1[id] = e1;
-  return (T)(e0 + e1);
+// A split location's two parts, held in registers between their load and
+// their store (FP64 parts, or float-float pairs).
+template <int SPL>
+struct Parts;
+template <>
+struct Parts<1> {
+  float2 a, b;
+};
+template <>
+struct Parts<0> {
+  double a, b;
+};
+
+template <int SPL>
+__device__ __forceinline__ Parts<SPL> load_parts(double* const* parts, long long id) {
+  if constexpr (SPL == 1)
+    return {reinterpret_cast<const float2*>(parts[0])[id], reinterpret_cast<const float2*>(parts[1])[id]};
+  else
+    return {parts[0][id], parts[1][id]};
 }
 
-// Advances one split location with parts along axes (A, B) at table indices
-// (ia, ib); node tables for E, centre tables for B.  Returns the new total.
+template <int SPL>
+__device__ __forceinline__ void store_parts(double* const* parts, long long id, const Parts<SPL>& pv) {
+  if constexpr (SPL == 1) {
+    reinterpret_cast<float2*>(parts[0])[id] = pv.a;
+    reinterpret_cast<float2*>(parts[1])[id] = pv.b;
+  } else {
+    parts[0][id] = pv.a;
+    parts[1][id] = pv.b;
+  }
+}
+
+// Advances one split location's parts (in registers) along axes (A, B) at
+// table indices (ia, ib); node tables for E, centre tables for B.  Each part
+// F <- e^{-s dt} F + (1 - e^{-s dt})/(s dt) (r + source), the source going to
+// the part with the larger conductivity.  Returns the new total.
 template <typename T, int SPL, bool CENT>
-__device__ __forceinline__ T advance(const Tables& tb, double* const* parts, long long id, int A, int ia, int B,
-                                     int ib, T r0, T r1, T src, float sA, float sB) {
+__device__ __forceinline__ T advance(const Tables& tb, Parts<SPL>& pv, int A, int ia, int B, int ib, T r0, T r1,
+                                     T src, float sA, float sB) {
   const bool into1 = sB > sA;
-  if (SPL == 1) {
+  if constexpr (SPL == 1) {
     const float2 one = make_float2(1.f, 0.f);
     const float2 ea0 = A >= 0 ? (CENT ? tb.ea2_c[A][ia] : tb.ea2_n[A][ia]) : one;
     const float2 eb0 = A >= 0 ? (CENT ? tb.eb2_c[A][ia] : tb.eb2_n[A][ia]) : one;
     const float2 ea1 = B >= 0 ? (CENT ? tb.ea2_c[B][ib] : tb.ea2_n[B][ib]) : one;
     const float2 eb1 = B >= 0 ? (CENT ? tb.eb2_c[B][ib] : tb.eb2_n[B][ib]) : one;
-    return (T)advff(reinterpret_cast<float2*>(parts[0]), reinterpret_cast<float2*>(parts[1]), id, (float)r0,
-                    (float)r1, (float)src, ea0, eb0, ea1, eb1, into1);
+    const float s = (float)src;
+    const ff e0 = ff_add(ff_mul(ea0, ff{pv.a.x, pv.a.y}), ff_mul(eb0, ff_two_sum((float)r0, into1 ? 0.f : s)));
+    const ff e1 = ff_add(ff_mul(ea1, ff{pv.b.x, pv.b.y}), ff_mul(eb1, ff_two_sum((float)r1, into1 ? s : 0.f)));
+    pv.a = make_float2(e0.h, e0.l);
+    pv.b = make_float2(e1.h, e1.l);
+    const ff t = ff_add(e0, e1);
+    return (T)__fadd_rn(t.h, t.l);
   } else {
     const double ea0 = A >= 0 ? (CENT ? tb.ea_c[A][ia] : tb.ea_n[A][ia]) : 1.0;
     const double eb0 = A >= 0 ? (CENT ? tb.eb_c[A][ia] : tb.eb_n[A][ia]) : 1.0;
     const double ea1 = B >= 0 ? (CENT ? tb.ea_c[B][ib] : tb.ea_n[B][ib]) : 1.0;
     const double eb1 = B >= 0 ? (CENT ? tb.eb_c[B][ib] : tb.eb_n[B][ib]) : 1.0;
-    return adv64<T>(parts[0], parts[1], id, r0, r1, src, ea0, eb0, ea1, eb1, into1);
+    const double e0 = ea0 * pv.a + eb0 * ((double)r0 + (into1 ? 0.0 : (double)src));
+    const double e1 = ea1 * pv.b + eb1 * ((double)r1 + (into1 ? (double)src : 0.0));
+    pv.a = e0;
+    pv.b = e1;
+    return (T)(e0 + e1);
   }
 }
 
@@ -62,9 +93,11 @@ __device__ __forceinline__ bool pml_cent(const Geom& g, int a, int i) {
 }
 
 // E^{n+1} at node (i,j,k).  by_m, bx_m: By, Bx at (i,j,k-1).  GEO: decide
-// the split locations from the box geometry (single boxes), so the split
-// parts' loads need not wait for the conductivity tables; else from the
-// tables (batched runs).
+// the split locations from the box geometry (the split parts' loads then need
+// no table load first); else from the conductivity tables.  Every load of the
+// node comes before any of its stores (the compiler cannot reorder loads
+// across stores to arrays that might alias), so a thread has all its memory
+// requests in flight at once.
 template <typename T, int DIM, int SPL, bool GEO = false>
 __device__ __forceinline__ void e_update(const Geom& g, const Tables& tb, const FieldPtrs<T>& f, int i, int j, int k,
                                          long long id, T by_m, T bx_m, T by0, T bx0, T bz0) {
@@ -79,46 +112,60 @@ __device__ __forceinline__ void e_update(const Geom& g, const Tables& tb, const 
   const bool px = GEO ? pml_node(g, 0, i) : sxn > 0.f;
   const bool py = DIM == 3 && (GEO ? pml_node(g, 1, j) : syn > 0.f);
   const bool pz = GEO ? pml_node(g, 2, k) : szn > 0.f;
-  // J' is consumed here: read once, zeroed where it was nonzero (most of the
-  // grid carries no current, so most threads write nothing back).
-  const T jx = f.J[0][id], jy = f.J[1][id], jz = f.J[2][id];
-  if (jx != T(0)) f.J[0][id] = T(0);
-  if (jy != T(0)) f.J[1][id] = T(0);
-  if (jz != T(0)) f.J[2][id] = T(0);
+  // Ex(i+1/2, j, k): parts along y (sigma_y at node j) and z (sigma_z at node k);
+  // Ey(i, j+1/2, k): parts along x and z; Ez(i, j, k+1/2): parts along x and y
+  const bool okx = i <= N0 - 1 && jin && kin;
+  const bool oky = iin && (DIM == 2 || j <= N1 - 1) && kin;
+  const bool okz = iin && jin && k <= N2 - 1;
+  const bool spx = okx && (py || pz), spy = oky && (px || pz), spz = okz && (px || py);
   const T* __restrict__ Bx = f.Bh[0];
   const T* __restrict__ By = f.Bh[1];
   const T* __restrict__ Bz = f.Bh[2];
-  // Ex(i+1/2, j, k): parts along y (sigma_y at node j) and z (sigma_z at node k)
-  if (i <= N0 - 1 && jin && kin) {
-    const T r0 = DIM == 3 ? Sy * (bz0 - Bz[id - g.sy]) : T(0);
+  // ---- loads: J' (consumed here), the B neighbours, E or the split parts ----
+  const T jx = f.J[0][id], jy = f.J[1][id], jz = f.J[2][id];
+  const T bz_ym = DIM == 3 && okx ? Bz[id - g.sy] : T(0);
+  const T bz_xm = oky ? Bz[id - 1] : T(0);
+  const T by_xm = okz ? By[id - 1] : T(0);
+  const T bx_ym = DIM == 3 && okz ? Bx[id - g.sy] : T(0);
+  T ex = okx && !spx ? f.E[0][id] : T(0);
+  T ey = oky && !spy ? f.E[1][id] : T(0);
+  T ez = okz && !spz ? f.E[2][id] : T(0);
+  Parts<SPL> qx{}, qy{}, qz{};
+  if (spx) qx = load_parts<SPL>(f.Es[0], id);
+  if (spy) qy = load_parts<SPL>(f.Es[1], id);
+  if (spz) qz = load_parts<SPL>(f.Es[2], id);
+  // ---- update ----
+  if (okx) {
+    const T r0 = DIM == 3 ? Sy * (bz0 - bz_ym) : T(0);
     const T r1 = -Sz * (by0 - by_m);
-    if (py || pz)
-      f.E[0][id] = advance<T, SPL, false>(tb, f.Es[0], id, DIM == 3 ? 1 : -1, j, 2, k, r0, r1, -jx, syn, szn);
-    else
-      f.E[0][id] += r0 + r1 - jx;
+    ex = spx ? advance<T, SPL, false>(tb, qx, DIM == 3 ? 1 : -1, j, 2, k, r0, r1, -jx, syn, szn) : ex + (r0 + r1 - jx);
   }
-  // Ey(i, j+1/2, k): parts along x (sigma_x at node i) and z
-  if (iin && (DIM == 2 || j <= N1 - 1) && kin) {
-    const T r0 = -Sx * (bz0 - Bz[id - 1]);
+  if (oky) {
+    const T r0 = -Sx * (bz0 - bz_xm);
     const T r1 = Sz * (bx0 - bx_m);
-    if (px || pz)
-      f.E[1][id] = advance<T, SPL, false>(tb, f.Es[1], id, 0, i, 2, k, r0, r1, -jy, sxn, szn);
-    else
-      f.E[1][id] += r0 + r1 - jy;
+    ey = spy ? advance<T, SPL, false>(tb, qy, 0, i, 2, k, r0, r1, -jy, sxn, szn) : ey + (r0 + r1 - jy);
   }
-  // Ez(i, j, k+1/2): parts along x and y
-  if (iin && jin && k <= N2 - 1) {
-    const T r0 = Sx * (by0 - By[id - 1]);
-    const T r1 = DIM == 3 ? -Sy * (bx0 - Bx[id - g.sy]) : T(0);
-    if (px || py)
-      f.E[2][id] = advance<T, SPL, false>(tb, f.Es[2], id, 0, i, DIM == 3 ? 1 : -1, j, r0, r1, -jz, sxn, syn);
-    else
-      f.E[2][id] += r0 + r1 - jz;
+  if (okz) {
+    const T r0 = Sx * (by0 - by_xm);
+    const T r1 = DIM == 3 ? -Sy * (bx0 - bx_ym) : T(0);
+    ez = spz ? advance<T, SPL, false>(tb, qz, 0, i, DIM == 3 ? 1 : -1, j, r0, r1, -jz, sxn, syn) : ez + (r0 + r1 - jz);
   }
+  // ---- stores; J' is zeroed where it was nonzero (most of the grid carries
+  //      no current, so most threads write nothing back) ----
+  if (okx) f.E[0][id] = ex;
+  if (oky) f.E[1][id] = ey;
+  if (okz) f.E[2][id] = ez;
+  if (spx) store_parts<SPL>(f.Es[0], id, qx);
+  if (spy) store_parts<SPL>(f.Es[1], id, qy);
+  if (spz) store_parts<SPL>(f.Es[2], id, qz);
+  if (jx != T(0)) f.J[0][id] = T(0);
+  if (jy != T(0)) f.J[1][id] = T(0);
+  if (jz != T(0)) f.J[2][id] = T(0);
 }
 
 // B^{n+3/2} at node (i,j,k) into Bp.  ex_p, ey_p: Ex, Ey at (i,j,k+1) (any
-// value when k = N2); ex0, ey0, ez0: values at (i,j,k).
+// value when k = N2); ex0, ey0, ez0: values at (i,j,k).  Loads before stores
+// as in e_update.
 template <typename T, int DIM, int SPL, bool GEO = false>
 __device__ __forceinline__ void b_update(const Geom& g, const Tables& tb, const FieldPtrs<T>& f, int i, int j, int k,
                                          long long id, T ex_p, T ey_p, T ex0, T ey0, T ez0) {
@@ -136,33 +183,45 @@ __device__ __forceinline__ void b_update(const Geom& g, const Tables& tb, const 
   const bool px = GEO ? (ic && pml_cent(g, 0, i)) : sxc > 0.f;
   const bool py = DIM == 3 && (GEO ? (jc && pml_cent(g, 1, j)) : syc > 0.f);
   const bool pz = GEO ? (kc && pml_cent(g, 2, k)) : szc > 0.f;
-  // Bx(i, j+1/2, k+1/2): parts along y (sigma_y at centre j) and z (centre k)
-  if (jc && kc) {
-    const T r0 = DIM == 3 ? -Sy * (Ez[id + g.sy] - ez0) : T(0);
+  // Bx(i, j+1/2, k+1/2): parts along y (centre j) and z (centre k);
+  // By(i+1/2, j, k+1/2): parts along x and z; Bz(i+1/2, j+1/2, k): x and y
+  const bool okx = jc && kc, oky = ic && kc, okz = ic && jc;
+  const bool spx = okx && (py || pz), spy = oky && (px || pz), spz = okz && (px || py);
+  // ---- loads ----
+  const T ez_yp = DIM == 3 && okx ? Ez[id + g.sy] : T(0);
+  const T ez_xp = oky ? Ez[id + 1] : T(0);
+  const T ey_xp = okz ? Ey[id + 1] : T(0);
+  const T ex_yp = DIM == 3 && okz ? Ex[id + g.sy] : T(0);
+  T bx = okx && !spx ? f.Bh[0][id] : T(0);
+  T by = oky && !spy ? f.Bh[1][id] : T(0);
+  T bz = okz && !spz ? f.Bh[2][id] : T(0);
+  Parts<SPL> qx{}, qy{}, qz{};
+  if (spx) qx = load_parts<SPL>(f.Bs[0], id);
+  if (spy) qy = load_parts<SPL>(f.Bs[1], id);
+  if (spz) qz = load_parts<SPL>(f.Bs[2], id);
+  // ---- update ----
+  if (okx) {
+    const T r0 = DIM == 3 ? -Sy * (ez_yp - ez0) : T(0);
     const T r1 = Sz * (ey_p - ey0);
-    if (py || pz)
-      f.Bp[0][id] = advance<T, SPL, true>(tb, f.Bs[0], id, DIM == 3 ? 1 : -1, j, 2, k, r0, r1, T(0), syc, szc);
-    else
-      f.Bp[0][id] = f.Bh[0][id] + (r0 + r1);
+    bx = spx ? advance<T, SPL, true>(tb, qx, DIM == 3 ? 1 : -1, j, 2, k, r0, r1, T(0), syc, szc) : bx + (r0 + r1);
   }
-  // By(i+1/2, j, k+1/2): parts along x (centre i) and z (centre k)
-  if (ic && kc) {
-    const T r0 = Sx * (Ez[id + 1] - ez0);
+  if (oky) {
+    const T r0 = Sx * (ez_xp - ez0);
     const T r1 = -Sz * (ex_p - ex0);
-    if (px || pz)
-      f.Bp[1][id] = advance<T, SPL, true>(tb, f.Bs[1], id, 0, i, 2, k, r0, r1, T(0), sxc, szc);
-    else
-      f.Bp[1][id] = f.Bh[1][id] + (r0 + r1);
+    by = spy ? advance<T, SPL, true>(tb, qy, 0, i, 2, k, r0, r1, T(0), sxc, szc) : by + (r0 + r1);
   }
-  // Bz(i+1/2, j+1/2, k): parts along x (centre i) and y (centre j)
-  if (ic && jc) {
-    const T r0 = -Sx * (Ey[id + 1] - ey0);
-    const T r1 = DIM == 3 ? Sy * (Ex[id + g.sy] - ex0) : T(0);
-    if (px || py)
-      f.Bp[2][id] = advance<T, SPL, true>(tb, f.Bs[2], id, 0, i, DIM == 3 ? 1 : -1, j, r0, r1, T(0), sxc, syc);
-    else
-      f.Bp[2][id] = f.Bh[2][id] + (r0 + r1);
+  if (okz) {
+    const T r0 = -Sx * (ey_xp - ey0);
+    const T r1 = DIM == 3 ? Sy * (ex_yp - ex0) : T(0);
+    bz = spz ? advance<T, SPL, true>(tb, qz, 0, i, DIM == 3 ? 1 : -1, j, r0, r1, T(0), sxc, syc) : bz + (r0 + r1);
   }
+  // ---- stores ----
+  if (okx) f.Bp[0][id] = bx;
+  if (oky) f.Bp[1][id] = by;
+  if (okz) f.Bp[2][id] = bz;
+  if (spx) store_parts<SPL>(f.Bs[0], id, qx);
+  if (spy) store_parts<SPL>(f.Bs[1], id, qy);
+  if (spz) store_parts<SPL>(f.Bs[2], id, qz);
 }
 
 }  // namespace fn

@@ -327,7 +327,7 @@ int pic_batch_particle_steps(pic_batch* b, long long* n);
 /* Block shape the batch autotuner chose at pic_batch_init (threads per
  * block, minimum resident blocks per SM) and the measured ms per step of the
  * ncand candidates (threads, min blocks) = (512,1), (256,2), (512,2),
- * (1024,1), (256,6), (256,8). */
+ * (1024,1), (256,6), (256,8), (256,3). */
 int pic_batch_tuning(pic_batch* b, int* threads, int* min_blocks, float* ms_per_step, int ncand);
 /* dt in use and the total number of cells of all runs. */
 int pic_batch_info(pic_batch* b, double* dt, long long* cells);

@@ -295,8 +295,8 @@ class Batch:
 
     def tuning(self):
         t, mb = C.c_int(), C.c_int()
-        ms = (C.c_float * 6)()
-        self._call(self.lib.pic_batch_tuning, C.byref(t), C.byref(mb), ms, 6)
+        ms = (C.c_float * 7)()
+        self._call(self.lib.pic_batch_tuning, C.byref(t), C.byref(mb), ms, 7)
         return {"threads": t.value, "min_blocks_per_sm": mb.value, "candidate_ms_per_step": list(ms)}
 
     def field(self, run, name, dtype=torch.float64):

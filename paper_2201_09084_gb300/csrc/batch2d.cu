@@ -302,11 +302,12 @@ template <>
 BatchArgs<double>& args<double>(pic_batch* b) { return b->ad; }
 
 // Block shapes the autotuner chooses from: (threads, minimum blocks per SM).
-// The last two cap registers (42 and 32 per thread) for more resident warps
-// in the field passes; the particle stage of a run, one thread's work, may
-// then spill.
-constexpr int kNumShapes = 6;
-constexpr int kShapes[kNumShapes][2] = {{512, 1}, {256, 2}, {512, 2}, {1024, 1}, {256, 6}, {256, 8}};
+// (256, 6) and (256, 8) cap registers (42 and 32 per thread) for more
+// resident warps in the FP32 field passes; the particle stage of a run, one
+// thread's work, may then spill.  (256, 3) leaves the FP64 node update its
+// registers (about 85) at 24 warps per SM.
+constexpr int kNumShapes = 7;
+constexpr int kShapes[kNumShapes][2] = {{512, 1}, {256, 2}, {512, 2}, {1024, 1}, {256, 6}, {256, 8}, {256, 3}};
 
 template <typename T, int ORDER, int SPL, int NT, int MINB>
 cudaError_t launch_shape(pic_batch* b, BatchArgs<T>& a, int parity, cudaStream_t s) {
@@ -330,6 +331,7 @@ cudaError_t launch_cfg(pic_batch* b, BatchArgs<T>& a, int parity, cudaStream_t s
     case 3: return launch_shape<T, ORDER, SPL, 1024, 1>(b, a, parity, s);
     case 4: return launch_shape<T, ORDER, SPL, 256, 6>(b, a, parity, s);
     case 5: return launch_shape<T, ORDER, SPL, 256, 8>(b, a, parity, s);
+    case 6: return launch_shape<T, ORDER, SPL, 256, 3>(b, a, parity, s);
     default: return launch_shape<T, ORDER, SPL, 512, 1>(b, a, parity, s);
   }
 }

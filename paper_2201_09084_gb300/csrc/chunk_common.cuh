@@ -68,17 +68,41 @@ __device__ __forceinline__ bool move_particle(const Geom& g, const T o[3], const
   return !out;
 }
 
+// Hints L2 to fetch the records of particles [base, base + count) (the
+// block's next chunk) while the current one is being worked on.
+template <typename T>
+__device__ __forceinline__ void prefetch_records(const SpeciesPtrs<T>& sp, long long base, long long count) {
+  if (count <= 0) return;
+  const unsigned bytes = (unsigned)(count * (long long)sizeof(T) * 4);   // multiple of 16
+  const char* p0 = reinterpret_cast<const char*>(sp.pos) + base * (long long)sizeof(T) * 4;
+  const char* p1 = reinterpret_cast<const char*>(sp.mom) + base * (long long)sizeof(T) * 4;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p0), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p1), "r"(bytes) : "memory");
+}
+
 // Stages particles [base, base + NT*P) with coalesced loads into the stage
 // (words 0-2 offsets, 3 weight, 4-6 u, 7 cell; row length ROW, particle q at
 // slot (q / P) * (P + 1) + q % P), removes and reports particles outside
 // their allowed cells, and leaves the bounding box of the live particles'
-// cells in s_lo / s_hi (s_hi[0] < 0: no live particle).  Ends with a barrier.
+// cells in s_lo / s_hi (s_hi[0] < 0: no live particle).  The records of the
+// block's next chunk (from next_base) are prefetched into L2.  The caller
+// must not read s_lo / s_hi of the previous chunk after its last barrier
+// before this call.  Ends with a barrier.
 template <typename T, int DIM, int P, int NT>
 __device__ __forceinline__ void stage_chunk(const Geom& g, const SpeciesPtrs<T>& sp, long long base, long long n,
-                                            T* stg, int ROW, unsigned* status, int (*s_red)[NT / 32], int* s_lo,
+                                            long long next_base, T* stg, int ROW, unsigned* status, int* s_lo,
                                             int* s_hi) {
   constexpr int PP = P + 1, C = NT * P;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      s_lo[a] = 1 << 30;
+      s_hi[a] = -1;
+    }
+    const long long left = n - next_base;
+    prefetch_records<T>(sp, next_base, left < C ? left : C);
+  }
   for (int q = tid; q < C; q += NT) {
     const long long gp = base + q;
     const int slot = (q / P) * PP + (q % P);
@@ -123,27 +147,17 @@ __device__ __forceinline__ void stage_chunk(const Geom& g, const SpeciesPtrs<T>&
       mx[a] = max(mx[a], c[a]);
     }
   }
+  if (DIM == 2) {  // one cell layer in y
+    mn[1] = 0;
+    mx[1] = mx[0] < 0 ? -1 : 0;
+  }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int lo = warp_min(mn[a]), hi = warp_max(mx[a]);
-    if (lane == 0) {
-      s_red[a][warp] = lo;
-      s_red[3 + a][warp] = hi;
+    if (lane == 0 && hi >= 0) {
+      atomicMin(s_lo + a, lo);
+      atomicMax(s_hi + a, hi);
     }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    for (int a = 0; a < 3; ++a) {
-      int lo = 1 << 30, hi = -1;
-      for (int w8 = 0; w8 < NT / 32; ++w8) {
-        lo = min(lo, s_red[a][w8]);
-        hi = max(hi, s_red[3 + a][w8]);
-      }
-      if (DIM == 2 && a == 1) lo = hi = 0;
-      s_lo[a] = lo;
-      s_hi[a] = hi;
-    }
-    if (s_hi[0] < 0) s_hi[0] = -1;
   }
   __syncthreads();
 }

@@ -155,9 +155,7 @@ __global__ void __launch_bounds__(kNT3, sizeof(T) == 4 ? 3 : 2)
   extern __shared__ __align__(16) unsigned char smraw[];
   T* stg = reinterpret_cast<T*>(smraw);
   T* bx_ = reinterpret_cast<T*>(smraw + PL::stage);
-  __shared__ int s_red[6][kNT3 / 32];
   __shared__ int s_lo[3], s_hi[3];
-  __shared__ int s_geo[8];
   const int tid = threadIdx.x, lane = tid & 31;
   const long long n = *sp.n_dev;
   const long long nchunks = (n + C - 1) / C;
@@ -167,21 +165,10 @@ __global__ void __launch_bounds__(kNT3, sizeof(T) == 4 ? 3 : 2)
   for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const long long base = ch * C;
     __syncthreads();
-    stage_chunk<T, 3, P, kNT3>(g, sp, base, n, stg, ROW, status, s_red, s_lo, s_hi);
-    if (tid == 0) {
-      const int dx = s_hi[0] - s_lo[0] + 6, dy = s_hi[1] - s_lo[1] + 6, dz = s_hi[2] - s_lo[2] + 6;
-      s_geo[6] = s_hi[0] >= 0 && dx <= BX && dy <= BY && dz <= BZ;
-      s_geo[0] = s_lo[0] - 2;
-      s_geo[1] = s_lo[1] - 2;
-      s_geo[2] = s_lo[2] - 2;
-      s_geo[3] = dx;
-      s_geo[4] = dy;
-      s_geo[5] = dz;
-    }
-    __syncthreads();
-    if (s_geo[6]) {
-      const int ox = s_geo[0], oy = s_geo[1], oz = s_geo[2];
-      const int bdx = s_geo[3], bdy = s_geo[4], bdz = s_geo[5];
+    stage_chunk<T, 3, P, kNT3>(g, sp, base, n, base + (long long)gridDim.x * C, stg, ROW, status, s_lo, s_hi);
+    const int ox = s_lo[0] - 2, oy = s_lo[1] - 2, oz = s_lo[2] - 2;
+    const int bdx = s_hi[0] - s_lo[0] + 6, bdy = s_hi[1] - s_lo[1] + 6, bdz = s_hi[2] - s_lo[2] + 6;
+    if (s_hi[0] >= 0 && bdx <= BX && bdy <= BY && bdz <= BZ) {
       const int NB = bdx * bdy * bdz;
       // ---- 2. E and the time-averaged B of the box ----
       for (int t = tid; t < NB; t += kNT3) {

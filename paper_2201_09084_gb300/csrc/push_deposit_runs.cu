@@ -5,20 +5,24 @@
 // all from shared memory:
 //   1. stage the chunk with coalesced 16-byte loads (structure of arrays, rows
 //      padded to P+1 words so a thread's strided reads are bank-conflict free)
-//      and find the bounding box of its cells;
+//      and find the bounding box of its cells; the block's next chunk is
+//      prefetched into L2 meanwhile;
 //   2. load E and the time-averaged B of that box (+ guard nodes);
 //   A. push: every thread gathers, rotates and moves its own P particles and
 //      keeps old and new positions in the stage;
 //   B. counting-sort the chunk by Esirkepov anchor (the per-axis minimum of
 //      old and new cell, where the order-1 current stencil of the move
-//      starts); the E/B box is dead now and becomes the current box;
-//   C. deposit: each thread takes P consecutive particles of the anchor order,
-//      so a run mostly shares one anchor, and accumulates the 2x3x3 prefix
-//      values of each component (54 in 3D) in registers; at the end, for each
-//      anchor held by at least three lanes of a warp, the warp sums those
-//      lanes' values with a reduce-scatter of shuffles (each lane ends with two
-//      sums) and adds them to the box with two shared-memory atomics per lane;
-//      lanes of smaller groups (sparse particles) add their runs directly;
+//      starts) and cut each anchor's particles into runs of at most L
+//      (P, or more when the chunk holds few anchors, so that there is still
+//      about one run per thread); the E/B box is dead now and becomes the
+//      current box;
+//   C. deposit: each thread takes a run, which shares one anchor, and
+//      accumulates the 2x3x3 prefix values of each component (54 in 3D) in
+//      registers; then, for each anchor held by at least three lanes of a
+//      warp, the warp sums those lanes' values with a reduce-scatter of
+//      shuffles (each lane ends with two sums) and adds them to the box with
+//      two shared-memory atomics per lane; lanes of smaller groups (sparse
+//      particles) add their runs directly;
 //   D. add the box to the grid with the charge factor and alpha (Eq. alpha,
 //      at each component's staggered location): the damping of Eq. MaxwellE's
 //      source term applied once per node in the flush.
@@ -217,7 +221,7 @@ constexpr int kMinGroupLanes = 3;
 // padded to P+1), the field box (E and time-averaged B, 6 arrays of NBOX
 // nodes with fixed strides BX, BX*BY, so every gather and deposit offset is a
 // compile-time constant; its first 3 arrays are the current box after the
-// push), the counters and the permutation of the anchor sort.  The box holds
+// push), the counters and the permutation of the anchor sort, and the runs.  The box holds
 // nodes lo-1 .. hi+2 of a chunk whose cells span lo .. hi: up to 9 cells
 // along x (two x-adjacent 4-cell sort tiles) and 5 along y and z.
 // Stage words: 0-2 old offsets, 3 weight, 4-6 u (replaced by the new offsets
@@ -234,12 +238,10 @@ struct Plan {
   static constexpr int NBOX = BXY * BZ;
   static constexpr size_t stage = (size_t)NW * ROW * sizeof(T);
   static constexpr size_t box = (size_t)6 * NBOX * sizeof(T);
-  // anchor counters; reused as the list of deferred particles (up to C)
-  static constexpr size_t cnt = (size_t)(NBOX + 1) * sizeof(int) > (size_t)C * sizeof(unsigned short)
-                                    ? (size_t)(NBOX + 1) * sizeof(int)
-                                    : (size_t)C * sizeof(unsigned short);
+  static constexpr size_t cnt = (size_t)(NBOX + 1) * sizeof(int);   // anchor counters
   static constexpr size_t perm = (size_t)C * sizeof(unsigned short);
-  static constexpr size_t total = stage + box + cnt + perm;
+  static constexpr size_t runs = (size_t)C * sizeof(unsigned short);  // run descriptors
+  static constexpr size_t total = stage + box + cnt + perm + runs;
 };
 
 // Order-1 interpolation from a shared-memory box with fixed strides; b is
@@ -325,18 +327,16 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
   T* bx_ = reinterpret_cast<T*>(smraw + PL::stage);
   int* cnt = reinterpret_cast<int*>(smraw + PL::stage + PL::box);
   unsigned short* perm = reinterpret_cast<unsigned short*>(smraw + PL::stage + PL::box + PL::cnt);
-  __shared__ int s_red[6][kNT / 32];
-  __shared__ int s_geo[8];   // box origin x, y, z and dims x, y, z
   __shared__ int s_lo[3], s_hi[3];
-  __shared__ int s_use_box;
   __shared__ int s_scan[kNT / 32];
-  __shared__ int s_ndefer;
   __shared__ int s_nanchor;
+  __shared__ int s_nrun;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long n = *sp.n_dev;
   const long long nchunks = (n + C - 1) / C;
   unsigned pushed = 0;
   if (sp.immobile) return;
+  unsigned short* runs = reinterpret_cast<unsigned short*>(smraw + PL::stage + PL::box + PL::cnt + PL::perm);
   // box offsets of the two (2D: one) reduce-scatter results this lane adds
   int goff[K];
 #pragma unroll
@@ -348,27 +348,14 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
   for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const long long base = ch * C;
     __syncthreads();
-    // ---- 1. stage the chunk, bounding box of its cells ----
-    stage_chunk<T, DIM, P, kNT>(g, sp, base, n, stg, ROW, status, s_red, s_lo, s_hi);
-    if (tid == 0) {
-      // nodes lo-1 .. hi+2 per axis: the gather reads from the cell's lower
-      // node minus one (half-staggered components) to its upper node, the
-      // deposit stencil of a move spans min(old, new cell) .. + 2
-      const int dx = s_hi[0] - s_lo[0] + 4, dy = DIM == 3 ? s_hi[1] - s_lo[1] + 4 : 1, dz = s_hi[2] - s_lo[2] + 4;
-      s_use_box = s_hi[0] >= 0 && dx <= BX && dy <= BY && dz <= BZ;
-      s_geo[0] = s_lo[0] - 1;
-      s_geo[1] = DIM == 3 ? s_lo[1] - 1 : 0;
-      s_geo[2] = s_lo[2] - 1;
-      s_geo[3] = dx;
-      s_geo[4] = dy;
-      s_geo[5] = dz;
-    }
-    __syncthreads();
-    const int use_box = s_use_box;
-
-    if (use_box) {
-      const int ox = s_geo[0], oy = s_geo[1], oz = s_geo[2];
-      const int bdx = s_geo[3], bdy = s_geo[4], bdz = s_geo[5];
+    // ---- 1. stage the chunk (and prefetch the next), bounding box of its cells ----
+    stage_chunk<T, DIM, P, kNT>(g, sp, base, n, base + (long long)gridDim.x * C, stg, ROW, status, s_lo, s_hi);
+    // nodes lo-1 .. hi+2 per axis: the gather reads from the cell's lower
+    // node minus one (half-staggered components) to its upper node, the
+    // deposit stencil of a move spans min(old, new cell) .. + 2
+    const int ox = s_lo[0] - 1, oy = DIM == 3 ? s_lo[1] - 1 : 0, oz = s_lo[2] - 1;
+    const int bdx = s_hi[0] - s_lo[0] + 4, bdy = DIM == 3 ? s_hi[1] - s_lo[1] + 4 : 1, bdz = s_hi[2] - s_lo[2] + 4;
+    if (s_hi[0] >= 0 && bdx <= BX && bdy <= BY && bdz <= BZ) {
       const int NB = bdx * bdy * bdz;   // nodes of the chunk's region (row length bdx)
       // ---- 2. E and the time-averaged B of the box ----
       for (int t = tid; t < NB; t += kNT) {
@@ -443,24 +430,30 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
         if constexpr (DIM == 2) stg[9 * ROW + slot] = stg[3 * ROW + slot] * u[1] * ig;
       }
       __syncthreads();
-      // ---- B. counting sort of the chunk by box-local anchor ----
-      // (the E/B box is dead: its first three arrays become the current box)
+      // ---- B. counting sort of the chunk by anchor ----
+      // (keys are compact indices of the chunk's region, key NB collects the
+      // particles that deposit nothing; the E/B box is dead: its first three
+      // arrays become the current box)
       T* const BJ = bx_;
-      for (int t = tid; t < 3 * NBOX; t += kNT) BJ[t] = T(0);
-      for (int t = tid; t <= NBOX; t += kNT) cnt[t] = 0;
+      {
+        float4* z = reinterpret_cast<float4*>(BJ);
+        constexpr int NZ = (int)(3 * NBOX * sizeof(T) / sizeof(float4));
+        for (int t = tid; t < NZ; t += kNT) z[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      for (int t = tid; t <= NB; t += kNT) cnt[t] = 0;
       if (tid == 0) {
-        s_ndefer = 0;
         s_nanchor = 0;
+        s_nrun = 0;
       }
       __syncthreads();
       auto anchor_key = [&](int slot) -> int {
         const int c0 = bits_to_cell<T>(stg[7 * ROW + slot]);
         const int c1 = bits_to_cell<T>(stg[8 * ROW + slot]);
-        if (c0 < 0 || c1 < 0) return NBOX;
+        if (c0 < 0 || c1 < 0) return NB;
         const int ax = min(cell_i(c0), cell_i(c1)) - ox;
         const int ay = DIM == 3 ? min(cell_j(c0), cell_j(c1)) - oy : 0;
         const int az = min(cell_k(c0), cell_k(c1)) - oz;
-        return ax + BX * ay + BXY * az;
+        return ax + bdx * (ay + bdy * az);
       };
       // count pass: each particle's key and its rank among the chunk's
       // particles of that key (warp-aggregated counter increments)
@@ -476,16 +469,15 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
         ranks[k] = __shfl_sync(0xffffffffu, b, leader) + __popc(m & ((1u << lane) - 1u));
       }
       __syncthreads();
-      {  // exclusive scan of cnt[0..NBOX]
-        const int per = (NBOX + 1 + kNT - 1) / kNT;
-        const int b0 = tid * per;
+      const int per = (NB + 1 + kNT - 1) / kNT;   // counters scanned per thread
+      const int b0 = tid * per;
+      {  // exclusive scan of cnt[0..NB]; number of anchors present
         int loc = 0, nz = 0;
         for (int t = 0; t < per; ++t)
-          if (b0 + t < NBOX) {
-            loc += cnt[b0 + t];
-            nz += cnt[b0 + t] != 0;
-          } else if (b0 + t == NBOX) {
-            loc += cnt[b0 + t];
+          if (b0 + t <= NB) {
+            const int c = cnt[b0 + t];
+            loc += c;
+            nz += b0 + t < NB && c != 0;
           }
         nz = __reduce_add_sync(0xffffffffu, nz);
         if (lane == 0 && nz) atomicAdd(&s_nanchor, nz);
@@ -501,7 +493,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
         for (int w8 = 0; w8 < warp; ++w8) wofs += s_scan[w8];
         int run = wofs + inc - loc;
         for (int t = 0; t < per; ++t)
-          if (b0 + t <= NBOX) {
+          if (b0 + t <= NB) {
             const int c0 = cnt[b0 + t];
             cnt[b0 + t] = run;
             run += c0;
@@ -514,14 +506,36 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
         const int q = tid + k * kNT;
         perm[cnt[keys[k]] + ranks[k]] = (unsigned short)((q / P) * PP + (q % P));
       }
+      // Runs: each anchor's particles (consecutive in the sorted order) are
+      // cut into runs of at most L, so a run never straddles two anchors.  L
+      // is P, or longer when the chunk holds few anchors, so that the runs
+      // still number at most one per thread.  Descriptor: start | length << 11.
+      {
+        const int nlive = cnt[NB], nanc = s_nanchor;
+        int L = P;
+        if (2 * nanc < kNT) {
+          const int l = (nlive + kNT - nanc - 1) / (kNT - nanc);
+          L = l > P ? l : P;
+        }
+        for (int t = 0; t < per; ++t) {
+          const int b = b0 + t;
+          if (b >= NB) break;
+          const int st = cnt[b], cb = cnt[b + 1] - st;
+          if (cb == 0) continue;
+          const int r = (cb + L - 1) / L;
+          const int rb = atomicAdd(&s_nrun, r);
+          for (int j = 0; j < r; ++j) {
+            const int len = min(L, cb - j * L);
+            runs[rb + j] = (unsigned short)((st + j * L) | (len << 11));
+          }
+        }
+      }
       __syncthreads();
-      // ---- C. deposit runs of P consecutive particles in anchor order ----
-      // Shape factors of a slot's move; returns the box-local anchor, or -1
-      // for a particle that deposits nothing.
+      // ---- C. deposit the runs, one per thread at a time ----
+      // Shape factors of a slot's move; returns the box offset of its anchor.
       auto prepare = [&](int slot, T (&S0)[3][3], T (&DS)[3][3]) -> int {
         const int cell1 = bits_to_cell<T>(stg[8 * ROW + slot]);
         const int cell0 = bits_to_cell<T>(stg[7 * ROW + slot]);
-        if (cell1 < 0 || cell0 < 0) return -1;
         const int c0[3] = {cell_i(cell0), cell_j(cell0), cell_k(cell0)};
         const int c1[3] = {cell_i(cell1), cell_j(cell1), cell_k(cell1)};
         int lo[3] = {0, 0, 0};
@@ -541,42 +555,25 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
         if constexpr (DIM == 2) return stg[9 * ROW + slot];
         return T(0);
       };
-      // A run keeps the anchor of its first particle; a particle with another
-      // anchor (a run that straddles two anchors after the sort) is deferred
-      // to a list deposited one particle per thread below, so no warp ever
-      // diverges into a flush inside the loop.
-      // A chunk with fewer than 2P particles per anchor (sparse particles)
-      // has straddling runs everywhere: there a run flushes and restarts at
-      // each new anchor instead.
-      unsigned short* defer = reinterpret_cast<unsigned short*>(cnt);  // the counters are dead now
-      const bool sparse = s_nanchor * (2 * P) > C;
-      AC acc;
-      acc.zero();
-      int key = -1;
-      for (int i = 0; i < P; ++i) {
-        const int slot = perm[tid * P + i];
-        T S0[3][3], DS[3][3];
-        const int k = prepare(slot, S0, DS);
-        if (k < 0) continue;
-        if (key < 0) {
-          key = k;
-        } else if (k != key) {
-          if (!sparse) {
-            defer[atomicAdd(&s_ndefer, 1)] = (unsigned short)slot;
-            continue;
+      const int R = s_nrun;
+      for (int rb = warp * 32; rb < R; rb += kNT) {
+        AC acc;
+        acc.zero();
+        int key = -1;
+        if (rb + lane < R) {
+          const unsigned d = runs[rb + lane];
+          const int st = d & 0x7ff, len = d >> 11;
+          for (int i = 0; i < len; ++i) {
+            const int slot = perm[st + i];
+            T S0[3][3], DS[3][3];
+            key = prepare(slot, S0, DS);
+            acc.add(S0, DS, stg[3 * ROW + slot], wvy_of(slot));
           }
-          acc.template flush_box<BX, BXY, NBOX>(BJ, key);
-          acc.zero();
-          key = k;
         }
-        acc.add(S0, DS, stg[3 * ROW + slot], wvy_of(slot));
-      }
-      // Lanes that share an anchor hold contiguous runs (anchor order).  A
-      // group of at least kMinGroupLanes lanes sums its runs with one
-      // reduce-scatter; the lanes of smaller groups (a few particles per
-      // cell) add their own runs to the box, where few lanes meet on an
-      // address.
-      {
+        // Lanes that share an anchor hold consecutive runs.  A group of at
+        // least kMinGroupLanes lanes sums its runs with one reduce-scatter;
+        // the lanes of smaller groups (a few particles per cell) add their
+        // own runs to the box, where few lanes meet on an address.
         const int up = __shfl_up_sync(0xffffffffu, key, 1);
         const bool head = key >= 0 && (lane == 0 || up != key);
         const unsigned heads = __ballot_sync(0xffffffffu, head);
@@ -599,16 +596,6 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
           }
           if (key >= 0 && !big) acc.template flush_box<BX, BXY, NBOX>(BJ, key);
         }
-      }
-      __syncthreads();
-      const int nd = s_ndefer;
-      for (int e = tid; e < nd; e += kNT) {
-        const int slot = defer[e];
-        T S0[3][3], DS[3][3];
-        const int k = prepare(slot, S0, DS);
-        acc.zero();
-        acc.add(S0, DS, stg[3 * ROW + slot], wvy_of(slot));
-        acc.template flush_box<BX, BXY, NBOX>(BJ, k);
       }
       __syncthreads();
       // ---- D. add the current box to the grid with the charge factor and alpha ----

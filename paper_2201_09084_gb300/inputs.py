@@ -113,6 +113,33 @@ EPS0 = 8.8541878128e-12
 C_LIGHT = 299792458.0
 
 
+def clustered_runs(dim, n_particles, lo, hi, run=4, u_rms=0.5, p_scatter=0.15, seed=SEED_BASE + 11,
+                   q=-Q_E, m=M_E, w=1.0):
+    """Particles in an order that no sort produces: consecutive runs of
+    `run` * k particles (k ~ U{1..24}) each sit in a 2-cell cube at a random
+    place of the box [lo, hi), and with probability p_scatter a single run of
+    `run` particles is scattered over the whole box instead.  Kept unsorted,
+    they give chunks whose cells span the box while short stretches of
+    consecutive particles stay compact.  Gaussian momenta."""
+    rng = np.random.default_rng(seed)
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    X = np.empty((n_particles, 3))
+    i = 0
+    while i < n_particles:
+        if rng.random() < p_scatter:
+            k = min(run, n_particles - i)
+            X[i:i + k] = lo + rng.random((k, 3)) * (hi - lo)
+        else:
+            k = min(run * int(rng.integers(1, 25)), n_particles - i)
+            corner = lo + rng.random(3) * (hi - lo - 2.0)
+            X[i:i + k] = corner + 2.0 * rng.random((k, 3))
+        i += k
+    u = rng.normal(0.0, u_rms, (n_particles, 3))
+    out = _pack(X, u, np.full(n_particles, w), dim)
+    return [dict(out, q=q, m=m, immobile=False)]
+
+
 def plasma_density(u_th, d):
     """Density n0 whose Debye length u_th c / omega_p equals the cell size d:
     omega_p = u_th c / d, n0 = eps0 m_e omega_p^2 / e^2."""

@@ -276,3 +276,34 @@ def test_autotune_restores_state(prec):
     gpu.step(8)
     err = max_field_err(ora, gpu)
     assert max(err.values()) < TOL[prec], err
+
+
+@pytest.mark.parametrize("ppt", [4, 8])
+@pytest.mark.parametrize("order", [1, 3])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_chunk_segments(prec, order, ppt):
+    """Unsorted particles whose chunks span the whole box while runs of
+    consecutive particles stay compact, and some threads' own particles lie
+    far apart: the chunk kernels split such chunks into segments of threads
+    that fit one box, and send only the scattered threads down the global
+    path.  A ragged last chunk.  Fields and particles against the oracle."""
+    if order == 3 and prec == "fp64" and ppt == 8:
+        pytest.skip("the FP64 order-3 kernel has one shape (4 particles per thread)")
+    nphys = (24, 20, 28)
+    pml = (6,) * 6
+    lo = (8, 8, 8)
+    hi = (28, 24, 32)
+    parts = I.clustered_runs(3, 3 * 128 * ppt + 77, lo, hi, run=ppt, seed=31 + order + ppt)
+    ora, gpu = make_pair(3, nphys, pml, D3, parts, order=order, prec=prec, alpha_mode="damped", sort_every=0)
+    gpu.set_tuning(ppt, 1)
+    for _ in range(2):
+        ora.step(3)
+        gpu.step(3)
+        err = max_field_err(ora, gpu)
+        assert max(err.values()) < TOL[prec], err
+    X, u, alive = gpu_positions(gpu, 0)
+    po = ora.particles()
+    assert np.array_equal(alive, po["alive"])
+    Xo = np.stack([po["X"], po["Y"], po["Z"]], axis=1)
+    tol = 1e-5 if prec == "fp32" else 1e-10
+    assert np.max(np.abs(X[alive] - Xo[alive])) < tol

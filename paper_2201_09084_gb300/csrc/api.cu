@@ -403,6 +403,16 @@ int pml_init(picpml_ctx* ctx, const pml_desc* p) {
         host2[(stag * 2 + 1) * total + base] = split2(eb);
       }
     }
+    {  // the run of nodes (and their centres) where alpha is exactly 1
+      const double* aln = q8 + 6 * nn;
+      const double* alc = q8 + 7 * nn;
+      int lo = 0;
+      while (lo < nn && !(aln[lo] == 1.0 && alc[lo] == 1.0)) ++lo;
+      int hi = lo;
+      while (hi + 1 < nn && aln[hi + 1] == 1.0 && alc[hi + 1] == 1.0) ++hi;
+      ctx->tb.al1_lo[a] = lo < nn ? lo : 1;
+      ctx->tb.al1_hi[a] = lo < nn ? hi : 0;   // empty when alpha is nowhere 1
+    }
     ctx->tb.ea_n[a] = td + 0 * total + off;
     ctx->tb.eb_n[a] = td + 1 * total + off;
     ctx->tb.sdt_n[a] = td + 2 * total + off;

@@ -96,6 +96,10 @@ __device__ __forceinline__ Tables run_tables(const BatchArgs<T>& a, const RunInf
   t.sdtf_n[1] = t.sdtf_c[1] = a.dummy_f0;                            // 0.f
   t.al_nf[1] = t.al_cf[1] = a.dummy_f1;                              // 1.f
   t.ea2_n[1] = t.eb2_n[1] = t.ea2_c[1] = t.eb2_c[1] = a.dummy_f2;    // (1, 0)
+  for (int ax = 0; ax < 3; ++ax) {  // no alpha-is-one ranges: tables always read
+    t.al1_lo[ax] = 1;
+    t.al1_hi[ax] = 0;
+  }
   return t;
 }
 

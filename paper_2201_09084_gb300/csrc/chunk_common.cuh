@@ -162,5 +162,121 @@ __device__ __forceinline__ void stage_chunk(const Geom& g, const SpeciesPtrs<T>&
   __syncthreads();
 }
 
+// Counting sort of a chunk's particles by anchor key, and the cut of each
+// anchor's particles into runs.  keys[k] is the key of particle
+// q = tid + k NT (stage slot (q / P) (P + 1) + q % P), nk for a particle that
+// deposits nothing.  cnt holds nk + 1 counters that the caller zeroed before
+// a barrier, together with *s_nanchor and *s_nrun.  Leaves perm (the slots in
+// key order) and runs[0 .. *s_nrun): descriptors start | length << 11 of
+// runs of consecutive sorted particles that share one key.  The runs are at
+// most L long: P, or more when the chunk holds few keys, so that there is
+// still about one run per thread.  Each key's runs are contiguous in runs[].
+// Ends with a barrier.
+template <int P, int NT>
+__device__ __forceinline__ void sort_runs(const int (&keys)[P], int nk, int* cnt, unsigned short* perm,
+                                          unsigned short* runs, int* s_scan, int* s_nanchor, int* s_nrun) {
+  constexpr int PP = P + 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // count pass: each particle's rank among the chunk's particles of its key
+  // (warp-aggregated counter increments)
+  int ranks[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    const unsigned m = __match_any_sync(0xffffffffu, keys[k]);
+    const int leader = __ffs(m) - 1;
+    int b = 0;
+    if (lane == leader) b = atomicAdd(cnt + keys[k], __popc(m));
+    ranks[k] = __shfl_sync(0xffffffffu, b, leader) + __popc(m & ((1u << lane) - 1u));
+  }
+  __syncthreads();
+  const int per = (nk + 1 + NT - 1) / NT;   // counters scanned per thread
+  const int b0 = tid * per;
+  {  // exclusive scan of cnt[0..nk]; number of keys present
+    int loc = 0, nz = 0;
+    for (int t = 0; t < per; ++t)
+      if (b0 + t <= nk) {
+        const int c = cnt[b0 + t];
+        loc += c;
+        nz += b0 + t < nk && c != 0;
+      }
+    nz = __reduce_add_sync(0xffffffffu, nz);
+    if (lane == 0 && nz) atomicAdd(s_nanchor, nz);
+    int inc = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    if (lane == 31) s_scan[warp] = inc;
+    __syncthreads();
+    int wofs = 0;
+    for (int w8 = 0; w8 < warp; ++w8) wofs += s_scan[w8];
+    int run = wofs + inc - loc;
+    for (int t = 0; t < per; ++t)
+      if (b0 + t <= nk) {
+        const int c0 = cnt[b0 + t];
+        cnt[b0 + t] = run;
+        run += c0;
+      }
+  }
+  __syncthreads();
+  // scatter pass: the scan turned the counters into each key's start
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    const int q = tid + k * NT;
+    perm[cnt[keys[k]] + ranks[k]] = (unsigned short)((q / P) * PP + (q % P));
+  }
+  const int nlive = cnt[nk], nanc = *s_nanchor;
+  int L = P;
+  if (2 * nanc < NT) {
+    const int l = (nlive + NT - nanc - 1) / (NT - nanc);
+    L = l > P ? l : P;
+  }
+  for (int t = 0; t < per; ++t) {
+    const int b = b0 + t;
+    if (b >= nk) break;
+    const int st = cnt[b], cb = cnt[b + 1] - st;
+    if (cb == 0) continue;
+    const int r = (cb + L - 1) / L;
+    const int rb = atomicAdd(s_nrun, r);
+    for (int j = 0; j < r; ++j) {
+      const int len = min(L, cb - j * L);
+      runs[rb + j] = (unsigned short)((st + j * L) | (len << 11));
+    }
+  }
+  __syncthreads();
+}
+
+// Adds the lanes' run accumulators of one warp to the shared current box J:
+// lanes that share an anchor (key >= 0) hold consecutive runs; a group of at
+// least min_lanes lanes sums its accumulators with one reduce-scatter
+// (acc.group_flush), the lanes of smaller groups add their own (acc.flush_box)
+// where few lanes meet on an address.  A warp holding one anchor in every
+// lane takes the reduce-scatter without membership masks.
+template <class ACC, typename T>
+__device__ __forceinline__ void flush_warp_runs(const ACC& acc, int key, int lane, T* J, int min_lanes) {
+  const int up = __shfl_up_sync(0xffffffffu, key, 1);
+  const bool head = key >= 0 && (lane == 0 || up != key);
+  const unsigned heads = __ballot_sync(0xffffffffu, head);
+  const unsigned live = __ballot_sync(0xffffffffu, key >= 0);
+  if (heads == 1u && live == 0xffffffffu) {
+    acc.template group_flush<true>(true, lane, J, key);
+    return;
+  }
+  const unsigned below = heads & ((2u << lane) - 1u);     // heads at or before this lane
+  const unsigned above = (heads | ~live) & ~((2u << lane) - 1u);
+  const int first = below ? 31 - __clz(below) : 0;
+  const int next = above ? __ffs(above) - 1 : 32;
+  const bool big = key >= 0 && next - first >= min_lanes;
+  unsigned pend = __ballot_sync(0xffffffffu, head && big);
+  while (pend) {
+    const int leader = __ffs(pend) - 1;
+    pend &= pend - 1;
+    const int gk = __shfl_sync(0xffffffffu, key, leader);
+    acc.template group_flush<false>(key == gk, lane, J, gk);
+  }
+  if (key >= 0 && !big) acc.flush_box(J, key);
+}
+
 }  // namespace chunk
 }  // namespace picpml

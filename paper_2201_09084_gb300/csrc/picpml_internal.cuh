@@ -69,6 +69,7 @@ struct Tables {
   const float* al_cf[3];
   const double* al_nd[3];   // FP64 copy
   const double* al_cd[3];
+  int al1_lo[3], al1_hi[3]; // alpha is exactly 1 at nodes and centres al1_lo .. al1_hi
 };
 
 template <typename T>

@@ -1,24 +1,26 @@
 // Fused gather + Boris + move + Esirkepov deposit + alpha-damped flush for
 // cubic (order-3) shapes in 3D, over particles sorted by tile.
 //
-// An order-3 move touches 4 x 5 x 5 prefix values per current component
-// (300 in all), too many to accumulate in registers, so the deposit goes
-// through shared memory.  A block takes a chunk of 128*P consecutive
-// particles:
+// An order-3 move adds 4 x 5 x 5 prefix values to each current component
+// (300 in all).  A block takes a chunk of 128*P consecutive particles:
 //   1. stage the chunk (coalesced) and find the bounding box of its cells;
 //   2. load E and the time-averaged B of that box with fixed strides
 //      (nodes lo-2 .. hi+3 per axis: the cubic gather reaches two nodes
 //      below the cell, the deposit stencil of a move three above);
 //   A. push every particle (64-point gather per component from the box),
 //      write its record back and keep old and new positions in the stage;
-//   C. every thread takes its P particles' moves into registers; the stage
-//      and the dead field box become K private copies of a compact current
-//      box over the chunk's nodes, and every thread adds its particles'
-//      Esirkepov values into copy (lane mod K) with shared-memory atomics, so
-//      lanes of a dense cell collide K times less often;
-//   D. sum the copies and add them to the grid with the charge factor and
-//      alpha at each component's staggered location (Eq. alpha, Sec. II.B),
-//      once per node: the damping of Eq. MaxwellE's source in the flush.
+//   B. counting-sort the chunk by anchor cell (the per-axis minimum of old and
+//      new cell) and cut each anchor's particles into runs (about one per
+//      thread); the E/B box is dead and becomes the current box;
+//   C. for each current component in turn, every thread accumulates the 100
+//      values of its run's moves in registers (the transverse factor as
+//      M M' + Q DS' with M = S0 + DS/2, Q = DS/12, times the prefix sums of
+//      DS along the component); a warp's lanes that share an anchor then sum
+//      their values by reduce-scatters of shuffles and add them to the box,
+//      lanes of smaller groups add their own;
+//   D. add the box to the grid with the charge factor and alpha at each
+//      component's staggered location (Eq. alpha, Sec. II.B), once per node:
+//      the damping of Eq. MaxwellE's source in the flush.
 // A chunk whose box does not fit (sparse particles) takes a per-particle
 // path with global loads and atomics.
 #include "chunk_common.cuh"
@@ -31,6 +33,8 @@ using namespace pc;
 using namespace chunk;
 
 constexpr int kNT3 = 128;
+// Fewest lanes of one anchor that a warp sums by reduce-scatters.
+constexpr int kMinGroupLanes3 = 3;
 
 template <typename T, int P>
 struct Plan3 {
@@ -41,9 +45,15 @@ struct Plan3 {
   static constexpr int BX = 14, BY = 10, BZ = 10;   // up to 8 cells along x (two 4-cell tiles), 4 along y, z
   static constexpr int BXY = BX * BY;
   static constexpr int NBOX = BXY * BZ;
-  static constexpr int KMAX = 16;                    // most private current copies
   static constexpr size_t stage = (size_t)NW * ROW * sizeof(T);
   static constexpr size_t box = (size_t)6 * NBOX * sizeof(T);
+  // anchor counters, permutation and runs, in the box's last three arrays
+  // (the time-averaged B, dead after the push)
+  static constexpr int NKEY = (BX - 4) * (BY - 4) * (BZ - 4) + 1;
+  static constexpr size_t cnt = (size_t)NKEY * sizeof(int);
+  static constexpr size_t perm = (size_t)C * sizeof(unsigned short);
+  static_assert(cnt + 2 * perm <= (size_t)3 * NBOX * sizeof(T), "sort arrays exceed the dead box");
+  static constexpr size_t sort_at = stage + (size_t)3 * NBOX * sizeof(T);
   static constexpr size_t total = stage + box;
 };
 
@@ -62,43 +72,89 @@ __device__ __forceinline__ T interp3_box(const T* F, int b, const T* wx, const T
   return acc;
 }
 
-// Esirkepov values of one order-3 move added into a current box copy J
-// (component arrays nb apart, strides 1, sy, sz; lo: box-local first node).
-// The transverse factor S0 S0' + DS S0'/2 + S0 DS'/2 + DS DS'/3 is evaluated
-// as M M' + Q DS' with M = S0 + DS/2, Q = DS/12.
-template <typename T>
-__device__ __forceinline__ void deposit3_box(T* J, int nb, int sy, int sz, const int lo[3], const T S0[3][5],
-                                             const T DS[3][5], T w) {
-  T M[3][5], Q[3][5];
+// Register accumulator of one current component CMP of a run of order-3
+// moves: w * (Esirkepov factor) prefix sums, 4 x 5 x 5 values with flat
+// index q = (td * 5 + tb) * 4 + ta: ta along CMP (the prefix sums of DS),
+// tb and td along the transverse axes B < D.  The transverse factor
+// S0 S0' + DS S0'/2 + S0 DS'/2 + DS DS'/3 is evaluated as M M' + Q DS' with
+// M = S0 + DS/2, Q = DS/12.  Box offsets use the strides 1, BX, BXY and the
+// component arrays NBOX apart.
+template <typename T, int CMP, int BX, int BXY, int NBOX>
+struct Acc3 {
+  static constexpr int B = CMP == 0 ? 1 : 0, D = CMP == 2 ? 1 : 2;
+  static constexpr int NV = 100;
+  T v[NV];
+
+  __device__ __forceinline__ void zero() {
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
+    for (int q = 0; q < NV; ++q) v[q] = T(0);
+  }
+
+  __device__ __forceinline__ void add(const T S0[3][5], const T DS[3][5], T w) {
+    T A[4];
+    T run = T(0);
 #pragma unroll
-    for (int t = 0; t < 5; ++t) {
-      M[a][t] = S0[a][t] + T(0.5) * DS[a][t];
-      Q[a][t] = T(1.0 / 12.0) * DS[a][t];
+    for (int ta = 0; ta < 4; ++ta) {
+      run += DS[CMP][ta];
+      A[ta] = w * run;
     }
-  const int st[3] = {1, sy, sz};
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const int b = c == 0 ? 1 : 0, d = c == 2 ? 1 : 2;   // transverse axes
-    T* Jc = J + c * nb;
-#pragma unroll
-    for (int td = 0; td < 5; ++td)
+    for (int td = 0; td < 5; ++td) {
+      const T Md = S0[D][td] + T(0.5) * DS[D][td];
 #pragma unroll
       for (int tb = 0; tb < 5; ++tb) {
-        const T Tl = M[b][tb] * M[d][td] + Q[b][tb] * DS[d][td];
-        if (Tl == T(0)) continue;
-        const T line = w * Tl;
-        T* row = Jc + (lo[b] + tb) * st[b] + (lo[d] + td) * st[d] + lo[c] * st[c];
-        T acc = T(0);
+        const T Mb = S0[B][tb] + T(0.5) * DS[B][tb];
+        const T Tl = Mb * Md + T(1.0 / 12.0) * DS[B][tb] * DS[D][td];
 #pragma unroll
-        for (int ta = 0; ta < 4; ++ta) {
-          acc += DS[c][ta];
-          if (acc != T(0)) atomicAdd(row + ta * st[c], line * acc);
+        for (int ta = 0; ta < 4; ++ta) v[(td * 5 + tb) * 4 + ta] += A[ta] * Tl;
+      }
+    }
+  }
+
+  __device__ __forceinline__ static int box_offset(int q) {
+    constexpr int st[3] = {1, BX, BXY};
+    const int ta = q & 3, tb = (q >> 2) % 5, td = q / 20;
+    return CMP * NBOX + ta * st[CMP] + tb * st[B] + td * st[D];
+  }
+
+  __device__ __forceinline__ void flush_box(T* J, int a) const {
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+      if (v[q] != T(0)) atomicAdd(J + a + box_offset(q), v[q]);
+  }
+
+  // Sums the values of the lanes with member == true (one anchor) by four
+  // reduce-scatters of 32 values each: after five halving steps lane L holds
+  // the group's sum of flat index 32 k + L of block k, which it adds to the
+  // box.  Every lane takes part and keeps its own values.
+  template <bool ALL>
+  __device__ __forceinline__ void group_flush(bool member, int lane, T* J, int a) const {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      T t[16];
+      const bool up = (lane & 16) != 0;
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int ql = 32 * k + i, qh = 32 * k + 16 + i;
+        const T lo = (ql < NV && (ALL || member)) ? v[ql < NV ? ql : 0] : T(0);
+        const T hi = (qh < NV && (ALL || member)) ? v[qh < NV ? qh : 0] : T(0);
+        t[i] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, 16);
+      }
+#pragma unroll
+      for (int lev = 1; lev < 5; ++lev) {
+        const int o = 16 >> lev;
+        const bool u2 = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+          const T lo = t[i], hi = t[i + o];
+          t[i] = (u2 ? hi : lo) + __shfl_xor_sync(0xffffffffu, u2 ? lo : hi, o);
         }
       }
+      const int q = 32 * k + lane;
+      if (q < NV && t[0] != T(0)) atomicAdd(J + a + box_offset(q), t[0]);
+    }
   }
-}
+};
 
 // The whole step of one particle from global memory (chunks whose box does
 // not fit): gather, push, move, deposit with global atomics; writes the
@@ -155,8 +211,14 @@ __global__ void __launch_bounds__(kNT3, sizeof(T) == 4 ? 3 : 2)
   extern __shared__ __align__(16) unsigned char smraw[];
   T* stg = reinterpret_cast<T*>(smraw);
   T* bx_ = reinterpret_cast<T*>(smraw + PL::stage);
+  int* cnt = reinterpret_cast<int*>(smraw + PL::sort_at);
+  unsigned short* perm = reinterpret_cast<unsigned short*>(smraw + PL::sort_at + PL::cnt);
+  unsigned short* runs = reinterpret_cast<unsigned short*>(smraw + PL::sort_at + PL::cnt + PL::perm);
   __shared__ int s_lo[3], s_hi[3];
-  const int tid = threadIdx.x, lane = tid & 31;
+  __shared__ int s_scan[kNT3 / 32];
+  __shared__ int s_nanchor;
+  __shared__ int s_nrun;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long n = *sp.n_dev;
   const long long nchunks = (n + C - 1) / C;
   unsigned pushed = 0;
@@ -232,48 +294,77 @@ __global__ void __launch_bounds__(kNT3, sizeof(T) == 4 ? 3 : 2)
         stg[8 * ROW + slot] = cell_to_bits<T>(cell1);
       }
       __syncthreads();
-      // ---- C. private current copies over the chunk's nodes (compact strides) ----
-      // Each thread keeps its own P particles' moves in registers, so the
-      // stage and the dead field box together hold the copies.
-      int mc0[P], mc1[P];
-      T mo0[P][3], mo1[P][3], mw[P];
-#pragma unroll
-      for (int i = 0; i < P; ++i) {
-        const int slot = tid * PP + i;
-        mc0[i] = bits_to_cell<T>(stg[7 * ROW + slot]);
-        mc1[i] = bits_to_cell<T>(stg[8 * ROW + slot]);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          mo0[i][a] = stg[a * ROW + slot];
-          mo1[i][a] = stg[(4 + a) * ROW + slot];
-        }
-        mw[i] = stg[3 * ROW + slot];
+      // ---- B. counting sort by anchor cell, runs ----
+      // (key: the anchor cell min(old, new) per axis, from s_lo - 1 to s_hi;
+      // key nk collects the particles that deposit nothing; the E/B box is
+      // dead: its first three arrays become the current box)
+      T* const BJ = bx_;
+      {
+        float4* z = reinterpret_cast<float4*>(BJ);
+        constexpr int NZ = (int)(3 * NBOX * sizeof(T) / sizeof(float4));
+        for (int t = tid; t < NZ; t += kNT3) z[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      const int kdx = bdx - 4, kdy = bdy - 4, nk = kdx * kdy * (bdz - 4);
+      for (int t = tid; t <= nk; t += kNT3) cnt[t] = 0;
+      if (tid == 0) {
+        s_nanchor = 0;
+        s_nrun = 0;
       }
       __syncthreads();
-      constexpr int kRoom = (int)((PL::stage + PL::box) / sizeof(T));
-      int K = 1;
-      while (K < PL::KMAX && 2 * K * 3 * NB <= kRoom) K *= 2;
-      T* const BJ = stg;
-      for (int t = tid; t < K * 3 * NB; t += kNT3) BJ[t] = T(0);
-      __syncthreads();
-      T* const Jmine = BJ + (lane & (K - 1)) * 3 * NB;
-#pragma unroll 1
-      for (int i = 0; i < P; ++i) {
-        if (mc1[i] < 0 || mc0[i] < 0) continue;
-        const int c0[3] = {cell_i(mc0[i]), cell_j(mc0[i]), cell_k(mc0[i])};
-        const int c1[3] = {cell_i(mc1[i]), cell_j(mc1[i]), cell_k(mc1[i])};
-        const int org[3] = {ox, oy, oz};
+      int keys[P];
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        const int q = tid + k * kNT3;
+        const int slot = (q / P) * PP + (q % P);
+        const int c0 = bits_to_cell<T>(stg[7 * ROW + slot]);
+        const int c1 = bits_to_cell<T>(stg[8 * ROW + slot]);
+        if (c0 < 0 || c1 < 0) {
+          keys[k] = nk;
+        } else {
+          const int ax = min(cell_i(c0), cell_i(c1)) - ox - 1;
+          const int ay = min(cell_j(c0), cell_j(c1)) - oy - 1;
+          const int az = min(cell_k(c0), cell_k(c1)) - oz - 1;
+          keys[k] = ax + kdx * (ay + kdy * az);
+        }
+      }
+      sort_runs<P, kNT3>(keys, nk, cnt, perm, runs, s_scan, &s_nanchor, &s_nrun);
+      // ---- C. deposit the runs, one component at a time ----
+      // Shape factors of a slot's move; returns the box offset of the first
+      // node of its stencil.
+      auto prepare = [&](int slot, T (&S0)[3][5], T (&DS)[3][5]) -> int {
+        const int cell1 = bits_to_cell<T>(stg[8 * ROW + slot]);
+        const int cell0 = bits_to_cell<T>(stg[7 * ROW + slot]);
+        const int c0[3] = {cell_i(cell0), cell_j(cell0), cell_k(cell0)};
+        const int c1[3] = {cell_i(cell1), cell_j(cell1), cell_k(cell1)};
         int lo[3];
-        T S0[3][5], DS[3][5];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          esk_axis<3, T>(c0[a], mo0[i][a], c1[a], mo1[i][a], lo[a], S0[a], DS[a]);
-          lo[a] -= org[a];
+        for (int a = 0; a < 3; ++a)
+          esk_axis<3, T>(c0[a], stg[a * ROW + slot], c1[a], stg[(4 + a) * ROW + slot], lo[a], S0[a], DS[a]);
+        return (lo[0] - ox) + BX * (lo[1] - oy) + BXY * (lo[2] - oz);
+      };
+      const int R = s_nrun;
+      auto deposit_component = [&](auto acc) {
+        for (int rb = warp * 32; rb < R; rb += kNT3) {
+          acc.zero();
+          int key = -1;
+          if (rb + lane < R) {
+            const unsigned d = runs[rb + lane];
+            const int st = d & 0x7ff, len = d >> 11;
+            for (int i = 0; i < len; ++i) {
+              const int slot = perm[st + i];
+              T S0[3][5], DS[3][5];
+              key = prepare(slot, S0, DS);
+              acc.add(S0, DS, stg[3 * ROW + slot]);
+            }
+          }
+          flush_warp_runs(acc, key, lane, BJ, kMinGroupLanes3);
         }
-        deposit3_box<T>(Jmine, NB, bdx, bdx * bdy, lo, S0, DS, mw[i]);
-      }
+      };
+      deposit_component(Acc3<T, 0, BX, BXY, NBOX>{});
+      deposit_component(Acc3<T, 1, BX, BXY, NBOX>{});
+      deposit_component(Acc3<T, 2, BX, BXY, NBOX>{});
       __syncthreads();
-      // ---- D. sum the copies, add to the grid with the charge factor and alpha ----
+      // ---- D. add the current box to the grid with the charge factor and alpha ----
       const T* anx = al_node<T>(tb, 0);
       const T* acx = al_cent<T>(tb, 0);
       const T* any = al_node<T>(tb, 1);
@@ -281,14 +372,10 @@ __global__ void __launch_bounds__(kNT3, sizeof(T) == 4 ? 3 : 2)
       const T* anz = al_node<T>(tb, 2);
       const T* acz = al_cent<T>(tb, 2);
       for (int t = tid; t < NB; t += kNT3) {
-        T j0 = T(0), j1 = T(0), j2 = T(0);
-        for (int k = 0; k < K; ++k) {
-          j0 += BJ[k * 3 * NB + t];
-          j1 += BJ[k * 3 * NB + NB + t];
-          j2 += BJ[k * 3 * NB + 2 * NB + t];
-        }
-        if (j0 == T(0) && j1 == T(0) && j2 == T(0)) continue;
         const int li = t % bdx, r = t / bdx, lj = r % bdy, lk = r / bdy;
+        const int bi = li + BX * lj + BXY * lk;
+        const T j0 = BJ[bi], j1 = BJ[NBOX + bi], j2 = BJ[2 * NBOX + bi];
+        if (j0 == T(0) && j1 == T(0) && j2 == T(0)) continue;
         const int gi = ox + li, gj = oy + lj, gk = oz + lk;
         const long long id = g.idx(gi, gj, gk);
         if (j0 != T(0)) atomicAdd(f.J[0] + id, sp.cj[0] * j0 * acx[gi] * any[gj] * anz[gk]);

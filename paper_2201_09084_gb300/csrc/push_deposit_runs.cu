@@ -45,7 +45,7 @@ using namespace chunk;
 // Flat layout, 3D: Jx [ix*9 + jy*3 + kz] (ix < 2), Jy 18 + [ix*6 + jy*3 + kz]
 // (jy < 2), Jz 36 + [ix*6 + jy*2 + kz] (kz < 2); 2D: Jx [ix*3 + kz],
 // Jy (out of plane) 6 + [ix*3 + kz], Jz 15 + [ix*2 + kz].
-template <typename T, int DIM>
+template <typename T, int DIM, int BX, int BXY, int NBOX>
 struct Acc1 {
   static constexpr int NX = DIM == 3 ? 18 : 6;
   static constexpr int NY = DIM == 3 ? 18 : 9;
@@ -156,7 +156,6 @@ struct Acc1 {
 
   // Box offset of flat index idx (component array comp * NBOX + node offset)
   // in a box with row length BX and plane size BXY.
-  template <int BX, int BXY, int NBOX>
   __device__ __forceinline__ static int box_offset(int idx) {
     int comp, ix, jy, kz;
     node_of(idx, comp, ix, jy, kz);
@@ -165,12 +164,11 @@ struct Acc1 {
 
   // Adds this thread's sums into the shared-memory current box at the local
   // anchor node a (linear box index).
-  template <int BX, int BXY, int NBOX>
   __device__ __forceinline__ void flush_box(T* J, int a) const {
 #pragma unroll
     for (int t = 0; t < NV; ++t) {
       const T val = v[t];
-      if (val != T(0)) atomicAdd(J + a + box_offset<BX, BXY, NBOX>(t), val);
+      if (val != T(0)) atomicAdd(J + a + box_offset(t), val);
     }
   }
 
@@ -212,6 +210,20 @@ struct Acc1 {
   }
 };
 
+// An accumulator with the lane's precomputed reduce-scatter offsets, in the
+// form flush_warp_runs takes.
+template <class AC>
+struct WithOffsets {
+  const AC& acc;
+  const int* goff;
+  template <bool ALL, typename T>
+  __device__ __forceinline__ void group_flush(bool member, int lane, T* J, int a) const {
+    acc.template group_flush<ALL>(member, lane, J, a, goff);
+  }
+  template <typename T>
+  __device__ __forceinline__ void flush_box(T* J, int a) const { acc.flush_box(J, a); }
+};
+
 constexpr int kNT = 128;
 // Fewest lanes of one anchor that a warp sums by reduce-scatter (about 330
 // instructions per anchor); smaller groups add their runs lane by lane.
@@ -221,7 +233,8 @@ constexpr int kMinGroupLanes = 3;
 // padded to P+1), the field box (E and time-averaged B, 6 arrays of NBOX
 // nodes with fixed strides BX, BX*BY, so every gather and deposit offset is a
 // compile-time constant; its first 3 arrays are the current box after the
-// push), the counters and the permutation of the anchor sort, and the runs.  The box holds
+// push), the counters and the permutation of the anchor sort, and the runs
+// (in 3D inside the box's last 3 arrays, which the push leaves dead).  The box holds
 // nodes lo-1 .. hi+2 of a chunk whose cells span lo .. hi: up to 9 cells
 // along x (two x-adjacent 4-cell sort tiles) and 5 along y and z.
 // Stage words: 0-2 old offsets, 3 weight, 4-6 u (replaced by the new offsets
@@ -241,7 +254,11 @@ struct Plan {
   static constexpr size_t cnt = (size_t)(NBOX + 1) * sizeof(int);   // anchor counters
   static constexpr size_t perm = (size_t)C * sizeof(unsigned short);
   static constexpr size_t runs = (size_t)C * sizeof(unsigned short);  // run descriptors
-  static constexpr size_t total = stage + box + cnt + perm + runs;
+  // the sort arrays live in the box's last three arrays (the time-averaged
+  // B, dead after the push) where they fit (3D), else after the box
+  static constexpr bool sort_in_box = cnt + perm + runs <= (size_t)3 * NBOX * sizeof(T);
+  static constexpr size_t sort_at = stage + (sort_in_box ? (size_t)3 * NBOX * sizeof(T) : box);
+  static constexpr size_t total = stage + box + (sort_in_box ? 0 : cnt + perm + runs);
 };
 
 // Order-1 interpolation from a shared-memory box with fixed strides; b is
@@ -318,15 +335,14 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
           const __grid_constant__ SpeciesPtrs<T> sp, int prescribed, unsigned* status,
           unsigned long long* pushed_total) {
   using PL = Plan<T, DIM, P>;
-  using AC = Acc1<T, DIM>;
+  using AC = Acc1<T, DIM, PL::BX, PL::BXY, PL::NBOX>;
   constexpr int PP = PL::PP, ROW = PL::ROW, C = PL::C;
   constexpr int BX = PL::BX, BY = PL::BY, BZ = PL::BZ, BXY = PL::BXY, NBOX = PL::NBOX;
-  constexpr int K = AC::NVP / 32;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* stg = reinterpret_cast<T*>(smraw);
   T* bx_ = reinterpret_cast<T*>(smraw + PL::stage);
-  int* cnt = reinterpret_cast<int*>(smraw + PL::stage + PL::box);
-  unsigned short* perm = reinterpret_cast<unsigned short*>(smraw + PL::stage + PL::box + PL::cnt);
+  int* cnt = reinterpret_cast<int*>(smraw + PL::sort_at);
+  unsigned short* perm = reinterpret_cast<unsigned short*>(smraw + PL::sort_at + PL::cnt);
   __shared__ int s_lo[3], s_hi[3];
   __shared__ int s_scan[kNT / 32];
   __shared__ int s_nanchor;
@@ -336,13 +352,14 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
   const long long nchunks = (n + C - 1) / C;
   unsigned pushed = 0;
   if (sp.immobile) return;
-  unsigned short* runs = reinterpret_cast<unsigned short*>(smraw + PL::stage + PL::box + PL::cnt + PL::perm);
+  unsigned short* runs = reinterpret_cast<unsigned short*>(smraw + PL::sort_at + PL::cnt + PL::perm);
   // box offsets of the two (2D: one) reduce-scatter results this lane adds
+  constexpr int K = AC::NVP / 32;
   int goff[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const int idx = k + K * lane;
-    goff[k] = idx < AC::NV ? AC::template box_offset<BX, BXY, NBOX>(idx) : -1;
+    goff[k] = idx < AC::NV ? AC::box_offset(idx) : -1;
   }
 
   for (long long ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
@@ -430,8 +447,8 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
         if constexpr (DIM == 2) stg[9 * ROW + slot] = stg[3 * ROW + slot] * u[1] * ig;
       }
       __syncthreads();
-      // ---- B. counting sort of the chunk by anchor ----
-      // (keys are compact indices of the chunk's region, key NB collects the
+      // ---- B. counting sort of the chunk by anchor, runs ----
+      // (keys are compact indices of the anchor cells, key nk collects the
       // particles that deposit nothing; the E/B box is dead: its first three
       // arrays become the current box)
       T* const BJ = bx_;
@@ -440,97 +457,31 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
         constexpr int NZ = (int)(3 * NBOX * sizeof(T) / sizeof(float4));
         for (int t = tid; t < NZ; t += kNT) z[t] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
-      for (int t = tid; t <= NB; t += kNT) cnt[t] = 0;
+      // key: the anchor cell min(old, new) per axis, from s_lo - 1 to s_hi
+      const int kdx = bdx - 2, kdy = DIM == 3 ? bdy - 2 : 1, nk = kdx * kdy * (bdz - 2);
+      for (int t = tid; t <= nk; t += kNT) cnt[t] = 0;
       if (tid == 0) {
         s_nanchor = 0;
         s_nrun = 0;
       }
       __syncthreads();
-      auto anchor_key = [&](int slot) -> int {
+      int keys[P];
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        const int q = tid + k * kNT;
+        const int slot = (q / P) * PP + (q % P);
         const int c0 = bits_to_cell<T>(stg[7 * ROW + slot]);
         const int c1 = bits_to_cell<T>(stg[8 * ROW + slot]);
-        if (c0 < 0 || c1 < 0) return NB;
-        const int ax = min(cell_i(c0), cell_i(c1)) - ox;
-        const int ay = DIM == 3 ? min(cell_j(c0), cell_j(c1)) - oy : 0;
-        const int az = min(cell_k(c0), cell_k(c1)) - oz;
-        return ax + bdx * (ay + bdy * az);
-      };
-      // count pass: each particle's key and its rank among the chunk's
-      // particles of that key (warp-aggregated counter increments)
-      int keys[P], ranks[P];
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        const int q = tid + k * kNT;
-        keys[k] = anchor_key((q / P) * PP + (q % P));
-        const unsigned m = __match_any_sync(0xffffffffu, keys[k]);
-        const int leader = __ffs(m) - 1;
-        int b = 0;
-        if (lane == leader) b = atomicAdd(cnt + keys[k], __popc(m));
-        ranks[k] = __shfl_sync(0xffffffffu, b, leader) + __popc(m & ((1u << lane) - 1u));
-      }
-      __syncthreads();
-      const int per = (NB + 1 + kNT - 1) / kNT;   // counters scanned per thread
-      const int b0 = tid * per;
-      {  // exclusive scan of cnt[0..NB]; number of anchors present
-        int loc = 0, nz = 0;
-        for (int t = 0; t < per; ++t)
-          if (b0 + t <= NB) {
-            const int c = cnt[b0 + t];
-            loc += c;
-            nz += b0 + t < NB && c != 0;
-          }
-        nz = __reduce_add_sync(0xffffffffu, nz);
-        if (lane == 0 && nz) atomicAdd(&s_nanchor, nz);
-        int inc = loc;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int v = __shfl_up_sync(0xffffffffu, inc, o);
-          if (lane >= o) inc += v;
-        }
-        if (lane == 31) s_scan[warp] = inc;
-        __syncthreads();
-        int wofs = 0;
-        for (int w8 = 0; w8 < warp; ++w8) wofs += s_scan[w8];
-        int run = wofs + inc - loc;
-        for (int t = 0; t < per; ++t)
-          if (b0 + t <= NB) {
-            const int c0 = cnt[b0 + t];
-            cnt[b0 + t] = run;
-            run += c0;
-          }
-      }
-      __syncthreads();
-      // scatter pass: the scan turned the counters into each key's start
-#pragma unroll
-      for (int k = 0; k < P; ++k) {
-        const int q = tid + k * kNT;
-        perm[cnt[keys[k]] + ranks[k]] = (unsigned short)((q / P) * PP + (q % P));
-      }
-      // Runs: each anchor's particles (consecutive in the sorted order) are
-      // cut into runs of at most L, so a run never straddles two anchors.  L
-      // is P, or longer when the chunk holds few anchors, so that the runs
-      // still number at most one per thread.  Descriptor: start | length << 11.
-      {
-        const int nlive = cnt[NB], nanc = s_nanchor;
-        int L = P;
-        if (2 * nanc < kNT) {
-          const int l = (nlive + kNT - nanc - 1) / (kNT - nanc);
-          L = l > P ? l : P;
-        }
-        for (int t = 0; t < per; ++t) {
-          const int b = b0 + t;
-          if (b >= NB) break;
-          const int st = cnt[b], cb = cnt[b + 1] - st;
-          if (cb == 0) continue;
-          const int r = (cb + L - 1) / L;
-          const int rb = atomicAdd(&s_nrun, r);
-          for (int j = 0; j < r; ++j) {
-            const int len = min(L, cb - j * L);
-            runs[rb + j] = (unsigned short)((st + j * L) | (len << 11));
-          }
+        if (c0 < 0 || c1 < 0) {
+          keys[k] = nk;
+        } else {
+          const int ax = min(cell_i(c0), cell_i(c1)) - ox;
+          const int ay = DIM == 3 ? min(cell_j(c0), cell_j(c1)) - oy : 0;
+          const int az = min(cell_k(c0), cell_k(c1)) - oz;
+          keys[k] = ax + kdx * (ay + kdy * az);
         }
       }
-      __syncthreads();
+      sort_runs<P, kNT>(keys, nk, cnt, perm, runs, s_scan, &s_nanchor, &s_nrun);
       // ---- C. deposit the runs, one per thread at a time ----
       // Shape factors of a slot's move; returns the box offset of its anchor.
       auto prepare = [&](int slot, T (&S0)[3][3], T (&DS)[3][3]) -> int {
@@ -570,32 +521,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
             acc.add(S0, DS, stg[3 * ROW + slot], wvy_of(slot));
           }
         }
-        // Lanes that share an anchor hold consecutive runs.  A group of at
-        // least kMinGroupLanes lanes sums its runs with one reduce-scatter;
-        // the lanes of smaller groups (a few particles per cell) add their
-        // own runs to the box, where few lanes meet on an address.
-        const int up = __shfl_up_sync(0xffffffffu, key, 1);
-        const bool head = key >= 0 && (lane == 0 || up != key);
-        const unsigned heads = __ballot_sync(0xffffffffu, head);
-        const unsigned live = __ballot_sync(0xffffffffu, key >= 0);
-        const unsigned below = heads & ((2u << lane) - 1u);     // heads at or before this lane
-        const unsigned above = (heads | ~live) & ~((2u << lane) - 1u);
-        const int first = below ? 31 - __clz(below) : 0;
-        const int next = above ? __ffs(above) - 1 : 32;
-        const bool big = key >= 0 && next - first >= kMinGroupLanes;
-        if (heads == 1u && live == 0xffffffffu) {
-          // the whole warp holds one anchor: no membership masks
-          acc.template group_flush<true>(true, lane, BJ, key, goff);
-        } else {
-          unsigned pend = __ballot_sync(0xffffffffu, head && big);
-          while (pend) {
-            const int leader = __ffs(pend) - 1;
-            pend &= pend - 1;
-            const int gk = __shfl_sync(0xffffffffu, key, leader);
-            acc.template group_flush<false>(key == gk, lane, BJ, gk, goff);
-          }
-          if (key >= 0 && !big) acc.template flush_box<BX, BXY, NBOX>(BJ, key);
-        }
+        flush_warp_runs(WithOffsets<AC>{acc, goff}, key, lane, BJ, kMinGroupLanes);
       }
       __syncthreads();
       // ---- D. add the current box to the grid with the charge factor and alpha ----
@@ -606,6 +532,10 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
       const T* anz = al_node<T>(tb, 2);
       const T* acz = al_cent<T>(tb, 2);
       const T qy = DIM == 3 ? sp.cj[1] : sp.cjy2d;
+      // axes along which the whole region lies where alpha is 1 skip its tables
+      const bool one_x = ox >= tb.al1_lo[0] && ox + bdx - 1 <= tb.al1_hi[0];
+      const bool one_y = DIM == 2 || (oy >= tb.al1_lo[1] && oy + bdy - 1 <= tb.al1_hi[1]);
+      const bool one_z = oz >= tb.al1_lo[2] && oz + bdz - 1 <= tb.al1_hi[2];
       for (int t = tid; t < NB; t += kNT) {
         const int li = t % bdx, r = t / bdx, lj = r % bdy, lk = r / bdy;
         const int bi = li + BX * lj + BXY * lk;
@@ -613,10 +543,12 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
         if (j0 == T(0) && j1 == T(0) && j2 == T(0)) continue;
         const int gi = ox + li, gj = oy + lj, gk = oz + lk;
         const long long id = g.idx(gi, gj, gk);
-        const T ay_n = DIM == 3 ? any[gj] : T(1), ay_c = DIM == 3 ? acy[gj] : T(1);
-        if (j0 != T(0)) atomicAdd(f.J[0] + id, sp.cj[0] * j0 * acx[gi] * ay_n * anz[gk]);
-        if (j1 != T(0)) atomicAdd(f.J[1] + id, qy * j1 * anx[gi] * ay_c * anz[gk]);
-        if (j2 != T(0)) atomicAdd(f.J[2] + id, sp.cj[2] * j2 * anx[gi] * ay_n * acz[gk]);
+        const T ax_n = one_x ? T(1) : anx[gi], ax_c = one_x ? T(1) : acx[gi];
+        const T ay_n = one_y ? T(1) : any[gj], ay_c = one_y ? T(1) : acy[gj];
+        const T az_n = one_z ? T(1) : anz[gk], az_c = one_z ? T(1) : acz[gk];
+        if (j0 != T(0)) atomicAdd(f.J[0] + id, sp.cj[0] * j0 * ax_c * ay_n * az_n);
+        if (j1 != T(0)) atomicAdd(f.J[1] + id, qy * j1 * ax_n * ay_c * az_n);
+        if (j2 != T(0)) atomicAdd(f.J[2] + id, sp.cj[2] * j2 * ax_n * ay_n * az_c);
       }
     } else {
       // sparse chunk: one particle at a time from global memory

@@ -72,49 +72,50 @@ __device__ __forceinline__ T interp3_box(const T* F, int b, const T* wx, const T
   return acc;
 }
 
-// Register accumulator of one current component CMP of a run of order-3
+// Register accumulator of one current component c of a run of order-3
 // moves: w * (Esirkepov factor) prefix sums, 4 x 5 x 5 values with flat
-// index q = (td * 5 + tb) * 4 + ta: ta along CMP (the prefix sums of DS),
-// tb and td along the transverse axes B < D.  The transverse factor
+// index q = (td * 5 + tb) * 4 + ta: ta along c (the prefix sums of DS),
+// tb and td along the transverse axes b < d.  The transverse factor
 // S0 S0' + DS S0'/2 + S0 DS'/2 + DS DS'/3 is evaluated as M M' + Q DS' with
-// M = S0 + DS/2, Q = DS/12.  Box offsets use the strides 1, BX, BXY and the
-// component arrays NBOX apart.
-template <typename T, int CMP, int BX, int BXY, int NBOX>
+// M = S0 + DS/2, Q = DS/12.  The component is a run-time value, so one copy
+// of the code serves all three: its box offsets are c NBOX + ta sc + tb sb +
+// td sd with the strides (1, BX, BXY) of axes c, b, d.
+template <typename T>
 struct Acc3 {
-  static constexpr int B = CMP == 0 ? 1 : 0, D = CMP == 2 ? 1 : 2;
   static constexpr int NV = 100;
   T v[NV];
+  int oc, sc, sb, sd;
 
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int q = 0; q < NV; ++q) v[q] = T(0);
   }
 
-  __device__ __forceinline__ void add(const T S0[3][5], const T DS[3][5], T w) {
+  // One move: DSc along the component, (Sb, DSb) and (Sd, DSd) along b, d.
+  __device__ __forceinline__ void add(const T* DSc, const T* Sb, const T* DSb, const T* Sd, const T* DSd, T w) {
     T A[4];
     T run = T(0);
 #pragma unroll
     for (int ta = 0; ta < 4; ++ta) {
-      run += DS[CMP][ta];
+      run += DSc[ta];
       A[ta] = w * run;
     }
 #pragma unroll
     for (int td = 0; td < 5; ++td) {
-      const T Md = S0[D][td] + T(0.5) * DS[D][td];
+      const T Md = Sd[td] + T(0.5) * DSd[td];
 #pragma unroll
       for (int tb = 0; tb < 5; ++tb) {
-        const T Mb = S0[B][tb] + T(0.5) * DS[B][tb];
-        const T Tl = Mb * Md + T(1.0 / 12.0) * DS[B][tb] * DS[D][td];
+        const T Mb = Sb[tb] + T(0.5) * DSb[tb];
+        const T Tl = Mb * Md + T(1.0 / 12.0) * DSb[tb] * DSd[td];
 #pragma unroll
         for (int ta = 0; ta < 4; ++ta) v[(td * 5 + tb) * 4 + ta] += A[ta] * Tl;
       }
     }
   }
 
-  __device__ __forceinline__ static int box_offset(int q) {
-    constexpr int st[3] = {1, BX, BXY};
+  __device__ __forceinline__ int box_offset(int q) const {
     const int ta = q & 3, tb = (q >> 2) % 5, td = q / 20;
-    return CMP * NBOX + ta * st[CMP] + tb * st[B] + td * st[D];
+    return oc + ta * sc + tb * sb + td * sd;
   }
 
   __device__ __forceinline__ void flush_box(T* J, int a) const {
@@ -329,40 +330,45 @@ __global__ void __launch_bounds__(kNT3, sizeof(T) == 4 ? 3 : 2)
       }
       sort_runs<P, kNT3>(keys, nk, cnt, perm, runs, s_scan, &s_nanchor, &s_nrun);
       // ---- C. deposit the runs, one component at a time ----
-      // Shape factors of a slot's move; returns the box offset of the first
-      // node of its stencil.
-      auto prepare = [&](int slot, T (&S0)[3][5], T (&DS)[3][5]) -> int {
-        const int cell1 = bits_to_cell<T>(stg[8 * ROW + slot]);
-        const int cell0 = bits_to_cell<T>(stg[7 * ROW + slot]);
-        const int c0[3] = {cell_i(cell0), cell_j(cell0), cell_k(cell0)};
-        const int c1[3] = {cell_i(cell1), cell_j(cell1), cell_k(cell1)};
-        int lo[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-          esk_axis<3, T>(c0[a], stg[a * ROW + slot], c1[a], stg[(4 + a) * ROW + slot], lo[a], S0[a], DS[a]);
-        return (lo[0] - ox) + BX * (lo[1] - oy) + BXY * (lo[2] - oz);
-      };
       const int R = s_nrun;
-      auto deposit_component = [&](auto acc) {
+#pragma unroll 1
+      for (int c = 0; c < 3; ++c) {
+        Acc3<T> acc;
+        const int b = c == 0 ? 1 : 0, dd = c == 2 ? 1 : 2;   // transverse axes
+        acc.oc = c * NBOX;
+        acc.sc = c == 0 ? 1 : (c == 1 ? BX : BXY);
+        acc.sb = b == 0 ? 1 : BX;
+        acc.sd = dd == 1 ? BX : BXY;
         for (int rb = warp * 32; rb < R; rb += kNT3) {
           acc.zero();
           int key = -1;
           if (rb + lane < R) {
             const unsigned d = runs[rb + lane];
-            const int st = d & 0x7ff, len = d >> 11;
+            const int st0 = d & 0x7ff, len = d >> 11;
             for (int i = 0; i < len; ++i) {
-              const int slot = perm[st + i];
-              T S0[3][5], DS[3][5];
-              key = prepare(slot, S0, DS);
-              acc.add(S0, DS, stg[3 * ROW + slot]);
+              const int slot = perm[st0 + i];
+              const int cell0 = bits_to_cell<T>(stg[7 * ROW + slot]);
+              const int cell1 = bits_to_cell<T>(stg[8 * ROW + slot]);
+              const int c0[3] = {cell_i(cell0), cell_j(cell0), cell_k(cell0)};
+              const int c1[3] = {cell_i(cell1), cell_j(cell1), cell_k(cell1)};
+              // box offset of the first stencil node (the anchor minus one)
+              key = (min(c0[0], c1[0]) - 1 - ox) + BX * (min(c0[1], c1[1]) - 1 - oy) +
+                    BXY * (min(c0[2], c1[2]) - 1 - oz);
+              auto pick = [](int a, int x, int y, int z) { return a == 0 ? x : (a == 1 ? y : z); };
+              int lo;
+              T Sc[5], DSc[5], Sb[5], DSb[5], Sd[5], DSd[5];
+              esk_axis<3, T>(pick(c, c0[0], c0[1], c0[2]), stg[c * ROW + slot], pick(c, c1[0], c1[1], c1[2]),
+                             stg[(4 + c) * ROW + slot], lo, Sc, DSc);
+              esk_axis<3, T>(pick(b, c0[0], c0[1], c0[2]), stg[b * ROW + slot], pick(b, c1[0], c1[1], c1[2]),
+                             stg[(4 + b) * ROW + slot], lo, Sb, DSb);
+              esk_axis<3, T>(pick(dd, c0[0], c0[1], c0[2]), stg[dd * ROW + slot], pick(dd, c1[0], c1[1], c1[2]),
+                             stg[(4 + dd) * ROW + slot], lo, Sd, DSd);
+              acc.add(DSc, Sb, DSb, Sd, DSd, stg[3 * ROW + slot]);
             }
           }
           flush_warp_runs(acc, key, lane, BJ, kMinGroupLanes3);
         }
-      };
-      deposit_component(Acc3<T, 0, BX, BXY, NBOX>{});
-      deposit_component(Acc3<T, 1, BX, BXY, NBOX>{});
-      deposit_component(Acc3<T, 2, BX, BXY, NBOX>{});
+      }
       __syncthreads();
       // ---- D. add the current box to the grid with the charge factor and alpha ----
       const T* anx = al_node<T>(tb, 0);

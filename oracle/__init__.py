@@ -59,6 +59,8 @@ def lib():
                                      C.c_double, C.c_double, C.c_double, C.c_double]
             L.ora_destroy.argtypes = [C.c_void_p]
             L.ora_set_prescribed.argtypes = [C.c_void_p, C.c_int]
+            L.ora_set_face_alpha.argtypes = [C.c_void_p, ip]
+            L.ora_set_face_alpha.restype = C.c_int
             L.ora_add_particles.restype = C.c_long
             L.ora_add_particles.argtypes = [C.c_void_p, C.c_long] + [dp] * 7 + [C.c_double, C.c_double, C.c_int]
             L.ora_num_particles.restype = C.c_long
@@ -180,7 +182,7 @@ class OracleSim:
     """
 
     def __init__(self, dim, n, pml, d, dt, order=1, alpha_mode="damped",
-                 sig_coef=4.0, delta=6.0, sig_exp=2.0, v_assumed=C_LIGHT):
+                 sig_coef=4.0, delta=6.0, sig_exp=2.0, v_assumed=C_LIGHT, face_alpha=None):
         L = lib()
         self.dim = dim
         n3 = (C.c_int * 3)(*[int(v) for v in n])
@@ -199,6 +201,16 @@ class OracleSim:
         self.d = tuple(float(v) for v in d)
         self.dt = float(dt)
         self.order = order
+        if face_alpha is not None:
+            self.set_face_alpha(face_alpha)
+
+    def set_face_alpha(self, modes):
+        """Per-face scheme, faces (-x, +x, -y, +y, -z, +z): "zero", "one" or
+        "damped" (the cavity discussion of Sec. III: undamped where particles
+        enter, damped where they leave)."""
+        m6 = (C.c_int * 6)(*[ALPHA_MODES[m] if isinstance(m, str) else int(m) for m in modes])
+        if lib().ora_set_face_alpha(self._h, m6) != 0:
+            raise ValueError("oracle: per-face alpha modes are zero, one or damped, and not in weight mode")
 
     def __del__(self):
         h = getattr(self, "_h", None)

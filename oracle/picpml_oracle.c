@@ -24,7 +24,7 @@
  *      Eqs. MaxwellE, MaxwellB, MaxwellSum in every location where a damping
  *      conductivity is nonzero.
  *
- * Readings of points the paper leaves open (each one is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - B lives at half-integer times; the push uses the time average of the two
  *     B half steps that bracket t^n (the classic Yee/Boris leapfrog).
  *   - The split components with d/dt F = R - s F, s = sigma/eps0, advance by
@@ -64,6 +64,7 @@
 
 typedef struct ora_sim {
   int dim, order, alpha_mode, prescribed;
+  int face_mode[6];                 /* alpha mode of each face (-x,+x,-y,+y,-z,+z) */
   int n[3], plo[3], phi[3], N[3];   /* physical cells, PML cells low/high, total cells */
   long nn[3];                       /* nodes per axis in the arrays (1 for y in 2D) */
   long ntot;
@@ -111,6 +112,12 @@ static double depth_of(const ora_sim* s, int a, double x) {
   return 0.0;
 }
 
+/* The face of axis a that position x lies beyond (its low face below the
+ * physical box, else its high face). */
+static int face_of(const ora_sim* s, int a, double x) {
+  return x < (double)s->plo[a] ? 2 * a : 2 * a + 1;
+}
+
 static void build_tables(ora_sim* s) {
   for (int a = 0; a < 3; ++a) {
     long nn = s->nn[a];
@@ -124,8 +131,10 @@ static void build_tables(ora_sim* s) {
       double dc = active ? depth_of(s, a, (double)i + 0.5) : 0.0;
       s->s_node[a][i] = ora_sigma_over_eps0(dn, s->d[a], s->sig_coef, s->delta, s->sig_exp);
       s->s_cent[a][i] = ora_sigma_over_eps0(dc, s->d[a], s->sig_coef, s->delta, s->sig_exp);
-      s->a_node[a][i] = ora_alpha(dn, s->sig_coef, s->delta, s->sig_exp, s->v_assumed, s->alpha_mode);
-      s->a_cent[a][i] = ora_alpha(dc, s->sig_coef, s->delta, s->sig_exp, s->v_assumed, s->alpha_mode);
+      int fn = s->face_mode[face_of(s, a, (double)i)];
+      int fc = s->face_mode[face_of(s, a, (double)i + 0.5)];
+      s->a_node[a][i] = ora_alpha(dn, s->sig_coef, s->delta, s->sig_exp, s->v_assumed, fn);
+      s->a_cent[a][i] = ora_alpha(dc, s->sig_coef, s->delta, s->sig_exp, s->v_assumed, fc);
     }
   }
 }
@@ -140,6 +149,7 @@ ora_sim* ora_create(int dim, const int* nphys, const int* pml, const double* d,
   if ((dim != 2 && dim != 3) || (order != 1 && order != 3)) return NULL;
   ora_sim* s = calloc(1, sizeof(ora_sim));
   s->dim = dim; s->order = order; s->alpha_mode = alpha_mode;
+  for (int f = 0; f < 6; ++f) s->face_mode[f] = alpha_mode;
   s->dt = dt; s->sig_coef = sig_coef; s->delta = delta; s->sig_exp = sig_exp;
   s->v_assumed = v_assumed > 0 ? v_assumed : ORA_C;
   for (int a = 0; a < 3; ++a) {
@@ -178,6 +188,25 @@ void ora_destroy(ora_sim* s) {
 
 void ora_set_prescribed(ora_sim* s, int flag) { s->prescribed = flag; }
 
+/* Per-face deposition schemes (the paper's cavity discussion, Sec. III: the
+ * undamped scheme on the face where particles enter, the damped one on the
+ * face where they leave).  modes[f] in {0, 1, 2} (alpha = 0, 1 or Eq. alpha
+ * inside face f) replaces the box's mode on that face: its alpha values and,
+ * for mode 0, the removal of particles at that face's interface.  Weight
+ * damping (mode 3) is a property of the macroparticles, not of a face: a box
+ * in mode 3 takes no per-face modes.  Returns 0, or -1 (nothing changed). */
+int ora_set_face_alpha(ora_sim* s, const int* modes) {
+  if (s->alpha_mode == 3) return -1;
+  for (int f = 0; f < 6; ++f)
+    if (modes[f] < 0 || modes[f] > 2) return -1;
+  for (int f = 0; f < 6; ++f) s->face_mode[f] = modes[f];
+  for (int a = 0; a < 3; ++a) {
+    free(s->s_node[a]); free(s->s_cent[a]); free(s->a_node[a]); free(s->a_cent[a]);
+  }
+  build_tables(s);
+  return 0;
+}
+
 static inline long IX(const ora_sim* s, long i, long j, long k) {
   return i + s->nn[0] * (j + s->nn[1] * k);
 }
@@ -189,9 +218,8 @@ static double margin(const ora_sim* s) { return s->order == 1 ? 2.0 : 3.0; }
 static int outside_allowed(const ora_sim* s, const double* X) {
   for (int a = 0; a < 3; ++a) {
     if (s->dim == 2 && a == 1) continue;
-    if (s->alpha_mode == 0) {
-      if (X[a] < (double)s->plo[a] || X[a] > (double)(s->plo[a] + s->n[a])) return 1;
-    }
+    if (s->face_mode[2 * a] == 0 && X[a] < (double)s->plo[a]) return 1;
+    if (s->face_mode[2 * a + 1] == 0 && X[a] > (double)(s->plo[a] + s->n[a])) return 1;
     double m = margin(s);
     if (X[a] < m || X[a] > (double)s->N[a] - m) return 1;
   }

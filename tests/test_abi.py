@@ -57,3 +57,27 @@ def test_init_rejects_bad_descriptions_without_gpu(lib):
     g.dt = 1e-14   # above the Courant limit 1.9e-15 s
     assert L.load().pic_init(ctypes.byref(ctx), ctypes.byref(g), None) == -4
     assert b"Courant" in L.load().pic_last_error(None)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the header's sizes and field
+    offsets (a C program compiled against include/picpml.h prints them)."""
+    import subprocess
+    from paper_2201_09084_gb300 import _lib as L
+    structs = {"pic_grid_desc": L.GridDesc, "pml_desc": L.PmlDesc, "pic_species": L.SpeciesDesc,
+               "pic_batch_desc": L.BatchDesc}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "picpml.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.rsplit(" ", 1) for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for cname, cls in structs.items():
+        assert int(got[f"{cname} size"]) == ctypes.sizeof(cls), cname
+        for fname, _ in cls._fields_:
+            assert int(got[f"{cname} {fname}"]) == getattr(cls, fname).offset, (cname, fname)

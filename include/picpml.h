@@ -105,6 +105,16 @@ typedef struct pml_desc {
   double exponent;      /* p */
   int alpha_mode;       /* pml_alpha_mode */
   double v_assumed;     /* v of Eq. alpha (m/s); <= 0 selects c */
+  int face_alpha_set;   /* 0: every face uses alpha_mode.  1: face f uses
+                           face_alpha[f] instead (PML_ALPHA_ZERO, _ONE or
+                           _DAMPED; the paper's cavity discussion, Sec. III,
+                           suggests the undamped scheme on the face where
+                           particles enter and the damped one where they
+                           leave).  A face in PML_ALPHA_ZERO removes particles
+                           at its own interface only.  PIC_EINVAL for another
+                           mode, or with alpha_mode PML_ALPHA_WEIGHT (weight
+                           damping belongs to the particles, not a face). */
+  int face_alpha[6];    /* per-face modes, -x,+x,-y,+y,-z,+z */
 } pml_desc;
 
 /* A species: caller-owned device arrays of `capacity` particles, n of them
@@ -232,12 +242,13 @@ int pic_num_particles(picpml_ctx* ctx, int sid, long long* n);
 int pic_diag(picpml_ctx* ctx, double* gauss, double* rho_scale, double* energy);
 
 /* Autotuner: times the fused particle kernel for each particles-per-thread
- * choice (order 1, and order 3 in 3D: 1, 4, 8; FP64: 1, 4) and the field
- * kernels for each
- * z-nodes-per-thread choice, `steps` steps per candidate, each from the same
- * state (a device snapshot, restored afterwards; the call allocates that
- * snapshot), keeps the fastest and returns the choices.  Results do not
- * depend on the choice beyond the summation order of the current. */
+ * choice (order 1, and order 3 in 3D: 1, 4, 8; FP64: 1, 4) over `steps`
+ * whole steps (the field step runs between them, untimed, so the particles
+ * see evolving fields), and the field kernels for each z-nodes-per-thread
+ * choice, each candidate from the same state (a device snapshot, restored
+ * afterwards; the call allocates that snapshot), keeps the fastest and
+ * returns the choices.  Results do not depend on the choice beyond the
+ * summation order of the current. */
 int pic_autotune(picpml_ctx* ctx, int steps, int* particles_per_thread, int* z_nodes_per_thread);
 
 /* Sets the launch shapes directly (e.g. the result of pic_autotune in

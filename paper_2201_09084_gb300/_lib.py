@@ -36,7 +36,8 @@ class GridDesc(C.Structure):
 
 class PmlDesc(C.Structure):
     _fields_ = [("ncell", C.c_int * 6), ("sigma_max_coef", C.c_double), ("delta_cells", C.c_double),
-                ("exponent", C.c_double), ("alpha_mode", C.c_int), ("v_assumed", C.c_double)]
+                ("exponent", C.c_double), ("alpha_mode", C.c_int), ("v_assumed", C.c_double),
+                ("face_alpha_set", C.c_int), ("face_alpha", C.c_int * 6)]
 
 
 class SpeciesDesc(C.Structure):

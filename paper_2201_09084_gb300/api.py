@@ -51,12 +51,25 @@ def unpack_particles(pos, mom, n):
     return dict(cell=cell, off=pos[:, :3].numpy(), w=pos[:, 3].numpy(), u=mom[:, :3].numpy(), alive=alive)
 
 
+def _set_face_alpha(p, face_alpha):
+    """Per-face schemes (faces -x, +x, -y, +y, -z, +z): "zero", "one" or
+    "damped" each, or None for the box's alpha_mode on every face."""
+    if face_alpha is None:
+        p.face_alpha_set = 0
+        return
+    if len(face_alpha) != 6:
+        raise ValueError("face_alpha needs six modes (-x, +x, -y, +y, -z, +z)")
+    p.face_alpha_set = 1
+    for f, m in enumerate(face_alpha):
+        p.face_alpha[f] = L.ALPHA[m] if isinstance(m, str) else int(m)
+
+
 class Sim:
     """One GPU simulation box (physical cells + PML cells on every face)."""
 
     def __init__(self, dim, n, d, pml, *, dt=0.0, cfl=0.99, order=1, prec="fp32", sort_every=0,
                  alpha_mode="damped", sigma_coef=4.0, delta=6.0, exponent=2.0, v_assumed=0.0,
-                 split_fp64=False, stream=None):
+                 split_fp64=False, face_alpha=None, stream=None):
         self.lib = L.load()
         self.prec = prec
         self.dim = dim
@@ -77,6 +90,7 @@ class Sim:
         p.sigma_max_coef, p.delta_cells, p.exponent = float(sigma_coef), float(delta), float(exponent)
         p.alpha_mode = L.ALPHA[alpha_mode] if isinstance(alpha_mode, str) else int(alpha_mode)
         p.v_assumed = float(v_assumed)
+        _set_face_alpha(p, face_alpha)
         self._call(self.lib.pml_init, C.byref(p))
         nn = (C.c_int * 3)()
         dtv = C.c_double()
@@ -229,7 +243,8 @@ class Batch:
     """Many independent 2D runs advanced together (pic_batch_* of the C ABI)."""
 
     def __init__(self, nx, nz, npml, d, pos, mom, q, m, *, dt=0.0, cfl=0.99, order=1, prec="fp32",
-                 alpha_mode="damped", sigma_coef=4.0, delta=6.0, exponent=2.0, v_assumed=0.0, stream=None):
+                 alpha_mode="damped", sigma_coef=4.0, delta=6.0, exponent=2.0, v_assumed=0.0, face_alpha=None,
+                 stream=None):
         self.lib = L.load()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.n = len(nx)
@@ -247,6 +262,7 @@ class Batch:
         d_.pml.sigma_max_coef, d_.pml.delta_cells, d_.pml.exponent = float(sigma_coef), float(delta), float(exponent)
         d_.pml.alpha_mode = L.ALPHA[alpha_mode] if isinstance(alpha_mode, str) else int(alpha_mode)
         d_.pml.v_assumed = float(v_assumed)
+        _set_face_alpha(d_.pml, face_alpha)
         d_.q, d_.m = float(q), float(m)
         want = torch.float64 if prec == "fp64" else torch.float32
         assert pos.is_cuda and pos.dtype == want and tuple(pos.shape) == (self.n, 4)

@@ -51,14 +51,16 @@ cudaError_t launch_sort(const Geom&, int pbytes, void* pos, void* mom, long long
 
 namespace picpml {
 double sigma_eps0_face(const pml_desc& p, double Delta, double dc);
-double alpha_face(const pml_desc& p, double dc);
+double alpha_face(const pml_desc& p, int face, double dc);
+int face_alpha_mode(const pml_desc& p, int face);
 
 // Per-axis coefficient tables of one box at the nodes i and centres i+1/2
 // (Sec. II.B): exponential-differencing factors, s dt and alpha, from the
-// closed forms of Eq. conductivity and Eq. alpha.  plo, nph: PML cells below
-// and physical cells along the axis; `active` false for the absent y axis of
-// 2D boxes (no PML, alpha = 1).
-void build_axis_table(const pml_desc& p, double Delta, double dt, int plo, int nph, int nn, bool active,
+// closed forms of Eq. conductivity and Eq. alpha.  axis: 0, 1, 2 (its faces
+// 2 axis and 2 axis + 1 pick the alpha mode below and above the physical
+// box); plo, nph: PML cells below and physical cells along the axis;
+// `active` false for the absent y axis of 2D boxes (no PML, alpha = 1).
+void build_axis_table(const pml_desc& p, int axis, double Delta, double dt, int plo, int nph, int nn, bool active,
                       double* ea_n, double* eb_n, double* sdt_n, double* ea_c, double* eb_c, double* sdt_c,
                       double* al_n, double* al_c) {
   for (int i = 0; i < nn; ++i) {
@@ -72,7 +74,7 @@ void build_axis_table(const pml_desc& p, double Delta, double dt, int plo, int n
       const double sdt = sigma_eps0_face(p, Delta, dc) * dt;
       const double ea = std::exp(-sdt);
       const double eb = sdt > 0 ? -std::expm1(-sdt) / sdt : 1.0;
-      const double al = alpha_face(p, dc);
+      const double al = alpha_face(p, x < plo ? 2 * axis : 2 * axis + 1, dc);
       (stag ? ea_c : ea_n)[i] = ea;
       (stag ? eb_c : eb_n)[i] = eb;
       (stag ? sdt_c : sdt_n)[i] = sdt;
@@ -173,10 +175,15 @@ double picpml::sigma_eps0_face(const pml_desc& p, double Delta, double dc) {
 
 // Eq. alpha in closed form for the power-law profile: the exponent is
 // int_0^d sigma/(eps0 v) dz = coef (c/v) delta (d/delta)^{p+1}/(p+1), d in cells.
-double picpml::alpha_face(const pml_desc& p, double dc) {
+int picpml::face_alpha_mode(const pml_desc& p, int face) {
+  return p.face_alpha_set ? p.face_alpha[face] : p.alpha_mode;
+}
+
+double picpml::alpha_face(const pml_desc& p, int face, double dc) {
   if (dc <= 0.0) return 1.0;
-  if (p.alpha_mode == PML_ALPHA_ZERO) return 0.0;
-  if (p.alpha_mode == PML_ALPHA_ONE || p.alpha_mode == PML_ALPHA_WEIGHT) return 1.0;
+  const int mode = face_alpha_mode(p, face);
+  if (mode == PML_ALPHA_ZERO) return 0.0;
+  if (mode == PML_ALPHA_ONE || mode == PML_ALPHA_WEIGHT) return 1.0;
   const double v = p.v_assumed > 0 ? p.v_assumed : kC;
   const double e = p.sigma_max_coef * (kC / v) * p.delta_cells *
                    std::pow(dc / p.delta_cells, p.exponent + 1.0) / (p.exponent + 1.0);
@@ -322,6 +329,12 @@ int pml_init(picpml_ctx* ctx, const pml_desc* p) {
   if (!ctx || !p) return fail(ctx, PIC_EINVAL, "null argument");
   if (ctx->ready) return fail(ctx, PIC_ESTATE, "pml_init called twice");
   if (p->alpha_mode < 0 || p->alpha_mode > 3) return fail(ctx, PIC_EINVAL, "bad alpha_mode");
+  if (p->face_alpha_set) {
+    if (p->alpha_mode == PML_ALPHA_WEIGHT) return fail(ctx, PIC_EINVAL, "per-face modes with weight damping");
+    for (int f = 0; f < 6; ++f)
+      if (p->face_alpha[f] < PML_ALPHA_ZERO || p->face_alpha[f] > PML_ALPHA_DAMPED)
+        return fail(ctx, PIC_EINVAL, "per-face alpha modes are zero, one or damped");
+  }
   if (p->sigma_max_coef < 0 || !(p->delta_cells > 0) || p->exponent < 0)
     return fail(ctx, PIC_EINVAL, "bad conductivity profile");
   const pic_grid_desc& gd = ctx->gd;
@@ -346,10 +359,8 @@ int pml_init(picpml_ctx* ctx, const pml_desc* p) {
     g.Sf[a] = (float)g.S[a];
     g.Sfl[a] = (float)(g.S[a] - (double)g.Sf[a]);
     int rmin = margin, rmax = g.N[a] - margin;
-    if (p->alpha_mode == PML_ALPHA_ZERO) {
-      rmin = std::max(rmin, lo);
-      rmax = std::min(rmax, lo + gd.n[a]);
-    }
+    if (face_alpha_mode(*p, 2 * a) == PML_ALPHA_ZERO) rmin = std::max(rmin, lo);   // removed at the interface
+    if (face_alpha_mode(*p, 2 * a + 1) == PML_ALPHA_ZERO) rmax = std::min(rmax, lo + gd.n[a]);
     g.rmin[a] = rmin;
     g.rmax[a] = rmax;
     if (rmax <= rmin) return fail(ctx, PIC_EINVAL, "grid too small for the particle shape");
@@ -386,7 +397,7 @@ int pml_init(picpml_ctx* ctx, const pml_desc* p) {
     const int nn = g.nn[a];
     std::vector<double> t8(8 * (size_t)nn);
     double* q8 = t8.data();
-    build_axis_table(*p, gd.d[a], ctx->dt, g.plo[a], g.nph[a], nn, !(gd.dim == 2 && a == 1), q8, q8 + nn,
+    build_axis_table(*p, a, gd.d[a], ctx->dt, g.plo[a], g.nph[a], nn, !(gd.dim == 2 && a == 1), q8, q8 + nn,
                      q8 + 2 * nn, q8 + 3 * nn, q8 + 4 * nn, q8 + 5 * nn, q8 + 6 * nn, q8 + 7 * nn);
     for (int i = 0; i < nn; ++i) {
       for (int stag = 0; stag < 2; ++stag) {
@@ -602,18 +613,31 @@ int pic_autotune(picpml_ctx* ctx, int steps, int* ppt, int* kz) {
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
+  // A particle candidate is timed over whole steps (push + deposit, then the
+  // field step, which is not timed): the fields the particles see then evolve
+  // as in a run; without the field steps they stay at their start values,
+  // which favoured the wrong launch shape for a beam starting in vacuum.
   auto time_it = [&](bool particles, float* ms) -> int {
     int rr = 0;
-    // warm-up launch, then the timed ones
+    *ms = 0.f;
+    // warm-up step, then the timed ones
     for (int t = 0; t <= steps; ++t) {
-      if (t == 1) CK(cudaEventRecord(e0, ctx->stream));
+      if (t >= 1) CK(cudaEventRecord(e0, ctx->stream));
       rr = particles ? (f64 ? run_particles<double>(ctx, 2) : run_particles<float>(ctx, 2))
                      : (f64 ? run_field<double>(ctx) : run_field<float>(ctx));
       if (rr) return rr;
+      if (t >= 1) {
+        CK(cudaEventRecord(e1, ctx->stream));
+        CK(cudaEventSynchronize(e1));
+        float one = 0.f;
+        CK(cudaEventElapsedTime(&one, e0, e1));
+        *ms += one;
+      }
+      if (particles) {
+        rr = f64 ? run_field<double>(ctx) : run_field<float>(ctx);
+        if (rr) return rr;
+      }
     }
-    CK(cudaEventRecord(e1, ctx->stream));
-    CK(cudaEventSynchronize(e1));
-    CK(cudaEventElapsedTime(ms, e0, e1));
     *ms /= steps;
     CK(restore());
     ctx->ff = ff0;

@@ -23,10 +23,11 @@
 namespace picpml {
 
 // Axis tables of one box, built from the closed forms of Eq. conductivity and
-// Eq. alpha (defined in api.cu).
-void build_axis_table(const pml_desc& p, double Delta, double dt, int plo, int nph, int nn, bool active,
+// Eq. alpha, and the alpha mode of a face (defined in api.cu).
+void build_axis_table(const pml_desc& p, int axis, double Delta, double dt, int plo, int nph, int nn, bool active,
                       double* ea_n, double* eb_n, double* sdt_n, double* ea_c, double* eb_c, double* sdt_c,
                       double* al_n, double* al_c);
+int face_alpha_mode(const pml_desc& p, int face);
 
 namespace {
 
@@ -447,6 +448,12 @@ int pic_batch_init(pic_batch** out, const pic_batch_desc* d, void* stream) {
     return bfail(b, PIC_EINVAL, "cell sizes, mass and particle arrays");
   if (d->pml.alpha_mode < 0 || d->pml.alpha_mode > 3 || !(d->pml.delta_cells > 0))
     return bfail(b, PIC_EINVAL, "PML profile");
+  if (d->pml.face_alpha_set) {
+    if (d->pml.alpha_mode == PML_ALPHA_WEIGHT) return bfail(b, PIC_EINVAL, "per-face modes with weight damping");
+    for (int f = 0; f < 6; ++f)
+      if (d->pml.face_alpha[f] < PML_ALPHA_ZERO || d->pml.face_alpha[f] > PML_ALPHA_DAMPED)
+        return bfail(b, PIC_EINVAL, "per-face alpha modes are zero, one or damped");
+  }
   const double lim = 1.0 / (kC * std::sqrt(1.0 / (d->d[0] * d->d[0]) + 1.0 / (d->d[1] * d->d[1])));
   double dt = d->dt;
   if (!(dt > 0)) {
@@ -470,10 +477,10 @@ int pic_batch_init(pic_batch** out, const pic_batch_desc* d, void* stream) {
     ri.nn0 = ri.N0 + 1;
     ri.nn2 = ri.N2 + 1;
     int r0 = margin, r1 = ri.N0 - margin, z0 = margin, z1 = ri.N2 - margin;
-    if (d->pml.alpha_mode == PML_ALPHA_ZERO) {
-      r0 = std::max(r0, p); r1 = std::min(r1, p + nx);
-      z0 = std::max(z0, p); z1 = std::min(z1, p + nz);
-    }
+    if (face_alpha_mode(d->pml, 0) == PML_ALPHA_ZERO) r0 = std::max(r0, p);   // removed at the interface
+    if (face_alpha_mode(d->pml, 1) == PML_ALPHA_ZERO) r1 = std::min(r1, p + nx);
+    if (face_alpha_mode(d->pml, 4) == PML_ALPHA_ZERO) z0 = std::max(z0, p);
+    if (face_alpha_mode(d->pml, 5) == PML_ALPHA_ZERO) z1 = std::min(z1, p + nz);
     if (r1 <= r0 || z1 <= z0) return bfail(b, PIC_EINVAL, "run " + std::to_string(r) + ": too small for the shape");
     ri.rmin0 = r0; ri.rmax0 = r1; ri.rmin2 = z0; ri.rmax2 = z1;
     ri.p = p; ri.nx = nx; ri.nz = nz;
@@ -501,7 +508,7 @@ int pic_batch_init(pic_batch** out, const pic_batch_desc* d, void* stream) {
       const int o = starts[ax], nn = nns[ax];
       std::vector<double> t8(8 * (size_t)nn);
       double* q8 = t8.data();
-      build_axis_table(d->pml, Dl[ax], dt, p, nph[ax], nn, true, q8, q8 + nn, q8 + 2 * nn, q8 + 3 * nn,
+      build_axis_table(d->pml, ax == 0 ? 0 : 2, Dl[ax], dt, p, nph[ax], nn, true, q8, q8 + nn, q8 + 2 * nn, q8 + 3 * nn,
                        q8 + 4 * nn, q8 + 5 * nn, q8 + 6 * nn, q8 + 7 * nn);
       for (int i = 0; i < nn; ++i) {
         for (int f = 0; f < 8; ++f) tabd[f * ntab + o + i] = q8[f * nn + i];

@@ -18,7 +18,12 @@ def _runs(n, seed):
     return I.batched_runs(n, size_range=(20, 44), pml_range=(6, 12), gamma_range=(1.5, 30.0), seed=seed)
 
 
-@pytest.mark.parametrize("mode", ["damped", "weight"])
+# per-face schemes on the faces the runs' particles leave through: +x removes
+# at its interface, +z deposits undamped
+FACES = {"faces": ["damped", "zero", "damped", "damped", "damped", "one"]}
+
+
+@pytest.mark.parametrize("mode", ["damped", "weight", "faces"])
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
 @pytest.mark.parametrize("order", [1, 3])
 def test_batched_runs_match_single_oracle_boxes(order, prec, mode):
@@ -26,14 +31,15 @@ def test_batched_runs_match_single_oracle_boxes(order, prec, mode):
     from paper_2201_09084_gb300.api import Batch, pack_particles
     r = _runs(7, seed=31 + order)
     dt = O.yee_dt(D2, 0.99, 2)
+    alpha, faces = ("damped", FACES[mode]) if mode in FACES else (mode, None)
     pos, mom = pack_particles(r["cell"], r["off"], r["u"], r["w"], prec)
     b = Batch(r["nx"], r["nz"], r["npml"], (D2[0], D2[2]), pos, mom, r["q"], r["m"], dt=dt, order=order,
-              prec=prec, alpha_mode=mode)
+              prec=prec, alpha_mode=alpha, face_alpha=faces)
     oras = []
     for k in range(7):
         p = int(r["npml"][k])
         s = O.OracleSim(2, (int(r["nx"][k]), 0, int(r["nz"][k])), (p, p, 0, 0, p, p), D2, dt, order=order,
-                        alpha_mode=mode)
+                        alpha_mode=alpha, face_alpha=faces)
         X = I.absolute(r["cell"][k:k + 1], r["off"][k:k + 1])
         u = r["u"][k].astype(np.float64)
         s.add_particles(X[:, 0], X[:, 1], X[:, 2], [u[0]], [u[1]], [u[2]], [1.0], r["q"], r["m"])

@@ -307,3 +307,27 @@ def test_chunk_segments(prec, order, ppt):
     Xo = np.stack([po["X"], po["Y"], po["Z"]], axis=1)
     tol = 1e-5 if prec == "fp32" else 1e-10
     assert np.max(np.abs(X[alive] - Xo[alive])) < tol
+
+
+@pytest.mark.parametrize("order", [1, 3])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_per_face_schemes(prec, order):
+    """Every face with its own scheme (zero, damped, one): fast particles
+    crossing all six interfaces; fields, removals and positions against the
+    oracle."""
+    faces = ["zero", "damped", "one", "zero", "one", "damped"]
+    nphys = (14, 12, 16)
+    pml = (6,) * 6
+    parts = I.random_particles(3, 600, [6.5, 6.5, 6.5], [19.5, 17.5, 21.5], u_rms=2.5, seed=71 + order)
+    ora, gpu = make_pair(3, nphys, pml, D3, parts, order=order, prec=prec, alpha_mode="damped", face_alpha=faces)
+    for _ in range(2):
+        ora.step(5)
+        gpu.step(5)
+        err = max_field_err(ora, gpu)
+        assert max(err.values()) < TOL[prec], err
+    X, u, alive = gpu_positions(gpu, 0)
+    po = ora.particles()
+    assert np.array_equal(alive, po["alive"])
+    assert 0 < int(alive.sum()) < len(alive)        # some particles were removed
+    Xo = np.stack([po["X"], po["Y"], po["Z"]], axis=1)
+    assert np.max(np.abs(X[alive] - Xo[alive])) < (1e-5 if prec == "fp32" else 1e-10)

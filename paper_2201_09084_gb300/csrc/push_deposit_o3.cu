@@ -268,13 +268,31 @@ __global__ void __launch_bounds__(kNT3, sizeof(T) == 4 ? 3 : 2)
           const int sx0 = b0[0] - ox, sxh = bh[0] - ox;
           const int sy0 = BX * (b0[1] - oy), syh = BX * (bh[1] - oy);
           const int sz0 = BXY * (b0[2] - oz), szh = BXY * (bh[2] - oz);
+          // one copy of the 64-point gather serves the six components (their
+          // half-node staggers chosen at run time: E_x, E_y, E_z are half a
+          // cell along x, y, z; B_x, B_y, B_z along the other two axes)
           T E[3], B[3];
-          E[0] = interp3_box<BX, BXY, T>(bx_ + 0 * NBOX, sxh + sy0 + sz0, wh[0], w0[1], w0[2]);
-          E[1] = interp3_box<BX, BXY, T>(bx_ + 1 * NBOX, sx0 + syh + sz0, w0[0], wh[1], w0[2]);
-          E[2] = interp3_box<BX, BXY, T>(bx_ + 2 * NBOX, sx0 + sy0 + szh, w0[0], w0[1], wh[2]);
-          B[0] = interp3_box<BX, BXY, T>(bx_ + 3 * NBOX, sx0 + syh + szh, w0[0], wh[1], wh[2]);
-          B[1] = interp3_box<BX, BXY, T>(bx_ + 4 * NBOX, sxh + sy0 + szh, wh[0], w0[1], wh[2]);
-          B[2] = interp3_box<BX, BXY, T>(bx_ + 5 * NBOX, sxh + syh + sz0, wh[0], wh[1], w0[2]);
+#pragma unroll 1
+          for (int comp = 0; comp < 6; ++comp) {
+            const bool hx = comp == 0 || comp == 4 || comp == 5;
+            const bool hy = comp == 1 || comp == 3 || comp == 5;
+            const bool hz = comp == 2 || comp == 3 || comp == 4;
+            T wx[4], wy[4], wz[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              wx[t] = hx ? wh[0][t] : w0[0][t];
+              wy[t] = hy ? wh[1][t] : w0[1][t];
+              wz[t] = hz ? wh[2][t] : w0[2][t];
+            }
+            const T v = interp3_box<BX, BXY, T>(bx_ + comp * NBOX, (hx ? sxh : sx0) + (hy ? syh : sy0) + (hz ? szh : sz0),
+                                                wx, wy, wz);
+            if (comp == 0) E[0] = v;
+            if (comp == 1) E[1] = v;
+            if (comp == 2) E[2] = v;
+            if (comp == 3) B[0] = v;
+            if (comp == 4) B[1] = v;
+            if (comp == 5) B[2] = v;
+          }
           boris<T>(u, E, B, sp.ke);
         }
         ++pushed;

@@ -3,9 +3,11 @@
 // tile.  Consecutive particles then share their cell, and any run of them
 // covers a compact 3D block of cells, which keeps the shared-memory field
 // and current box of the particle kernel small.
-//   1. histogram of the linear cell index (atomics),
+//   1. histogram of the linear cell index (atomics, one per cell present in
+//      a warp: the lanes that share a cell add their count together),
 //   2. exclusive scan of the histogram (block scans + recursive carry),
-//   3. scatter into scratch arrays (order within a cell is not kept),
+//   3. scatter into scratch arrays (the same warp-aggregated atomics hand
+//      out the places; the order within a cell is not kept across warps),
 //   4. copy back, live count := number of kept particles.
 #include "picpml_internal.cuh"
 
@@ -28,13 +30,32 @@ __device__ __forceinline__ int read_cell(const void* mom, long long p) {
   return (int)__double_as_longlong(reinterpret_cast<const dbl4*>(mom)[p].w);
 }
 
+// Warp-aggregated counting: the lanes of a warp that share a key (particles
+// of one cell, consecutive after an earlier sort) take one atomic together,
+// issued by their lowest lane; *rank is the lane's place among them.
+// key < 0: no particle.  Every lane of the warp calls it.
+__device__ __forceinline__ unsigned warp_count(unsigned* cnt, long long key, unsigned* rank) {
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned m = __match_any_sync(0xffffffffu, key);
+  const int leader = __ffs(m) - 1;
+  unsigned base = 0;
+  if (key >= 0 && lane == (unsigned)leader) base = atomicAdd(cnt + key, (unsigned)__popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  *rank = (unsigned)__popc(m & ((1u << lane) - 1u));
+  return base;
+}
+
 template <int PB>
 __global__ void k_hist(Geom g, const void* mom, const long long* n_dev, unsigned* cnt) {
   const long long n = *n_dev;
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-       p += (long long)gridDim.x * blockDim.x) {
-    int c = read_cell<PB>(mom, p);
-    if (c >= 0) atomicAdd(cnt + lin_cell(g, c), 1u);
+  // whole warps step together (blockDim is a multiple of 32)
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long pw = w0; pw < n; pw += stride) {
+    const long long p = pw + (threadIdx.x & 31);
+    const int c = p < n ? read_cell<PB>(mom, p) : -1;
+    unsigned rank;
+    warp_count(cnt, c >= 0 ? lin_cell(g, c) : -1LL, &rank);
   }
 }
 
@@ -88,11 +109,15 @@ template <int PB>
 __global__ void k_scatter(Geom g, const void* pos, const void* mom, const long long* n_dev, unsigned* cursor,
                           void* pos_out, void* mom_out) {
   const long long n = *n_dev;
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-       p += (long long)gridDim.x * blockDim.x) {
-    int c = read_cell<PB>(mom, p);
+  const long long w0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31LL;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long pw = w0; pw < n; pw += stride) {
+    const long long p = pw + (threadIdx.x & 31);
+    const int c = p < n ? read_cell<PB>(mom, p) : -1;
+    unsigned rank;
+    const unsigned d0 = warp_count(cursor, c >= 0 ? lin_cell(g, c) : -1LL, &rank);
     if (c < 0) continue;
-    unsigned d = atomicAdd(cursor + lin_cell(g, c), 1u);
+    const unsigned d = d0 + rank;
     if (PB == 16) {
       reinterpret_cast<float4*>(pos_out)[d] = reinterpret_cast<const float4*>(pos)[p];
       reinterpret_cast<float4*>(mom_out)[d] = reinterpret_cast<const float4*>(mom)[p];

@@ -235,6 +235,20 @@ int pic_set_prescribed(picpml_ctx* ctx, int flag);
 /* Live particle count of a species (synchronises the stream). */
 int pic_num_particles(picpml_ctx* ctx, int sid, long long* n);
 
+/* Appends `count` particles to species sid, between steps: pos and mom are
+ * device arrays of `count` records in the species' layout (as in
+ * pic_species, same alignment), copied after the species' live particles.
+ * This is the continuous injection of a beam through a face (Sec. III: the
+ * cavity beam is injected on one side and absorbed on the other; particles
+ * may start inside the entry face's PML).  The live count is read and
+ * advanced on the device, so the call does not synchronise; the caller keeps
+ * pos/mom valid until the stream has run the copy.  Records beyond the
+ * capacity are dropped and pic_sync then reports PIC_EOVERFLOW.  Particles
+ * outside their allowed cells are removed at the next push and reported like
+ * any other (PIC_EPARTICLE).  PIC_EINVAL for a bad species id, count < 0 or
+ * misaligned arrays. */
+int pic_inject(picpml_ctx* ctx, int sid, const void* pos, const void* mom, long long count);
+
 /* Diagnostics (synchronise the stream).  gauss: max |div E - rho/eps0| over
  * nodes at least one cell inside the physical region, in V/m^2; rho_scale:
  * max |rho/eps0| there; energy: field energy integral of

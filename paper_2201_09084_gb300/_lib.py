@@ -76,6 +76,7 @@ SIGNATURES = {
     "pic_set_old_positions": (C.c_int, [VP, C.c_int, VP]),
     "pic_get_current_fixed": (C.c_int, [VP, C.c_int, VP]),
     "pic_num_particles": (C.c_int, [VP, C.c_int, C.POINTER(C.c_longlong)]),
+    "pic_inject": (C.c_int, [VP, C.c_int, VP, VP, C.c_longlong]),
     "pic_diag": (C.c_int, [VP, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "pic_diag_static": (C.c_int, [VP, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "pic_sync": (C.c_int, [VP]),

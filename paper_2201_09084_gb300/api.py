@@ -129,6 +129,17 @@ class Sim:
         self.species.append((pos, mom))
         return sid.value
 
+    def inject(self, sid, pos, mom, count=None):
+        """Appends particles (device tensors in the species' layout) after the
+        live ones of species sid (pic_inject); keeps the tensors alive until
+        the stream has copied them."""
+        want = torch.float64 if self.prec == "fp64" else torch.float32
+        assert pos.is_cuda and mom.is_cuda and pos.dtype == want and mom.dtype == want
+        assert pos.shape == mom.shape and pos.shape[1] == 4 and pos.is_contiguous() and mom.is_contiguous()
+        n = int(pos.shape[0]) if count is None else int(count)
+        self._call(self.lib.pic_inject, int(sid), C.c_void_p(pos.data_ptr()), C.c_void_p(mom.data_ptr()), n)
+        self._inflight = (pos, mom)
+
     def num_particles(self, sid):
         n = C.c_longlong()
         self._call(self.lib.pic_num_particles, int(sid), C.byref(n))

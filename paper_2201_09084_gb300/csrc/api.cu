@@ -44,6 +44,8 @@ cudaError_t launch_push_deposit_o3(int ppt, const Geom&, const Tables&, const Fi
 long long sort_scratch_words(long long ncell);
 int sort_launches(long long ncell);
 long long sort_keys(const Geom& g);
+cudaError_t launch_inject(int pbytes, void* pos, void* mom, long long* n_dev, long long cap, const void* ipos,
+                          const void* imom, long long count, unsigned* status, cudaStream_t s);
 cudaError_t static_diag_buffers(double** rho, double** out, long long* cap);
 cudaError_t launch_sort(const Geom&, int pbytes, void* pos, void* mom, long long* n_dev, long long cap,
                         unsigned* scratch, void* tmp_pos, void* tmp_mom, cudaStream_t);
@@ -805,6 +807,21 @@ int pic_sync(picpml_ctx* ctx) {
   CK(cudaMemcpy(&st, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (st & ST_BAD_PARTICLE) return fail(ctx, PIC_EPARTICLE, "a particle was outside its allowed cells (skipped)");
   if (st & ST_FIXED_OVERFLOW) return fail(ctx, PIC_EOVERFLOW, "fixed-point current overflow");
+  if (st & ST_INJECT_OVERFLOW) return fail(ctx, PIC_EOVERFLOW, "injected particles beyond the species capacity (dropped)");
+  return PIC_OK;
+}
+
+int pic_inject(picpml_ctx* ctx, int sid, const void* pos, const void* mom, long long count) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (sid < 0 || sid >= (int)ctx->sp.size()) return fail(ctx, PIC_EINVAL, "bad species id");
+  if (count < 0 || (count > 0 && (!pos || !mom))) return fail(ctx, PIC_EINVAL, "bad particle arrays");
+  if ((reinterpret_cast<uintptr_t>(pos) | reinterpret_cast<uintptr_t>(mom)) % ctx->pbytes())
+    return fail(ctx, PIC_EINVAL, "particle arrays must be aligned to one particle record");
+  Species& s = ctx->sp[sid];
+  CK(launch_inject(ctx->pbytes(), s.desc.pos, s.desc.mom, s.n_dev, s.desc.capacity, pos, mom, count, ctx->status,
+                   ctx->stream));
+  ctx->launches += count > 0 ? 2 : 0;
   return PIC_OK;
 }
 

@@ -115,6 +115,6 @@ constexpr double kFixMaxWq = 4294967296.0;         // |w q/e| above 2^32 is refu
 constexpr double kQe = 1.602176634e-19;
 
 // Device status word bits.
-enum : unsigned { ST_BAD_PARTICLE = 1u, ST_FIXED_OVERFLOW = 2u };
+enum : unsigned { ST_BAD_PARTICLE = 1u, ST_FIXED_OVERFLOW = 2u, ST_INJECT_OVERFLOW = 4u };
 
 }  // namespace picpml

@@ -128,6 +128,35 @@ __global__ void k_scatter(Geom g, const void* pos, const void* mom, const long l
   }
 }
 
+// Appends `count` records after the n live ones (n read from the device
+// before k_inject_count advances it); records past the capacity are dropped
+// and flagged.
+template <int PB>
+__global__ void k_inject(void* pos, void* mom, const long long* n_dev, long long cap, const void* ipos,
+                         const void* imom, long long count, unsigned* status) {
+  const long long n = *n_dev;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long d = n + i;
+    if (d >= cap) {
+      atomicOr(status, ST_INJECT_OVERFLOW);
+      continue;
+    }
+    if (PB == 16) {
+      reinterpret_cast<float4*>(pos)[d] = reinterpret_cast<const float4*>(ipos)[i];
+      reinterpret_cast<float4*>(mom)[d] = reinterpret_cast<const float4*>(imom)[i];
+    } else {
+      reinterpret_cast<dbl4*>(pos)[d] = reinterpret_cast<const dbl4*>(ipos)[i];
+      reinterpret_cast<dbl4*>(mom)[d] = reinterpret_cast<const dbl4*>(imom)[i];
+    }
+  }
+}
+
+__global__ void k_inject_count(long long* n_dev, long long cap, long long count) {
+  const long long n = *n_dev + count;
+  *n_dev = n < cap ? n : cap;
+}
+
 // After the scatter every cursor holds the end offset of its cell, so the
 // last one is the number of kept particles.
 __global__ void k_set_count(const unsigned* cursor, long long ncell, long long* n_dev) {
@@ -197,6 +226,17 @@ cudaError_t launch_sort(const Geom& g, int pbytes, void* pos, void* mom, long lo
   e = cudaMemcpyAsync(pos, tmp_pos, cap * pbytes, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
   return cudaMemcpyAsync(mom, tmp_mom, cap * pbytes, cudaMemcpyDeviceToDevice, s);
+}
+
+cudaError_t launch_inject(int pbytes, void* pos, void* mom, long long* n_dev, long long cap, const void* ipos,
+                          const void* imom, long long count, unsigned* status, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  long long blocks = (count + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (pbytes == 16) k_inject<16><<<(unsigned)blocks, 256, 0, s>>>(pos, mom, n_dev, cap, ipos, imom, count, status);
+  else k_inject<32><<<(unsigned)blocks, 256, 0, s>>>(pos, mom, n_dev, cap, ipos, imom, count, status);
+  k_inject_count<<<1, 1, 0, s>>>(n_dev, cap, count);
+  return cudaGetLastError();
 }
 
 }  // namespace picpml

@@ -331,3 +331,69 @@ def test_per_face_schemes(prec, order):
     assert 0 < int(alive.sum()) < len(alive)        # some particles were removed
     Xo = np.stack([po["X"], po["Y"], po["Z"]], axis=1)
     assert np.max(np.abs(X[alive] - Xo[alive])) < (1e-5 if prec == "fp32" else 1e-10)
+
+
+@pytest.mark.parametrize("order", [1, 3])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_injection_through_entry_face(prec, order):
+    """A beam injected continuously (pic_inject, between steps) inside the
+    -z PML, which deposits undamped (per-face scheme), and crossing into the
+    box: fields and particles against the oracle, which adds the same
+    particles at the same steps."""
+    import torch
+    from paper_2201_09084_gb300.api import pack_particles
+    nphys = (14, 12, 16)
+    pml = (6, 6, 6, 6, 8, 6)
+    faces = ["damped", "damped", "damped", "damped", "one", "damped"]
+    cap = 400
+    ora, gpu = make_pair(3, nphys, pml, D3, [], order=order, prec=prec, alpha_mode="damped", face_alpha=faces)
+    # the GPU species: capacity for every injection
+    pos0, mom0 = pack_particles(np.zeros((cap, 3), np.int64), np.zeros((cap, 3), np.float32),
+                                np.zeros((cap, 3), np.float32), np.zeros(cap, np.float32), prec)
+    sid = gpu.add_species(pos0, mom0, 0, -O.Q_E, O.M_E)
+    rng = np.random.default_rng(90 + order)
+    for step in range(12):
+        if step < 9:
+            k = 20
+            X = np.stack([6 + rng.uniform(2, 12, k), 6 + rng.uniform(2, 10, k), rng.uniform(3.6, 5.6, k)], 1)
+            u = np.stack([rng.normal(0, 0.2, k), rng.normal(0, 0.2, k), rng.uniform(2.0, 4.0, k)], 1)
+            cell, off = I.split_position(X)
+            pos, mom = pack_particles(cell, off, u.astype(np.float32), np.full(k, 1.5, np.float32), prec)
+            gpu.inject(sid, pos, mom)
+            Xa = I.absolute(cell, off)
+            ua = u.astype(np.float32).astype(np.float64)
+            assert ora.add_particles(Xa[:, 0], Xa[:, 1], Xa[:, 2], ua[:, 0], ua[:, 1], ua[:, 2], np.full(k, 1.5),
+                                     -O.Q_E, O.M_E) == 0
+        ora.step(1)
+        gpu.step(1)
+    torch.cuda.synchronize()
+    gpu.sync()
+    err = max_field_err(ora, gpu)
+    assert max(err.values()) < TOL[prec], err
+    assert gpu.num_particles(sid) == 180
+    X, u, alive = gpu_positions(gpu, sid)
+    po = ora.particles()
+    assert np.array_equal(alive, po["alive"])
+    Xo = np.stack([po["X"], po["Y"], po["Z"]], axis=1)
+    assert np.max(np.abs(X[alive] - Xo[alive])) < (1e-5 if prec == "fp32" else 1e-10)
+    assert np.min(Xo[alive][:, 2]) < 8.0 < np.max(Xo[alive][:, 2])   # still entering, and inside
+
+
+def test_injection_beyond_capacity_is_reported():
+    from paper_2201_09084_gb300 import _lib as L
+    from paper_2201_09084_gb300.api import Sim, pack_particles
+    gpu = Sim(3, (8, 8, 8), D3, (4,) * 6, order=1, prec="fp32")
+    cap = 30
+    pos0, mom0 = pack_particles(np.zeros((cap, 3), np.int64), np.zeros((cap, 3), np.float32),
+                                np.zeros((cap, 3), np.float32), np.zeros(cap, np.float32), "fp32")
+    sid = gpu.add_species(pos0, mom0, 0, -O.Q_E, O.M_E)
+    cell = np.tile([[8, 8, 8]], (20, 1))
+    pos, mom = pack_particles(cell, np.full((20, 3), 0.5, np.float32), np.zeros((20, 3), np.float32),
+                              np.ones(20, np.float32), "fp32")
+    gpu.inject(sid, pos, mom)
+    gpu.sync()
+    gpu.inject(sid, pos, mom)
+    with pytest.raises(L.PicError) as e:
+        gpu.sync()
+    assert e.value.code == -5   # PIC_EOVERFLOW
+    assert gpu.num_particles(sid) == cap

@@ -59,6 +59,8 @@ def lib():
                                      C.c_double, C.c_double, C.c_double, C.c_double]
             L.ora_destroy.argtypes = [C.c_void_p]
             L.ora_set_prescribed.argtypes = [C.c_void_p, C.c_int]
+            L.ora_set_filter.argtypes = [C.c_void_p, C.c_int]
+            L.ora_filter_J.argtypes = [C.c_void_p]
             L.ora_set_face_alpha.argtypes = [C.c_void_p, ip]
             L.ora_set_face_alpha.restype = C.c_int
             L.ora_add_particles.restype = C.c_long
@@ -182,7 +184,7 @@ class OracleSim:
     """
 
     def __init__(self, dim, n, pml, d, dt, order=1, alpha_mode="damped",
-                 sig_coef=4.0, delta=6.0, sig_exp=2.0, v_assumed=C_LIGHT, face_alpha=None):
+                 sig_coef=4.0, delta=6.0, sig_exp=2.0, v_assumed=C_LIGHT, face_alpha=None, filter_passes=0):
         L = lib()
         self.dim = dim
         n3 = (C.c_int * 3)(*[int(v) for v in n])
@@ -203,6 +205,12 @@ class OracleSim:
         self.order = order
         if face_alpha is not None:
             self.set_face_alpha(face_alpha)
+        if filter_passes:
+            lib().ora_set_filter(self._h, int(filter_passes))
+
+    def filter_J(self):
+        """One binomial pass per axis on the deposited current (App. A)."""
+        lib().ora_filter_J(self._h)
 
     def set_face_alpha(self, modes):
         """Per-face scheme, faces (-x, +x, -y, +y, -z, +z): "zero", "one" or
@@ -295,7 +303,7 @@ class OracleSim:
         return self._shape3(out)
 
     def set_field(self, which, arr):
-        base = {"E": 0, "Bh": 9, "Bp": 12}[which[:-1]]
+        base = {"E": 0, "J": 6, "Bh": 9, "Bp": 12}[which[:-1]]
         c = "xyz".index(which[-1])
         a = _f64(np.asarray(arr)).reshape(-1)
         assert a.size == self.nn[0] * self.nn[1] * self.nn[2]

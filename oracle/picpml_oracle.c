@@ -64,6 +64,7 @@
 
 typedef struct ora_sim {
   int dim, order, alpha_mode, prescribed;
+  int filter_passes;                /* binomial passes on J before each E update */
   int face_mode[6];                 /* alpha mode of each face (-x,+x,-y,+y,-z,+z) */
   int n[3], plo[3], phi[3], N[3];   /* physical cells, PML cells low/high, total cells */
   long nn[3];                       /* nodes per axis in the arrays (1 for y in 2D) */
@@ -579,7 +580,36 @@ static double advance(double old, double* sp0, double* sp1, const double* R,
 }
 
 /* E^{n+1} = E^n + dt (c^2 curl B^{n+1/2} - J/eps0)  (Eqs. MaxwellE, MaxwellSum). */
+/* Binomial filter of the deposited current (App. A: "an additional binomial
+ * filter is applied to the deposited current before updating the fields";
+ * Birdsall and Langdon): one pass replaces every J value by
+ * (J[i-1] + 2 J[i] + J[i+1])/4 along x, then along y (3D), then along z,
+ * for each component at its own staggered points; values beyond the arrays
+ * count as zero. */
+void ora_filter_J(ora_sim* s) {
+  double* tmp = malloc(s->ntot * sizeof(double));
+  const long nn[3] = {s->nn[0], s->nn[1], s->nn[2]};
+  for (int c = 0; c < 3; ++c)
+    for (int a = 0; a < 3; ++a) {
+      if (nn[a] < 2) continue;   /* the absent y axis of 2D boxes */
+      for (long k = 0; k < nn[2]; ++k)
+        for (long j = 0; j < nn[1]; ++j)
+          for (long i = 0; i < nn[0]; ++i) {
+            long x[3] = {i, j, k};
+            double lo = 0.0, hi = 0.0;
+            if (x[a] > 0) { x[a] -= 1; lo = s->J[c][IX(s, x[0], x[1], x[2])]; x[a] += 1; }
+            if (x[a] < nn[a] - 1) { x[a] += 1; hi = s->J[c][IX(s, x[0], x[1], x[2])]; x[a] -= 1; }
+            tmp[IX(s, i, j, k)] = 0.25 * lo + 0.5 * s->J[c][IX(s, i, j, k)] + 0.25 * hi;
+          }
+      memcpy(s->J[c], tmp, s->ntot * sizeof(double));
+    }
+  free(tmp);
+}
+
+void ora_set_filter(ora_sim* s, int passes) { s->filter_passes = passes > 0 ? passes : 0; }
+
 void ora_field_E(ora_sim* s) {
+  for (int f = 0; f < s->filter_passes; ++f) ora_filter_J(s);
   const double c2 = ORA_C * ORA_C, dt = s->dt;
   const double dx = s->d[0], dy = s->d[1], dz = s->d[2];
   const int d3 = s->dim == 3;
@@ -702,14 +732,16 @@ int ora_get_field(const ora_sim* s, int which, double* out) {
   return 0;
 }
 
-/* Sets E^n (which 0-2), B^{n+1/2} (9-11) or B^{n-1/2} (12-14).  Splits at a
- * split location take the whole value in their first part. */
+/* Sets E^n (which 0-2), the current J (6-8), B^{n+1/2} (9-11) or B^{n-1/2}
+ * (12-14).  Splits at a split location take the whole value in their first
+ * part. */
 int ora_set_field(ora_sim* s, int which, const double* in) {
   int c = which % 3;
   double* dst;
   double** sp;
   switch (which / 3) {
     case 0: dst = s->E[c]; sp = s->Es[c]; break;
+    case 2: dst = s->J[c]; sp = NULL; break;
     case 3: dst = s->Bh[c]; sp = s->Bs[c]; break;
     case 4: dst = s->Bp[c]; sp = NULL; break;
     default: return -1;

@@ -93,6 +93,11 @@ typedef struct pic_grid_desc {
   int split_fp64;       /* PIC_FP32 only: 1 = PML split parts in IEEE FP64;
                            0 (default) = float-float pairs (hi + lo, ~48-bit
                            significand, 8 bytes) computed on the FP32 pipes */
+  int filter_passes;    /* 0 (default): none.  n = 1..8: field_step first
+                           filters the deposited current n times with the
+                           binomial (1, 2, 1)/4 stencil along each axis (App.
+                           A; values beyond the node arrays count as zero);
+                           the field then conserves the filtered charge */
 } pic_grid_desc;
 
 /* PML description: conductivity sigma(d) = coef eps0 c / Delta (d/delta)^p at

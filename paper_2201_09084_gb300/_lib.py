@@ -31,7 +31,7 @@ class PicError(RuntimeError):
 class GridDesc(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("d", C.c_double * 3), ("dt", C.c_double),
                 ("cfl", C.c_double), ("shape_order", C.c_int), ("prec", C.c_int),
-                ("sort_every", C.c_int), ("split_fp64", C.c_int)]
+                ("sort_every", C.c_int), ("split_fp64", C.c_int), ("filter_passes", C.c_int)]
 
 
 class PmlDesc(C.Structure):

@@ -19,6 +19,8 @@ cudaError_t launch_field_E(const Geom&, const Tables&, const FieldPtrs<T>&, int 
 template <typename T>
 cudaError_t launch_field_B(const Geom&, const Tables&, const FieldPtrs<T>&, int split_ff, int kz, cudaStream_t);
 template <typename T>
+cudaError_t launch_filter_J(const Geom&, const FieldPtrs<T>&, T* const O[3], cudaStream_t);
+template <typename T>
 cudaError_t launch_particles(int mode, int order, const Geom&, const Tables&, const FieldPtrs<T>&,
                              const SpeciesPtrs<T>&, int prescribed, unsigned* status, unsigned long long* pushed,
                              int nsm, cudaStream_t);
@@ -121,6 +123,7 @@ struct picpml_ctx {
   double* diag = nullptr;
   double* rho = nullptr;
   unsigned* sort_scratch = nullptr;
+  void* filter_tmp[3] = {nullptr, nullptr, nullptr};   // binomial filter scratch (x pass)
   std::vector<Species> sp;
   int prescribed = 0;
   int ppt = 0;        // particles per thread of the shared-memory chunk kernels (order 1; order 3
@@ -254,6 +257,11 @@ int run_particles(picpml_ctx* ctx, int mode) {
 template <typename T>
 int run_field(picpml_ctx* ctx) {
   FieldPtrs<T>& f = fields<T>(ctx);
+  for (int p = 0; p < ctx->gd.filter_passes; ++p) {   // App. A: the current is filtered first
+    T* const O[3] = {(T*)ctx->filter_tmp[0], (T*)ctx->filter_tmp[1], (T*)ctx->filter_tmp[2]};
+    CK(launch_filter_J<T>(ctx->g, f, O, ctx->stream));
+    ctx->launches += 2;
+  }
   CK(launch_field_E<T>(ctx->g, ctx->tb, f, ctx->split_ff(), ctx->kz, ctx->stream));
   CK(launch_field_B<T>(ctx->g, ctx->tb, f, ctx->split_ff(), ctx->kz, ctx->stream));
   ctx->launches += 2;
@@ -300,6 +308,7 @@ int pic_init(picpml_ctx** out, const pic_grid_desc* g, void* stream) {
     return fail(nullptr, PIC_EINVAL, "bad prec");
   if (g->prec == PIC_FP32_FIXED64 && g->dim != 3)
     return fail(nullptr, PIC_ENOTIMPL, "fixed-point deposition is built for 3D grids only");
+  if (g->filter_passes < 0 || g->filter_passes > 8) return fail(nullptr, PIC_EINVAL, "filter_passes must be 0..8");
   for (int a = 0; a < 3; ++a) {
     if (g->dim == 2 && a == 1) continue;
     if (g->n[a] < 1 || !(g->d[a] > 0)) return fail(nullptr, PIC_EINVAL, "cells and cell sizes must be positive");
@@ -473,6 +482,12 @@ int pml_init(picpml_ctx* ctx, const pml_desc* p) {
       ctx->ff.Es[c][h] = ctx->fd.Es[c][h] = e;
       ctx->ff.Bs[c][h] = ctx->fd.Bs[c][h] = b;
     }
+  if (gd.filter_passes > 0) {
+    char* ft = (char*)dev_alloc(ctx, (size_t)g.size * 3 * es);
+    if (!ft) return fail(ctx, PIC_ENOMEM, "filter scratch");
+    CK(cudaMemsetAsync(ft, 0, (size_t)g.size * 3 * es, ctx->stream));
+    for (int c = 0; c < 3; ++c) ctx->filter_tmp[c] = ft + (size_t)c * g.size * es;
+  }
   if (ctx->fixed()) {
     long long* jq = (long long*)dev_alloc(ctx, (size_t)g.size * 3 * sizeof(long long));
     if (!jq) return fail(ctx, PIC_ENOMEM, "fixed-point current");

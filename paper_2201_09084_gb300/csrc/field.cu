@@ -115,7 +115,75 @@ cudaError_t launch_B(const Geom& g, const Tables& tb, const FieldPtrs<T>& f, cud
   return cudaGetLastError();
 }
 
+// Binomial filter of the deposited current (App. A: applied before the field
+// update; Birdsall and Langdon's (1, 2, 1)/4 stencil along each axis, values
+// beyond the node arrays counting as zero).  One thread per node and
+// component set, x fastest (coalesced).  k_filter_x does the x pass from J
+// into the scratch arrays O; k_filter_yz does the y and z passes together
+// (the outer product of the two stencils) from O back into J.
+template <typename T>
+__global__ void __launch_bounds__(256) k_filter_x(Geom g, FieldPtrs<T> f, T* O0, T* O1, T* O2) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long plane = (long long)g.nn[0] * g.nn[1];
+  if (t >= plane * g.nn[2]) return;
+  const int i = (int)(t % g.nn[0]);
+  const long long r = t / g.nn[0];
+  const int j = (int)(r % g.nn[1]), k = (int)(r / g.nn[1]);
+  const long long id = g.idx(i, j, k);
+  T* const out[3] = {O0, O1, O2};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T* J = f.J[c];
+    const T lo = i > 0 ? J[id - 1] : T(0), hi = i + 1 < g.nn[0] ? J[id + 1] : T(0);
+    out[c][id] = T(0.25) * lo + T(0.5) * J[id] + T(0.25) * hi;
+  }
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_filter_yz(Geom g, FieldPtrs<T> f, const T* I0, const T* I1, const T* I2) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long plane = (long long)g.nn[0] * g.nn[1];
+  if (t >= plane * g.nn[2]) return;
+  const int i = (int)(t % g.nn[0]);
+  const long long r = t / g.nn[0];
+  const int j = (int)(r % g.nn[1]), k = (int)(r / g.nn[1]);
+  const T w[3] = {T(0.25), T(0.5), T(0.25)};
+  const T* const in[3] = {I0, I1, I2};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    T acc = T(0);
+#pragma unroll
+    for (int dk = -1; dk <= 1; ++dk) {
+      if (k + dk < 0 || k + dk >= g.nn[2]) continue;
+      T row = T(0);
+#pragma unroll
+      for (int dj = (DIM == 3 ? -1 : 0); dj <= (DIM == 3 ? 1 : 0); ++dj) {
+        if (j + dj < 0 || j + dj >= g.nn[1]) continue;
+        row += (DIM == 3 ? w[dj + 1] : T(1)) * in[c][g.idx(i, j + dj, k + dk)];
+      }
+      acc += w[dk + 1] * row;
+    }
+    f.J[c][g.idx(i, j, k)] = acc;
+  }
+}
+
 }  // namespace
+
+// One pass of the binomial current filter: J -> O (x), O -> J (y, z).
+template <typename T>
+cudaError_t launch_filter_J(const Geom& g, const FieldPtrs<T>& f, T* const O[3], cudaStream_t s) {
+  const long long n = (long long)g.nn[0] * g.nn[1] * g.nn[2];
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  k_filter_x<T><<<blocks, 256, 0, s>>>(g, f, O[0], O[1], O[2]);
+  if (g.dim == 3)
+    k_filter_yz<T, 3><<<blocks, 256, 0, s>>>(g, f, O[0], O[1], O[2]);
+  else
+    k_filter_yz<T, 2><<<blocks, 256, 0, s>>>(g, f, O[0], O[1], O[2]);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_filter_J<float>(const Geom&, const FieldPtrs<float>&, float* const[3], cudaStream_t);
+template cudaError_t launch_filter_J<double>(const Geom&, const FieldPtrs<double>&, double* const[3], cudaStream_t);
 
 // split_ff: 1 = float-float split parts (FP32 fields only), 0 = FP64 parts;
 // kz: nodes per thread along z (1, 2 or 4).

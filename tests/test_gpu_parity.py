@@ -397,3 +397,24 @@ def test_injection_beyond_capacity_is_reported():
         gpu.sync()
     assert e.value.code == -5   # PIC_EOVERFLOW
     assert gpu.num_particles(sid) == cap
+
+
+@pytest.mark.parametrize("passes", [1, 2])
+@pytest.mark.parametrize("dim,order", [(3, 1), (3, 3), (2, 3)])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_binomial_filter(prec, dim, order, passes):
+    """field_step filters the deposited current (App. A) before the E update:
+    fields against the oracle with the same filter, particles crossing the
+    PML with the damped current."""
+    nphys = (16, 12, 18)
+    pml = (6,) * 6
+    lo = [7.0, 7.0 if dim == 3 else 0.0, 7.0]
+    hi = [21.0, 17.0 if dim == 3 else 1.0, 23.0]
+    parts = I.random_particles(dim, 500, lo, hi, u_rms=1.5, seed=41 + order + 3 * passes)
+    ora, gpu = make_pair(dim, nphys, pml, D3, parts, order=order, prec=prec, alpha_mode="damped",
+                         filter_passes=passes)
+    for _ in range(2):
+        ora.step(6)
+        gpu.step(6)
+        err = max_field_err(ora, gpu)
+        assert max(err.values()) < TOL[prec], err

@@ -249,12 +249,13 @@ __device__ __forceinline__ void sort_runs(const int (&keys)[P], int nk, int* cnt
 
 // Adds the lanes' run accumulators of one warp to the shared current box J:
 // lanes that share an anchor (key >= 0) hold consecutive runs; a group of at
-// least min_lanes lanes sums its accumulators with one reduce-scatter
+// least MIN_LANES lanes sums its accumulators with one reduce-scatter
 // (acc.group_flush), the lanes of smaller groups add their own (acc.flush_box)
-// where few lanes meet on an address.  A warp holding one anchor in every
+// where few lanes meet on an address.  MIN_LANES = 1: every group takes the
+// reduce-scatter (no flush_box needed).  A warp holding one anchor in every
 // lane takes the reduce-scatter without membership masks.
-template <class ACC, typename T>
-__device__ __forceinline__ void flush_warp_runs(const ACC& acc, int key, int lane, T* J, int min_lanes) {
+template <int MIN_LANES, class ACC, typename T>
+__device__ __forceinline__ void flush_warp_runs(const ACC& acc, int key, int lane, T* J) {
   const int up = __shfl_up_sync(0xffffffffu, key, 1);
   const bool head = key >= 0 && (lane == 0 || up != key);
   const unsigned heads = __ballot_sync(0xffffffffu, head);
@@ -267,7 +268,7 @@ __device__ __forceinline__ void flush_warp_runs(const ACC& acc, int key, int lan
   const unsigned above = (heads | ~live) & ~((2u << lane) - 1u);
   const int first = below ? 31 - __clz(below) : 0;
   const int next = above ? __ffs(above) - 1 : 32;
-  const bool big = key >= 0 && next - first >= min_lanes;
+  const bool big = key >= 0 && next - first >= MIN_LANES;
   unsigned pend = __ballot_sync(0xffffffffu, head && big);
   while (pend) {
     const int leader = __ffs(pend) - 1;
@@ -275,7 +276,9 @@ __device__ __forceinline__ void flush_warp_runs(const ACC& acc, int key, int lan
     const int gk = __shfl_sync(0xffffffffu, key, leader);
     acc.template group_flush<false>(key == gk, lane, J, gk);
   }
-  if (key >= 0 && !big) acc.flush_box(J, key);
+  if constexpr (MIN_LANES > 1) {
+    if (key >= 0 && !big) acc.flush_box(J, key);
+  }
 }
 
 }  // namespace chunk

@@ -16,8 +16,9 @@
 //      values of its run's moves in registers (the transverse factor as
 //      M M' + Q DS' with M = S0 + DS/2, Q = DS/12, times the prefix sums of
 //      DS along the component); a warp's lanes that share an anchor then sum
-//      their values by reduce-scatters of shuffles and add them to the box,
-//      lanes of smaller groups add their own;
+//      their values by reduce-scatters of shuffles and add them to the box
+//      (every group, however small: a per-lane flush of 100 atomics made the
+//      kernel's code large enough to stall on instruction fetch);
 //   D. add the box to the grid with the charge factor and alpha at each
 //      component's staggered location (Eq. alpha, Sec. II.B), once per node:
 //      the damping of Eq. MaxwellE's source in the flush.
@@ -33,8 +34,6 @@ using namespace pc;
 using namespace chunk;
 
 constexpr int kNT3 = 128;
-// Fewest lanes of one anchor that a warp sums by reduce-scatters.
-constexpr int kMinGroupLanes3 = 3;
 
 template <typename T, int P>
 struct Plan3 {
@@ -116,12 +115,6 @@ struct Acc3 {
   __device__ __forceinline__ int box_offset(int q) const {
     const int ta = q & 3, tb = (q >> 2) % 5, td = q / 20;
     return oc + ta * sc + tb * sb + td * sd;
-  }
-
-  __device__ __forceinline__ void flush_box(T* J, int a) const {
-#pragma unroll
-    for (int q = 0; q < NV; ++q)
-      if (v[q] != T(0)) atomicAdd(J + a + box_offset(q), v[q]);
   }
 
   // Sums the values of the lanes with member == true (one anchor) by four
@@ -384,7 +377,7 @@ __global__ void __launch_bounds__(kNT3, sizeof(T) == 4 ? 3 : 2)
               acc.add(DSc, Sb, DSb, Sd, DSd, stg[3 * ROW + slot]);
             }
           }
-          flush_warp_runs(acc, key, lane, BJ, kMinGroupLanes3);
+          flush_warp_runs<1>(acc, key, lane, BJ);
         }
       }
       __syncthreads();

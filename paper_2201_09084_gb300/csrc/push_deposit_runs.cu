@@ -18,11 +18,10 @@
 //      current box;
 //   C. deposit: each thread takes a run, which shares one anchor, and
 //      accumulates the 2x3x3 prefix values of each component (54 in 3D) in
-//      registers; then, for each anchor held by at least three lanes of a
-//      warp, the warp sums those lanes' values with a reduce-scatter of
-//      shuffles (each lane ends with two sums) and adds them to the box with
-//      two shared-memory atomics per lane; lanes of smaller groups (sparse
-//      particles) add their runs directly;
+//      registers; then, for each anchor held by lanes of a warp (every
+//      group, however small), the warp sums those lanes' values with a
+//      reduce-scatter of shuffles (each lane ends with two sums) and adds
+//      them to the box with two shared-memory atomics per lane;
 //   D. add the box to the grid with the charge factor and alpha (Eq. alpha,
 //      at each component's staggered location): the damping of Eq. MaxwellE's
 //      source term applied once per node in the flush.
@@ -162,15 +161,6 @@ struct Acc1 {
     return comp * NBOX + ix + BX * jy + BXY * kz;
   }
 
-  // Adds this thread's sums into the shared-memory current box at the local
-  // anchor node a (linear box index).
-  __device__ __forceinline__ void flush_box(T* J, int a) const {
-#pragma unroll
-    for (int t = 0; t < NV; ++t) {
-      const T val = v[t];
-      if (val != T(0)) atomicAdd(J + a + box_offset(t), val);
-    }
-  }
 
   // Sums the accumulators of the lanes with member == true (one anchor) by a
   // reduce-scatter of shuffles into a scratch array: after five halving steps
@@ -220,14 +210,15 @@ struct WithOffsets {
   __device__ __forceinline__ void group_flush(bool member, int lane, T* J, int a) const {
     acc.template group_flush<ALL>(member, lane, J, a, goff);
   }
-  template <typename T>
-  __device__ __forceinline__ void flush_box(T* J, int a) const { acc.flush_box(J, a); }
 };
 
 constexpr int kNT = 128;
 // Fewest lanes of one anchor that a warp sums by reduce-scatter (about 330
-// instructions per anchor); smaller groups add their runs lane by lane.
-constexpr int kMinGroupLanes = 3;
+// instructions per anchor).  With runs cut at anchor boundaries every group,
+// even a single lane, takes the reduce-scatter: the per-lane flush (54
+// shared atomics) was slower on the 4M beam (0.322 vs 0.300 ms per step) and
+// its code is not needed.
+constexpr int kMinGroupLanes = 1;
 
 // Shared memory of one block: the staged chunk (NW words per particle, rows
 // padded to P+1), the field box (E and time-averaged B, 6 arrays of NBOX
@@ -521,7 +512,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? (P >= 8 ? 3 : 4) : 2)
             acc.add(S0, DS, stg[3 * ROW + slot], wvy_of(slot));
           }
         }
-        flush_warp_runs(WithOffsets<AC>{acc, goff}, key, lane, BJ, kMinGroupLanes);
+        flush_warp_runs<kMinGroupLanes>(WithOffsets<AC>{acc, goff}, key, lane, BJ);
       }
       __syncthreads();
       // ---- D. add the current box to the grid with the charge factor and alpha ----

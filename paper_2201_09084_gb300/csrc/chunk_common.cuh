@@ -253,17 +253,15 @@ __device__ __forceinline__ void sort_runs(const int (&keys)[P], int nk, int* cnt
 // (acc.group_flush), the lanes of smaller groups add their own (acc.flush_box)
 // where few lanes meet on an address.  MIN_LANES = 1: every group takes the
 // reduce-scatter (no flush_box needed).  A warp holding one anchor in every
-// lane takes the reduce-scatter without membership masks.
+// lane takes the same masked reduce-scatter: a mask-free copy of it made the
+// code larger and the kernels slower.
 template <int MIN_LANES, class ACC, typename T>
 __device__ __forceinline__ void flush_warp_runs(const ACC& acc, int key, int lane, T* J) {
   const int up = __shfl_up_sync(0xffffffffu, key, 1);
   const bool head = key >= 0 && (lane == 0 || up != key);
   const unsigned heads = __ballot_sync(0xffffffffu, head);
   const unsigned live = __ballot_sync(0xffffffffu, key >= 0);
-  if (heads == 1u && live == 0xffffffffu) {
-    acc.template group_flush<true>(true, lane, J, key);
-    return;
-  }
+
   const unsigned below = heads & ((2u << lane) - 1u);     // heads at or before this lane
   const unsigned above = (heads | ~live) & ~((2u << lane) - 1u);
   const int first = below ? 31 - __clz(below) : 0;

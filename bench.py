@@ -16,8 +16,11 @@ device); cell-updates/s of the Yee/PML update is reported beside it.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
-Prints one JSON line.  --impl reference times the FP64 CPU oracle on a
-bounded sample of the same workload (see cpu_sample()).
+Prints one JSON line.  Beside the FP32 result it carries "fp64": the same
+workload in the plain FP64 form (fields, particles and PML parts in FP64),
+and "batch2d": the batched 2D runs in FP32 and FP64.  --impl reference times
+the FP64 CPU oracle on a bounded sample of the same workload (see
+cpu_sample()).
 """
 from __future__ import annotations
 
@@ -495,6 +498,7 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 2D runs measurement")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 run of the main workload")
     ap.add_argument("--batch-runs", type=int, default=4096, help="number of batched 2D runs")
     ap.add_argument("--particles", type=int, default=NPART,
                     help="beam macroparticles (default 4194304; smaller only for profiling captures)")
@@ -517,6 +521,16 @@ def main():
         out = run_reference(args, rank, world)
     else:
         out = run_gpu(args, rank, world)
+        if args.prec == "fp32" and not args.no_fp64:
+            # the same workload, steps and timing with FP64 fields, particles and
+            # parts (the plain FP64 form), for the FP32-vs-FP64 comparison
+            a64 = argparse.Namespace(**vars(args))
+            a64.prec, a64.tuning = "fp64", None
+            o64 = run_gpu(a64, rank, world)
+            out["fp64"] = {"value": o64["value"], "unit": o64["unit"], "ms_per_step": o64["ms_per_step"],
+                           "kernel_ms": o64["kernel_ms"], "autotune": o64["autotune"],
+                           "roofline_frac": o64["roofline"]["frac"], "e2e": o64["e2e"]["value"]}
+            out["fp32_over_fp64"] = out["value"] / o64["value"]
         if not args.no_batch:
             nb = min(args.steps, 200)
             out["batch2d"] = {"fp32": run_batch(nb, 3, "fp32", nruns=args.batch_runs),

@@ -51,7 +51,10 @@ typedef enum {
   PIC_ETIMEOUT = -6,    /* a bounded device wait gave up */
   PIC_ENOTIMPL = -7,    /* combination not built */
   PIC_ESTATE = -8,      /* call out of order (e.g. push before pml_init) */
-  PIC_EPARTICLE = -9    /* a particle was found outside its allowed cells */
+  PIC_EPARTICLE = -9    /* a particle record was invalid (outside its allowed
+                           cells, an offset outside [0,1), or a momentum or
+                           weight that is not finite); it was removed before
+                           it touched the fields */
 } pic_status;
 
 typedef enum {

@@ -820,7 +820,8 @@ int pic_sync(picpml_ctx* ctx) {
   CK(cudaStreamSynchronize(ctx->stream));
   unsigned st = 0;
   CK(cudaMemcpy(&st, ctx->status, sizeof(unsigned), cudaMemcpyDeviceToHost));
-  if (st & ST_BAD_PARTICLE) return fail(ctx, PIC_EPARTICLE, "a particle was outside its allowed cells (skipped)");
+  if (st & ST_BAD_PARTICLE)
+    return fail(ctx, PIC_EPARTICLE, "a particle was outside its allowed cells or not finite (removed)");
   if (st & ST_FIXED_OVERFLOW) return fail(ctx, PIC_EOVERFLOW, "fixed-point current overflow");
   if (st & ST_INJECT_OVERFLOW) return fail(ctx, PIC_EOVERFLOW, "injected particles beyond the species capacity (dropped)");
   return PIC_OK;

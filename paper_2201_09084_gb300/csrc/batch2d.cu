@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(NT, MINB) k_batch_step(BatchArgs<T> a, int par
       PIO<T>::load(a.pos, a.mom, run, o, w, u, cell);
       if (cell >= 0) {
         int c[3] = {cell_i(cell), 0, cell_k(cell)};
-        bool bad = false;
+        bool bad = !finite_value(w) || !finite_value(u[0]) || !finite_value(u[1]) || !finite_value(u[2]);
         for (int ax = 0; ax < 3; ax += 2)
           if (c[ax] < g.rmin[ax] || c[ax] > g.rmax[ax] || !(o[ax] >= T(0) && o[ax] < T(1))) bad = true;
         if (bad) {

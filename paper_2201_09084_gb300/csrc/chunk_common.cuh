@@ -83,7 +83,7 @@ __device__ __forceinline__ void prefetch_records(const SpeciesPtrs<T>& sp, long 
 // Stages particles [base, base + NT*P) with coalesced loads into the stage
 // (words 0-2 offsets, 3 weight, 4-6 u, 7 cell; row length ROW, particle q at
 // slot (q / P) * (P + 1) + q % P), removes and reports particles outside
-// their allowed cells, and leaves the bounding box of the live particles'
+// their allowed cells or with a non-finite momentum or weight, and leaves the bounding box of the live particles'
 // cells in s_lo / s_hi (s_hi[0] < 0: no live particle).  The records of the
 // block's next chunk (from next_base) are prefetched into L2.  The caller
 // must not read s_lo / s_hi of the previous chunk after its last barrier
@@ -129,9 +129,11 @@ __device__ __forceinline__ void stage_chunk(const Geom& g, const SpeciesPtrs<T>&
     const int cell = bits_to_cell<T>(stg[7 * ROW + slot]);
     if (cell < 0) continue;
     const int c[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
-    bool bad = false;
+    // (a non-finite momentum or weight would poison the current: refused too)
+    bool bad = !finite_value(stg[3 * ROW + slot]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
+      if (!finite_value(stg[(4 + a) * ROW + slot])) bad = true;
       if (DIM == 2 && a == 1) continue;
       const T o = stg[a * ROW + slot];
       if (c[a] < g.rmin[a] || c[a] > g.rmax[a] || !(o >= T(0) && o < T(1))) bad = true;

@@ -60,6 +60,11 @@ struct PIO<double> {
   }
 };
 
+// False for NaN and infinities (and values beyond 1e30, which no momentum or
+// weight of a run reaches).
+template <typename T>
+__device__ __forceinline__ bool finite_value(T v) { return fabs(v) < T(1e30); }
+
 // B-spline weights of the ORDER+1 nodes around a point at offset f in [0,1)
 // from node `base` (nodes base - (ORDER==3) ... base - (ORDER==3) + ORDER).
 template <int ORDER, typename T>

@@ -56,15 +56,17 @@ __global__ void __launch_bounds__(256) k_particles(Geom g, Tables tb, FieldPtrs<
       continue;
     }
     int c[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
-    bool bad = false;
+    bool bad = !finite_value(w);   // (a non-finite momentum or weight is refused too)
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
+      if (!finite_value(u[a])) bad = true;
       if (DIM == 2 && a == 1) continue;
       if (c[a] < g.rmin[a] || c[a] > g.rmax[a] || !(o[a] >= T(0) && o[a] < T(1))) bad = true;
     }
-    if (bad) {
+    if (bad) {  // removed, as the chunk kernels do: cell -1 in the record
       atomicOr(status, ST_BAD_PARTICLE);
       if (MODE == 0) PIO<T>::save(sp.save_pos, p, o, -1);
+      PIO<T>::store(sp.pos, sp.mom, p, o, w, u, -1);
       continue;
     }
     if (sp.immobile) {

@@ -146,8 +146,7 @@ def count_cells():
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
 #       --clock-control none -k regex:k_pd1 -s 3 -c 1
 #       python bench.py --tuning 4,1 --steps 3 --warmup 3 --no-cpu-baseline --no-batch
-# (the first timed step: 138.8 MB read + 79.1 MB written).
-NCU_TRAFFIC = {(1, 4, "fp32", 0.0, 4194304): 217.90e6}
+NCU_TRAFFIC = {}
 
 
 def combine_ranks(ms, psteps, ms_e2e, ps_e2e, world, device):

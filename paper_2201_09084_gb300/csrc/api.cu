@@ -12,6 +12,7 @@
 
 #include "../../include/picpml.h"
 #include "picpml_internal.cuh"
+#include <nvtx3/nvToolsExt.h>
 
 namespace picpml {
 template <typename T>
@@ -104,6 +105,15 @@ struct Species {
 
 thread_local std::string g_init_error;
 
+}  // namespace
+
+namespace {
+// A named NVTX range around a host entry point (shown by a timeline profiler;
+// a no-op when no tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 }  // namespace
 
 struct picpml_ctx {
@@ -540,30 +550,35 @@ int pic_add_species(picpml_ctx* ctx, const pic_species* s, int* sid) {
 }
 
 int push(picpml_ctx* ctx) {
+  NvtxRange nvtx_("picpml push");
   int r = check_ready(ctx);
   if (r) return r;
   return ctx->gd.prec == PIC_FP64 ? run_particles<double>(ctx, 0) : run_particles<float>(ctx, 0);
 }
 
 int deposit(picpml_ctx* ctx) {
+  NvtxRange nvtx_("picpml deposit");
   int r = check_ready(ctx);
   if (r) return r;
   return ctx->gd.prec == PIC_FP64 ? run_particles<double>(ctx, 1) : run_particles<float>(ctx, 1);
 }
 
 int field_step(picpml_ctx* ctx) {
+  NvtxRange nvtx_("picpml field_step");
   int r = check_ready(ctx);
   if (r) return r;
   return ctx->gd.prec == PIC_FP64 ? run_field<double>(ctx) : run_field<float>(ctx);
 }
 
 int pic_sort(picpml_ctx* ctx) {
+  NvtxRange nvtx_("picpml pic_sort");
   int r = check_ready(ctx);
   if (r) return r;
   return ctx->gd.prec == PIC_FP64 ? do_sort<double>(ctx) : do_sort<float>(ctx);
 }
 
 int push_deposit(picpml_ctx* ctx) {
+  NvtxRange nvtx_("picpml push_deposit");
   int r = check_ready(ctx);
   if (r) return r;
   return ctx->gd.prec == PIC_FP64 ? run_particles<double>(ctx, 2) : run_particles<float>(ctx, 2);
@@ -593,6 +608,7 @@ struct Snapshot {
 // the particle records and the counters, restored afterwards), and keeps the
 // fastest.  The result does not depend on the choice beyond round-off order.
 int pic_autotune(picpml_ctx* ctx, int steps, int* ppt, int* kz) {
+  NvtxRange nvtx_("picpml pic_autotune");
   int r = check_ready(ctx);
   if (r) return r;
   if (steps < 1) steps = 3;
@@ -712,6 +728,7 @@ int pic_launch_count(picpml_ctx* ctx, long long* n) {
 }
 
 int step_n(picpml_ctx* ctx, int n) {
+  NvtxRange nvtx_("picpml step_n");
   int r = check_ready(ctx);
   if (r) return r;
   if (n < 0) return fail(ctx, PIC_EINVAL, "negative step count");
@@ -828,6 +845,7 @@ int pic_sync(picpml_ctx* ctx) {
 }
 
 int pic_inject(picpml_ctx* ctx, int sid, const void* pos, const void* mom, long long count) {
+  NvtxRange nvtx_("picpml pic_inject");
   int r = check_ready(ctx);
   if (r) return r;
   if (sid < 0 || sid >= (int)ctx->sp.size()) return fail(ctx, PIC_EINVAL, "bad species id");
@@ -842,6 +860,7 @@ int pic_inject(picpml_ctx* ctx, int sid, const void* pos, const void* mom, long 
 }
 
 int pic_diag(picpml_ctx* ctx, double* gauss, double* rho_scale, double* energy) {
+  NvtxRange nvtx_("picpml pic_diag");
   int r = check_ready(ctx);
   if (r) return r;
   if (!ctx->rho) {

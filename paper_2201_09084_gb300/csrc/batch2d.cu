@@ -19,6 +19,7 @@
 #include "../../include/picpml.h"
 #include "field_node.cuh"
 #include "particle_common.cuh"
+#include <nvtx3/nvToolsExt.h>
 
 namespace picpml {
 
@@ -601,7 +602,16 @@ int pic_batch_init(pic_batch** out, const pic_batch_desc* d, void* stream) {
   return PIC_OK;
 }
 
+static int batch_step_impl(pic_batch* b, int n);
+
 int pic_batch_step(pic_batch* b, int n) {
+  nvtxRangePushA("picpml pic_batch_step");
+  const int r_ = batch_step_impl(b, n);
+  nvtxRangePop();
+  return r_;
+}
+
+static int batch_step_impl(pic_batch* b, int n) {
   if (!b || !b->pair) return bfail(b, PIC_ESTATE, "batch not initialised");
   if (n < 0) return bfail(b, PIC_EINVAL, "negative step count");
   while (n > 0) {

@@ -312,9 +312,12 @@ __global__ void __launch_bounds__(kNT3, sizeof(T) == 4 ? 3 : 2)
       // dead: its first three arrays become the current box)
       T* const BJ = bx_;
       {
+        // 16-byte stores, then the values of a last partial group
         float4* z = reinterpret_cast<float4*>(BJ);
-        constexpr int NZ = (int)(3 * NBOX * sizeof(T) / sizeof(float4));
+        constexpr int PER = (int)(sizeof(float4) / sizeof(T));
+        constexpr int NZ = 3 * NBOX / PER;
         for (int t = tid; t < NZ; t += kNT3) z[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int t = NZ * PER + tid; t < 3 * NBOX; t += kNT3) BJ[t] = T(0);
       }
       const int kdx = bdx - 4, kdy = bdy - 4, nk = kdx * kdy * (bdz - 4);
       for (int t = tid; t <= nk; t += kNT3) cnt[t] = 0;

@@ -418,3 +418,26 @@ def test_binomial_filter(prec, dim, order, passes):
         gpu.step(6)
         err = max_field_err(ora, gpu)
         assert max(err.values()) < TOL[prec], err
+
+
+@pytest.mark.parametrize("ppt", [1, 4])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_thermal_plasma_chunks(prec, ppt):
+    """A thermal plasma filling the box, 8 particles per cell, tile-sorted once
+    and then left unsorted while particles leave their tiles (most chunks then
+    take the chunk kernel's per-particle global path): one thread per particle
+    and the chunk kernel against the oracle."""
+    nphys = (16, 16, 20)
+    pml = (6,) * 6
+    n = 8 * 16 * 16 * 20
+    parts = I.random_particles(3, n, [6, 6, 6], [22, 22, 26], u_rms=0.3, seed=77)
+    ora, gpu = make_pair(3, nphys, pml, D3, parts, order=1, prec=prec, alpha_mode="damped")
+    gpu.sort()
+    gpu.set_tuning(ppt, 1)
+    # the oracle has no particle order; the GPU's is compared as a set below
+    for _ in range(2):
+        ora.step(6)
+        gpu.step(6)
+        err = max_field_err(ora, gpu)
+        assert max(err.values()) < TOL[prec], err
+    assert int(gpu.particles(0)["alive"].sum()) == int(ora.particles()["alive"].sum())

@@ -99,6 +99,9 @@ def lib():
                                               C.c_int, C.c_longlong, C.c_longlong, C.c_longlong, lp_, lp_, lp_]
             L.ora_fixed_rho3d.argtypes = [C.c_int, C.c_longlong, ip_, fp_,
                                           C.c_longlong, C.c_longlong, C.c_longlong, lp_]
+            L.ora_fixed_deposit2d.argtypes = [C.c_int, C.c_longlong, ip_, fp_, ip_, fp_, fp_, fp_, C.c_double,
+                                              C.c_int, C.c_longlong, C.c_longlong, lp_, lp_, lp_]
+            L.ora_fixed_rho2d.argtypes = [C.c_int, C.c_longlong, ip_, fp_, C.c_longlong, C.c_longlong, lp_]
             _lib = L
     return _lib
 
@@ -168,6 +171,37 @@ def fixed_rho3d(order, cell, off, nn):
     lib().ora_fixed_rho3d(int(order), len(c) // 3, c.ctypes.data_as(ip), f.ctypes.data_as(fp),
                           nn[0], nn[1], nn[2], out.ctypes.data_as(lp))
     return out.reshape(nn[2], nn[1], nn[0])
+
+
+def fixed_deposit2d(order, cell0, off0, cell1, off1, w, u, qn, nn, raw=False):
+    """Integer currents of the deterministic deposition mode for 2D (x, z)
+    boxes: returns (Jx, Jy, Jz) int64 arrays indexed [k, i] (nn = (nx, nz)
+    nodes); see ``ora_fixed_deposit2d``.  u: (n, 3) float32 momenta (J_y
+    carries v_y/c)."""
+    c0 = np.ascontiguousarray(cell0, dtype=np.int32).reshape(-1)
+    c1 = np.ascontiguousarray(cell1, dtype=np.int32).reshape(-1)
+    f0 = np.ascontiguousarray(off0, dtype=np.float32).reshape(-1)
+    f1 = np.ascontiguousarray(off1, dtype=np.float32).reshape(-1)
+    wf = np.ascontiguousarray(w, dtype=np.float32).reshape(-1)
+    uf = np.ascontiguousarray(u, dtype=np.float32).reshape(-1)
+    out = [np.zeros(nn[0] * nn[1], dtype=np.int64) for _ in range(3)]
+    ip, fp, lp = C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_longlong)
+    lib().ora_fixed_deposit2d(int(order), len(wf), c0.ctypes.data_as(ip), f0.ctypes.data_as(fp),
+                              c1.ctypes.data_as(ip), f1.ctypes.data_as(fp), wf.ctypes.data_as(fp),
+                              uf.ctypes.data_as(fp), float(qn), int(bool(raw)), nn[0], nn[1],
+                              *[o.ctypes.data_as(lp) for o in out])
+    return [o.reshape(nn[1], nn[0]) for o in out]
+
+
+def fixed_rho2d(order, cell, off, nn):
+    """Integer node charge 6 S S of a 2D box (units 2^-40), indexed [k, i]."""
+    c = np.ascontiguousarray(cell, dtype=np.int32).reshape(-1)
+    f = np.ascontiguousarray(off, dtype=np.float32).reshape(-1)
+    out = np.zeros(nn[0] * nn[1], dtype=np.int64)
+    ip, fp, lp = C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_longlong)
+    lib().ora_fixed_rho2d(int(order), len(c) // 3, c.ctypes.data_as(ip), f.ctypes.data_as(fp), nn[0], nn[1],
+                          out.ctypes.data_as(lp))
+    return out.reshape(nn[1], nn[0])
 
 
 def yee_dt(d, cfl, dim):

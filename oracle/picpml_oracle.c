@@ -904,6 +904,78 @@ void ora_fixed_deposit3d(int order, long long n, const int* cell0, const float* 
   }
 }
 
+/* The replay for 2D (x, z) boxes (d/dy = 0).  J_x and J_z come from the
+ * integer Esirkepov sums of the two in-plane axes, 6 W_x = DS_x (6 S0_z +
+ * 3 DS_z) (prefix sums along x; likewise z), in units 2^-40, so one rounding
+ * val = rint((acc w q/e) 2^-16) gives the unit of the 3D replay, e/(6 2^24).
+ * J_y (out of the plane) is the mid-move shape product 6 S0_x S0_z +
+ * 3 DS_x S0_z + 3 S0_x DS_z + 2 DS_x DS_z times v_y/c, which is formed in
+ * FP64 from the FP32 momentum with correctly rounded operations in a fixed
+ * order, v_y/c = u_y / sqrt(((1 + u_x^2) + u_y^2) + u_z^2), and rounded once:
+ * val = rint(((T w q/e) v_y/c) 2^-16).  u: 3 floats per particle.  Arrays
+ * are laid out i + nx k.  raw = 1 stores the unrounded integers (J_y without
+ * the weight and velocity). */
+void ora_fixed_deposit2d(int order, long long n, const int* cell0, const float* off0, const int* cell1,
+                         const float* off1, const float* w, const float* u, double qn, int raw, long long nx,
+                         long long nz, long long* Jx, long long* Jy, long long* Jz) {
+  const int W = order + 2;
+  const double down = ldexp(1.0, -16);
+  for (long long p = 0; p < n; ++p) {
+    long long S0[3][5], DS[3][5];
+    int lo[3] = {0, 0, 0};
+    for (int a = 0; a < 3; a += 2)
+      lo[a] = fixed_axis(order, cell0[3 * p + a], off0[3 * p + a], cell1[3 * p + a], off1[3 * p + a], S0[a], DS[a]);
+    const double wq = (double)w[p] * qn;
+    const double ux = u[3 * p], uy = u[3 * p + 1], uz = u[3 * p + 2];
+    const double vyc = uy / sqrt(((1.0 + ux * ux) + uy * uy) + uz * uz);
+    for (int tk = 0; tk < W; ++tk) {        /* J_x: prefix sums along x */
+      const long long T = 6 * S0[2][tk] + 3 * DS[2][tk];
+      long long acc = 0;
+      for (int ti = 0; ti < W - 1; ++ti) {
+        acc += DS[0][ti] * T;
+        const long long i = lo[0] + ti, k = lo[2] + tk;
+        if (acc == 0 || i < 0 || i >= nx || k < 0 || k >= nz) continue;
+        Jx[i + nx * k] += raw ? acc : llrint(((double)acc * wq) * down);
+      }
+    }
+    for (int ti = 0; ti < W; ++ti) {        /* J_z: prefix sums along z */
+      const long long T = 6 * S0[0][ti] + 3 * DS[0][ti];
+      long long acc = 0;
+      for (int tk = 0; tk < W - 1; ++tk) {
+        acc += DS[2][tk] * T;
+        const long long i = lo[0] + ti, k = lo[2] + tk;
+        if (acc == 0 || i < 0 || i >= nx || k < 0 || k >= nz) continue;
+        Jz[i + nx * k] += raw ? acc : llrint(((double)acc * wq) * down);
+      }
+    }
+    for (int tk = 0; tk < W; ++tk)          /* J_y: mid-move shape product */
+      for (int ti = 0; ti < W; ++ti) {
+        const long long T = 6 * S0[0][ti] * S0[2][tk] + 3 * DS[0][ti] * S0[2][tk] + 3 * S0[0][ti] * DS[2][tk] +
+                            2 * DS[0][ti] * DS[2][tk];
+        const long long i = lo[0] + ti, k = lo[2] + tk;
+        if (T == 0 || i < 0 || i >= nx || k < 0 || k >= nz) continue;
+        Jy[i + nx * k] += raw ? T : llrint((((double)T * wq) * vyc) * down);
+      }
+  }
+}
+
+/* Integer node charge of 2D boxes, 6 S_int,x S_int,z (units 2^-40). */
+void ora_fixed_rho2d(int order, long long n, const int* cell, const float* off, long long nx, long long nz,
+                     long long* rho) {
+  const int lo = order == 3 ? 1 : 0;
+  for (long long p = 0; p < n; ++p) {
+    long long w[3][4];
+    fixed_shape(order, off[3 * p], w[0]);
+    fixed_shape(order, off[3 * p + 2], w[2]);
+    for (int tk = 0; tk <= order; ++tk)
+      for (int ti = 0; ti <= order; ++ti) {
+        const long long i = cell[3 * p] - lo + ti, k = cell[3 * p + 2] - lo + tk;
+        if (i < 0 || i >= nx || k < 0 || k >= nz) continue;
+        rho[i + nx * k] += 6 * w[0][ti] * w[2][tk];
+      }
+  }
+}
+
 /* Integer node charge 6 S_int,x S_int,y S_int,z (units 2^-60 of the particle
  * charge): the quantity whose change the raw integer currents carry exactly. */
 void ora_fixed_rho3d(int order, long long n, const int* cell, const float* off, long long nx, long long ny,

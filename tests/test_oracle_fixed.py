@@ -137,3 +137,87 @@ def test_fixed_weighted_is_rounded_raw():
     for r, v in zip(raw, val):
         exact = r.astype(np.float64) * (float(w[0]) * 3.0) * 2.0 ** -36
         assert np.max(np.abs(v - exact)) <= 0.5 + 1e-9 * np.max(np.abs(exact))
+
+
+# 2D (x, z) boxes: J_x, J_z from the in-plane integer sums, J_y from the
+# mid-move shape product times v_y/c (formed in FP64 from the FP32 momentum)
+
+NN2 = (14, 13)   # nodes along x, z
+
+
+def _moves2d(rng, n, order):
+    c0, f0, c1, f1 = _moves(rng, n, order)
+    for a in (c0, c1):
+        a[:, 1] = 0
+    f0[:, 1] = 0.0
+    f1[:, 1] = 0.0
+    return c0, f0, c1, f1
+
+
+@pytest.mark.parametrize("order", [1, 3])
+def test_fixed_continuity_exact_2d(order):
+    rng = np.random.default_rng(61 + order)
+    c0, f0, c1, f1 = _moves2d(rng, 25, order)
+    assert all(np.any(c1[:, a] > c0[:, a]) and np.any(c1[:, a] < c0[:, a]) for a in (0, 2))
+    w = np.ones(len(c0), np.float32)
+    u = np.zeros((len(c0), 3), np.float32)
+    Jx, Jy, Jz = O.fixed_deposit2d(order, c0, f0, c1, f1, w, u, 1.0, NN2, raw=True)
+    r0 = O.fixed_rho2d(order, c0, f0, NN2)
+    r1 = O.fixed_rho2d(order, c1, f1, NN2)
+    div = np.zeros_like(Jx)
+    div[:, 0] += Jx[:, 0]
+    div[:, 1:] += Jx[:, 1:] - Jx[:, :-1]
+    div[0, :] += Jz[0, :]
+    div[1:, :] += Jz[1:, :] - Jz[:-1, :]
+    assert np.array_equal(div, r1 - r0)
+    assert np.count_nonzero(Jx) and np.count_nonzero(Jz)
+    # the raw out-of-plane values: the mid-move shape sums to 6 2^40 per move
+    assert Jy.sum() == 6 * 2 ** (2 * O.FIXED_SHAPE_BITS) * len(c0)
+
+
+@pytest.mark.parametrize("order", [1, 3])
+def test_fixed_matches_fp64_esirkepov_2d(order):
+    rng = np.random.default_rng(71 + order)
+    d = (1e-6, 1.0, 0.9e-6)
+    dt = O.yee_dt(d, 0.9, 2)
+    n = (NN2[0] - 1, 0, NN2[1] - 1)
+    s = O.OracleSim(2, n, (0,) * 6, d, dt, order=order, alpha_mode="one")
+    c0, f0, c1, f1 = _moves2d(rng, 12, order)
+    w = rng.uniform(0.5, 3.0, len(c0)).astype(np.float32)
+    u = rng.normal(0.0, 2.0, (len(c0), 3)).astype(np.float32)
+    qn = -1.0
+    for p in range(len(c0)):
+        X0 = c0[p] + f0[p].astype(np.float64)
+        X1 = c1[p] + f1[p].astype(np.float64)
+        ud = u[p].astype(np.float64)
+        vyc = ud[1] / np.sqrt(((1.0 + ud[0] * ud[0]) + ud[1] * ud[1]) + ud[2] * ud[2])
+        s.esirkepov(X0, X1, qn * O.Q_E * float(w[p]), O.C_LIGHT * vyc)
+    Jx, Jy, Jz = O.fixed_deposit2d(order, c0, f0, c1, f1, w, u, qn, NN2)
+    got = {"x": -(O.Q_E / (d[2] * dt)) * Jx / O.FIXED_UNIT,
+           "z": -(O.Q_E / (d[0] * dt)) * Jz / O.FIXED_UNIT,
+           "y": (O.Q_E * O.C_LIGHT / (d[0] * d[2])) * Jy / O.FIXED_UNIT}
+    for c in "xyz":
+        ref = s.field("J" + c)[:, 0, :]
+        scale = np.max(np.abs(ref))
+        assert scale > 0
+        assert np.max(np.abs(got[c] - ref)) <= 2e-5 * scale, c
+
+
+def test_fixed_2d_sign_translation_and_order():
+    rng = np.random.default_rng(83)
+    for order in (1, 3):
+        c0, f0, c1, f1 = _moves2d(rng, 10, order)
+        w = rng.uniform(0.1, 10.0, len(c0)).astype(np.float32)
+        u = rng.normal(0.0, 1.0, (len(c0), 3)).astype(np.float32)
+        a = O.fixed_deposit2d(order, c0, f0, c1, f1, w, u, 2.0, NN2)
+        b = O.fixed_deposit2d(order, c0, f0, c1, f1, w, u, -2.0, NN2)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, -y)
+        sh = np.array([2, 0, -1])
+        t = O.fixed_deposit2d(order, c0 + sh, f0, c1 + sh, f1, w, u, 2.0, NN2)
+        for x, y in zip(a, t):
+            assert np.array_equal(np.roll(x, (-1, 2), axis=(0, 1)), y)
+        perm = rng.permutation(len(c0))
+        r = O.fixed_deposit2d(order, c0[perm], f0[perm], c1[perm], f1[perm], w[perm], u[perm], 2.0, NN2)
+        for x, y in zip(a, r):
+            assert np.array_equal(x, y)

@@ -61,7 +61,7 @@ typedef enum {
   PIC_FP32 = 0,         /* FP32 fields, momenta and offsets; FP64 PML splits */
   PIC_FP64 = 1,         /* everything FP64 (the plain FP64 form) */
   PIC_FP32_FIXED64 = 2  /* as PIC_FP32, current accumulated in int64 fixed
-                           point: deterministic, bit-identical J (3D only;
+                           point: deterministic, bit-identical J (3D and 2D;
                            see pic_get_current_fixed) */
 } pic_prec;
 
@@ -196,8 +196,15 @@ int pic_set_old_positions(picpml_ctx* ctx, int sid, const void* src);
  * Units: one integer is e / (6 * 2^24) of charge crossing the component's
  * cell face, i.e. J_x = -(e / (dy dz dt)) Jq_x / (6 * 2^24) in A/m^2 before
  * damping.  The deposit then writes J = alpha_c * that (Eq. alpha) over the
- * whole grid (replacing, not adding to, J).  Limits: |w q/e| <= 2^32 per
- * particle and |Jq| <= 2^62 per node, else PIC_EOVERFLOW at pic_sync. */
+ * whole grid (replacing, not adding to, J).  2D boxes: J_x and J_z from the
+ * in-plane sums 6 W_x = DSx (6 S0z + 3 DSz), rounded as rint(acc (w q/e)
+ * 2^-16) (the same unit, with faces 1 m long along y); J_y from the
+ * mid-move shape product 6 S0x S0z + 3 DSx S0z + 3 S0x DSz + 2 DSx DSz times
+ * v_y/c, formed in FP64 from the FP32 momentum with correctly rounded
+ * operations, u_y / sqrt(((1 + u_x^2) + u_y^2) + u_z^2), rounded as
+ * rint(((T (w q/e)) v_y/c) 2^-16): one integer is e c / (6 2^24 dx dz) of
+ * J_y.  Limits: |w q/e| <= 2^32 per particle and |Jq| <= 2^62 per node, else
+ * PIC_EOVERFLOW at pic_sync. */
 int pic_get_current_fixed(picpml_ctx* ctx, int comp, long long* dst);
 
 /* Field update: E^{n+1} = E^n + dt (c^2 curl B^{n+1/2} - J/eps0), then

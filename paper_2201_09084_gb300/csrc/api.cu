@@ -256,8 +256,13 @@ int run_particles(picpml_ctx* ctx, int mode) {
   }
   if (fixed) {
     const double* d = ctx->gd.d;
-    const double K[3] = {-kQe / (kEps0 * d[1] * d[2]) / kFixUnit, -kQe / (kEps0 * d[0] * d[2]) / kFixUnit,
-                         -kQe / (kEps0 * d[0] * d[1]) / kFixUnit};
+    // integer unit e/(6 2^24) of charge crossing a face (3D; in 2D the faces
+    // are 1 m long along y), and for the 2D J_y e (v_y/c) per node
+    const double Ly = 1.0;
+    const double K[3] = {ctx->gd.dim == 3 ? -kQe / (kEps0 * d[1] * d[2]) / kFixUnit : -kQe / (kEps0 * d[2] * Ly) / kFixUnit,
+                         ctx->gd.dim == 3 ? -kQe / (kEps0 * d[0] * d[2]) / kFixUnit
+                                          : kQe * ctx->dt * kC / (kEps0 * d[0] * d[2] * Ly) / kFixUnit,
+                         ctx->gd.dim == 3 ? -kQe / (kEps0 * d[0] * d[1]) / kFixUnit : -kQe / (kEps0 * d[0] * Ly) / kFixUnit};
     CK(launch_fixed_flush(ctx->g, ctx->tb, ctx->ff, K, ctx->status, ctx->stream));
     ctx->launches += 1;
   }
@@ -316,8 +321,6 @@ int pic_init(picpml_ctx** out, const pic_grid_desc* g, void* stream) {
   if (g->shape_order != 1 && g->shape_order != 3) return fail(nullptr, PIC_EINVAL, "shape_order must be 1 or 3");
   if (g->prec != PIC_FP32 && g->prec != PIC_FP64 && g->prec != PIC_FP32_FIXED64)
     return fail(nullptr, PIC_EINVAL, "bad prec");
-  if (g->prec == PIC_FP32_FIXED64 && g->dim != 3)
-    return fail(nullptr, PIC_ENOTIMPL, "fixed-point deposition is built for 3D grids only");
   if (g->filter_passes < 0 || g->filter_passes > 8) return fail(nullptr, PIC_EINVAL, "filter_passes must be 0..8");
   for (int a = 0; a < 3; ++a) {
     if (g->dim == 2 && a == 1) continue;

@@ -519,6 +519,65 @@ __device__ __forceinline__ void deposit_fixed(const Geom& g, const FieldPtrs<flo
   }
 }
 
+// The 2D (x, z) form: J_x and J_z from the in-plane integer sums,
+// 6 W_x = DSx (6 S0z + 3 DSz) (units 2^-40, so the rounding factor is 2^-16
+// for the same unit e/(6 2^24)); J_y (out of the plane) from the mid-move
+// shape product 6 S0x S0z + 3 DSx S0z + 3 S0x DSz + 2 DSx DSz times v_y/c,
+// which is formed in FP64 from the FP32 momentum with correctly rounded
+// operations in a fixed order, u_y / sqrt(((1 + u_x^2) + u_y^2) + u_z^2).
+template <int ORDER>
+__device__ __forceinline__ void deposit_fixed2d(const Geom& g, const FieldPtrs<float>& f, double qn, const int c0[3],
+                                                const float o0[3], const int c1[3], const float o1[3], float w,
+                                                const float u[3], unsigned* status) {
+  constexpr int W = ORDER + 2;
+  constexpr double kDown2 = 1.0 / 65536.0;   // 2^-16
+  long long S0[2][W], DS[2][W];
+  const int lox = fixed_axis<ORDER>(c0[0], o0[0], c1[0], o1[0], S0[0], DS[0]);
+  const int loz = fixed_axis<ORDER>(c0[2], o0[2], c1[2], o1[2], S0[1], DS[1]);
+  const double wq = __dmul_rn((double)w, qn);
+  if (!(fabs(wq) <= kFixMaxWq)) {
+    atomicOr(status, ST_FIXED_OVERFLOW);
+    return;
+  }
+  const double ux = u[0], uy = u[1], uz = u[2];
+  const double g2 = __dadd_rn(__dadd_rn(__dadd_rn(1.0, __dmul_rn(ux, ux)), __dmul_rn(uy, uy)), __dmul_rn(uz, uz));
+  const double vyc = __ddiv_rn(uy, __dsqrt_rn(g2));
+  auto add = [&](int c, int i, int k, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(f.Jq[c] + g.idx(i, 0, k)), static_cast<unsigned long long>(v));
+  };
+#pragma unroll
+  for (int tk = 0; tk < W; ++tk) {   // J_x: prefix sums along x
+    const long long T = 6 * S0[1][tk] + 3 * DS[1][tk];
+    long long acc = 0;
+#pragma unroll
+    for (int ti = 0; ti < W - 1; ++ti) {
+      acc += DS[0][ti] * T;
+      if (acc != 0) add(0, lox + ti, loz + tk, __double2ll_rn(__dmul_rn(__dmul_rn(__ll2double_rn(acc), wq), kDown2)));
+    }
+  }
+#pragma unroll
+  for (int ti = 0; ti < W; ++ti) {   // J_z: prefix sums along z
+    const long long T = 6 * S0[0][ti] + 3 * DS[0][ti];
+    long long acc = 0;
+#pragma unroll
+    for (int tk = 0; tk < W - 1; ++tk) {
+      acc += DS[1][tk] * T;
+      if (acc != 0) add(2, lox + ti, loz + tk, __double2ll_rn(__dmul_rn(__dmul_rn(__ll2double_rn(acc), wq), kDown2)));
+    }
+  }
+  if (vyc == 0.0) return;
+#pragma unroll
+  for (int tk = 0; tk < W; ++tk)     // J_y: mid-move shape product
+#pragma unroll
+    for (int ti = 0; ti < W; ++ti) {
+      const long long T = 6 * S0[0][ti] * S0[1][tk] + 3 * DS[0][ti] * S0[1][tk] + 3 * S0[0][ti] * DS[1][tk] +
+                          2 * DS[0][ti] * DS[1][tk];
+      if (T == 0) continue;
+      const double v = __dmul_rn(__dmul_rn(__dmul_rn(__ll2double_rn(T), wq), vyc), kDown2);
+      add(1, lox + ti, loz + tk, __double2ll_rn(v));
+    }
+}
+
 // Deposit of one 2D particle of a batched run (same arithmetic).
 template <int ORDER, typename T>
 __device__ __forceinline__ void deposit_run_particle(const Geom& g, const Tables& tb, const FieldPtrs<T>& f,

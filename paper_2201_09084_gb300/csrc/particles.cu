@@ -17,8 +17,8 @@ namespace {
 using namespace pc;
 
 // MODE 0: push only (saves x^n); MODE 1: deposit only (from saved x^n);
-// MODE 2: fused push + deposit.  FIX: deterministic int64 deposition (3D
-// FP32 only) instead of the floating-point one.
+// MODE 2: fused push + deposit.  FIX: deterministic int64 deposition (FP32
+// only) instead of the floating-point one.
 template <int ORDER, int DIM, typename T, int MODE, bool FIX = false>
 __global__ void __launch_bounds__(256) k_particles(Geom g, Tables tb, FieldPtrs<T> f, SpeciesPtrs<T> sp,
                                                    int prescribed, unsigned* status,
@@ -44,7 +44,10 @@ __global__ void __launch_bounds__(256) k_particles(Geom g, Tables tb, FieldPtrs<
         PIO<T>::store(sp.pos, sp.mom, p, o, w * exp(-I), u, cell);
       }
       if constexpr (FIX) {
-        deposit_fixed<ORDER>(g, f, sp.qn, c0, o0, c1, o, wd, status);
+        if constexpr (DIM == 3)
+          deposit_fixed<ORDER>(g, f, sp.qn, c0, o0, c1, o, wd, status);
+        else
+          deposit_fixed2d<ORDER>(g, f, sp.qn, c0, o0, c1, o, wd, u, status);
       } else {
         const T g2 = sqrt(T(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
         deposit_one<ORDER, DIM, T>(g, tb, f, sp, c0, o0, c1, o, wd, u[1] / g2);
@@ -133,7 +136,12 @@ __global__ void __launch_bounds__(256) k_particles(Geom g, Tables tb, FieldPtrs<
     }
     PIO<T>::store(sp.pos, sp.mom, p, out ? o : o1, wn, u, cell1);
     if constexpr (MODE == 2 && FIX) {
-      if (!out) deposit_fixed<ORDER>(g, f, sp.qn, c, o, c1, o1, wd, status);
+      if (!out) {
+        if constexpr (DIM == 3)
+          deposit_fixed<ORDER>(g, f, sp.qn, c, o, c1, o1, wd, status);
+        else
+          deposit_fixed2d<ORDER>(g, f, sp.qn, c, o, c1, o1, wd, u, status);
+      }
     } else if (MODE == 2 && !out) {
       deposit_one<ORDER, DIM, T>(g, tb, f, sp, c, o, c1, o1, wd, u[1] * ig);
     }
@@ -166,8 +174,10 @@ cudaError_t launch_mode(int mode, const Geom& g, const Tables& tb, const FieldPt
 }
 
 // Deterministic mode, after all species have deposited: the damped current
-// J'_c = alpha_c K_c Jq_c with K_c = -e / (eps0 d_a d_b) / (6 2^24) (a, b the
-// axes transverse to c) and alpha_c at the component's staggered location
+// J'_c = alpha_c K_c Jq_c with K_c the value of one unit of component c's
+// integer sum (in 3D -e / (eps0 d_a d_b) / (6 2^24), a and b the axes
+// transverse to c; in 2D the host's per-component 2D units, j = 0) and
+// alpha_c at the component's staggered location
 // (Eq. alpha, Sec. II.B), one thread per node; J' is overwritten, the integer
 // sums are kept until the next deposit clears them.  |Jq| above 2^62 is
 // reported as an overflow.
@@ -199,9 +209,13 @@ cudaError_t launch_particles(int mode, int order, const Geom& g, const Tables& t
                              const SpeciesPtrs<T>& sp, int prescribed, unsigned* status,
                              unsigned long long* pushed, int nsm, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    if (f.Jq[0] && g.dim == 3)
-      return order == 1 ? launch_mode<1, 3, T, true>(mode, g, tb, f, sp, prescribed, status, pushed, nsm, s)
-                        : launch_mode<3, 3, T, true>(mode, g, tb, f, sp, prescribed, status, pushed, nsm, s);
+    if (f.Jq[0]) {
+      if (g.dim == 3)
+        return order == 1 ? launch_mode<1, 3, T, true>(mode, g, tb, f, sp, prescribed, status, pushed, nsm, s)
+                          : launch_mode<3, 3, T, true>(mode, g, tb, f, sp, prescribed, status, pushed, nsm, s);
+      return order == 1 ? launch_mode<1, 2, T, true>(mode, g, tb, f, sp, prescribed, status, pushed, nsm, s)
+                        : launch_mode<3, 2, T, true>(mode, g, tb, f, sp, prescribed, status, pushed, nsm, s);
+    }
   }
   if (order == 1) {
     return g.dim == 3 ? launch_mode<1, 3, T>(mode, g, tb, f, sp, prescribed, status, pushed, nsm, s)
@@ -213,7 +227,7 @@ cudaError_t launch_particles(int mode, int order, const Geom& g, const Tables& t
 
 cudaError_t launch_fixed_flush(const Geom& g, const Tables& tb, const FieldPtrs<float>& f, const double K[3],
                                unsigned* status, cudaStream_t s) {
-  if (g.dim != 3 || !f.Jq[0]) return cudaErrorInvalidValue;
+  if (!f.Jq[0]) return cudaErrorInvalidValue;
   dim3 blk(128, 1, 1), grd((g.nn[0] + 127) / 128, g.nn[1], g.nn[2]);
   k_fixed_flush<<<grd, blk, 0, s>>>(g, tb, f, K[0], K[1], K[2], status);
   return cudaGetLastError();

@@ -105,3 +105,90 @@ def test_fixed_beam_exit_matches_oracle(order):
         gpu.step(12)
         err = max_field_err(ora, gpu)
         assert max(err.values()) < TOL["fixed64"], err
+
+
+D2 = (1e-6, 1.0, 0.9e-6)
+
+
+@pytest.mark.parametrize("order", [1, 3])
+def test_fixed_deposit_bit_exact_2d(order):
+    """2D boxes: the int64 sums of prescribed moves (J_x, J_z in-plane, J_y
+    from the momenta's v_y) equal the oracle's 2D replay bit for bit, and the
+    damped current handed to the field update is alpha_c K Jq."""
+    from paper_2201_09084_gb300.api import Sim, pack_particles
+    nphys = (41, 0, 37)
+    pml = (6, 9, 0, 0, 8, 7)
+    N = (nphys[0] + 15, 0, nphys[2] + 15)
+    margin = 2 if order == 1 else 3
+    lo = [margin + 1, 0, margin + 1]
+    hi = [N[0] - margin - 1, 0.5, N[2] - margin - 1]
+    dt = O.yee_dt(D2, 0.99, 2)
+    gpu = Sim(2, nphys, D2, pml, dt=dt, order=order, prec="fixed64", alpha_mode="damped")
+    nn = gpu.nn
+    expect = [np.zeros((nn[2], nn[0]), np.int64) for _ in range(3)]
+    keep = []
+    rng = np.random.default_rng(17 + order)
+    for q, m, n, seed in [(-O.Q_E, O.M_E, 5000, 31), (2 * O.Q_E, O.M_P, 2001, 47)]:
+        c0, f0, c1, f1, w = I.random_moves(n, lo, hi, seed=seed + order)
+        for a in (c0, c1):
+            a[:, 1] = 0
+        f0[:, 1] = 0.0
+        f1[:, 1] = 0.0
+        u = rng.normal(0.0, 1.5, (n, 3)).astype(np.float32)
+        pos, mom = pack_particles(c1, f1, u, w, "fixed64")
+        sid = gpu.add_species(pos, mom, n, q, m)
+        keep.append(gpu.set_old_positions(sid, c0, f0))
+        J = O.fixed_deposit2d(order, c0, f0, c1, f1, w, u, q / O.Q_E, (nn[0], nn[2]))
+        for c in range(3):
+            expect[c] += J[c]
+    gpu.deposit()
+    gpu.sync()
+    for c in range(3):
+        got = gpu.current_fixed(c).cpu().numpy()[:, 0, :]
+        assert np.count_nonzero(expect[c]) > 500
+        assert np.array_equal(got, expect[c]), (c, int(np.count_nonzero(got != expect[c])))
+    ora = O.OracleSim(2, nphys, pml, D2, dt, order=order, alpha_mode="damped")
+    an = [ora.table("a_node", a) for a in (0, 2)]
+    ac = [ora.table("a_cent", a) for a in (0, 2)]
+    conv = {"x": -(O.Q_E / (D2[2] * dt)), "y": O.Q_E * O.C_LIGHT / (D2[0] * D2[2]), "z": -(O.Q_E / (D2[0] * dt))}
+    for c, name in enumerate("xyz"):
+        ax = ac[0] if c == 0 else an[0]
+        az = ac[1] if c == 2 else an[1]
+        ref = conv[name] * expect[c].astype(np.float64) / O.FIXED_UNIT * az[:, None] * ax[None, :]
+        got = gpu.field("J" + name).cpu().numpy()[:, 0, :]
+        scale = np.abs(ref).max()
+        assert np.abs(got - ref).max() <= 1e-6 * scale, name
+    del keep
+
+
+@pytest.mark.parametrize("order", [1, 3])
+def test_fixed_2d_whole_steps_order_independent_and_near_oracle(order):
+    """2D single particles exiting through the damped PML: the deterministic
+    run is bit-identical with its particles permuted, and within the FP32
+    tolerance of the FP64 oracle."""
+    import torch
+    from paper_2201_09084_gb300.api import Sim, pack_particles
+    nphys = (40, 0, 44)
+    pml = (8, 8, 0, 0, 8, 8)
+    rng = np.random.default_rng(5 + order)
+    n = 60
+    X = np.stack([8 + rng.uniform(10, 30, n), np.zeros(n), 8 + rng.uniform(14, 34, n)], 1)
+    u = np.stack([rng.normal(0, 2, n), rng.normal(0, 2, n), rng.normal(0, 3, n)], 1).astype(np.float32)
+    cell, off = I.split_position(X)
+    w = np.ones(n, np.float32)
+    dt = O.yee_dt(D2, 0.99, 2)
+    parts = [dict(cell=cell, off=off, u=u, w=w, q=-O.Q_E, m=O.M_E, immobile=False),
+             dict(cell=cell, off=off, u=np.zeros_like(u), w=w, q=O.Q_E, m=O.M_E, immobile=True)]
+    ora, gpu = make_pair(2, nphys, pml, D2, parts, order=order, prec="fixed64", alpha_mode="damped")
+    perm = rng.permutation(n)
+    p2 = [dict(parts[0], cell=cell[perm], off=off[perm], u=u[perm]), dict(parts[1], cell=cell[perm], off=off[perm])]
+    _, gpu2 = make_pair(2, nphys, pml, D2, p2, order=order, prec="fixed64", alpha_mode="damped")
+    for _ in range(3):
+        ora.step(10)
+        gpu.step(10)
+        gpu2.step(10)
+        err = max_field_err(ora, gpu)
+        assert max(err.values()) < TOL["fixed64"], err
+    torch.cuda.synchronize()
+    for f in ("Ex", "Ey", "Ez", "Bx", "By", "Bz"):
+        assert torch.equal(gpu.field(f), gpu2.field(f)), f

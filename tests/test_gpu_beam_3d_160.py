@@ -26,7 +26,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
 
-def test_config2_full_size_10_steps():
+def test_beam_3d_160_full_size_10_steps():
     import torch
     import bench
     from paper_2201_09084_gb300.api import Sim, pack_particles

@@ -44,7 +44,7 @@ def _pair(nphys, pml, start=None, mode="damped"):
 
 
 @pytest.mark.parametrize("mode", ["damped", "zero"])
-def test_config1_full_size(mode):
+def test_single_particle_2d_160_full_size(mode):
     start = np.array([PML[0] + 64.3, 0.0, PML[4] + 64.2])
     ora, gpu = _pair(NPHYS, PML, start=start, mode=mode)
     for _ in range(4):

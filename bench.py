@@ -488,6 +488,117 @@ def run_precision_study(args):
     out["value"] = small["fp32"]["err_vs_oracle"]["20"]
     return out
 
+# DRAM bytes per particle-step of the one-thread-per-particle kernel on the
+# thermal plasma (dram__bytes_read.sum + dram__bytes_write.sum of the three
+# launches of one step, electrons + protons + beam, 557,966,080 B for
+# 8,429,785 particles), from one ncu capture of the 64 x 64 x 128 case with
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,... --clock-control none
+#       -k regex:k_particles -s 9 -c 3
+#       python bench.py --plasma --plasma-cells 64,64,128 --tuning 1,1 --steps 3 --warmup 3
+# The plasma fills the box at a fixed 8 particles per cell, so the traffic
+# grows with the particle count; the full-size figure is scaled by it.  Set
+# to None whenever that kernel changes.
+PLASMA_NCU_BYTES_PER_PARTICLE = 557_966_080 / 8_429_785
+
+
+def run_plasma(args):
+    """Throughput on the thermal plasma + drifting beam workload (electrons
+    and protons 8 per cell filling the physical box, Maxwellian u_th = 0.01,
+    a beam at u_z = 5 with immobile neutralising ions; 16-cell PML, order 1,
+    FP32, sort every 20 steps; 128 x 128 x 256 physical cells by default,
+    --plasma-cells for smaller profiling captures).  Particles move a small
+    fraction of a cell per step and scatter over the whole grid, so the
+    particle kernel's current lands on many distinct nodes.  Prints its own
+    JSON line; the roofline uses the same byte model as the beam."""
+    import torch
+    from paper_2201_09084_gb300 import inputs as I
+    from paper_2201_09084_gb300.api import Sim, pack_particles
+    from paper_2201_09084_gb300 import build as B
+    B.build()
+    nphys = tuple(int(x) for x in args.plasma_cells.split(","))
+    parts = I.plasma(nphys, PML, D[0])
+    stream = torch.cuda.current_stream()
+    sim = Sim(3, nphys, D, PML, cfl=0.99, order=1, prec="fp32", alpha_mode="damped", sort_every=0,
+              stream=stream)
+    keep = []
+    for sp in parts:
+        pos, mom = pack_particles(sp["cell"], sp["off"], sp["u"], sp["w"], "fp32")
+        sim.add_species(pos, mom, len(sp["w"]), sp["q"], sp["m"], sp["immobile"])
+        keep.append((pos, mom, sp["immobile"]))
+    sim.sort()
+    if args.tuning:
+        p_, k_ = (int(x) for x in args.tuning.split(","))
+        sim.set_tuning(p_, k_)
+        tuning = {"particles_per_thread": p_, "z_nodes_per_thread": k_, "source": "--tuning"}
+    else:
+        tuning = sim.autotune(steps=3)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+
+    def one_step(i, ev=None):
+        if i % SORT_EVERY == 0:
+            sim.sort()
+        if ev is not None:
+            ev[0].record(stream)
+        sim.push_deposit()
+        if ev is not None:
+            ev[1].record(stream)
+        sim.field_step()
+        if ev is not None:
+            ev[2].record(stream)
+
+    for i in range(args.warmup):
+        one_step(i)
+    sim.sync()
+    ps0 = sim.particle_steps()
+    l0 = sim.launch_count()
+    cells = []
+    for pos, mom, imm in keep:
+        if not imm:
+            c = mom.view(torch.int32)[:, 3]
+            cells.append(c[c >= 0])
+    occ = int(torch.unique(torch.cat(cells)).numel())
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(torch.cuda.current_device())
+    torch.cuda.synchronize()
+    clocks.start()
+    t0.record(stream)
+    for i in range(args.steps):
+        one_step(args.warmup + i, evs[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sim.sync()
+    ms = t0.elapsed_time(t1)
+    psteps = sim.particle_steps() - ps0
+    launches = sim.launch_count() - l0
+    t_pd = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    t_f = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    N = [n + 2 * p for n, p in zip(nphys, PML[::2])]
+    total = N[0] * N[1] * N[2]
+    interior = nphys[0] * nphys[1] * nphys[2]
+    b_part, b_field = algorithmic_bytes(psteps / args.steps, occ, interior, total - interior, "fp32")
+    peak, kind = measured_peak()
+    achieved = b_part / (t_pd / 1e3) / 1e9
+    p_ = tuning["particles_per_thread"]
+    traffic = (PLASMA_NCU_BYTES_PER_PARTICLE * psteps / args.steps
+               if PLASMA_NCU_BYTES_PER_PARTICLE and p_ == 1 else None)
+    sim.close()
+    return {"metric": METRIC, "value": psteps / (ms / 1e3), "unit": "particle-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"thermal plasma + drifting beam: {nphys[0]}x{nphys[1]}x{nphys[2]} + "
+                                   f"{PML[0]}-cell PML, e- and p+ 8 per cell, u_th 0.01, beam u_z 5, order 1, "
+                                   "fp32 fields + float-float PML parts",
+                       "particles": int(sum(len(sp["w"]) for sp in parts if not sp["immobile"])),
+                       "sort_every": SORT_EVERY, "l2": "working set > L2"},
+            "kernel_ms": {"push_deposit": t_pd, "field_step": t_f},
+            "roofline": {"bound": "hbm", "kernel": "push_deposit (particle kernels)", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{kind} (copy)",
+                         "traffic": traffic, "traffic_note": "per step; ncu of the 64x64x128 case, scaled by particles",
+                         "algorithmic_bytes_per_step": b_part,
+                         "note": "one launch per mobile species per step; time and bytes are per step"},
+            "gpu_launches": int(launches), "autotune": tuning, "clocks": clk}
+
 
 def main():
     ap = argparse.ArgumentParser()
@@ -506,6 +617,9 @@ def main():
                     help="beam macroparticles (default 4194304; smaller only for profiling captures)")
     ap.add_argument("--precision-study", action="store_true",
                     help="FP32 forms vs FP64 on the plasma + beam workload (prints its own JSON line)")
+    ap.add_argument("--plasma", action="store_true",
+                    help="throughput on the thermal plasma + beam workload (prints its own JSON line)")
+    ap.add_argument("--plasma-cells", default="128,128,256", help="physical cells of the --plasma workload")
     ap.add_argument("--tuning", default=None,
                     help="P,KZ launch shapes instead of the autotuner (profiling captures)")
     args = ap.parse_args()
@@ -519,6 +633,8 @@ def main():
         torch.distributed.init_process_group("nccl" if args.impl == "gb300" else "gloo")
     if args.precision_study:
         out = run_precision_study(args) if rank == 0 else None
+    elif args.plasma and args.impl == "gb300":
+        out = run_plasma(args) if rank == 0 else None
     elif args.impl == "reference":
         out = run_reference(args, rank, world)
     else:

@@ -47,9 +47,14 @@ typedef enum {
   PIC_ENOMEM = -2,      /* device allocation failed */
   PIC_ECUDA = -3,       /* a CUDA runtime call failed */
   PIC_ECFL = -4,        /* dt above the Yee Courant limit */
-  PIC_EOVERFLOW = -5,   /* fixed-point current accumulator overflow */
-  PIC_ETIMEOUT = -6,    /* a bounded device wait gave up */
-  PIC_ENOTIMPL = -7,    /* combination not built */
+  PIC_EOVERFLOW = -5,   /* fixed-point current accumulator overflow, or an
+                           injection past a species' capacity */
+  PIC_ETIMEOUT = -6,    /* a bounded device wait gave up (reserved: no kernel
+                           waits on another block) */
+  PIC_ENOTIMPL = -7,    /* combination not built (reserved: pic_init takes
+                           every dim, order, precision and alpha mode; the
+                           batch API takes FP32 and FP64 and answers
+                           PIC_EINVAL to the fixed-point mode) */
   PIC_ESTATE = -8,      /* call out of order (e.g. push before pml_init) */
   PIC_EPARTICLE = -9    /* a particle record was invalid (outside its allowed
                            cells, an offset outside [0,1), or a momentum or

@@ -226,23 +226,30 @@ def test_pml_absorbs_pec_reflects():
     assert back_pml < 1e-3 * first
 
 
-def _guide_mode_run(nx, coef, L, nz=400, z0=200.0, width=60.0, lam=32.0):
-    """TE mode E_y ~ sin(pi x / (nx dx)) with a Gaussian envelope of carrier
-    wavelength lam cells in a 2D box with conducting x-walls and a z-PML of
-    L cells on both sides.  E_y(z) at t = 0 is decomposed into Fourier modes
-    along z; each mode gets the B_x and B_z of the discrete Yee plane wave
-    travelling towards +z (discrete wavenumbers 2/d sin(k d/2), frequency
-    from the Yee dispersion relation), at B's own staggered points and at
-    t = +-dt/2.  Returns the oracle run, a function returning the Yee
-    energy (eps0 E^n.E^n + B^{n-1/2}.B^{n+1/2}/mu0)/2 over the physical
-    cells, the propagation angle of the carrier and dt."""
+
+def _guide_mode_run(dim, orient, nt, coef, L, nz=400, z0=200.0, width=60.0, lam=32.0):
+    """Waveguide mode between conducting walls entering a z-PML of L cells
+    on both sides.  orient "x": E_y ~ sin(pi x / (nt dx)) with B_x, B_z
+    (2D, or 3D uniform along y over 2 cells); orient "y" (3D): E_x ~
+    sin(pi y / (nt dy)) with B_y, B_z, uniform along x.  The envelope is a
+    Gaussian of carrier wavelength lam cells.  E(z) at t = 0 is decomposed
+    into Fourier modes along z; each gets the B of the discrete Yee plane wave
+    travelling towards +z (discrete wavenumbers 2/d sin(k d/2), frequency from
+    the Yee dispersion relation) at B's own staggered points and at
+    t = +-dt/2.  Returns the oracle run, a function giving the Yee energy
+    (eps0 E^n.E^n + B^{n-1/2}.B^{n+1/2}/mu0)/2 over the physical z range, the
+    carrier's angle to the z axis and dt."""
     d = (1e-6, 1e-6, 1e-6)
-    dt = O.yee_dt(d, 0.99, 2)
-    sim = O.OracleSim(2, (nx, 0, nz), (0, 0, 0, 0, L, L), d, dt, alpha_mode="one",
+    dt = O.yee_dt(d, 0.99, dim)
+    if dim == 2:
+        n = (nt, 0, nz)
+    else:
+        n = (nt, 2, nz) if orient == "x" else (2, nt, nz)
+    sim = O.OracleSim(dim, n, (0, 0, 0, 0, L, L), d, dt, alpha_mode="one",
                       sig_coef=coef, delta=float(L), sig_exp=2.0)
-    NX, _, NZ = sim.nn
-    dx, dz = d[0], d[2]
-    kx = np.pi / (nx * dx)
+    NZ = sim.nn[2]
+    dz = d[2]
+    kt = np.pi / (nt * d[0])
     kz0 = 2 * np.pi / (lam * dz)
     z = np.arange(NZ) * dz
     zc = (L + z0) * dz
@@ -250,38 +257,50 @@ def _guide_mode_run(nx, coef, L, nz=400, z0=200.0, width=60.0, lam=32.0):
     Ek = np.fft.fft(E)
     k = 2 * np.pi * np.fft.fftfreq(NZ, d=dz)
     sg = np.sign(k)
-    ktx = 2 / dx * np.sin(kx * dx / 2)
+    ktt = 2 / d[0] * np.sin(kt * d[0] / 2)
     ktz = 2 / dz * np.sin(k * dz / 2)
-    wt = C * np.sqrt(ktx ** 2 + ktz ** 2)             # 2/dt sin(w dt/2)
+    wt = C * np.sqrt(ktt ** 2 + ktz ** 2)             # 2/dt sin(w dt/2)
     w = 2 / dt * np.arcsin(wt * dt / 2)
-    xi = np.arange(NX) * dx
-    xh = (np.arange(NX) + 0.5) * dx
-    sx = np.sin(kx * xi)
-    sx[0] = sx[-1] = 0.0
-    cx = np.cos(kx * xh)
-    cx[-1] = 0.0
-    sim.set_field("Ey", (E[:, None] * sx[None, :])[:, None, :])
+    s_node = np.sin(kt * np.arange(nt + 1) * d[0])    # transverse profile at nodes
+    s_node[0] = s_node[-1] = 0.0
+    c_half = np.cos(kt * (np.arange(nt + 1) + 0.5) * d[0])   # at half nodes
+    c_half[-1] = 0.0
+    if dim == 2:
+        u_half = np.ones(1)                           # no y staggering in 2D
+    else:
+        u_half = np.ones(3)                           # uniform axis, half nodes
+        u_half[-1] = 0.0
+
+    def place(zp, tp):
+        if orient == "x":
+            return zp[:, None, None] * u_half[None, :, None] * tp[None, None, :]
+        return zp[:, None, None] * tp[None, :, None] * u_half[None, None, :]
+
+    # orient x: E_y, B_x = -(k_z/w) E, B_z ~ +(k_x/w); orient y: E_x, B_y = +(k_z/w) E, B_z ~ -(k_y/w)
+    sgn = -1.0 if orient == "x" else 1.0
+    sim.set_field("Ey" if orient == "x" else "Ex", place(E, s_node))
     for t, tag in ((dt / 2, "h"), (-dt / 2, "p")):
         ph = np.exp(-1j * sg * w * t)
-        bx = np.real(np.fft.ifft(-(np.abs(ktz) / wt) * Ek * np.exp(1j * k * dz / 2) * ph))
-        bx[-1] = 0.0
-        bz = np.real(np.fft.ifft(-1j * sg * (ktx / wt) * Ek * ph))
-        sim.set_field("B" + tag + "x", (bx[:, None] * sx[None, :])[:, None, :])
-        sim.set_field("B" + tag + "z", (bz[:, None] * cx[None, :])[:, None, :])
+        bt = np.real(np.fft.ifft(sgn * (np.abs(ktz) / wt) * Ek * np.exp(1j * k * dz / 2) * ph))
+        bt[-1] = 0.0
+        bz = np.real(np.fft.ifft(sgn * 1j * sg * (ktt / wt) * Ek * ph))
+        sim.set_field("B" + tag + orient, place(bt, s_node))
+        sim.set_field("B" + tag + "z", place(bz, c_half))
 
     def energy():
-        e = sim.field("Ey")[L:L + nz + 1]
-        b = sum((sim.field("Bh" + c) * sim.field("Bp" + c))[L:L + nz].sum() for c in "xz")
-        return 0.5 * O.EPS0 * (e * e).sum() + 0.5 * b * O.EPS0 * C * C
+        e = sum((sim.field("E" + c) ** 2)[L:L + nz + 1].sum() for c in "xyz")
+        b = sum((sim.field("Bh" + c) * sim.field("Bp" + c))[L:L + nz + 1].sum() for c in "xyz")
+        return 0.5 * O.EPS0 * e + 0.5 * b * O.EPS0 * C * C
 
-    return sim, energy, np.arctan2(kx, kz0), dt
+    return sim, energy, np.arctan2(kt, kz0), dt
 
 
-@pytest.mark.parametrize("nx", [28, 16, 9])
-def test_pml_oblique_reflection_coefficient(nx):
+@pytest.mark.parametrize("dim,orient,nt", [(2, "x", 28), (2, "x", 16), (2, "x", 9), (3, "x", 16),
+                                           (3, "y", 9)])
+def test_pml_oblique_reflection_coefficient(dim, orient, nt):
     # weak profile, delta = L = 60 cells: int sigma/(eps0 c) dz = coef * L / 3 = 1
     coef, L = 0.05, 60
-    sim, energy, theta, dt = _guide_mode_run(nx, coef, L)
+    sim, energy, theta, dt = _guide_mode_run(dim, orient, nt, coef, L)
     w0 = energy()
     # the carrier's centre goes 260 cells to the conductor and back at the
     # guide's group velocity c cos(theta); the pulse is then back inside
@@ -291,5 +310,24 @@ def test_pml_oblique_reflection_coefficient(nx):
     expect = np.exp(-4 * np.cos(theta) * coef * L / 3)
     assert r2 == pytest.approx(expect, rel=0.03), (np.degrees(theta), r2, expect)
     # an angle-blind attenuation would give exp(-4) = 0.018 at every angle
-    if nx == 9:
+    if nt == 9:
         assert r2 > 5 * np.exp(-4 * coef * L / 3)
+
+
+def test_guide_mode_travels_forward_and_conserves_energy_without_pml_loss():
+    """The set-up of the oblique test is a pure +z wave: with sigma = 0 the
+    Yee energy is conserved, and the pulse's centre moves at the group
+    velocity c cos(theta) of the guide."""
+    sim, energy, theta, dt = _guide_mode_run(3, "x", 16, 0.0, 60)
+    w0 = energy()
+
+    def centre():
+        e = (sim.field("Ey") ** 2).sum(axis=(1, 2))
+        return (np.arange(len(e)) * e).sum() / e.sum()
+
+    z0 = centre()
+    steps = 100          # the pulse (+-150 cells around cell 200) stays inside the 400 cells
+    sim.step(steps)
+    assert energy() / w0 == pytest.approx(1.0, abs=1e-3)
+    moved = centre() - z0
+    assert moved == pytest.approx(steps * C * dt * np.cos(theta) / 1e-6, rel=0.03)

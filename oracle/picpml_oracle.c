@@ -106,6 +106,8 @@ double ora_alpha(double dcells, double coef, double delta, double p, double v,
   return exp(-integral);
 }
 
+/* Depth (cells) of coordinate x beyond the physical box along axis a; the
+ * interface is the last physical node plane, depth 0 inside (Sec. II.B). */
 static double depth_of(const ora_sim* s, int a, double x) {
   double lo = (double)s->plo[a], hi = (double)(s->plo[a] + s->n[a]);
   if (x < lo) return lo - x;
@@ -119,6 +121,10 @@ static int face_of(const ora_sim* s, int a, double x) {
   return x < (double)s->plo[a] ? 2 * a : 2 * a + 1;
 }
 
+/* Per-axis tables at nodes and cell centres: sigma/eps0 from
+ * Eq. conductivity and alpha from Eq. alpha at each location's depth, with
+ * the face's own alpha mode (Sec. II.B staggering: E and j_x, j_y at nodes,
+ * B and j_z at centres along the damping axis). */
 static void build_tables(ora_sim* s) {
   for (int a = 0; a < 3; ++a) {
     long nn = s->nn[a];
@@ -332,6 +338,10 @@ static double gather_one(const ora_sim* s, const double* F, const double* o,
 static const double STAG_E[3][3] = {{0.5, 0, 0}, {0, 0.5, 0}, {0, 0, 0.5}};
 static const double STAG_B[3][3] = {{0, 0.5, 0.5}, {0.5, 0, 0.5}, {0.5, 0.5, 0}};
 
+/* E^n and B^n = (B^{n-1/2} + B^{n+1/2})/2 at absolute position X (cells),
+ * each component interpolated at its own staggered points with the
+ * B-spline of the deposit's order (App. A shape order; energy-conserving
+ * gather). */
 void ora_gather(const ora_sim* s, const double* X, double* Eout, double* Bout) {
   for (int c = 0; c < 3; ++c) {
     Eout[c] = gather_one(s, s->E[c], STAG_E[c], X);
@@ -554,6 +564,8 @@ void ora_damp_J(ora_sim* s) {
       }
 }
 
+/* Esirkepov deposit of every moving particle, then J_c <- alpha_c J_c at
+ * each component's staggered location (App. A, Eq. alpha, Sec. II.B). */
 void ora_deposit(ora_sim* s) { ora_deposit_raw(s); ora_damp_J(s); }
 
 /* ------------------------------------------------------------------------- */
@@ -580,9 +592,9 @@ static double advance(double old, double* sp0, double* sp1, const double* R,
 }
 
 /* E^{n+1} = E^n + dt (c^2 curl B^{n+1/2} - J/eps0)  (Eqs. MaxwellE, MaxwellSum). */
-/* Binomial filter of the deposited current (App. A: "an additional binomial
- * filter is applied to the deposited current before updating the fields";
- * Birdsall and Langdon): one pass replaces every J value by
+/* Binomial filter of the deposited current (App. A: the paper's runs smooth
+ * the current with a binomial filter, after Birdsall and Langdon, before the
+ * field update): one pass replaces every J value by
  * (J[i-1] + 2 J[i] + J[i+1])/4 along x, then along y (3D), then along z,
  * for each component at its own staggered points; values beyond the arrays
  * count as zero. */
@@ -606,8 +618,11 @@ void ora_filter_J(ora_sim* s) {
   free(tmp);
 }
 
+/* Number of binomial passes applied to J at the start of each E update. */
 void ora_set_filter(ora_sim* s, int passes) { s->filter_passes = passes > 0 ? passes : 0; }
 
+/* E^{n+1} from E^n, B^{n+1/2} and the damped (and filtered) J^{n+1/2}
+ * (Eqs. MaxwellE, MaxwellSum; split parts in PML cells, Sec. II.B). */
 void ora_field_E(ora_sim* s) {
   for (int f = 0; f < s->filter_passes; ++f) ora_filter_J(s);
   const double c2 = ORA_C * ORA_C, dt = s->dt;
@@ -833,6 +848,9 @@ void ora_dims(const ora_sim* s, long* nn) { nn[0] = s->nn[0]; nn[1] = s->nn[1]; 
 
 #define FIX_QB 20
 
+/* B-spline shape values of an in-cell offset f, computed in FP32 and
+ * quantised to 2^-20 with the remainder on one node so the values sum to
+ * 2^20 exactly (order 1: 2 nodes, order 3: 4 nodes). */
 static void fixed_shape(int order, float f, long long* w) {
   const float scale = (float)(1 << FIX_QB);
   const long long one = 1LL << FIX_QB;

@@ -500,6 +500,43 @@ def run_precision_study(args):
 # to None whenever that kernel changes.
 PLASMA_NCU_BYTES_PER_PARTICLE = 557_966_080 / 8_429_785
 
+# Plasma boxes with more particles per species than this are generated and
+# packed one z-plane of cells at a time (inputs.plasma_planes) instead of in
+# one piece, so host memory holds one plane.
+STREAM_PARTICLES = 1 << 27
+
+
+def plasma_species(nphys, device):
+    """Species of the plasma + beam workload as (pos, mom, n, q, m, immobile)
+    FP32 particle records on `device`: electrons, protons, beam, beam ions."""
+    import torch
+    from paper_2201_09084_gb300 import inputs as I
+    from paper_2201_09084_gb300.api import pack_particles
+    out = []
+    per_plane = nphys[0] * nphys[1] * 8
+    if per_plane * nphys[2] <= STREAM_PARTICLES:
+        for sp in I.plasma(nphys, PML, D[0]):
+            pos, mom = pack_particles(sp["cell"], sp["off"], sp["u"], sp["w"], "fp32", device=device)
+            out.append((pos, mom, len(sp["w"]), sp["q"], sp["m"], sp["immobile"]))
+        return out
+    beam, planes = I.plasma_planes(nphys, PML, D[0])
+    n = per_plane * nphys[2]
+    recs = [(torch.empty((n, 4), dtype=torch.float32, device=device),
+             torch.empty((n, 4), dtype=torch.float32, device=device)) for _ in range(2)]
+    qm = [None, None]
+    for k, el, pr in planes:
+        for s_, sp in enumerate((el, pr)):
+            pos, mom = pack_particles(sp["cell"], sp["off"], sp["u"], sp["w"], "fp32", device="cpu")
+            recs[s_][0][k * per_plane:(k + 1) * per_plane].copy_(pos)
+            recs[s_][1][k * per_plane:(k + 1) * per_plane].copy_(mom)
+            qm[s_] = (sp["q"], sp["m"])
+    for s_ in range(2):
+        out.append((recs[s_][0], recs[s_][1], n, qm[s_][0], qm[s_][1], False))
+    for sp in beam:
+        pos, mom = pack_particles(sp["cell"], sp["off"], sp["u"], sp["w"], "fp32", device=device)
+        out.append((pos, mom, len(sp["w"]), sp["q"], sp["m"], sp["immobile"]))
+    return out
+
 
 def run_plasma(args):
     """Throughput on the thermal plasma + drifting beam workload (electrons
@@ -516,15 +553,14 @@ def run_plasma(args):
     from paper_2201_09084_gb300 import build as B
     B.build()
     nphys = tuple(int(x) for x in args.plasma_cells.split(","))
-    parts = I.plasma(nphys, PML, D[0])
+    species = plasma_species(nphys, "cuda")
     stream = torch.cuda.current_stream()
     sim = Sim(3, nphys, D, PML, cfl=0.99, order=1, prec="fp32", alpha_mode="damped", sort_every=0,
               stream=stream)
     keep = []
-    for sp in parts:
-        pos, mom = pack_particles(sp["cell"], sp["off"], sp["u"], sp["w"], "fp32")
-        sim.add_species(pos, mom, len(sp["w"]), sp["q"], sp["m"], sp["immobile"])
-        keep.append((pos, mom, sp["immobile"]))
+    for pos, mom, n, q, m, imm in species:
+        sim.add_species(pos, mom, n, q, m, imm)
+        keep.append((pos, mom, imm))
     sim.sort()
     if args.tuning:
         p_, k_ = (int(x) for x in args.tuning.split(","))
@@ -589,7 +625,7 @@ def run_plasma(args):
             "config": {"workload": f"thermal plasma + drifting beam: {nphys[0]}x{nphys[1]}x{nphys[2]} + "
                                    f"{PML[0]}-cell PML, e- and p+ 8 per cell, u_th 0.01, beam u_z 5, order 1, "
                                    "fp32 fields + float-float PML parts",
-                       "particles": int(sum(len(sp["w"]) for sp in parts if not sp["immobile"])),
+                       "particles": int(sum(sp[2] for sp in species if not sp[5])),
                        "sort_every": SORT_EVERY, "l2": "working set > L2"},
             "kernel_ms": {"push_deposit": t_pd, "field_step": t_f},
             "roofline": {"bound": "hbm", "kernel": "push_deposit (particle kernels)", "achieved": achieved,

@@ -178,7 +178,13 @@ def plasma(nphys, pml, d, ppc=8, u_th=0.01, beam_uz=5.0, beam_radius=16.0, beam_
     up = rng.normal(0.0, u_th, (n, 3))
     el = _pack(X, ue, np.full(n, w), 3)
     pr = _pack(X, up, np.full(n, w), 3)
-    # drifting beam: cylinder along z, front beam_length before the +z interface
+    bm, bi = _beam_cylinder(rng, lo, ncell, ppc, w, beam_uz, beam_radius, beam_length, beam_density)
+    return [dict(el, q=-Q_E, m=M_E, immobile=False), dict(pr, q=Q_E, m=M_P, immobile=False), bm, bi]
+
+
+def _beam_cylinder(rng, lo, ncell, ppc, w, beam_uz, beam_radius, beam_length, beam_density):
+    """The drifting electron beam of `plasma` (a cylinder along z whose front
+    sits beam_length cells before the +z interface) and its immobile ions."""
     zf = lo[2] + ncell[2] - beam_length
     cx, cy = lo[0] + ncell[0] / 2, lo[1] + ncell[1] / 2
     vol = np.pi * beam_radius ** 2 * beam_length
@@ -190,8 +196,37 @@ def plasma(nphys, pml, d, ppc=8, u_th=0.01, beam_uz=5.0, beam_radius=16.0, beam_
     ub[:, 2] = beam_uz
     bm = _pack(Xb, ub, np.full(nb, w), 3)
     bi = _pack(Xb, np.zeros((nb, 3)), np.full(nb, w), 3)
-    return [dict(el, q=-Q_E, m=M_E, immobile=False), dict(pr, q=Q_E, m=M_P, immobile=False),
-            dict(bm, q=-Q_E, m=M_E, immobile=False), dict(bi, q=Q_E, m=M_P, immobile=True)]
+    return dict(bm, q=-Q_E, m=M_E, immobile=False), dict(bi, q=Q_E, m=M_P, immobile=True)
+
+
+def plasma_planes(nphys, pml, d, ppc=8, u_th=0.01, beam_uz=5.0, beam_radius=16.0, beam_length=64.0,
+                  beam_density=0.1, seed=SEED_BASE + 13):
+    """The plasma + beam workload of `plasma`, drawn one z-plane of physical
+    cells at a time for boxes whose particles do not fit the host at once.
+    Plane k comes from its own stream (seed, k) and the beam from
+    (seed, nz), so the draws do not depend on how planes are grouped, and
+    host memory holds one plane.  Same distributions as `plasma` (other
+    draws).  Returns (beam species, generator of (k, electrons, protons))."""
+    lo = np.array([pml[0], pml[2], pml[4]], dtype=np.float64)
+    ncell = np.asarray(nphys, dtype=np.int64)
+    w = plasma_density(u_th, d) * d ** 3 / ppc
+    beam = _beam_cylinder(np.random.default_rng([seed, int(ncell[2])]), lo, ncell, ppc, w, beam_uz,
+                          beam_radius, beam_length, beam_density)
+    ij = np.stack(np.meshgrid(np.arange(ncell[0]), np.arange(ncell[1]), indexing="ij"), -1).reshape(-1, 2)
+    ij = np.repeat(ij, ppc, axis=0)
+    n = len(ij)
+
+    def planes():
+        for k in range(int(ncell[2])):
+            rng = np.random.default_rng([seed, k])
+            cells = np.column_stack([ij, np.full(n, k)])
+            X = lo + cells + rng.random((n, 3))
+            ue = rng.normal(0.0, u_th, (n, 3))
+            up = rng.normal(0.0, u_th, (n, 3))
+            yield (k, dict(_pack(X, ue, np.full(n, w), 3), q=-Q_E, m=M_E, immobile=False),
+                   dict(_pack(X, up, np.full(n, w), 3), q=Q_E, m=M_P, immobile=False))
+
+    return list(beam), planes()
 
 
 def random_moves(n, lo, hi, max_step=0.95, seed=SEED_BASE + 9, w_range=(0.5, 4.0)):

@@ -381,6 +381,40 @@ def cpu_sample(order, theta, sample, steps):
     return value, desc, step_full
 
 
+def cpu_batch_sample(nruns=4096, sample=64, steps=20, order=3):
+    """The oracle on a bounded sample of the batched 2D runs: the first
+    `sample` of the same `nruns` runs (their sizes, PML widths, angles and
+    Lorentz factors), one FP64 box each, `steps` steps, one after another on
+    one core.  The time per cell-step of the sample scales to the whole batch
+    by its cell count.  Returns (particle-steps/s, cell-updates/s,
+    description)."""
+    import oracle as O
+    from paper_2201_09084_gb300 import inputs as I
+    O.build()
+    r = I.batched_runs(nruns)
+    dt = O.yee_dt(D, 0.99, 2)
+    nx, nz, npml = r["nx"].astype(np.int64), r["nz"].astype(np.int64), r["npml"].astype(np.int64)
+    cells_all = int(np.sum((nx + 2 * npml) * (nz + 2 * npml)))
+    t = 0.0
+    cells_sample = 0
+    for k in range(sample):
+        p = int(npml[k])
+        sim = O.OracleSim(2, (int(nx[k]), 0, int(nz[k])), (p, p, 0, 0, p, p), D, dt, order=order,
+                          alpha_mode="damped")
+        X = I.absolute(r["cell"][k:k + 1], r["off"][k:k + 1])
+        u = r["u"][k].astype(np.float64)
+        sim.add_particles(X[:, 0], X[:, 1], X[:, 2], [u[0]], [u[1]], [u[2]], [1.0], r["q"], r["m"])
+        a = time.perf_counter()
+        sim.step(steps)
+        t += time.perf_counter() - a
+        cells_sample += (int(nx[k]) + 2 * p) * (int(nz[k]) + 2 * p)
+    per_cell_step = t / (steps * cells_sample)
+    step_all = per_cell_step * cells_all
+    desc = (f"FP64 C oracle, 1 thread: the first {sample} of the {nruns} runs, {steps} steps each, "
+            f"scaled by cells ({cells_sample} of {cells_all})")
+    return nruns / step_all, cells_all / step_all, desc
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -693,6 +727,10 @@ def main():
                               "fp64": run_batch(nb, 3, "fp64", nruns=args.batch_runs)}
             out["batch2d"]["fp32_over_fp64_particle_steps"] = (
                 out["batch2d"]["fp32"]["particle_steps_per_s"] / out["batch2d"]["fp64"]["particle_steps_per_s"])
+            if rank == 0 and world == 1 and not args.no_cpu_baseline:
+                bv, bc, bdesc = cpu_batch_sample(nruns=args.batch_runs)
+                out["batch2d"]["cpu_baseline"] = {"value": bv, "unit": "particle-steps/s", "cores": 1,
+                                                  "kind": "oracle", "sample": bdesc, "cell_updates_per_s": bc}
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
             v, desc, _ = cpu_sample(args.order, args.theta, 65536, 8)
             out["cpu_baseline"] = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",

@@ -81,3 +81,16 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert "4194304 macroparticles" in d["config"]["workload"]
+
+
+def test_batched_runs_cpu_baseline_is_a_scaled_oracle_sample():
+    """The batched runs' oracle baseline times a few of the same runs and
+    scales by cells: positive rates, cell-updates = particle-steps x mean
+    cells per run (one particle per run)."""
+    import bench
+    from paper_2201_09084_gb300 import inputs as I
+    ps, cu, desc = bench.cpu_batch_sample(nruns=16, sample=2, steps=2)
+    r = I.batched_runs(16)
+    cells = int(((r["nx"] + 2 * r["npml"]) * (r["nz"] + 2 * r["npml"])).sum())
+    assert ps > 0 and cu > 0 and "oracle" in desc
+    assert abs(cu / ps - cells / 16) < 1e-6 * cells

@@ -18,9 +18,13 @@ device); cell-updates/s of the Yee/PML update is reported beside it.
 
 Prints one JSON line.  Beside the FP32 result it carries "fp64": the same
 workload in the plain FP64 form (fields, particles and PML parts in FP64),
-and "batch2d": the batched 2D runs in FP32 and FP64.  --impl reference times
-the FP64 CPU oracle on a bounded sample of the same workload (see
-cpu_sample()).
+"batch2d": the batched 2D runs in FP32 and FP64 with the oracle timed on a
+sample of them, and "cpu_baseline": the oracle on a sample of the beam.
+"e2e" uploads the particles from pinned host memory once and reads each
+step's particle-step count back to the host.  --impl reference times the
+FP64 CPU oracle on a bounded sample of the same workload (see cpu_sample()).
+--plasma measures the thermal plasma + beam workload instead (its own JSON
+line); --precision-study compares the FP32 forms with FP64 and the oracle.
 """
 from __future__ import annotations
 

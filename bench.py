@@ -419,6 +419,112 @@ def cpu_batch_sample(nruns=4096, sample=64, steps=20, order=3):
     return nruns / step_all, cells_all / step_all, desc
 
 
+SP_NPHYS = (128, 0, 128)
+SP_PML = (16, 16, 0, 0, 16, 16)
+SP_GAMMA = float(np.sqrt(101.0))
+
+
+def single_particle_bytes():
+    """Algorithmic bytes of one FP64 field step of the 2D single-particle box:
+    interior cell E, B, J read and E, B written (120 B); PML cell 8 FP64 split
+    parts read and written plus J read and E, B written (200 B)."""
+    nint = SP_NPHYS[0] * SP_NPHYS[2]
+    total = (SP_NPHYS[0] + SP_PML[0] + SP_PML[1]) * (SP_NPHYS[2] + SP_PML[4] + SP_PML[5])
+    return 120 * nint + 200 * (total - nint), total
+
+
+def cpu_single_particle(steps):
+    """The oracle on the whole 2D single-particle workload (it is small
+    enough to run in full): 128 x 128 cells + 16-cell PML, an electron with
+    u_z = 10 and its motionless partner, order 1, damped PML, `steps` steps on
+    one core.  Returns (particle-steps/s, cell-updates/s, description)."""
+    import oracle as O
+    from paper_2201_09084_gb300 import inputs as I
+    O.build()
+    dt = O.yee_dt(D, 0.99, 2)
+    sim = O.OracleSim(2, SP_NPHYS, SP_PML, D, dt, order=1, alpha_mode="damped")
+    for sp in I.single_pair(2, SP_NPHYS, SP_PML, gamma=SP_GAMMA):
+        X = I.absolute(sp["cell"], sp["off"])
+        u = sp["u"].astype(np.float64)
+        sim.add_particles(X[:, 0], X[:, 1], X[:, 2], u[:, 0], u[:, 1], u[:, 2], sp["w"].astype(np.float64),
+                          sp["q"], sp["m"], sp["immobile"])
+    t, psteps = 0.0, 0
+    for _ in range(steps):
+        psteps += int(sim.particles()["alive"][0])   # the mover, before this step's push
+        a = time.perf_counter()
+        sim.step(1)
+        t += time.perf_counter() - a
+    _, total = single_particle_bytes()
+    desc = f"FP64 C oracle, 1 thread: the whole workload, {steps} steps"
+    return psteps / t, total * steps / t, desc
+
+
+def run_single_particle(args):
+    """The 2D FP64 single-particle workload of the paper's studies: 128 x 128
+    cells of 1 um + 16-cell PML on all sides, an electron with u_z = 10
+    (gamma = sqrt(101)) and its motionless partner at the centre moving into
+    the +z PML, order 1, damped PML, dt = 0.99 x the Courant limit.  W
+    untimed steps on a throw-away box, then `steps` steps of a fresh box from
+    t = 0 (the workload is 400 steps) through step_n, timed with CUDA events.
+    The step is one field update of 25,600 cells and a push of at most one
+    particle: launch- and latency-bound.  Prints its own JSON line."""
+    import torch
+    from paper_2201_09084_gb300 import inputs as I
+    from paper_2201_09084_gb300.api import Sim, pack_particles
+    from paper_2201_09084_gb300 import build as B
+    B.build()
+    stream = torch.cuda.current_stream()
+
+    def make():
+        sim = Sim(2, SP_NPHYS, D, SP_PML, cfl=0.99, order=1, prec="fp64", alpha_mode="damped", sort_every=0,
+                  stream=stream)
+        keep = []
+        for sp in I.single_pair(2, SP_NPHYS, SP_PML, gamma=SP_GAMMA):
+            pos, mom = pack_particles(sp["cell"], sp["off"], sp["u"], sp["w"], "fp64")
+            sim.add_species(pos, mom, len(sp["w"]), sp["q"], sp["m"], sp["immobile"])
+            keep.append((pos, mom))
+        return sim, keep
+
+    warm, keep_w = make()
+    warm.step(args.warmup)
+    warm.sync()
+    sim, keep = make()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
+    l0 = sim.launch_count()
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    psteps = sim.particle_steps()
+    launches = sim.launch_count() - l0
+    byts, total = single_particle_bytes()
+    peak, kind = measured_peak()
+    achieved = byts / (ms / args.steps / 1e3) / 1e9
+    out = {"metric": METRIC, "value": psteps / (ms / 1e3), "unit": "particle-steps/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "2D single particle: 128x128 + 16-cell PML, electron u_z 10 + partner, "
+                                  "order 1, fp64, damped PML", "cells": total},
+           "cell_updates_per_s": total * args.steps / (ms / 1e3),
+           "roofline": {"bound": "hbm", "kernel": "whole step (field update + push)", "achieved": achieved,
+                        "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"{kind} (copy)",
+                        "traffic": None, "algorithmic_bytes_per_step": byts,
+                        "note": "3.8 MB per step fits in L2; the step is launch- and latency-bound"},
+           "gpu_launches": int(launches), "clocks": clk}
+    if not args.no_cpu_baseline:
+        v, cu, desc = cpu_single_particle(args.steps)
+        out["cpu_baseline"] = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                               "sample": desc, "cell_updates_per_s": cu}
+    sim.close()
+    warm.close()
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -696,6 +802,8 @@ def main():
     ap.add_argument("--plasma", action="store_true",
                     help="throughput on the thermal plasma + beam workload (prints its own JSON line)")
     ap.add_argument("--plasma-cells", default="128,128,256", help="physical cells of the --plasma workload")
+    ap.add_argument("--single-particle", action="store_true",
+                    help="the 2D FP64 single-particle workload (run it with --steps 400; own JSON line)")
     ap.add_argument("--tuning", default=None,
                     help="P,KZ launch shapes instead of the autotuner (profiling captures)")
     args = ap.parse_args()
@@ -711,6 +819,8 @@ def main():
         out = run_precision_study(args) if rank == 0 else None
     elif args.plasma and args.impl == "gb300":
         out = run_plasma(args) if rank == 0 else None
+    elif args.single_particle and args.impl == "gb300":
+        out = run_single_particle(args) if rank == 0 else None
     elif args.impl == "reference":
         out = run_reference(args, rank, world)
     else:

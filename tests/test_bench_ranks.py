@@ -94,3 +94,14 @@ def test_batched_runs_cpu_baseline_is_a_scaled_oracle_sample():
     cells = int(((r["nx"] + 2 * r["npml"]) * (r["nz"] + 2 * r["npml"])).sum())
     assert ps > 0 and cu > 0 and "oracle" in desc
     assert abs(cu / ps - cells / 16) < 1e-6 * cells
+
+
+def test_single_particle_cpu_baseline_counts_the_mover_until_removal():
+    """The 2D single-particle oracle baseline runs the whole workload: the
+    electron (u_z = 10, 64 cells from the +z interface at 0.70 cells per
+    step) is pushed until it is removed at the outer PML edge, ~115 steps."""
+    import bench
+    ps, cu, desc = bench.cpu_single_particle(200)
+    pushes = 25600 * 200 * ps / cu
+    assert 100 <= round(pushes) <= 130, pushes
+    assert bench.single_particle_bytes() == (120 * 128 * 128 + 200 * (160 * 160 - 128 * 128), 25600)

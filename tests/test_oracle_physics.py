@@ -17,6 +17,13 @@
     (Sec. III.A, Fig. 2 discussion).  Cubic shapes as in App. A.
 Superposition: with prescribed trajectories the field update is linear, so
 the fields of two particles are the sum of the single-particle runs.
+Inside the PML (Eq. PMLfield, Sec. II.B): with the damped current and alpha
+built for the particle's own speed, the magnetic field of a uniformly moving
+charge that has entered the PML is alpha(z) times its boosted vacuum field.
+B is used because only currents produce it: the motionless partner adds a
+static E whose continuation into the PML the paper does not give (Eq.
+PMLfield describes a charge that has always moved).  The undamped and
+Berenger schemes, and alpha built for v = c, miss it by far.
 """
 import numpy as np
 import pytest
@@ -134,6 +141,68 @@ def test_boosted_coulomb_field_converges():
     e1 = _coulomb_error(1)
     e2 = _coulomb_error(2)
     assert max(e2.values()) < max(e1.values()), (e1, e2)
+
+
+def _pml_b_error(mode, steps=56, v_matched=True, g=1.1, coef=1.2, delta=24.0):
+    """Max relative deviation of B from alpha(z) x Eq. physicalfield on the
+    shell 6-9 cells around a uniformly moving charge ball that started 4
+    cells before a +z PML (40 cells, sigma of Eq. conductivity with
+    delta = 24 cells), over the shell's nodes at least one cell inside the
+    PML and behind the start transient."""
+    D = 1e-6
+    d = (D, D, D)
+    dt = O.yee_dt(d, 0.99, 3)
+    box, nzp, T, R, npart = 64, 40, 40, 2.0, 2000
+    u = np.sqrt(g * g - 1)
+    v = u / g
+    va = v * C if v_matched else C
+    s = O.OracleSim(3, (box, box, nzp), (0, 0, 0, 0, 0, T), d, dt, order=3, alpha_mode=mode,
+                    sig_coef=coef, delta=delta, sig_exp=2.0, v_assumed=va)
+    x0 = np.array([box / 2 + 0.3, box / 2 + 0.1, nzp - 4 + 0.2])
+    q = -O.Q_E
+    rng = np.random.default_rng(0)
+    p = rng.normal(size=(npart, 3))
+    p /= np.linalg.norm(p, axis=1)[:, None]
+    p *= R * rng.random(npart)[:, None] ** (1 / 3)
+    P = x0 + p
+    w = np.ones(npart) / npart
+    z = np.zeros(npart)
+    s.add_particles(P[:, 0], P[:, 1], P[:, 2], z, z, np.full(npart, u), w, q, O.M_E)
+    s.add_particles(P[:, 0], P[:, 1], P[:, 2], z, z, z, w, -q, O.M_E, immobile=True)
+    s.set_prescribed(True)
+    s.step(steps)
+    t = steps * dt
+    zp = x0[2] + v * C * t / D
+    ct = C * t / D
+    nx, ny, nz = s.nn
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    worst = {}
+    for comp, st in (("Bx", (0, 0.5, 0.5)), ("By", (0.5, 0, 0.5))):
+        F = s.field(comp)
+        Pp = np.stack([(i + st[0]), (j + st[1]), (k + st[2])]).astype(float)
+        rx = Pp - np.array([x0[0], x0[1], zp])[:, None, None, None]
+        rp = np.sqrt(rx[0] ** 2 + rx[1] ** 2 + g * g * rx[2] ** 2) * D
+        Em = g * q / (4 * np.pi * O.EPS0) / rp ** 3 * rx * D
+        depth = np.maximum(Pp[2] - nzp, 0.0)
+        # Eq. alpha with sigma of Eq. conductivity (depths in cells, v in units of c):
+        # int_0^d sigma/(eps0 v) dz = coef (c/v) delta (d/delta)^3 / 3
+        alpha = np.exp(-(1.0 / v) * coef * delta * (depth / delta) ** 3 / 3)
+        an = alpha * (v / C) * (-Em[1] if comp == "Bx" else Em[0])
+        r = np.sqrt(((Pp - x0[:, None, None, None]) ** 2).sum(0))
+        dp = np.sqrt((rx ** 2).sum(0))
+        m = (dp >= 6) & (dp < 9) & (r <= 0.6 * ct) & (Pp[2] >= nzp + 1)
+        assert m.sum() > 1000
+        worst[comp] = float(np.abs(F[m] - an[m]).max() / np.abs(an[m]).max())
+    return worst
+
+
+def test_magnetic_field_inside_pml_is_alpha_scaled():
+    for steps in (46, 56):                     # alpha at the charge 0.54, 0.24
+        e = _pml_b_error("damped", steps)
+        assert max(e.values()) < 0.10, (steps, e)
+    for mode in ("one", "zero"):
+        assert min(_pml_b_error(mode).values()) > 0.5, mode
+    assert min(_pml_b_error("damped", v_matched=False).values()) > 0.3
 
 
 def _exit_run(mode, steps, theta, ref=False, gamma=10.0, nphys=16, npml=8, m=26):

@@ -107,3 +107,24 @@ def test_weight_damping_lifts_the_velocity_limit():
     # with the particle's own velocity in Eq. alpha the damped current does about as well
     e_matched = O.rel_error(_exit_2d("damped", steps, gamma, v_assumed=0.6 * C)[0], ref, offset)
     assert e["weight"] < 2.0 * e_matched, (e, e_matched)
+
+
+def test_alpha_built_for_c_costs_accuracy_only_for_slow_particles():
+    """Eq. alpha with v = c (the paper's choice) against alpha built for the
+    particle's own speed (Sec. III, discussion of the velocity limitation):
+    for a slow particle (gamma = 1.05, v = 0.3 c) the v = c damping leaves an
+    interior error many times that of the matched one, and weight damping
+    recovers most of it; for gamma v / c > 1 the two are the same."""
+    out = {}
+    for gamma in (1.05, 10.0):
+        v = np.sqrt(gamma ** 2 - 1) / gamma
+        steps = int(40 / (v * 0.70) + 20)          # 24 cells to the PML + 16 through it, then 20 more
+        ref, off_r = _exit_2d(None, steps, gamma, ref=True)
+        offset = (off_r - 16, 0, off_r - 16)
+        out[gamma] = {"c": O.rel_error(_exit_2d("damped", steps, gamma)[0], ref, offset),
+                      "own": O.rel_error(_exit_2d("damped", steps, gamma, v_assumed=v * C)[0], ref, offset),
+                      "weight": O.rel_error(_exit_2d("weight", steps, gamma)[0], ref, offset)}
+    slow, fast = out[1.05], out[10.0]
+    assert slow["c"] > 10 * slow["own"], out
+    assert slow["weight"] < 0.25 * slow["c"], out
+    assert abs(fast["c"] - fast["own"]) < 0.1 * fast["own"], out

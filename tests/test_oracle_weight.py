@@ -15,6 +15,9 @@ path, trapezoid rule per step).
 - The point of the scheme: for a particle slower than the v assumed by
   Eq. alpha, weight damping leaves a smaller Eq. error than the damped
   current with v = c (2D, cubic shapes, exit through the +z PML).
+- The v = c assumption costs accuracy only for slow particles: at
+  gamma = 1.05 alpha built for c errs many times more than alpha built for
+  the particle's speed; at gamma = 10 the two are the same.
 """
 import numpy as np
 import pytest

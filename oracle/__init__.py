@@ -362,11 +362,12 @@ class OracleSim:
         return out
 
 
-def rel_error(sim, ref, offset=(0, 0, 0)):
+def rel_error(sim, ref, offset=(0, 0, 0), parts=False):
     """Eq. error: int[(E-Eref)^2 + c^2 (B-Bref)^2] / int[Eref^2 + c^2 Bref^2]
     over the physical cells of ``sim``; ``offset`` is the node index of sim's
     node (0,0,0) inside ``ref``.  Every component is sampled at its own
-    staggered points that lie in the closed physical box."""
+    staggered points that lie in the closed physical box.  parts=True
+    returns (numerator, denominator) instead of their ratio."""
     num = 0.0
     den = 0.0
     lo = [sim.pml[0], sim.pml[2], sim.pml[4]]
@@ -395,4 +396,4 @@ def rel_error(sim, ref, offset=(0, 0, 0)):
             Bv = b[slr[2], slr[1], slr[0]]
             num += scale * np.sum((A - Bv) ** 2)
             den += scale * np.sum(Bv ** 2)
-    return num / den
+    return (num, den) if parts else num / den

@@ -17,6 +17,10 @@
     (Sec. III.A, Fig. 2 discussion).  Cubic shapes as in App. A.
 Superposition: with prescribed trajectories the field update is linear, so
 the fields of two particles are the sum of the single-particle runs.
+After the particle has left (Sec. II.A): Berenger's scheme (alpha = 0, the
+particle removed at the interface) leaves a static error field in the box
+that does not decay, while alpha = 1 removes it and leaves only a pulse that
+propagates out, so its error falls with time.
 Inside the PML (Eq. PMLfield, Sec. II.B): with the damped current and alpha
 built for the particle's own speed, the magnetic field of a uniformly moving
 charge that has entered the PML is alpha(z) times its boosted vacuum field.
@@ -259,3 +263,16 @@ def test_superposition(dim):
         tot = a.field(f) + b.field(f)
         scale = np.abs(tot).max()
         assert np.abs(ab.field(f) - tot).max() < 1e-13 * scale
+
+
+def test_alpha_zero_leaves_a_static_error_alpha_one_a_pulse_that_leaves():
+    from test_oracle_weight import _exit_2d
+    err = {}
+    for steps in (100, 220):        # absorbed by ~90; the reference box's walls answer after ~260
+        ref, off_r = _exit_2d(None, steps, 10.0, ref=True)
+        offset = (off_r - 16, 0, off_r - 16)
+        err[steps] = {m: O.rel_error(_exit_2d(m, steps, 10.0)[0], ref, offset, parts=True)[0]
+                      for m in ("zero", "one")}
+    assert err[220]["zero"] > 0.9 * err[100]["zero"], err
+    assert err[220]["one"] < 0.3 * err[100]["one"], err
+    assert err[100]["one"] < 0.1 * err[100]["zero"], err

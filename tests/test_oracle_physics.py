@@ -21,6 +21,9 @@ After the particle has left (Sec. II.A): Berenger's scheme (alpha = 0, the
 particle removed at the interface) leaves a static error field in the box
 that does not decay, while alpha = 1 removes it and leaves only a pulse that
 propagates out, so its error falls with time.
+The damped scheme is built for particles that leave (Sec. II, limitations):
+for one emitted from inside the PML into the box it gains little over
+alpha = 1 and leaves a far larger error than for a particle that exits.
 Inside the PML (Eq. PMLfield, Sec. II.B): with the damped current and alpha
 built for the particle's own speed, the magnetic field of a uniformly moving
 charge that has entered the PML is alpha(z) times its boosted vacuum field.
@@ -276,3 +279,36 @@ def test_alpha_zero_leaves_a_static_error_alpha_one_a_pulse_that_leaves():
     assert err[220]["zero"] > 0.9 * err[100]["zero"], err
     assert err[220]["one"] < 0.3 * err[100]["one"], err
     assert err[100]["one"] < 0.1 * err[100]["zero"], err
+
+
+def _emit_2d(mode, steps, ref=False, gamma=10.0, n=48, npml=16, m=90, depth=8.0):
+    """2D box with 16-cell PML; a particle starts `depth` cells inside the -z
+    PML (with its motionless partner) and moves along +z into the box."""
+    d = (1e-6, 1e-6, 1e-6)
+    dt = O.yee_dt(d, 0.99, 2)
+    if ref:
+        s = O.OracleSim(2, (n + 2 * m, 0, n + 2 * m), (0,) * 6, d, dt, order=3, alpha_mode="one")
+        off = m
+    else:
+        s = O.OracleSim(2, (n, 0, n), (npml, npml, 0, 0, npml, npml), d, dt, order=3, alpha_mode=mode)
+        off = npml
+    X = [off + n / 2 + 0.3, 0.0, off - depth + 0.2]
+    _pair(s, X, [0.0, 0.0, np.sqrt(gamma ** 2 - 1)])
+    s.set_prescribed(True)
+    s.step(steps)
+    return s, off
+
+
+def test_damped_scheme_is_not_built_for_emitted_particles():
+    from test_oracle_weight import _exit_2d
+    steps = 50                                     # the emitted particle crossed at ~12
+    ref, off_r = _emit_2d(None, steps, ref=True)
+    offset = (off_r - 16, 0, off_r - 16)
+    emitted = {m: O.rel_error(_emit_2d(m, steps)[0], ref, offset) for m in ("one", "damped")}
+    steps = 100                                    # the exiting particle crossed at ~34
+    ref, off_r = _exit_2d(None, steps, 10.0, ref=True)
+    offset = (off_r - 16, 0, off_r - 16)
+    exiting = {m: O.rel_error(_exit_2d(m, steps, 10.0)[0], ref, offset) for m in ("one", "damped")}
+    assert emitted["damped"] > 0.8 * emitted["one"], (emitted, exiting)
+    assert exiting["damped"] < 0.4 * exiting["one"], (emitted, exiting)
+    assert emitted["damped"] > 5 * exiting["damped"], (emitted, exiting)

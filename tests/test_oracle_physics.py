@@ -212,6 +212,56 @@ def test_magnetic_field_inside_pml_is_alpha_scaled():
     assert min(_pml_b_error("damped", v_matched=False).values()) > 0.3
 
 
+def test_boosted_coulomb_field_2d():
+    """2D (x, z) form of check (b): a uniformly moving line charge (lambda = q
+    per metre of y, a macroparticle being 1 m long) carries
+    E = gamma lambda / (2 pi eps0) (x, z - v t) / r'^2 with
+    r'^2 = x^2 + gamma^2 (z - v t)^2 and B_y = v E_x / c^2, plus its
+    partner's static field -lambda / (2 pi eps0) (x, z) / r^2; compared on a
+    shell 6-9 cells around a charge disk behind the start transient."""
+    D = 1e-6
+    d = (D, D, D)
+    dt = O.yee_dt(d, 0.99, 2)
+    box, steps, R, npart, g = 96, 50, 2.0, 2000, 1.1
+    s = O.OracleSim(2, (box, 0, box), (0,) * 6, d, dt, order=3, alpha_mode="one")
+    u = np.sqrt(g * g - 1)
+    v = u / g
+    x0 = np.array([box / 2 + 0.3, 0.0, box / 2 + 0.2])
+    q = -O.Q_E
+    rng = np.random.default_rng(0)
+    ph = 2 * np.pi * rng.random(npart)
+    rr = R * np.sqrt(rng.random(npart))
+    P = np.stack([x0[0] + rr * np.cos(ph), np.zeros(npart), x0[2] + rr * np.sin(ph)], 1)
+    w = np.ones(npart) / npart
+    z = np.zeros(npart)
+    s.add_particles(P[:, 0], P[:, 1], P[:, 2], z, z, np.full(npart, u), w, q, O.M_E)
+    s.add_particles(P[:, 0], P[:, 1], P[:, 2], z, z, z, w, -q, O.M_E, immobile=True)
+    s.set_prescribed(True)
+    s.step(steps)
+    t = steps * dt
+    zp = x0[2] + v * C * t / D
+    ct = C * t / D
+    lam = q                                        # weights sum to 1; L_y = 1 m
+    nx, _, nz = s.nn
+    k, i = np.meshgrid(np.arange(nz), np.arange(nx), indexing="ij")
+    for comp, st in (("Ex", (0.5, 0)), ("Ez", (0, 0.5)), ("By", (0.5, 0.5))):
+        F = s.field(comp)[:, 0, :]
+        Px, Pz = i + st[0], k + st[1]
+        rx, rz = (Px - x0[0]) * D, (Pz - zp) * D
+        rp2 = rx ** 2 + g * g * rz ** 2
+        Em = g * lam / (2 * np.pi * O.EPS0) * np.stack([rx, rz]) / rp2
+        sx, sz = (Px - x0[0]) * D, (Pz - x0[2]) * D
+        r2 = sx ** 2 + sz ** 2
+        Es = -lam / (2 * np.pi * O.EPS0) * np.stack([sx, sz]) / r2
+        an = {"Ex": Em[0] + Es[0], "Ez": Em[1] + Es[1], "By": (v / C) * Em[0]}[comp]
+        dp = np.sqrt(rx ** 2 + rz ** 2) / D
+        r = np.sqrt(r2) / D
+        m = (dp >= 6) & (dp < 9) & (r <= 0.6 * ct) & (r >= 6)
+        assert m.sum() > 100
+        err = float(np.abs(F[m] - an[m]).max() / np.abs(an[m]).max())
+        assert err < 0.04, (comp, err)
+
+
 def _exit_run(mode, steps, theta, ref=False, gamma=10.0, nphys=16, npml=8, m=26):
     d = (1e-6, 1e-6, 1e-6)
     dt = O.yee_dt(d, 0.99, 3)

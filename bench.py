@@ -401,6 +401,7 @@ def cpu_batch_sample(nruns=4096, sample=64, steps=20, order=3):
     cells_all = int(np.sum((nx + 2 * npml) * (nz + 2 * npml)))
     t = 0.0
     cells_sample = 0
+    sample = min(sample, nruns)
     for k in range(sample):
         p = int(npml[k])
         sim = O.OracleSim(2, (int(nx[k]), 0, int(nz[k])), (p, p, 0, 0, p, p), D, dt, order=order,

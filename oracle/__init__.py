@@ -60,6 +60,7 @@ def lib():
             L.ora_destroy.argtypes = [C.c_void_p]
             L.ora_set_prescribed.argtypes = [C.c_void_p, C.c_int]
             L.ora_set_filter.argtypes = [C.c_void_p, C.c_int]
+            L.ora_set_conductor.argtypes = [C.c_void_p, C.c_void_p]
             L.ora_filter_J.argtypes = [C.c_void_p]
             L.ora_set_face_alpha.argtypes = [C.c_void_p, ip]
             L.ora_set_face_alpha.restype = C.c_int
@@ -241,6 +242,20 @@ class OracleSim:
             self.set_face_alpha(face_alpha)
         if filter_passes:
             lib().ora_set_filter(self._h, int(filter_passes))
+
+    def set_conductor(self, mask):
+        """Zeroed-field (perfect conductor) cells: mask of shape (Nz, Ny, Nx)
+        over the cells of the whole grid (Ny = 1 in 2D), True where the cell
+        is a conductor; None removes them.  Every E component on a marked
+        cell's edges is zero after each E update."""
+        if mask is None:
+            lib().ora_set_conductor(self._h, None)
+            return
+        m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8))
+        ny = self.nn[1] - 1 if self.dim == 3 else 1
+        assert m.shape == (self.nn[2] - 1, ny, self.nn[0] - 1), m.shape
+        self._cond = m
+        lib().ora_set_conductor(self._h, m.ctypes.data_as(C.c_void_p))
 
     def filter_J(self):
         """One binomial pass per axis on the deposited current (App. A)."""

@@ -77,6 +77,7 @@ typedef struct ora_sim {
   long np, cap;
   double *X[3], *X0[3], *u[3], *w, *q, *m;
   int *alive, *immobile, *moved;
+  unsigned char* cond;              /* conductor cells (NULL: none), i + N0 (j + N1 k) */
 } ora_sim;
 
 /* ------------------------------------------------------------------------- */
@@ -190,6 +191,7 @@ void ora_destroy(ora_sim* s) {
     free(s->X[c]); free(s->X0[c]); free(s->u[c]);
   }
   free(s->w); free(s->q); free(s->m); free(s->alive); free(s->immobile); free(s->moved);
+  free(s->cond);
   free(s);
 }
 
@@ -621,8 +623,50 @@ void ora_filter_J(ora_sim* s) {
 /* Number of binomial passes applied to J at the start of each E update. */
 void ora_set_filter(ora_sim* s, int passes) { s->filter_passes = passes > 0 ? passes : 0; }
 
+/* Zeroed-field cells (the cavity run of Sec. III has cells where E and B
+ * are zero; the paper gives no geometry).  A marked cell is a perfect
+ * conductor: every E component on its 12 edges is zero after each E update,
+ * so E is tangentially zero on its faces and B inside it keeps its initial
+ * value.  mask: one byte per cell of the whole grid (PML included), laid out
+ * i + N0 (j + N1 k) (N1 = 1 in 2D); NULL removes all.  Returns 0. */
+int ora_set_conductor(ora_sim* s, const unsigned char* mask) {
+  free(s->cond);
+  s->cond = NULL;
+  if (!mask) return 0;
+  const long N1 = s->dim == 3 ? s->N[1] : 1;
+  const long nc = (long)s->N[0] * N1 * s->N[2];
+  s->cond = malloc(nc);
+  memcpy(s->cond, mask, nc);
+  return 0;
+}
+
+static void zero_E(ora_sim* s, int c, long i, long j, long k) {
+  const long id = IX(s, i, j, k);
+  s->E[c][id] = 0.0;
+  s->Es[c][0][id] = 0.0;
+  s->Es[c][1][id] = 0.0;
+}
+
+static void apply_conductor(ora_sim* s) {
+  const int d3 = s->dim == 3;
+  const long N0 = s->N[0], N1 = d3 ? s->N[1] : 1, N2 = s->N[2];
+  for (long k = 0; k < N2; ++k)
+    for (long j = 0; j < N1; ++j)
+      for (long i = 0; i < N0; ++i) {
+        if (!s->cond[i + N0 * (j + N1 * k)]) continue;
+        const long jt = d3 ? 1 : 0;   /* the y nodes of the cell: j, j + 1 (2D: 0) */
+        for (long b = 0; b <= jt; ++b)
+          for (long c = 0; c <= 1; ++c) zero_E(s, 0, i, j + b, k + c);       /* Ex(i+1/2, ., .) */
+        for (long a = 0; a <= 1; ++a)
+          for (long c = 0; c <= 1; ++c) zero_E(s, 1, i + a, j, k + c);       /* Ey(., j+1/2, .) */
+        for (long a = 0; a <= 1; ++a)
+          for (long b = 0; b <= jt; ++b) zero_E(s, 2, i + a, j + b, k);      /* Ez(., ., k+1/2) */
+      }
+}
+
 /* E^{n+1} from E^n, B^{n+1/2} and the damped (and filtered) J^{n+1/2}
- * (Eqs. MaxwellE, MaxwellSum; split parts in PML cells, Sec. II.B). */
+ * (Eqs. MaxwellE, MaxwellSum; split parts in PML cells, Sec. II.B), then the
+ * conductor cells' edges set to zero. */
 void ora_field_E(ora_sim* s) {
   for (int f = 0; f < s->filter_passes; ++f) ora_filter_J(s);
   const double c2 = ORA_C * ORA_C, dt = s->dt;
@@ -668,6 +712,7 @@ void ora_field_E(ora_sim* s) {
         s->E[2][id] = advance(s->E[2][id], &s->Es[2][0][id], &s->Es[2][1][id], R, sA, sB,
                               -s->J[2][id] / ORA_EPS0, dt);
       }
+  if (s->cond) apply_conductor(s);
 }
 
 /* B^{n+3/2} = B^{n+1/2} - dt curl E^{n+1}  (Eqs. MaxwellB, MaxwellSum). */

@@ -256,10 +256,11 @@ int run_particles(picpml_ctx* ctx, int mode) {
   }
   if (fixed) {
     const double* d = ctx->gd.d;
-    // One integer unit is e/(6 2^24) of charge crossing a cell face (3D; in
-    // 2D the faces are 1 m long along y), so K_c = -e/(eps0 face area)/unit.
-    // The 2D J_y sums shape products times v_y/c with the charge sign already
-    // applied, so one unit is e c dt (v_y/c)/(eps0 dx dz Ly) of J' = J dt/eps0.
+    // Every integer sum already carries the particle's charge number q/e.
+    // J_x, J_z (and 3D J_y) are minus the prefix sums of Esirkepov's W, one
+    // unit being e/(6 2^24) of charge crossing a cell face (in 2D the faces
+    // are 1 m long along y): K_c = -e/(eps0 face area)/(6 2^24) of J' = J dt/eps0.
+    // The 2D J_y sums shape products times v_y/c: K_y = +e c dt/(eps0 dx dz Ly)/(6 2^24).
     const double Ly = 1.0;
     const double K[3] = {ctx->gd.dim == 3 ? -kQe / (kEps0 * d[1] * d[2]) / kFixUnit : -kQe / (kEps0 * d[2] * Ly) / kFixUnit,
                          ctx->gd.dim == 3 ? -kQe / (kEps0 * d[0] * d[2]) / kFixUnit

@@ -59,6 +59,43 @@ def test_init_rejects_bad_descriptions_without_gpu(lib):
     assert b"Courant" in L.load().pic_last_error(None)
 
 
+def test_init_rejects_each_bad_field_without_gpu(lib):
+    """Every descriptor check answers PIC_EINVAL with its own message before
+    any device work: precision, filter passes, cell counts and sizes, and a
+    Courant fraction outside (0, 1] when dt is left to the library."""
+    from paper_2201_09084_gb300 import _lib as L
+    lb = L.load()
+    ctx = ctypes.c_void_p()
+
+    def good():
+        g = L.GridDesc()
+        g.dim, g.shape_order, g.prec = 3, 1, 0
+        for a in range(3):
+            g.n[a] = 16
+            g.d[a] = 1e-6
+        g.dt, g.cfl = 0.0, 0.9
+        return g
+
+    cases = [("prec", 7, b"prec"), ("filter_passes", 9, b"filter_passes"),
+             ("filter_passes", -1, b"filter_passes"), ("cfl", 1.5, b"cfl"), ("cfl", 0.0, b"cfl")]
+    for field, value, msg in cases:
+        g = good()
+        setattr(g, field, value)
+        assert lb.pic_init(ctypes.byref(ctx), ctypes.byref(g), None) == -1, field
+        assert msg in lb.pic_last_error(None), (field, lb.pic_last_error(None))
+    for a, (n, d) in enumerate([(0, 1e-6), (16, 0.0), (16, -1e-6)]):
+        g = good()
+        g.n[a], g.d[a] = n, d
+        assert lb.pic_init(ctypes.byref(ctx), ctypes.byref(g), None) == -1
+        assert b"positive" in lb.pic_last_error(None)
+    # in 2D the y extent is ignored
+    g = good()
+    g.dim, g.n[1], g.d[1], g.prec = 2, 0, 0.0, 7
+    assert lb.pic_init(ctypes.byref(ctx), ctypes.byref(g), None) == -1
+    assert b"prec" in lb.pic_last_error(None)
+    assert lb.pic_init(None, ctypes.byref(g), None) == -1
+
+
 def test_struct_layouts_match_the_header(tmp_path):
     """The binding's ctypes structures have the header's sizes and field
     offsets (a C program compiled against include/picpml.h prints them)."""

@@ -49,8 +49,10 @@ typedef enum {
   PIC_ECFL = -4,        /* dt above the Yee Courant limit */
   PIC_EOVERFLOW = -5,   /* fixed-point current accumulator overflow, or an
                            injection past a species' capacity */
-  PIC_ETIMEOUT = -6,    /* a bounded device wait gave up (reserved: no kernel
-                           waits on another block) */
+  PIC_ETIMEOUT = -6,    /* a bounded device wait gave up: the tile kernel
+                           (PIC_TUNING_TILE) waits at most 2 s for the TMA
+                           copy of a field box, then stops and reports this
+                           at pic_sync */
   PIC_ENOTIMPL = -7,    /* combination not built (reserved: pic_init takes
                            every dim, order, precision and alpha mode; the
                            batch API takes FP32 and FP64 and answers
@@ -227,9 +229,11 @@ int push_deposit(picpml_ctx* ctx);
  * then field_step; particles are sorted by cell every sort_every steps. */
 int step_n(picpml_ctx* ctx, int n);
 
-/* Sorts every species by cell (counting sort on a tile-major key: 4x4x4-cell
- * tiles, then the cell inside the tile; the order within a cell is not kept)
- * and drops removed particles; the live count is updated on the device. */
+/* Sorts every species by cell (counting sort on a tile-major key: 8x4x4-cell
+ * tiles in 3D, 4x4 in 2D, then the cell inside the tile, x fastest; the
+ * order within a cell is not kept) and drops removed particles; the live
+ * count is updated on the device.  In 3D it also records where each tile's
+ * particles end, the work ranges of the tile kernel (PIC_TUNING_TILE). */
 int pic_sort(picpml_ctx* ctx);
 
 /* Node counts of the field arrays (nx, ny, nz): N+1 per axis (ny = 1 in 2D),
@@ -289,8 +293,16 @@ int pic_autotune(picpml_ctx* ctx, int steps, int* particles_per_thread, int* z_n
  * another context).  Particles per thread (order 1; order 3 in 3D): 4 or 8
  * = the shared-memory chunk kernel with that many particles per thread
  * (dense particles), 1 = one thread per particle with global atomics (a few
- * particles per cell), 0 = default (4; FP64 uses 4 for 8).  z nodes per
- * thread of the field kernels: 1, 2 or 4. */
+ * particles per cell), 0 = default (4; FP64 uses 4 for 8), PIC_TUNING_TILE
+ * = the tile-resident kernel: 3D PIC_FP32 boxes of shape order 1 only (else
+ * the default), one launch for every species sorted since it was added
+ * (pic_sort or sort_every; the others run one thread per particle): a block
+ * per 16x4x4-cell unit loads the unit's E and B box with TMA, pushes the
+ * particles that sat in the unit at the last sort, and adds the unit's
+ * current box to the grid once, damped by alpha (a thermal plasma's few
+ * particles per cell and short moves).  z nodes per thread of the field
+ * kernels: 1, 2 or 4. */
+#define PIC_TUNING_TILE 2
 int pic_set_tuning(picpml_ctx* ctx, int particles_per_thread, int z_nodes_per_thread);
 
 /* Particle-steps done so far: the number of live particles each push has

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libpicpml.so")
 PIC_FP32, PIC_FP64, PIC_FP32_FIXED64 = 0, 1, 2
 PREC = {"fp32": PIC_FP32, "fp64": PIC_FP64, "fixed64": PIC_FP32_FIXED64}
 ALPHA = {"zero": 0, "one": 1, "damped": 2, "weight": 3}
+TUNING_TILE = 2   # PIC_TUNING_TILE: the tile-resident particle kernel
 STATUS = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECUDA", -4: "PIC_ECFL",
           -5: "PIC_EOVERFLOW", -6: "PIC_ETIMEOUT", -7: "PIC_ENOTIMPL", -8: "PIC_ESTATE",
           -9: "PIC_EPARTICLE"}

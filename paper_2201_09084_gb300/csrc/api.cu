@@ -52,6 +52,12 @@ cudaError_t launch_inject(int pbytes, void* pos, void* mom, long long* n_dev, lo
 cudaError_t static_diag_buffers(double** rho, double** out, long long* cap);
 cudaError_t launch_sort(const Geom&, int pbytes, void* pos, void* mom, long long* n_dev, long long cap,
                         unsigned* scratch, void* tmp_pos, void* tmp_mom, cudaStream_t);
+long long tile_count(const Geom&);
+cudaError_t launch_tile_ends(const Geom&, const unsigned* cursor, long long* tile_end, cudaStream_t);
+cudaError_t make_tile_tensor_map(const Geom&, const float* base, void* map_out);
+int tile_map_bytes();
+cudaError_t launch_tile(const Geom&, const Tables&, const FieldPtrs<float>&, const TileLaunch&, const void* map,
+                        unsigned* status, unsigned long long* pushed, int nsm, cudaStream_t);
 }  // namespace picpml
 
 namespace picpml {
@@ -96,7 +102,9 @@ namespace {
 struct Species {
   pic_species desc{};
   long long* n_dev = nullptr;
-  void* save = nullptr;      // x^n saved by push() for deposit()
+  void* save = nullptr;      // x^n saved by push() for deposit() (allocated at the first stage call)
+  long long* tile_end = nullptr;   // per sort tile: end of its particles at the last sort (3D)
+  bool tiled = false;              // sorted since registration: tile_end is valid
   void* tmp_pos = nullptr;   // sort scratch, allocated at the first sort
   void* tmp_mom = nullptr;
   double ke = 0, cj[3] = {0, 0, 0}, cjy2d = 0;
@@ -138,7 +146,10 @@ struct picpml_ctx {
   int prescribed = 0;
   int ppt = 0;        // particles per thread of the shared-memory chunk kernels (order 1; order 3
                       // in 3D): 4 or 8 (0 = default 4), or 1 = one thread per particle with
-                      // global atomics
+                      // global atomics, or PIC_TUNING_TILE = the tile-resident kernel (3D FP32
+                      // order 1, sorted species)
+  alignas(64) unsigned char tmap[128];   // TMA tensor map of the FP32 field arrays (3D)
+  bool tmap_ok = false;
   int kz = 1;         // nodes per thread along z in the field kernels
   long long steps_done = 0;
   long long launches = 0;
@@ -231,6 +242,44 @@ SpeciesPtrs<T> species_ptrs(picpml_ctx* ctx, Species& s) {
   return p;
 }
 
+// The tile-resident kernel serves 3D FP32 (not fixed-point) order-1 boxes.
+bool tile_capable(picpml_ctx* ctx) {
+  return ctx->gd.dim == 3 && ctx->gd.prec == PIC_FP32 && ctx->gd.shape_order == 1 && ctx->tmap_ok;
+}
+
+// x^n scratch of the stage calls push() / deposit(), allocated on first use.
+int ensure_save(picpml_ctx* ctx, Species& s) {
+  if (s.save) return PIC_OK;
+  s.save = dev_alloc(ctx, (size_t)std::max<long long>(s.desc.capacity, 1) * ctx->pbytes());
+  return s.save ? PIC_OK : fail(ctx, PIC_ENOMEM, "species scratch");
+}
+
+// One launch of the tile-resident kernel for every sorted mobile species (up
+// to kTileMaxSpecies); the others are marked in `done` as not handled.
+int run_tile(picpml_ctx* ctx, std::vector<char>& done) {
+  TileLaunch L{};
+  L.prescribed = ctx->prescribed;
+  const FieldPtrs<float>& f = ctx->ff;
+  const float* base = f.E[0];
+  for (int c = 0; c < 3; ++c) {
+    L.arr_E[c] = (int)((f.E[c] - base) / ctx->g.size);
+    L.arr_Bh[c] = (int)((f.Bh[c] - base) / ctx->g.size);
+    L.arr_Bp[c] = (int)((f.Bp[c] - base) / ctx->g.size);
+  }
+  for (size_t i = 0; i < ctx->sp.size(); ++i) {
+    Species& s = ctx->sp[i];
+    if (s.desc.immobile || s.desc.capacity <= 0 || !s.tiled || L.nsp >= kTileMaxSpecies) continue;
+    L.s[L.nsp].sp = species_ptrs<float>(ctx, s);
+    L.s[L.nsp].tile_end = s.tile_end;
+    ++L.nsp;
+    done[i] = 1;
+  }
+  if (L.nsp == 0) return PIC_OK;
+  CK(launch_tile(ctx->g, ctx->tb, f, L, ctx->tmap, ctx->status, ctx->pushed, ctx->nsm, ctx->stream));
+  ctx->launches += 1;
+  return PIC_OK;
+}
+
 template <typename T>
 int run_particles(picpml_ctx* ctx, int mode) {
   const bool fixed = ctx->fixed() && mode != 0;
@@ -239,11 +288,26 @@ int run_particles(picpml_ctx* ctx, int mode) {
     const size_t jb = (size_t)ctx->g.size * sizeof(long long);
     for (int c = 0; c < 3; ++c) CK(cudaMemsetAsync(ctx->ff.Jq[c], 0, jb, ctx->stream));
   }
-  for (auto& s : ctx->sp) {
+  std::vector<char> done(ctx->sp.size(), 0);
+  const bool tile = mode == 2 && ctx->ppt == PIC_TUNING_TILE && tile_capable(ctx);
+  if (tile) {
+    int r = run_tile(ctx, done);
+    if (r) return r;
+  }
+  for (size_t i = 0; i < ctx->sp.size(); ++i) {
+    Species& s = ctx->sp[i];
+    if (done[i]) continue;
     if (s.desc.immobile && mode != 0) continue;
+    if (mode != 2 && s.desc.capacity > 0) {
+      int r = ensure_save(ctx, s);
+      if (r) return r;
+    }
     SpeciesPtrs<T> p = species_ptrs<T>(ctx, s);
     if (s.desc.capacity <= 0) continue;
-    if (mode == 2 && ctx->gd.shape_order == 1 && ctx->ppt != 1 && !ctx->fixed())
+    if (tile)   // a species not sorted since it was added: one thread per particle
+      CK(launch_particles<T>(mode, ctx->gd.shape_order, ctx->g, ctx->tb, fields<T>(ctx), p, ctx->prescribed,
+                             ctx->status, ctx->pushed, ctx->nsm, ctx->stream));
+    else if (mode == 2 && ctx->gd.shape_order == 1 && ctx->ppt != 1 && !ctx->fixed())
       CK(launch_push_deposit_runs<T>(ctx->ppt, ctx->g, ctx->tb, fields<T>(ctx), p, ctx->prescribed, ctx->status,
                                      ctx->pushed, ctx->nsm, ctx->stream));
     else if (mode == 2 && ctx->gd.shape_order == 3 && ctx->gd.dim == 3 && ctx->ppt != 1 && !ctx->fixed())
@@ -309,6 +373,16 @@ int do_sort(picpml_ctx* ctx) {
     CK(launch_sort(ctx->g, ctx->pbytes(), s.desc.pos, s.desc.mom, s.n_dev, s.desc.capacity, ctx->sort_scratch,
                    s.tmp_pos, s.tmp_mom, ctx->stream));
     ctx->launches += sort_launches(ncell);
+    const long long nt = tile_count(ctx->g);
+    if (nt > 0) {   // 3D: where each sort tile's particles end (the tile kernel's work ranges)
+      if (!s.tile_end) {
+        s.tile_end = (long long*)dev_alloc(ctx, (size_t)nt * sizeof(long long));
+        if (!s.tile_end) return fail(ctx, PIC_ENOMEM, "tile offsets");
+      }
+      CK(launch_tile_ends(ctx->g, ctx->sort_scratch, s.tile_end, ctx->stream));
+      ctx->launches += 1;
+      s.tiled = true;
+    }
   }
   return PIC_OK;
 }
@@ -510,6 +584,8 @@ int pml_init(picpml_ctx* ctx, const pml_desc* p) {
     CK(cudaMemsetAsync(jq, 0, (size_t)g.size * 3 * sizeof(long long), ctx->stream));
     for (int c = 0; c < 3; ++c) ctx->ff.Jq[c] = jq + (size_t)c * g.size;
   }
+  if (gd.dim == 3 && gd.prec != PIC_FP64 && tile_map_bytes() <= (int)sizeof(ctx->tmap))
+    ctx->tmap_ok = make_tile_tensor_map(g, ctx->ff.E[0], ctx->tmap) == cudaSuccess;
   ctx->status = (unsigned*)dev_alloc(ctx, 64);
   ctx->pushed = (unsigned long long*)(ctx->status + 8);
   ctx->diag = (double*)dev_alloc(ctx, 8 * sizeof(double));
@@ -532,8 +608,7 @@ int pic_add_species(picpml_ctx* ctx, const pic_species* s, int* sid) {
   Species sp;
   sp.desc = *s;
   sp.n_dev = (long long*)dev_alloc(ctx, sizeof(long long));
-  sp.save = dev_alloc(ctx, (size_t)std::max<long long>(s->capacity, 1) * ctx->pbytes());
-  if (!sp.n_dev || !sp.save) return fail(ctx, PIC_ENOMEM, "species scratch");
+  if (!sp.n_dev) return fail(ctx, PIC_ENOMEM, "species scratch");
   CK(cudaMemcpyAsync(sp.n_dev, &s->n, sizeof(long long), cudaMemcpyHostToDevice, ctx->stream));
   const pic_grid_desc& gd = ctx->gd;
   const double q = s->q, dt = ctx->dt;
@@ -687,8 +762,12 @@ int pic_autotune(picpml_ctx* ctx, int steps, int* ppt, int* kz) {
   int best_p = ctx->ppt, best_k = ctx->kz;
   if ((ctx->gd.shape_order == 1 || ctx->gd.dim == 3) && !ctx->fixed()) {
     float best = 1e30f;
-    for (int p : {1, 4, 8}) {
+    bool all_tiled = tile_capable(ctx);
+    for (auto& s : ctx->sp)
+      if (!s.desc.immobile && s.desc.capacity > 0 && !s.tiled) all_tiled = false;
+    for (int p : {1, PIC_TUNING_TILE, 4, 8}) {
       if (f64 && p == 8) continue;
+      if (p == PIC_TUNING_TILE && !all_tiled) continue;
       ctx->ppt = p;
       float ms = 0;
       r = time_it(true, &ms);
@@ -720,8 +799,9 @@ int pic_autotune(picpml_ctx* ctx, int steps, int* ppt, int* kz) {
 
 int pic_set_tuning(picpml_ctx* ctx, int ppt, int kz) {
   if (!ctx) return fail(nullptr, PIC_EINVAL, "null context");
-  if (!(ppt == 0 || ppt == 1 || ppt == 4 || ppt == 8) || !(kz == 1 || kz == 2 || kz == 4))
-    return fail(ctx, PIC_EINVAL, "particles per thread must be 0, 1, 4 or 8; z nodes per thread 1, 2 or 4");
+  if (!(ppt == 0 || ppt == 1 || ppt == PIC_TUNING_TILE || ppt == 4 || ppt == 8) || !(kz == 1 || kz == 2 || kz == 4))
+    return fail(ctx, PIC_EINVAL,
+                "particles per thread must be 0, 1, 2 (tile kernel), 4 or 8; z nodes per thread 1, 2 or 4");
   ctx->ppt = ppt;
   ctx->kz = kz;
   return PIC_OK;
@@ -758,6 +838,10 @@ int pic_set_old_positions(picpml_ctx* ctx, int sid, const void* src) {
   if (r) return r;
   if (sid < 0 || sid >= (int)ctx->sp.size() || !src) return fail(ctx, PIC_EINVAL, "bad species id or source");
   Species& s = ctx->sp[sid];
+  if (s.desc.capacity > 0) {
+    r = ensure_save(ctx, s);
+    if (r) return r;
+  }
   if (s.desc.capacity > 0)
     CK(cudaMemcpyAsync(s.save, src, (size_t)s.desc.capacity * ctx->pbytes(), cudaMemcpyDeviceToDevice,
                        ctx->stream));
@@ -847,6 +931,7 @@ int pic_sync(picpml_ctx* ctx) {
     return fail(ctx, PIC_EPARTICLE, "a particle was outside its allowed cells or not finite (removed)");
   if (st & ST_FIXED_OVERFLOW) return fail(ctx, PIC_EOVERFLOW, "fixed-point current overflow");
   if (st & ST_INJECT_OVERFLOW) return fail(ctx, PIC_EOVERFLOW, "injected particles beyond the species capacity (dropped)");
+  if (st & ST_TIMEOUT) return fail(ctx, PIC_ETIMEOUT, "a kernel gave up waiting for its field box copy (2 s)");
   return PIC_OK;
 }
 

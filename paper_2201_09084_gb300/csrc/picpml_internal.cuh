@@ -99,6 +99,21 @@ struct SpeciesPtrs {
   float4* save_mom;
 };
 
+// Species of one launch of the tile-resident particle kernel (3D FP32,
+// order 1): each with the end offset of every sort tile's particles at the
+// species' last sort (device array of one entry per tile).
+constexpr int kTileMaxSpecies = 8;
+struct TileSpecies {
+  SpeciesPtrs<float> sp;
+  const long long* tile_end;
+};
+struct TileLaunch {
+  int nsp;
+  int prescribed;
+  int arr_E[3], arr_Bh[3], arr_Bp[3];   // field array of each component (4th tensor-map coordinate)
+  TileSpecies s[kTileMaxSpecies];
+};
+
 // 32-byte aligned quadruple of doubles (FP64 particle layout).
 struct __align__(32) dbl4 {
   double x, y, z, w;
@@ -115,6 +130,6 @@ constexpr double kFixMaxWq = 4294967296.0;         // |w q/e| above 2^32 is refu
 constexpr double kQe = 1.602176634e-19;
 
 // Device status word bits.
-enum : unsigned { ST_BAD_PARTICLE = 1u, ST_FIXED_OVERFLOW = 2u, ST_INJECT_OVERFLOW = 4u };
+enum : unsigned { ST_BAD_PARTICLE = 1u, ST_FIXED_OVERFLOW = 2u, ST_INJECT_OVERFLOW = 4u, ST_TIMEOUT = 8u };
 
 }  // namespace picpml

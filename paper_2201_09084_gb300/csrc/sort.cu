@@ -1,6 +1,6 @@
 // Counting sort of one species by cell, dropping removed particles.  The key
-// is tile-major: 4x4x4-cell tiles in x,y,z order, then the cell inside the
-// tile.  Consecutive particles then share their cell, and any run of them
+// is tile-major: 8x4x4-cell tiles in x,y,z order (4x4 in 2D), then the cell
+// inside the tile.  Consecutive particles then share their cell, and any run of them
 // covers a compact 3D block of cells, which keeps the shared-memory field
 // and current box of the particle kernel small.
 //   1. histogram of the linear cell index (atomics, one per cell present in
@@ -15,13 +15,19 @@ namespace picpml {
 
 namespace {
 
-// Tile-major key; tiles per axis tx, ty (2D: one tile layer in y).
+// Tile-major key.  3D: tiles of 8 x 4 x 4 cells (x, y, z) in x, y, z order,
+// then the cell inside the tile, x fastest: 32 consecutive cells are one
+// 8 x 4 layer of a tile.  2D: 4 x 4 tiles of the (x, z) plane.
 __device__ __forceinline__ long long lin_cell(const Geom& g, int cell) {
   const int i = cell_i(cell), j = cell_j(cell), k = cell_k(cell);
-  const long long tx = (g.N[0] + 3) >> 2, ty = g.dim == 3 ? (g.N[1] + 3) >> 2 : 1;
-  const long long tile = (i >> 2) + tx * ((j >> 2) + ty * (k >> 2));
-  const int in_tile = g.dim == 3 ? (i & 3) + 4 * ((j & 3) + 4 * (k & 3)) : (i & 3) + 4 * (k & 3);
-  return tile * (g.dim == 3 ? 64 : 16) + in_tile;
+  if (g.dim == 3) {
+    const long long tx = (g.N[0] + 7) >> 3, ty = (g.N[1] + 3) >> 2;
+    const long long tile = (i >> 3) + tx * ((j >> 2) + ty * (k >> 2));
+    return tile * 128 + ((i & 7) + 8 * ((j & 3) + 4 * (k & 3)));
+  }
+  const long long tx = (g.N[0] + 3) >> 2;
+  const long long tile = (i >> 2) + tx * (k >> 2);
+  return tile * 16 + ((i & 3) + 4 * (k & 3));
 }
 
 template <int PB>
@@ -200,8 +206,12 @@ long long sort_scratch_words(long long ncell) { return ncell + 1 + ncell / 512 +
 
 // Number of sort keys (cells padded to whole tiles).
 long long sort_keys(const Geom& g) {
-  const long long tx = (g.N[0] + 3) >> 2, ty = g.dim == 3 ? (g.N[1] + 3) >> 2 : 1, tz = (g.N[2] + 3) >> 2;
-  return tx * ty * tz * (g.dim == 3 ? 64 : 16);
+  if (g.dim == 3) {
+    const long long tx = (g.N[0] + 7) >> 3, ty = (g.N[1] + 3) >> 2, tz = (g.N[2] + 3) >> 2;
+    return tx * ty * tz * 128;
+  }
+  const long long tx = (g.N[0] + 3) >> 2, tz = (g.N[2] + 3) >> 2;
+  return tx * tz * 16;
 }
 
 cudaError_t launch_sort(const Geom& g, int pbytes, void* pos, void* mom, long long* n_dev, long long cap,

@@ -1,30 +1,34 @@
 """Benchmark of the damped-current PML PIC step on GB300.
 
-Workload (one step = one PIC time step over the whole particle set, i.e. all
-hot-path stages: sort every 20 steps, gather + Boris push + move + Esirkepov
-deposit + alpha-damped flush, split-field PML Yee update):
-  3D FP32 fields, 128^3 physical cells + 16-cell PML on every face (160^3),
-  a relativistic electron beam of 4,194,304 macroparticles (Gaussian,
-  sigma 4 cells transverse, 8 cells along the axis, u_z ~ N(50, 0.5), 1 nC),
-  centred 24 cells (3 sigma_z) before the +z PML interface so that it
-  crosses into the damped-current PML during the timed steps (the default
-  60 steps after 5 warm-up steps; by step ~120 the whole beam has left
-  through the outer wall, so much longer runs push fewer particles); order 1
-  (order 3 selectable), dt = 0.99 x Courant limit, seed-generated.
+Default workload (the N=1 line; one step = one PIC time step over the whole
+particle set, i.e. all hot-path stages: sort every 20 steps, gather + Boris
+push + move + Esirkepov deposit + alpha-damped flush, split-field PML Yee
+update of E and B):
+  3D plasma + drifting beam: 256 x 256 x 512 physical cells of 1 um + a
+  16-cell damped-current PML on every face (288 x 288 x 544 cells), electrons
+  and protons 8 per cell each (536,870,912 macroparticles, drawn on the
+  device from a seeded generator), Maxwellian u_th = 0.01, plus an electron
+  beam at u_z = 5 (41,177 particles, neutralised by immobile ions) heading
+  into the +z PML; order 1, dt = 0.99 x Courant limit, FP32 fields and
+  momenta with IEEE FP64 PML split parts.  The autotuner picks the launch
+  shapes (the tile-resident particle kernel for this plasma).
 Metric: particle-steps/s (live particles pushed per second, counted on the
-device); cell-updates/s of the Yee/PML update is reported beside it.
+device); cell-updates/s of the Yee/PML update beside it.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
-Prints one JSON line.  Beside the FP32 result it carries "fp64": the same
-workload in the plain FP64 form (fields, particles and PML parts in FP64),
-"batch2d": the batched 2D runs in FP32 and FP64 with the oracle timed on a
-sample of them, and "cpu_baseline": the oracle on a sample of the beam.
-"e2e" uploads the particles from pinned host memory once and reads each
-step's particle-step count back to the host.  --impl reference times the
-FP64 CPU oracle on a bounded sample of the same workload (see cpu_sample()).
---plasma measures the thermal plasma + beam workload instead (its own JSON
-line); --precision-study compares the FP32 forms with FP64 and the oracle.
+Prints one JSON line with "roofline" (the particle kernel's algorithmic
+bytes per launch over its CUDA-event time, against the measured copy
+bandwidth), "e2e" (the same steps through the C ABI with the particle
+records uploaded from pinned host memory inside the timed region and each
+step's particle-step count read back), "float_float_parts" (the same run with
+float-float PML parts), "beam_3d" (the 128^3 + 16 beam of 4,194,304
+particles), "batch2d" (4096 batched 2D runs, FP32 and FP64) and
+"cpu_baseline" (the FP64 oracle on the plasma + beam workload reduced to
+24 x 24 x 48 + 8 cells, with the GPU's max relative field error on that
+sample).  --impl reference times the oracle alone on that sample.
+--beam, --plasma, --single-particle and --precision-study measure the other
+workloads (their own JSON lines).
 """
 from __future__ import annotations
 
@@ -647,6 +651,14 @@ def run_precision_study(args):
 # to None whenever that kernel changes.
 PLASMA_NCU_BYTES_PER_PARTICLE = 557_966_080 / 8_429_785
 
+# DRAM bytes per particle-step of the tile kernel on the plasma (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch over the particles it pushed), from an ncu
+# capture of the 64 x 64 x 128 case; the plasma fills the box at a fixed 8 particles
+# per cell and species, so the traffic grows with the particle count and the
+# full-size figure is scaled by it.  None until captured on the current kernel.
+HEADLINE_NCU_BYTES_PER_PARTICLE = None
+HEADLINE_NCU_NOTE = None
+
 # Plasma boxes with more particles per species than this are generated and
 # packed one z-plane of cells at a time (inputs.plasma_planes) instead of in
 # one piece, so host memory holds one plane.
@@ -783,25 +795,301 @@ def run_plasma(args):
             "gpu_launches": int(launches), "autotune": tuning, "clocks": clk}
 
 
+# ----------------------------------------------------------------------------
+# The default workload: the 537M-particle plasma + beam box.
+HL_NPHYS = (256, 256, 512)
+HL_SMALL = ((24, 24, 48), (8,) * 6)   # the reduced box the oracle steps (cpu_baseline)
+
+
+def headline_workload(nphys, split64):
+    N = [n + 2 * p for n, p in zip(nphys, PML[::2])]
+    return {"workload": f"thermal plasma + drifting beam: {nphys[0]}x{nphys[1]}x{nphys[2]} + {PML[0]}-cell PML "
+                        f"({N[0]}x{N[1]}x{N[2]} cells), e- and p+ 8 per cell, u_th 0.01, beam u_z 5 into the +z PML, "
+                        "order 1, damped PML, sort every 20 steps, fp32 fields and momenta with "
+                        + ("IEEE fp64" if split64 else "float-float") + " PML split parts",
+            "grid": N, "shape_order": 1, "alpha": "damped (Eq. alpha, v=c)", "sort_every": SORT_EVERY,
+            "l2": "working set > L2 (particles 17 GB)", "data": "synthetic (seeded, drawn on the device)"}
+
+
+def headline_records(nphys, device):
+    """Initial records of the default workload as [(pos, mom, n, q, m,
+    immobile)] on `device`: electrons and protons drawn on the device, the
+    beam and its ions on the host."""
+    import torch
+    from paper_2201_09084_gb300 import inputs as I
+    from paper_2201_09084_gb300.api import pack_particles, pack_records
+    out = []
+    for sp in I.plasma_device(nphys, PML, D[0], device=device):
+        pos, mom = pack_records(sp["cell"], sp["off"], sp["u"], sp["w"])
+        out.append((pos, mom, pos.shape[0], sp["q"], sp["m"], False))
+        del sp
+    torch.cuda.empty_cache()
+    for sp in I.plasma_beam(nphys, PML, D[0]):
+        pos, mom = pack_particles(sp["cell"], sp["off"], sp["u"], sp["w"], "fp32", device=device)
+        out.append((pos, mom, len(sp["w"]), sp["q"], sp["m"], sp["immobile"]))
+    return out
+
+
+def run_headline(args, rank, world):
+    import torch
+    from paper_2201_09084_gb300.api import Sim
+    from paper_2201_09084_gb300 import build as B
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    nphys = HL_NPHYS if args.cells is None else tuple(int(x) for x in args.cells.split(","))
+    recs = headline_records(nphys, "cuda")
+    # the initial records, kept in pinned host memory (reloaded for each run)
+    host = []
+    for pos, mom, n, q, m, imm in recs:
+        hp = torch.empty(pos.shape, dtype=pos.dtype, pin_memory=True)
+        hm = torch.empty(mom.shape, dtype=mom.dtype, pin_memory=True)
+        hp.copy_(pos)
+        hm.copy_(mom)
+        host.append((hp, hm))
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    n_mobile = sum(r[2] for r in recs if not r[5])
+    rec_bytes = sum(2 * r[0].numel() * 4 for r in recs)
+
+    def make(split64):
+        sim = Sim(3, nphys, D, PML, cfl=0.99, order=1, prec="fp32", alpha_mode="damped", sort_every=SORT_EVERY,
+                  split_fp64=split64, stream=stream)
+        for pos, mom, n, q, m, imm in recs:
+            sim.add_species(pos, mom, n, q, m, imm)
+        return sim
+
+    def reload():
+        for (pos, mom, *_), (hp, hm) in zip(recs, host):
+            pos.copy_(hp, non_blocking=True)
+            mom.copy_(hm, non_blocking=True)
+
+    def timed(sim, tuning):
+        """W untimed steps, then K timed ones (sort every 20 steps inside);
+        returns (ms, particle-steps, launches, mean push_deposit ms, mean
+        field_step ms, clocks)."""
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+
+        def one_step(i, ev=None):
+            if i % SORT_EVERY == 0:
+                sim.sort()
+            if ev is not None:
+                ev[0].record(stream)
+            sim.push_deposit()
+            if ev is not None:
+                ev[1].record(stream)
+            sim.field_step()
+            if ev is not None:
+                ev[2].record(stream)
+
+        sim.set_tuning(tuning["particles_per_thread"], tuning["z_nodes_per_thread"])
+        for i in range(args.warmup):
+            one_step(i)
+        sim.sync()
+        ps0, l0 = sim.particle_steps(), sim.launch_count()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        clocks = Clocks(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        t0.record(stream)
+        for i in range(args.steps):
+            one_step(args.warmup + i, evs[i])
+        t1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clk = clocks.stop()
+        sim.sync()
+        return (t0.elapsed_time(t1), sim.particle_steps() - ps0, sim.launch_count() - l0,
+                float(np.mean([e[0].elapsed_time(e[1]) for e in evs])),
+                float(np.mean([e[1].elapsed_time(e[2]) for e in evs])), clk)
+
+    # ---- the measured form: IEEE FP64 PML parts ----
+    sim = make(True)
+    sim.sort()
+    if args.tuning:
+        p_, k_ = (int(x) for x in args.tuning.split(","))
+        tuning = {"particles_per_thread": p_, "z_nodes_per_thread": k_, "source": "--tuning"}
+    else:
+        tuning = sim.autotune(steps=3)   # from a restored snapshot
+    sim.close()
+    reload()
+    sim = make(True)
+    ms, psteps, launches, t_pd, t_f, clk = timed(sim, tuning)
+    sim.close()
+
+    # ---- end to end: the records uploaded from pinned host memory inside the timed region ----
+    sim = make(True)
+    sim.set_tuning(tuning["particles_per_thread"], tuning["z_nodes_per_thread"])
+    torch.cuda.synchronize()
+    nsteps_e2e = args.warmup + args.steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reload()
+    for _ in range(nsteps_e2e):
+        sim.step(1)
+        ps_e2e = sim.particle_steps()   # each step's result read back (synchronising 8-byte copy)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+    sim.close()
+
+    # ---- the same run with float-float PML parts ----
+    ff = None
+    if not args.no_extra:
+        reload()
+        sim = make(False)
+        ms2, ps2, _, t_pd2, t_f2, _ = timed(sim, tuning)
+        sim.close()
+        ff = {"value": ps2 / (ms2 / 1e3), "unit": "particle-steps/s", "ms_per_step": ms2 / args.steps,
+              "kernel_ms": {"push_deposit": t_pd2, "field_step": t_f2}}
+    del recs, host
+    torch.cuda.empty_cache()
+
+    ms, psteps, ms_e2e, ps_e2e = combine_ranks(ms, psteps, ms_e2e, ps_e2e, world, "cuda")
+    N = [n + 2 * p for n, p in zip(nphys, PML[::2])]
+    total = N[0] * N[1] * N[2]
+    interior = nphys[0] * nphys[1] * nphys[2]
+    n_live = (psteps / world) / args.steps
+    # occupied cells: the plasma fills every physical cell
+    b_part, b_field = algorithmic_bytes(n_live, interior, interior, total - interior, "fp32")
+    peak, kind = measured_peak()
+    achieved = b_part / (t_pd / 1e3) / 1e9
+    p_ = tuning["particles_per_thread"]
+    traffic = (HEADLINE_NCU_BYTES_PER_PARTICLE * n_live
+               if HEADLINE_NCU_BYTES_PER_PARTICLE and p_ == 2 else None)
+    kname = ("k_tile (tile-resident fused gather/push/move/deposit/damp)" if p_ == 2
+             else "particle kernels (fused gather/push/move/deposit/damp)")
+    out = {
+        "metric": METRIC, "value": psteps / (ms / 1e3), "unit": "particle-steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(headline_workload(nphys, True), particles=int(n_mobile), parallelism=f"replicas x{world}"),
+        "cell_updates_per_s": world * total * args.steps / (ms / 1e3),
+        "kernel_ms": {"push_deposit": t_pd, "field_step": t_f},
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": f"{kind} (copy)", "traffic": traffic,
+                     "traffic_note": HEADLINE_NCU_NOTE if traffic else None,
+                     "algorithmic_bytes_per_launch": b_part,
+                     "bytes_model": "60 B per live particle (32 read, 28 written) + 48 B per occupied cell "
+                                    "(9 field words read, 3 current words written)"},
+        "e2e": {"value": ps_e2e / (ms_e2e / 1e3), "unit": "particle-steps/s",
+                "h2d_bytes_per_step": rec_bytes / nsteps_e2e, "d2h_bytes_per_step": 8,
+                "note": f"the initial particle records ({rec_bytes / 1e9:.1f} GB) copied from pinned host memory "
+                        f"once per run of {nsteps_e2e} steps (h2d bytes are that copy per step); every step runs "
+                        "step_n (sorting every 20 steps) and reads its particle-step count back to the host"},
+        "gpu_launches": int(launches),
+        "autotune": tuning,
+        "clocks": clk,
+    }
+    if ff is not None:
+        out["float_float_parts"] = ff
+    return out
+
+
+def cpu_plasma_sample(steps, gpu_check=True, threads=None):
+    """The oracle on the plasma + beam workload reduced to 24 x 24 x 48
+    physical cells + 8-cell PML (221,186 mobile particles; the same
+    distributions, beam radius 4 and length 12 cells), `steps` steps on the
+    host's cores.  Returns (particle-steps/s, threads used, description,
+    ms per step, max relative field error of the GPU's FP32 form on the same
+    sample or None)."""
+    import oracle as O
+    from paper_2201_09084_gb300 import inputs as I
+    O.build()
+    nphys, pml = HL_SMALL
+    parts = I.plasma(nphys, pml, D[0], beam_radius=4.0, beam_length=12.0)
+    dt = O.yee_dt(D, 0.99, 3)
+    nthreads = O.set_threads(threads)
+    ora = O.OracleSim(3, nphys, pml, D, dt, order=1, alpha_mode="damped")
+    for sp in parts:
+        X = I.absolute(sp["cell"], sp["off"])
+        u = sp["u"].astype(np.float64)
+        ora.add_particles(X[:, 0], X[:, 1], X[:, 2], u[:, 0], u[:, 1], u[:, 2], sp["w"].astype(np.float64),
+                          sp["q"], sp["m"], sp["immobile"])
+    nmob = int(sum(len(sp["w"]) for sp in parts if not sp["immobile"]))
+    t = 0.0
+    psteps = 0
+    for _ in range(steps):
+        psteps += int(np.count_nonzero(ora.particles()["alive"][:nmob]))
+        a = time.perf_counter()
+        ora.step(1)
+        t += time.perf_counter() - a
+    desc = (f"FP64 C oracle, {nthreads} threads: the workload reduced to {nphys[0]}x{nphys[1]}x{nphys[2]} + "
+            f"{pml[0]}-cell PML ({nmob} mobile particles), {steps} steps")
+    err = None
+    if gpu_check:
+        import torch
+        from paper_2201_09084_gb300.api import Sim, pack_particles
+        gpu = Sim(3, nphys, D, pml, dt=dt, order=1, prec="fp32", alpha_mode="damped", sort_every=SORT_EVERY,
+                  split_fp64=True)
+        keep = []
+        for sp in parts:
+            pos, mom = pack_particles(sp["cell"], sp["off"], sp["u"], sp["w"], "fp32")
+            gpu.add_species(pos, mom, len(sp["w"]), sp["q"], sp["m"], sp["immobile"])
+            keep.append((pos, mom))
+        gpu.set_tuning(2, 1)
+        gpu.step(steps)
+        gpu.sync()
+        names = ("Ex", "Ey", "Ez", "Bx", "By", "Bz")
+        unit = {k: (O.C_LIGHT if k[0] == "B" else 1.0) for k in names}
+        a_ = {k: ora.field(k) * unit[k] for k in names}
+        b_ = {k: gpu.field(k).cpu().numpy() * unit[k] for k in names}
+        scale = max(np.abs(v).max() for v in a_.values())
+        err = float(max(np.abs(a_[k] - b_[k]).max() for k in names) / scale)
+        gpu.close()
+    return psteps / t, nthreads, desc, 1e3 * t / steps, err
+
+
+def run_reference_plasma(args, rank, world):
+    """The reference arm: the FP64 oracle on the default workload reduced to
+    the sample cpu_plasma_sample() steps (bounded: W + K steps), timed on the
+    host's cores; rank 0 only."""
+    if rank != 0:
+        return None
+    v, nthreads, desc, ms_step, _ = cpu_plasma_sample(args.warmup + args.steps, gpu_check=False)
+    cfg = dict(headline_workload(HL_NPHYS, True), parallelism="cpu oracle",
+               sample=desc + "; the GPU line runs the full 256x256x512 box")
+    return {"metric": METRIC, "value": v, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference", "config": cfg,
+            "cpu_baseline": {"value": v, "unit": "particle-steps/s", "cores": nthreads, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": v, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cells", default=None,
+                    help="physical cells of the default plasma workload (default 256,256,512; smaller only for "
+                         "profiling captures)")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default workload only (no float-float form, beam, batched runs)")
+    ap.add_argument("--beam", action="store_true",
+                    help="the 3D beam workload (128^3 + 16, 4,194,304 particles) as the main line")
     ap.add_argument("--order", type=int, default=1, choices=[1, 3])
     ap.add_argument("--theta", type=float, default=0.0)
     ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 2D runs measurement")
-    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 run of the main workload")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 run of the beam workload")
     ap.add_argument("--batch-runs", type=int, default=4096, help="number of batched 2D runs")
     ap.add_argument("--particles", type=int, default=NPART,
                     help="beam macroparticles (default 4194304; smaller only for profiling captures)")
     ap.add_argument("--precision-study", action="store_true",
                     help="FP32 forms vs FP64 on the plasma + beam workload (prints its own JSON line)")
     ap.add_argument("--plasma", action="store_true",
-                    help="throughput on the thermal plasma + beam workload (prints its own JSON line)")
+                    help="throughput on the host-drawn plasma + beam workload (prints its own JSON line)")
     ap.add_argument("--plasma-cells", default="128,128,256", help="physical cells of the --plasma workload")
     ap.add_argument("--single-particle", action="store_true",
                     help="the 2D FP64 single-particle workload (run it with --steps 400; own JSON line)")
@@ -823,38 +1111,69 @@ def main():
     elif args.single_particle and args.impl == "gb300":
         out = run_single_particle(args) if rank == 0 else None
     elif args.impl == "reference":
-        out = run_reference(args, rank, world)
+        out = run_reference(args, rank, world) if args.beam else run_reference_plasma(args, rank, world)
+    elif args.beam:
+        out = run_beam_line(args, rank, world)
     else:
-        out = run_gpu(args, rank, world)
-        if args.prec == "fp32" and not args.no_fp64:
-            # the same workload, steps and timing with FP64 fields, particles and
-            # parts (the plain FP64 form), for the FP32-vs-FP64 comparison
-            a64 = argparse.Namespace(**vars(args))
-            a64.prec, a64.tuning = "fp64", None
-            o64 = run_gpu(a64, rank, world)
-            out["fp64"] = {"value": o64["value"], "unit": o64["unit"], "ms_per_step": o64["ms_per_step"],
-                           "kernel_ms": o64["kernel_ms"], "autotune": o64["autotune"],
-                           "roofline_frac": o64["roofline"]["frac"], "e2e": o64["e2e"]["value"]}
-            out["fp32_over_fp64"] = out["value"] / o64["value"]
-        if not args.no_batch:
-            nb = min(args.steps, 200)
-            out["batch2d"] = {"fp32": run_batch(nb, 3, "fp32", nruns=args.batch_runs),
-                              "fp64": run_batch(nb, 3, "fp64", nruns=args.batch_runs)}
-            out["batch2d"]["fp32_over_fp64_particle_steps"] = (
-                out["batch2d"]["fp32"]["particle_steps_per_s"] / out["batch2d"]["fp64"]["particle_steps_per_s"])
-            if rank == 0 and world == 1 and not args.no_cpu_baseline:
-                bv, bc, bdesc = cpu_batch_sample(nruns=args.batch_runs)
-                out["batch2d"]["cpu_baseline"] = {"value": bv, "unit": "particle-steps/s", "cores": 1,
-                                                  "kind": "oracle", "sample": bdesc, "cell_updates_per_s": bc}
+        out = run_headline(args, rank, world)
+        if not args.no_extra:
+            b = argparse.Namespace(**vars(args))
+            b.tuning, b.no_batch, b.no_cpu_baseline = None, True, True
+            ob = run_beam_line(b, rank, world)
+            out["beam_3d"] = {"workload": ob["config"]["workload"], "value": ob["value"], "unit": ob["unit"],
+                              "ms_per_step": ob["ms_per_step"], "kernel_ms": ob["kernel_ms"],
+                              "roofline_frac": ob["roofline"]["frac"], "autotune": ob["autotune"],
+                              "fp64": ob.get("fp64"), "fp32_over_fp64": ob.get("fp32_over_fp64")}
+            if not args.no_batch:
+                out["batch2d"] = batch_lines(args, rank, world)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            v, desc, _ = cpu_sample(args.order, args.theta, 65536, 8)
-            out["cpu_baseline"] = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-                                   "sample": desc}
+            v, nthreads, desc, _, err = cpu_plasma_sample(SORT_EVERY)
+            out["cpu_baseline"] = {"value": v, "unit": "particle-steps/s", "cores": nthreads, "kind": "oracle",
+                                   "sample": desc, "gpu_max_rel_field_error_on_sample": err,
+                                   "gpu_error_note": "the GPU's FP32 form (tile kernel, IEEE fp64 PML parts) on "
+                                                     "the same sample and steps: max |GPU - oracle| over the six "
+                                                     "components / max(|E|, c|B|)"}
     if rank == 0 and out is not None:
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()
+
+
+def batch_lines(args, rank, world):
+    """Batched 2D runs in FP32 and FP64 (each under its CUDA graph), with the
+    oracle on a sample of them (rank 0, N=1)."""
+    nb = min(args.steps, 200)
+    out = {"fp32": run_batch(nb, 3, "fp32", nruns=args.batch_runs),
+           "fp64": run_batch(nb, 3, "fp64", nruns=args.batch_runs)}
+    out["fp32_over_fp64_particle_steps"] = (out["fp32"]["particle_steps_per_s"] /
+                                            out["fp64"]["particle_steps_per_s"])
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        bv, bc, bdesc = cpu_batch_sample(nruns=args.batch_runs)
+        out["cpu_baseline"] = {"value": bv, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                               "sample": bdesc, "cell_updates_per_s": bc}
+    return out
+
+
+def run_beam_line(args, rank, world):
+    """The 3D beam workload (128^3 + 16-cell PML, 4,194,304 particles) in FP32
+    with the FP64 form beside it."""
+    out = run_gpu(args, rank, world)
+    if args.prec == "fp32" and not args.no_fp64:
+        a64 = argparse.Namespace(**vars(args))
+        a64.prec, a64.tuning = "fp64", None
+        o64 = run_gpu(a64, rank, world)
+        out["fp64"] = {"value": o64["value"], "unit": o64["unit"], "ms_per_step": o64["ms_per_step"],
+                       "kernel_ms": o64["kernel_ms"], "autotune": o64["autotune"],
+                       "roofline_frac": o64["roofline"]["frac"], "e2e": o64["e2e"]["value"]}
+        out["fp32_over_fp64"] = out["value"] / o64["value"]
+    if not args.no_batch:
+        out["batch2d"] = batch_lines(args, rank, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, desc, _ = cpu_sample(args.order, args.theta, 65536, 8)
+        out["cpu_baseline"] = {"value": v, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                               "sample": desc}
+    return out
 
 
 if __name__ == "__main__":

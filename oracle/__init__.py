@@ -40,10 +40,16 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + f".tmp{os.getpid()}"
         subprocess.check_call(
-            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-fopenmp",
              "-o", tmp, SRC, "-lm"])
         os.replace(tmp, LIB)
     return LIB
+
+
+def set_threads(n=None):
+    """Host threads of the oracle's particle and field loops (None: every
+    core; 1: the serial loops, the default).  Returns the number in use."""
+    return int(lib().ora_set_threads(0 if n is None else int(n)))
 
 
 def lib():

@@ -59,8 +59,31 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #define ORA_C 299792458.0
 #define ORA_EPS0 8.8541878128e-12
+
+/* Host threads of the particle and field loops (1 = the plain serial loops,
+ * the default; the tests run that way).  With T > 1 the push and field loops
+ * split their independent iterations over T threads, and the deposit gives
+ * each thread its own current arrays for a contiguous share of the
+ * particles, summed afterwards in thread order: the result is deterministic
+ * for a given T and equals the serial one up to the summation order. */
+static int g_threads = 1;
+
+int ora_set_threads(int n) {
+#ifdef _OPENMP
+  if (n < 1) n = omp_get_num_procs();
+  g_threads = n;
+#else
+  (void)n;
+  g_threads = 1;
+#endif
+  return g_threads;
+}
 
 typedef struct ora_sim {
   int dim, order, alpha_mode, prescribed;
@@ -78,6 +101,8 @@ typedef struct ora_sim {
   double *X[3], *X0[3], *u[3], *w, *q, *m;
   int *alive, *immobile, *moved;
   unsigned char* cond;              /* conductor cells (NULL: none), i + N0 (j + N1 k) */
+  double* jt;                       /* per-thread current arrays of the threaded deposit */
+  int jt_threads;
 } ora_sim;
 
 /* ------------------------------------------------------------------------- */
@@ -192,6 +217,7 @@ void ora_destroy(ora_sim* s) {
   }
   free(s->w); free(s->q); free(s->m); free(s->alive); free(s->immobile); free(s->moved);
   free(s->cond);
+  free(s->jt);
   free(s);
 }
 
@@ -381,6 +407,7 @@ void ora_boris(double* u, const double* E, const double* B, double q, double m,
 
 /* Gather + Boris + move + removal for every live particle. */
 void ora_push(ora_sim* s) {
+#pragma omp parallel for num_threads(g_threads) schedule(static) if (g_threads > 1)
   for (long p = 0; p < s->np; ++p) {
     s->moved[p] = 0;
     if (!s->alive[p]) continue;
@@ -432,8 +459,17 @@ static int esk_axis(int order, double x0, double x1, long* lo, double* S0, doubl
  * 2D (x,z): W_x = DSx (S0z + DSz/2), W_z = DSz (S0x + DSx/2) with the same
  * prefix sums, and J_y = qw v_y (S0x S0z + DSx S0z/2 + S0x DSz/2 + DSx DSz/3)/V
  * for the out-of-plane component.  V uses a 1 m depth in 2D. */
+static void esirkepov_into(const ora_sim* s, double* const* J, const double* X0, const double* X1, double qw,
+                           double vy);
+
 void ora_esirkepov(ora_sim* s, const double* X0, const double* X1, double qw,
                    double vy) {
+  esirkepov_into(s, s->J, X0, X1, qw, vy);
+}
+
+/* ora_esirkepov adding into the arrays J[0..2] instead of the sim's own. */
+static void esirkepov_into(const ora_sim* s, double* const* J, const double* X0, const double* X1, double qw,
+                           double vy) {
   int order = s->order;
   long lo[3]; int W[3];
   double S0[3][6], S1[3][6], DS[3][6];
@@ -453,7 +489,7 @@ void ora_esirkepov(ora_sim* s, const double* X0, const double* X1, double qw,
         double acc = 0.0;
         for (int ti = 0; ti < W[0]; ++ti) {
           acc += DS[0][ti] * T;
-          s->J[0][IX(s, lo[0] + ti, lo[1] + tj, lo[2] + tk)] += cx * acc;
+          J[0][IX(s, lo[0] + ti, lo[1] + tj, lo[2] + tk)] += cx * acc;
         }
       }
     for (int tk = 0; tk < W[2]; ++tk)
@@ -463,7 +499,7 @@ void ora_esirkepov(ora_sim* s, const double* X0, const double* X1, double qw,
         double acc = 0.0;
         for (int tj = 0; tj < W[1]; ++tj) {
           acc += DS[1][tj] * T;
-          s->J[1][IX(s, lo[0] + ti, lo[1] + tj, lo[2] + tk)] += cy * acc;
+          J[1][IX(s, lo[0] + ti, lo[1] + tj, lo[2] + tk)] += cy * acc;
         }
       }
     for (int tj = 0; tj < W[1]; ++tj)
@@ -473,7 +509,7 @@ void ora_esirkepov(ora_sim* s, const double* X0, const double* X1, double qw,
         double acc = 0.0;
         for (int tk = 0; tk < W[2]; ++tk) {
           acc += DS[2][tk] * T;
-          s->J[2][IX(s, lo[0] + ti, lo[1] + tj, lo[2] + tk)] += cz * acc;
+          J[2][IX(s, lo[0] + ti, lo[1] + tj, lo[2] + tk)] += cz * acc;
         }
       }
   } else {
@@ -485,7 +521,7 @@ void ora_esirkepov(ora_sim* s, const double* X0, const double* X1, double qw,
       double acc = 0.0;
       for (int ti = 0; ti < W[0]; ++ti) {
         acc += DS[0][ti] * T;
-        s->J[0][IX(s, lo[0] + ti, 0, lo[2] + tk)] += cx * acc;
+        J[0][IX(s, lo[0] + ti, 0, lo[2] + tk)] += cx * acc;
       }
     }
     for (int ti = 0; ti < W[0]; ++ti) {
@@ -493,14 +529,14 @@ void ora_esirkepov(ora_sim* s, const double* X0, const double* X1, double qw,
       double acc = 0.0;
       for (int tk = 0; tk < W[2]; ++tk) {
         acc += DS[2][tk] * T;
-        s->J[2][IX(s, lo[0] + ti, 0, lo[2] + tk)] += cz * acc;
+        J[2][IX(s, lo[0] + ti, 0, lo[2] + tk)] += cz * acc;
       }
     }
     for (int tk = 0; tk < W[2]; ++tk)
       for (int ti = 0; ti < W[0]; ++ti) {
         double Wy = S0[0][ti] * S0[2][tk] + 0.5 * DS[0][ti] * S0[2][tk] +
                     0.5 * S0[0][ti] * DS[2][tk] + DS[0][ti] * DS[2][tk] / 3.0;
-        s->J[1][IX(s, lo[0] + ti, 0, lo[2] + tk)] += cyy * Wy;
+        J[1][IX(s, lo[0] + ti, 0, lo[2] + tk)] += cyy * Wy;
       }
   }
 }
@@ -532,27 +568,70 @@ double ora_weight_integral(const ora_sim* s, const double* X0, const double* X1)
 
 /* Step 3 of the time step: J^{n+1/2} of every particle moved by ora_push
  * (with weight damping: at the mid-step weight, then the weight decays). */
+/* One particle's share of the deposit (with weight damping: at the
+ * mid-step weight, then the weight decays). */
+static void deposit_particle(ora_sim* s, double* const* J, long p) {
+  double X0[3] = {s->X0[0][p], s->X0[1][p], s->X0[2][p]};
+  double X1[3] = {s->X[0][p], s->X[1][p], s->X[2][p]};
+  double g = sqrt(1.0 + s->u[0][p] * s->u[0][p] + s->u[1][p] * s->u[1][p] + s->u[2][p] * s->u[2][p]);
+  double vy = ORA_C * s->u[1][p] / g;
+  double wd = s->w[p];
+  double I = 0.0;
+  if (s->alpha_mode == 3) {
+    I = ora_weight_integral(s, X0, X1);
+    wd *= exp(-0.5 * I);
+  }
+  esirkepov_into(s, J, X0, X1, s->q[p] * wd, vy);
+  if (s->alpha_mode == 3) s->w[p] *= exp(-I);
+}
+
 void ora_deposit_raw(ora_sim* s) {
   ora_zero_J(s);
-  for (long p = 0; p < s->np; ++p) {
-    if (!s->moved[p]) continue;
-    double X0[3] = {s->X0[0][p], s->X0[1][p], s->X0[2][p]};
-    double X1[3] = {s->X[0][p], s->X[1][p], s->X[2][p]};
-    double g = sqrt(1.0 + s->u[0][p] * s->u[0][p] + s->u[1][p] * s->u[1][p] + s->u[2][p] * s->u[2][p]);
-    double vy = ORA_C * s->u[1][p] / g;
-    double wd = s->w[p];
-    double I = 0.0;
-    if (s->alpha_mode == 3) {
-      I = ora_weight_integral(s, X0, X1);
-      wd *= exp(-0.5 * I);
+  const int T = g_threads;
+  if (T <= 1) {
+    for (long p = 0; p < s->np; ++p)
+      if (s->moved[p]) deposit_particle(s, s->J, p);
+    return;
+  }
+  if (s->jt_threads != T) {
+    free(s->jt);
+    s->jt = (double*)malloc(sizeof(double) * 3 * (size_t)s->ntot * (size_t)T);
+    s->jt_threads = s->jt ? T : 0;
+    if (!s->jt) { /* no room for the per-thread arrays: the serial loop */
+      for (long p = 0; p < s->np; ++p)
+        if (s->moved[p]) deposit_particle(s, s->J, p);
+      return;
     }
-    ora_esirkepov(s, X0, X1, s->q[p] * wd, vy);
-    if (s->alpha_mode == 3) s->w[p] *= exp(-I);
+  }
+#pragma omp parallel num_threads(T)
+  {
+#ifdef _OPENMP
+    const int t = omp_get_thread_num();
+#else
+    const int t = 0;
+#endif
+    double* Jt[3];
+    for (int c = 0; c < 3; ++c) {
+      Jt[c] = s->jt + ((size_t)t * 3 + c) * (size_t)s->ntot;
+      memset(Jt[c], 0, sizeof(double) * (size_t)s->ntot);
+    }
+    const long p0 = s->np * t / T, p1 = s->np * (t + 1) / T;
+    for (long p = p0; p < p1; ++p)
+      if (s->moved[p]) deposit_particle(s, Jt, p);
+#pragma omp barrier
+#pragma omp for schedule(static)
+    for (long id = 0; id < s->ntot; ++id)
+      for (int c = 0; c < 3; ++c) {
+        double v = 0.0;
+        for (int q = 0; q < T; ++q) v += s->jt[((size_t)q * 3 + c) * (size_t)s->ntot + id];
+        s->J[c][id] = v;
+      }
   }
 }
 
 /* Step 4: J_c <- alpha_c J_c at each component's staggered location. */
 void ora_damp_J(ora_sim* s) {
+#pragma omp parallel for num_threads(g_threads) schedule(static) if (g_threads > 1)
   for (long k = 0; k < s->nn[2]; ++k)
     for (long j = 0; j < s->nn[1]; ++j)
       for (long i = 0; i < s->nn[0]; ++i) {
@@ -676,6 +755,7 @@ void ora_field_E(ora_sim* s) {
   double *Bx = s->Bh[0], *By = s->Bh[1], *Bz = s->Bh[2];
   long j0 = d3 ? 1 : 0, j1 = d3 ? N1 - 1 : 0;
   /* Ex(i+1/2, j, k): splits (xy, xz) */
+#pragma omp parallel for num_threads(g_threads) schedule(static) if (g_threads > 1)
   for (long k = 1; k <= N2 - 1; ++k)
     for (long j = j0; j <= j1; ++j)
       for (long i = 0; i <= N0 - 1; ++i) {
@@ -689,6 +769,7 @@ void ora_field_E(ora_sim* s) {
       }
   /* Ey(i, j+1/2, k): splits (yx, yz) */
   long jy1 = d3 ? N1 - 1 : 0;
+#pragma omp parallel for num_threads(g_threads) schedule(static) if (g_threads > 1)
   for (long k = 1; k <= N2 - 1; ++k)
     for (long j = 0; j <= jy1; ++j)
       for (long i = 1; i <= N0 - 1; ++i) {
@@ -701,6 +782,7 @@ void ora_field_E(ora_sim* s) {
                               -s->J[1][id] / ORA_EPS0, dt);
       }
   /* Ez(i, j, k+1/2): splits (zx, zy) */
+#pragma omp parallel for num_threads(g_threads) schedule(static) if (g_threads > 1)
   for (long k = 0; k <= N2 - 1; ++k)
     for (long j = j0; j <= j1; ++j)
       for (long i = 1; i <= N0 - 1; ++i) {
@@ -724,6 +806,7 @@ void ora_field_B(ora_sim* s) {
   double *Ex = s->E[0], *Ey = s->E[1], *Ez = s->E[2];
   long jc1 = d3 ? N1 - 1 : 0, jn1 = d3 ? N1 : 0;
   /* Bx(i, j+1/2, k+1/2): splits (xy, xz) */
+#pragma omp parallel for num_threads(g_threads) schedule(static) if (g_threads > 1)
   for (long k = 0; k <= N2 - 1; ++k)
     for (long j = 0; j <= jc1; ++j)
       for (long i = 0; i <= N0; ++i) {
@@ -735,6 +818,7 @@ void ora_field_B(ora_sim* s) {
         s->Bp[0][id] = advance(s->Bh[0][id], &s->Bs[0][0][id], &s->Bs[0][1][id], R, sA, sB, 0.0, dt);
       }
   /* By(i+1/2, j, k+1/2): splits (yx, yz) */
+#pragma omp parallel for num_threads(g_threads) schedule(static) if (g_threads > 1)
   for (long k = 0; k <= N2 - 1; ++k)
     for (long j = 0; j <= jn1; ++j)
       for (long i = 0; i <= N0 - 1; ++i) {
@@ -746,6 +830,7 @@ void ora_field_B(ora_sim* s) {
         s->Bp[1][id] = advance(s->Bh[1][id], &s->Bs[1][0][id], &s->Bs[1][1][id], R, sA, sB, 0.0, dt);
       }
   /* Bz(i+1/2, j+1/2, k): splits (zx, zy) */
+#pragma omp parallel for num_threads(g_threads) schedule(static) if (g_threads > 1)
   for (long k = 0; k <= N2; ++k)
     for (long j = 0; j <= jc1; ++j)
       for (long i = 0; i <= N0 - 1; ++i) {

@@ -37,6 +37,22 @@ def pack_particles(cell, off, u, w, prec="fp32", capacity=None, device="cuda"):
     return pos.to(device), mom.to(device)
 
 
+def pack_records(cell, off, u, w, capacity=None):
+    """FP32 pos/mom records (include/picpml.h) from device tensors: cell (n, 3)
+    int32, off (n, 3) and u (n, 3) float32, w a scalar or (n,) tensor.
+    Returns (pos, mom) of shape (capacity, 4) on the tensors' device."""
+    n = cell.shape[0]
+    cap = n if capacity is None else capacity
+    pos = torch.zeros((cap, 4), dtype=torch.float32, device=cell.device)
+    mom = torch.zeros((cap, 4), dtype=torch.float32, device=cell.device)
+    pos[:n, :3] = off
+    pos[:n, 3] = w
+    mom[:n, :3] = u
+    packed = cell[:, 0] | (cell[:, 1] << 10) | (cell[:, 2] << 20)
+    mom.view(torch.int32)[:n, 3] = packed.to(torch.int32)
+    return pos, mom
+
+
 def unpack_particles(pos, mom, n):
     """Inverse of pack_particles (host numpy): cell (n,3), off (n,3), u, w, alive."""
     pos = pos[:n].cpu()

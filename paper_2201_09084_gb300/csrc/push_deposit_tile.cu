@@ -50,7 +50,7 @@ constexpr int BXY = BX * BY, BN = BXY * BZ;
 constexpr int OX = 4, OY = 2, OZ = 2;
 constexpr int NT = 256, PT = 8;           // threads per block, particles per thread per pass
 constexpr int kBoxBytes = 9 * BN * 4;
-constexpr int kSmemBytes = kBoxBytes + 80 * 4 + (NT / 32) * 11 * 32 * 4 + 64;
+constexpr int kSmemBytes = kBoxBytes + 80 * 4 + (NT / 32) * 11 * 32 * 4 + 16 + 8 * 8;
 
 // A particle whose cell (local to the box) lies in [OX-1, OX+UX] x [OY-1, OY+TY]
 // x [OZ-1, OZ+TZ] gathers from nodes l-1 .. l+1 and deposits to nodes l .. l+1
@@ -342,6 +342,14 @@ __device__ __noinline__ void particle_global(const Geom& g, const Tables& tb, co
   if (ok) deposit_one<1, 3, float>(g, tb, f, sp, c, o, c1, o1, wd, 0.0f);
 }
 
+// The values of a species the box path reads per particle, held in registers
+// (the species table itself lives in the kernel's parameter space).
+struct Hot {
+  float4* pos;
+  float4* mom;
+  float ke, cj0, cj1, cj2;
+};
+
 // What the box path leaves for the deposit: nothing (removed or refused), an
 // in-cell move, a move across a face inside the box, or the whole particle
 // for the global path (its cell, or its new cell, lies outside the box; the
@@ -351,8 +359,7 @@ enum : int { DEP_NONE = 0, DEP_IN_CELL = 1, DEP_ACROSS = 2, DEP_OUT = 3 };
 // One particle of the box path: checks, gather from the box, Boris push,
 // move, record write-back.  Returns the deposit kind with the local cells
 // L0, L1, the offsets o (before) and o1 (after) and the mid-step weight.
-__device__ __forceinline__ int box_particle(const Geom& g, const Tables& tb, const FieldPtrs<float>& f,
-                                            const SpeciesPtrs<float>& sp, long long p, float4 a, float4 b,
+__device__ __forceinline__ int box_particle(const Geom& g, const Hot& h, long long p, float4 a, float4 b,
                                             const float* F, const int org[3], int prescribed, unsigned* status,
                                             unsigned& pushed, int& L0, int& L1, float o[3], float o1[3],
                                             float& wd) {
@@ -370,8 +377,8 @@ __device__ __forceinline__ int box_particle(const Geom& g, const Tables& tb, con
     if (!finite_value(u[ax])) bad = true;
     if (c[ax] < g.rmin[ax] || c[ax] > g.rmax[ax] || !(o[ax] >= 0.0f && o[ax] < 1.0f)) bad = true;
   }
-  float4* P = reinterpret_cast<float4*>(sp.pos);
-  float4* Mo = reinterpret_cast<float4*>(sp.mom);
+  float4* P = h.pos;
+  float4* Mo = h.mom;
   if (bad) {
     atomicOr(status, ST_BAD_PARTICLE);
     Mo[p] = make_float4(b.x, b.y, b.z, __int_as_float(-1));
@@ -392,7 +399,7 @@ __device__ __forceinline__ int box_particle(const Geom& g, const Tables& tb, con
     B[0] = tri(F + 3 * BN, l[0], o[0], bc[1], wc[1], bc[2], wc[2]);
     B[1] = tri(F + 4 * BN, bc[0], wc[0], l[1], o[1], bc[2], wc[2]);
     B[2] = tri(F + 5 * BN, bc[0], wc[0], bc[1], wc[1], l[2], o[2]);
-    boris<float>(u, E, B, sp.ke);
+    boris<float>(u, E, B, h.ke);
   }
   int c1[3];
   bool ok;
@@ -452,30 +459,37 @@ __device__ __forceinline__ int box_particle(const Geom& g, const Tables& tb, con
   return DEP_ACROSS;
 }
 
-// One thread's PT consecutive particles [p0, p1) of a species (the whole warp
-// calls it together): box path, register runs, deferred queue, then the
+// One thread's consecutive particles [p0, p1) of a species, at most `iters`
+// (the whole block calls it together with the same `iters`): box path, register runs, deferred queue, then the
 // flush of the runs and the drain of the queue.
 __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, const FieldPtrs<float>& f,
-                                            const SpeciesPtrs<float>& sp, long long p0, long long p1,
+                                            const SpeciesPtrs<float>& sp, long long p0, long long p1, int iters,
                                             const float* F, float* J, Queue& Q, int& qn, const int org[3],
                                             int prescribed, unsigned* status, unsigned& pushed) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
-  const float4* P = reinterpret_cast<const float4*>(sp.pos);
-  const float4* Mo = reinterpret_cast<const float4*>(sp.mom);
+  const Hot h = {reinterpret_cast<float4*>(sp.pos), reinterpret_cast<float4*>(sp.mom), sp.ke, sp.cj[0], sp.cj[1],
+                 sp.cj[2]};
+  const float4* P = h.pos;
+  const float4* Mo = h.mom;
   Runs R;
   R.clear();
   unsigned out = 0;   // particles of this thread for the global path
-  for (int i = 0; i < PT; ++i) {
+  float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
+  if (p0 < p1) {
+    na = P[p0];
+    nb = Mo[p0];
+  }
+  for (int i = 0; i < iters; ++i) {
     const long long p = p0 + i;
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-    if (p < p1) {
-      a = P[p];
-      b = Mo[p];
+    const float4 a = na, b = nb;
+    if (p + 1 < p1) {   // the next record is loaded while this one is worked on
+      na = P[p + 1];
+      nb = Mo[p + 1];
     }
     int L0 = -1, L1 = -1, kind = DEP_NONE;
     float o[3], o1[3], wd = 0.0f;
-    if (p < p1) kind = box_particle(g, tb, f, sp, p, a, b, F, org, prescribed, status, pushed, L0, L1, o, o1, wd);
+    if (p < p1) kind = box_particle(g, h, p, a, b, F, org, prescribed, status, pushed, L0, L1, o, o1, wd);
     if (kind == DEP_OUT) out |= 1u << i;
     bool toq = kind == DEP_ACROSS;
     if (kind == DEP_IN_CELL) {
@@ -484,7 +498,7 @@ __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, con
       if (r0) R.cell[0] = L0;
       if (r1) R.cell[1] = L0;
       toq = !r0 && !r1;
-      const float qw[3] = {sp.cj[0] * wd, sp.cj[1] * wd, sp.cj[2] * wd};
+      const float qw[3] = {h.cj0 * wd, h.cj1 * wd, h.cj2 * wd};
       add_in_cell(R, o, o1, qw, r0 ? 1.0f : 0.0f, r1 ? 1.0f : 0.0f);
     }
     const unsigned m = __ballot_sync(0xffffffffu, toq);
@@ -494,7 +508,7 @@ __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, con
         qn = 0;
       }
       if (toq) {
-        const float qw[3] = {sp.cj[0] * wd, sp.cj[1] * wd, sp.cj[2] * wd};
+        const float qw[3] = {h.cj0 * wd, h.cj1 * wd, h.cj2 * wd};
         Q.put(qn + __popc(m & lt), L0, o, L1, o1, qw);
       }
       qn += __popc(m);
@@ -524,10 +538,8 @@ __global__ void __launch_bounds__(NT, 2)
   const int tx = (g.N[0] + TX - 1) / TX, ty = (g.N[1] + TY - 1) / TY, tz = (g.N[2] + TZ - 1) / TZ;
   const int ux = (tx + UXT - 1) / UXT;
   const long long nunits = (long long)ux * ty * tz;
-  long long nlive[kTileMaxSpecies];
-#pragma unroll
-  for (int s = 0; s < kTileMaxSpecies; ++s) nlive[s] = s < L.nsp ? *L.s[s].sp.n_dev : 0;
-
+  long long* nlive = reinterpret_cast<long long*>(bar + 1);   // live count of each species
+  if (tid < L.nsp) nlive[tid] = *L.s[tid].sp.n_dev;
   if (tid == 0) {
     mbar_init(bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -615,9 +627,15 @@ __global__ void __launch_bounds__(NT, 2)
       const TileSpecies& S = L.s[s];
       long long beg, end;
       unit_range(S, t0, nt, nlive[s], beg, end);
-      for (long long base = beg; base < end; base += NT * PT) {
-        const long long p0 = base + (long long)tid * PT;
-        thread_pass(g, tb, f, S.sp, p0, min(p0 + PT, end), F, J, Q, qn, org, L.prescribed, status, pushed);
+      // passes of at most NT * PT particles, split evenly over the threads
+      // (consecutive runs of ceil or floor of the pass size / NT)
+      const long long npass = (end - beg + NT * PT - 1) / (NT * PT);
+      for (long long k = 0; k < npass; ++k) {
+        const long long b0 = beg + (end - beg) * k / npass, b1 = beg + (end - beg) * (k + 1) / npass;
+        const long long m = b1 - b0;
+        const long long p0 = b0 + m * tid / NT, p1 = b0 + m * (tid + 1) / NT;
+        thread_pass(g, tb, f, S.sp, p0, p1, (int)((m + NT - 1) / NT), F, J, Q, qn, org, L.prescribed, status,
+                    pushed);
       }
     }
     if (qn) drain_queue(Q.q, qn, J);

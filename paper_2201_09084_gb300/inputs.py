@@ -229,6 +229,49 @@ def plasma_planes(nphys, pml, d, ppc=8, u_th=0.01, beam_uz=5.0, beam_radius=16.0
     return list(beam), planes()
 
 
+def plasma_device(nphys, pml, d, ppc=8, u_th=0.01, species=("e", "p"), seed=SEED_BASE + 17, device="cuda"):
+    """The thermal plasma of `plasma` drawn on the device, for boxes whose
+    hundreds of millions of particles would take minutes to draw on the host:
+    electrons and protons, ppc per physical cell each, uniform in the cell
+    (protons on their electrons), Maxwellian u_th for both, weight
+    n0 d^3 / ppc.  Draws come from torch's counter-based generator on
+    `device` seeded with `seed` (species k uses seed + k for its momenta), so
+    a run is reproducible on the same software stack.  Cells are in x-fastest
+    order, ppc consecutive particles per cell.  Returns a list of dicts
+    (cell (n, 3) int32, off (n, 3) float32, u (n, 3) float32, w scalar, q,
+    m) of torch tensors on `device`.  The beam of `plasma` is drawn on the
+    host (`plasma_beam`)."""
+    import torch
+    lo = [int(pml[0]), int(pml[2]), int(pml[4])]
+    nx, ny, nz = (int(v) for v in nphys)
+    n = nx * ny * nz * ppc
+    w = plasma_density(u_th, d) * d ** 3 / ppc
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    idx = torch.arange(n, device=device, dtype=torch.int64) // ppc
+    cell = torch.stack([idx % nx + lo[0], (idx // nx) % ny + lo[1], idx // (nx * ny) + lo[2]], 1).to(torch.int32)
+    del idx
+    off = torch.rand((n, 3), generator=g, device=device, dtype=torch.float32)
+    out = []
+    for k, sp in enumerate(species):
+        g.manual_seed(int(seed) + 1 + k)
+        u = torch.randn((n, 3), generator=g, device=device, dtype=torch.float32) * u_th
+        q, m = (-Q_E, M_E) if sp == "e" else (Q_E, M_P)
+        out.append(dict(cell=cell, off=off, u=u, w=w, q=q, m=m, immobile=False))
+    return out
+
+
+def plasma_beam(nphys, pml, d, ppc=8, u_th=0.01, beam_uz=5.0, beam_radius=16.0, beam_length=64.0,
+                beam_density=0.1, seed=SEED_BASE + 19):
+    """The drifting beam of `plasma` (and its immobile ions) alone, drawn on
+    the host: the companion of `plasma_device`."""
+    lo = np.array([pml[0], pml[2], pml[4]], dtype=np.float64)
+    ncell = np.asarray(nphys, dtype=np.int64)
+    w = plasma_density(u_th, d) * d ** 3 / ppc
+    return list(_beam_cylinder(np.random.default_rng(seed), lo, ncell, ppc, w, beam_uz, beam_radius, beam_length,
+                               beam_density))
+
+
 def random_moves(n, lo, hi, max_step=0.95, seed=SEED_BASE + 9, w_range=(0.5, 4.0)):
     """Prescribed one-step moves for depositing in isolation: start positions
     uniform in [lo, hi) (cells, 3D), displacements uniform in +-max_step per

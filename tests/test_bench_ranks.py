@@ -54,6 +54,7 @@ def test_reference_arm_other_ranks_do_no_work():
     import bench
     args = argparse.Namespace(steps=1, warmup=3, order=1, theta=0.0)
     assert bench.run_reference(args, rank=1, world=2) is None
+    assert bench.run_reference_plasma(args, rank=1, world=2) is None
 
 
 def test_single_rank_is_identity():
@@ -80,7 +81,7 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
-    assert "4194304 macroparticles" in d["config"]["workload"]
+    assert "256x256x512" in d["config"]["workload"] and "oracle" in d["cpu_baseline"]["sample"]
 
 
 def test_batched_runs_cpu_baseline_is_a_scaled_oracle_sample():

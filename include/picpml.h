@@ -314,17 +314,17 @@ int pic_launch_count(picpml_ctx* ctx, long long* n);
 
 /* Same results as pic_diag, but allocates no device memory, ever.  The paper
  * has no counterpart: this serves callers that cannot allocate when they ask
- * for a diagnostic -- a step loop being captured into a CUDA graph (no
- * cudaMalloc during capture), a host whose device memory belongs to a pool
+ * for a diagnostic -- a host whose device memory belongs to a pool
  * allocator, a real-time loop that must not pay for or fail on an
  * allocation.  pic_diag allocates its charge-density scratch on first use;
  * this variant uses a file-scope device array of 8,388,608 doubles (64 MiB)
- * that every GPU loading the library holds until the process exits.
- * Grids whose padded node count (x rows padded to 8) exceeds that return
+ * that every GPU loading the library holds until the process exits.  Grids
+ * whose padded node count (x rows padded to 8) exceeds that return
  * PIC_EINVAL.  The first call on a device looks up the array's device
  * address; make that first call before any stream capture.  All calls share
  * the array (each call clears it first): calls that overlap on the GPU race
- * and their results are undefined.  Synchronises the stream. */
+ * and their results are undefined.  Like pic_diag it reads the results back
+ * and synchronises the stream. */
 int pic_diag_static(picpml_ctx* ctx, double* gauss, double* rho_scale, double* energy);
 
 /* Waits for the stream and reports any device-side status word. */

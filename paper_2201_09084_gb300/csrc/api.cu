@@ -950,50 +950,14 @@ int pic_inject(picpml_ctx* ctx, int sid, const void* pos, const void* mom, long 
   return PIC_OK;
 }
 
-int pic_diag(picpml_ctx* ctx, double* gauss, double* rho_scale, double* energy) {
-  NvtxRange nvtx_("picpml pic_diag");
-  int r = check_ready(ctx);
-  if (r) return r;
-  if (!ctx->rho) {
-    ctx->rho = (double*)dev_alloc(ctx, (size_t)ctx->g.size * sizeof(double));
-    if (!ctx->rho) return fail(ctx, PIC_ENOMEM, "rho");
-  }
-  CK(cudaMemsetAsync(ctx->rho, 0, (size_t)ctx->g.size * sizeof(double), ctx->stream));
-  CK(cudaMemsetAsync(ctx->diag, 0, 8 * sizeof(double), ctx->stream));
-  const pic_grid_desc& gd = ctx->gd;
-  const double V = gd.d[0] * gd.d[2] * (gd.dim == 3 ? gd.d[1] : 1.0);
-  for (auto& s : ctx->sp) {
-    const double qoe = s.desc.q / (kEps0 * V);
-    if (gd.prec == PIC_FP64)
-      CK(launch_rho<double>(gd.shape_order, ctx->g, s.desc.pos, s.desc.mom, s.n_dev, s.desc.capacity, qoe, ctx->rho,
-                            ctx->stream));
-    else
-      CK(launch_rho<float>(gd.shape_order, ctx->g, s.desc.pos, s.desc.mom, s.n_dev, s.desc.capacity, qoe, ctx->rho,
-                           ctx->stream));
-  }
-  if (gd.prec == PIC_FP64) CK(launch_gauss<double>(ctx->g, ctx->fd, ctx->rho, gd.d, ctx->diag, ctx->stream));
-  else CK(launch_gauss<float>(ctx->g, ctx->ff, ctx->rho, gd.d, ctx->diag, ctx->stream));
-  double h[3];
-  CK(cudaMemcpyAsync(h, ctx->diag, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  if (gauss) *gauss = h[0];
-  if (rho_scale) *rho_scale = h[1];
-  if (energy) *energy = h[2];
-  return pic_sync(ctx);
-}
+}  // extern "C"
 
-int pic_diag_static(picpml_ctx* ctx, double* gauss, double* rho_scale, double* energy) {
-  int r = check_ready(ctx);
-  if (r) return r;
-  double* rho = nullptr;
-  double* out = nullptr;
-  long long cap = 0;
-  CK(static_diag_buffers(&rho, &out, &cap));
-  if (ctx->g.size > cap)
-    return fail(ctx, PIC_EINVAL,
-                "pic_diag_static: the grid needs " + std::to_string(ctx->g.size) +
-                    " scratch nodes (x rows padded to 8); the static scratch holds " + std::to_string(cap));
-  // the shared array keeps the last call's contents: clear what accumulates
+namespace {
+// The Gauss-law residual, charge-density scale and field energy of the
+// current state into out[0..2] with rho as charge-density scratch (zeroed
+// here), read back to the host.  Shared by pic_diag (scratch allocated on
+// first use) and pic_diag_static (file-scope scratch).
+int diag_into(picpml_ctx* ctx, double* rho, double* out, double* gauss, double* rho_scale, double* energy) {
   CK(cudaMemsetAsync(rho, 0, (size_t)ctx->g.size * sizeof(double), ctx->stream));
   CK(cudaMemsetAsync(out, 0, 3 * sizeof(double), ctx->stream));
   const pic_grid_desc& gd = ctx->gd;
@@ -1016,6 +980,36 @@ int pic_diag_static(picpml_ctx* ctx, double* gauss, double* rho_scale, double* e
   if (rho_scale) *rho_scale = h[1];
   if (energy) *energy = h[2];
   return pic_sync(ctx);
+}
+}  // namespace
+
+extern "C" {
+
+int pic_diag(picpml_ctx* ctx, double* gauss, double* rho_scale, double* energy) {
+  NvtxRange nvtx_("picpml pic_diag");
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (!ctx->rho) {
+    ctx->rho = (double*)dev_alloc(ctx, (size_t)ctx->g.size * sizeof(double));
+    if (!ctx->rho) return fail(ctx, PIC_ENOMEM, "rho");
+  }
+  return diag_into(ctx, ctx->rho, ctx->diag, gauss, rho_scale, energy);
+}
+
+int pic_diag_static(picpml_ctx* ctx, double* gauss, double* rho_scale, double* energy) {
+  NvtxRange nvtx_("picpml pic_diag_static");
+  int r = check_ready(ctx);
+  if (r) return r;
+  double* rho = nullptr;
+  double* out = nullptr;
+  long long cap = 0;
+  CK(static_diag_buffers(&rho, &out, &cap));
+  if (ctx->g.size > cap)
+    return fail(ctx, PIC_EINVAL,
+                "pic_diag_static: the grid needs " + std::to_string(ctx->g.size) +
+                    " scratch nodes (x rows padded to 8); the static scratch holds " + std::to_string(cap));
+  // the shared array keeps the last call's contents: diag_into clears what accumulates
+  return diag_into(ctx, rho, out, gauss, rho_scale, energy);
 }
 
 int pic_state_size(picpml_ctx* ctx, long long* bytes) {

@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace picpml {
 
 constexpr double kC = 299792458.0;
@@ -128,6 +130,22 @@ constexpr double kFixDown = 1.0 / 68719476736.0;   // 2^-36
 constexpr double kFixUnit = 6.0 * 16777216.0;      // 6 * 2^24
 constexpr double kFixMaxWq = 4294967296.0;         // |w q/e| above 2^32 is refused
 constexpr double kQe = 1.602176634e-19;
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, once per device (the attribute belongs to the device's context;
+// `done` holds one bit per device ordinal < 64, shared by the callers of one
+// kernel).  Threads racing on the first launch may both set it: harmless.
+template <typename K>
+inline cudaError_t smem_limit_once(K kernel, int bytes, std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
 
 // Device status word bits.
 enum : unsigned { ST_BAD_PARTICLE = 1u, ST_FIXED_OVERFLOW = 2u, ST_INJECT_OVERFLOW = 4u, ST_TIMEOUT = 8u };

@@ -565,11 +565,10 @@ cudaError_t launch_pd1_p(const Geom& g, const Tables& tb, const FieldPtrs<T>& f,
                          int prescribed, unsigned* status, unsigned long long* pushed, int nsm, int blocks_per_sm,
                          cudaStream_t s) {
   const size_t smem = Plan<T, DIM, P>::total;
-  static bool configured = false;  // per template instance, once per process
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_pd1<T, DIM, P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static std::atomic<unsigned long long> configured{0};   // devices whose limit is set
+  {
+    cudaError_t e = smem_limit_once(k_pd1<T, DIM, P>, (int)smem, configured);
     if (e != cudaSuccess) return e;
-    configured = true;
   }
   const long long C = (long long)kNT * P;
   long long chunks = (sp.capacity + C - 1) / C;

@@ -730,11 +730,10 @@ int tile_map_bytes() { return (int)sizeof(CUtensorMap); }
 cudaError_t launch_tile(const Geom& g, const Tables& tb, const FieldPtrs<float>& f, const TileLaunch& L,
                         const void* map, unsigned* status, unsigned long long* pushed, int nsm, cudaStream_t s) {
   if (L.nsp <= 0) return cudaSuccess;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  static std::atomic<unsigned long long> configured{0};   // devices whose limit is set
+  {
+    cudaError_t e = smem_limit_once(k_tile, kSmemBytes, configured);
     if (e != cudaSuccess) return e;
-    configured = true;
   }
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile, NT, kSmemBytes);

@@ -6,9 +6,11 @@ macroparticles in the relativistic beam (Gaussian, sigma 4 / 4 / 8 cells,
 u_z ~ N(50, 0.5), 1 nC) centred 24 cells before the +z interface, order-1
 shapes, damped-current PML, dt = 0.99 x Courant limit, sorted before the
 first step; the GPU uses the launch shapes its autotuner picks (as the
-benchmark does).  After 10 steps every field component on every node is
-compared with the FP64 oracle (combined field scale, FP32 tolerance), and
-the live particles' positions as sets.
+benchmark does).  After 10 and after 100 steps (by then the beam's head
+has crossed the damped PML and left through the outer wall) every field
+component on every node is compared with the FP64 oracle (combined field
+scale, FP32 tolerance), and the live particles' positions as sets.  The
+oracle runs threaded (its loops split over the host's cores).
 """
 import os
 import sys
@@ -26,7 +28,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
 
-def test_beam_3d_160_full_size_10_steps():
+def test_beam_3d_160_full_size_100_steps():
     import torch
     import bench
     from paper_2201_09084_gb300.api import Sim, pack_particles
@@ -42,11 +44,20 @@ def test_beam_3d_160_full_size_10_steps():
     u = parts["u"].astype(np.float64)
     assert ora.add_particles(X[:, 0], X[:, 1], X[:, 2], u[:, 0], u[:, 1], u[:, 2],
                              parts["w"].astype(np.float64), parts["q"], parts["m"], False) == 0
-    gpu.step(10)
-    ora.step(10)
-    torch.cuda.synchronize()
+    O.set_threads(None)
+    try:
+        gpu.step(10)
+        ora.step(10)
+        torch.cuda.synchronize()
+        err = max_field_err(ora, gpu)
+        assert max(err.values()) < TOL["fp32"], (10, err, tuning)
+        gpu.step(90)
+        ora.step(90)
+        torch.cuda.synchronize()
+    finally:
+        O.set_threads(1)
     err = max_field_err(ora, gpu)
-    assert max(err.values()) < TOL["fp32"], (err, tuning)
+    assert max(err.values()) < TOL["fp32"], (100, err, tuning)
     # the live particles agree as sets (the GPU reorders them when sorting):
     # per axis, the sorted coordinates differ by at most the largest
     # per-particle difference (sorting is 1-Lipschitz in the max norm)
@@ -56,5 +67,7 @@ def test_beam_3d_160_full_size_10_steps():
     Xg = (pg["cell"] + pg["off"].astype(np.float64))[pg["alive"]]
     Xo = np.stack([po["X"], po["Y"], po["Z"]], 1)[po["alive"]]
     for a in range(3):
-        assert np.abs(np.sort(Xg[:, a]) - np.sort(Xo[:, a])).max() < 2e-6
-    print(f"\nfull-size beam, 10 steps, tuning {tuning}: max rel field error {max(err.values()):.3e}")
+        assert np.abs(np.sort(Xg[:, a]) - np.sort(Xo[:, a])).max() < 1e-5
+    assert int(po["alive"].sum()) < bench.NPART, "part of the beam has left through the PML"
+    print(f"\nfull-size beam, 100 steps, tuning {tuning}: max rel field error {max(err.values()):.3e}, "
+          f"{int(po['alive'].sum())} of {bench.NPART} particles left")

@@ -94,7 +94,15 @@ def test_push_deposit_stage_parity(dim, order, prec, mode):
     ora.deposit()
     gpu.deposit()
     err = max_field_err(ora, gpu, ("Jx", "Jy", "Jz"))
-    assert max(err.values()) < 10 * TOL[prec], err
+    print(f"\nJ error of max |J| ({dim}D order {order} {prec} {mode}): {max(err.values()):.3e}")
+    assert max(err.values()) < TOL[prec], err
+    # node by node where the current is not small: relative to the node's own value
+    for n in ("Jx", "Jy", "Jz"):
+        a = ora.field(n)
+        g = gpu.field(n).cpu().numpy()
+        big = np.abs(a) > 0.01 * np.abs(a).max()
+        rel = float((np.abs(g[big] - a[big]) / np.abs(a[big])).max())
+        assert rel < (1e-3 if prec == "fp32" else 1e-9), (n, rel)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
@@ -191,9 +199,9 @@ def test_sort_keeps_particles_and_drops_removed():
     after = pos[:n].cpu().numpy()
     c = mom.view(torch.int32)[:n, 3].cpu().numpy().astype(np.int64)
     i, j, k = c & 1023, (c >> 10) & 1023, (c >> 20) & 2047
-    # tile-major order: 4x4x4-cell tiles, then the cell inside the tile
-    tx, ty = (38 + 3) // 4, (28 + 3) // 4
-    key = ((i >> 2) + tx * ((j >> 2) + ty * (k >> 2))) * 64 + (i & 3) + 4 * ((j & 3) + 4 * (k & 3))
+    # tile-major order: 8x4x4-cell tiles, then the cell inside the tile, x fastest
+    tx, ty = (38 + 7) // 8, (28 + 3) // 4
+    key = ((i >> 3) + tx * ((j >> 2) + ty * (k >> 2))) * 128 + (i & 7) + 8 * ((j & 3) + 4 * (k & 3))
     assert np.all(np.diff(key) >= 0)
     key = lambda a: np.lexsort(a.T[::-1])
     assert np.array_equal(before[key(before)], after[key(after)])

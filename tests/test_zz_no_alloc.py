@@ -1,9 +1,8 @@
 """pic_diag_static, the diagnostic entry point that allocates no device memory.
 
-Callers that cannot allocate while they run -- a step loop being recorded
-into a CUDA graph, a device whose memory belongs to a pool allocator, a
-real-time loop -- call pic_diag_static instead of pic_diag, which allocates
-its charge-density scratch on first use.  The static variant keeps that
+Callers that cannot allocate while they run -- a device whose memory belongs
+to a pool allocator, a real-time loop -- call pic_diag_static instead of
+pic_diag, which allocates its charge-density scratch on first use.  The static variant keeps that
 scratch in a file-scope device array shared by all calls, so each call must
 clear it: two calls in a row must both agree with pic_diag.
 

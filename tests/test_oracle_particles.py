@@ -204,3 +204,33 @@ def test_boris_ExB_drift():
     uavg /= n
     vd = np.cross(E, B) / (B @ B)
     np.testing.assert_allclose(uavg * C, vd, rtol=2e-3, atol=2e-3 * np.linalg.norm(vd))
+
+
+def test_threaded_oracle_equals_serial_up_to_summation_order():
+    """The oracle's threaded loops (per-thread current arrays summed in thread
+    order) give the serial result up to the order of the floating-point sums,
+    and the same bits on a repeat with the same thread count."""
+    import oracle as O
+    from paper_2201_09084_gb300 import inputs as I
+    D = (1e-6, 1.1e-6, 0.9e-6)
+    nphys, pml = (12, 10, 14), (4,) * 6
+    parts = I.random_particles(3, 3000, [3, 3, 3], [17, 15, 19], u_rms=0.6, seed=21)[0]
+    dt = O.yee_dt(D, 0.95, 3)
+    out = {}
+    try:
+        for label, T in (("serial", 1), ("t4", 4), ("t4b", 4)):
+            O.set_threads(T)
+            s = O.OracleSim(3, nphys, pml, D, dt, order=3, alpha_mode="damped")
+            X = I.absolute(parts["cell"], parts["off"])
+            u = parts["u"].astype(np.float64)
+            s.add_particles(X[:, 0], X[:, 1], X[:, 2], u[:, 0], u[:, 1], u[:, 2], parts["w"].astype(np.float64),
+                            parts["q"], parts["m"])
+            s.step(8)
+            out[label] = {k: s.field(k) for k in ("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx")}
+    finally:
+        O.set_threads(1)
+    for k, a in out["serial"].items():
+        scale = np.abs(a).max()
+        assert scale > 0
+        assert np.abs(out["t4"][k] - a).max() <= 1e-12 * scale, k
+        assert np.array_equal(out["t4"][k], out["t4b"][k]), k

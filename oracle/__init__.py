@@ -66,6 +66,7 @@ def lib():
             L.ora_destroy.argtypes = [C.c_void_p]
             L.ora_set_prescribed.argtypes = [C.c_void_p, C.c_int]
             L.ora_set_filter.argtypes = [C.c_void_p, C.c_int]
+            L.ora_set_solver.argtypes = [C.c_void_p, C.c_int]
             L.ora_set_conductor.argtypes = [C.c_void_p, C.c_void_p]
             L.ora_filter_J.argtypes = [C.c_void_p]
             L.ora_set_face_alpha.argtypes = [C.c_void_p, ip]
@@ -211,6 +212,12 @@ def fixed_rho2d(order, cell, off, nn):
     return out.reshape(nn[1], nn[0])
 
 
+def ck_dt(d, cfl, dim):
+    """dt = cfl * Courant limit of the Cole-Karkkainen scheme, min(d)/c."""
+    axes = (0, 1, 2) if dim == 3 else (0, 2)
+    return cfl * min(d[a] for a in axes) / C_LIGHT
+
+
 def yee_dt(d, cfl, dim):
     """dt = cfl * Courant limit of the Yee scheme, 1/(c sqrt(sum 1/d_i^2))."""
     axes = (0, 1, 2) if dim == 3 else (0, 2)
@@ -225,7 +232,8 @@ class OracleSim:
     """
 
     def __init__(self, dim, n, pml, d, dt, order=1, alpha_mode="damped",
-                 sig_coef=4.0, delta=6.0, sig_exp=2.0, v_assumed=C_LIGHT, face_alpha=None, filter_passes=0):
+                 sig_coef=4.0, delta=6.0, sig_exp=2.0, v_assumed=C_LIGHT, face_alpha=None, filter_passes=0,
+                 solver="yee"):
         L = lib()
         self.dim = dim
         n3 = (C.c_int * 3)(*[int(v) for v in n])
@@ -248,6 +256,10 @@ class OracleSim:
             self.set_face_alpha(face_alpha)
         if filter_passes:
             lib().ora_set_filter(self._h, int(filter_passes))
+        if solver not in ("yee", "ck"):
+            raise ValueError("solver is 'yee' or 'ck'")
+        self.solver = solver
+        lib().ora_set_solver(self._h, int(solver == "ck"))
 
     def set_conductor(self, mask):
         """Zeroed-field (perfect conductor) cells: mask of shape (Nz, Ny, Nx)

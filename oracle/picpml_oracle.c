@@ -88,6 +88,7 @@ int ora_set_threads(int n) {
 typedef struct ora_sim {
   int dim, order, alpha_mode, prescribed;
   int filter_passes;                /* binomial passes on J before each E update */
+  int ck;                           /* 1: Cole-Karkkainen differences in Faraday's law */
   int face_mode[6];                 /* alpha mode of each face (-x,+x,-y,+y,-z,+z) */
   int n[3], plo[3], phi[3], N[3];   /* physical cells, PML cells low/high, total cells */
   long nn[3];                       /* nodes per axis in the arrays (1 for y in 2D) */
@@ -702,6 +703,64 @@ void ora_filter_J(ora_sim* s) {
 /* Number of binomial passes applied to J at the start of each E update. */
 void ora_set_filter(ora_sim* s, int passes) { s->filter_passes = passes > 0 ? passes : 0; }
 
+/* Field solver: 0 = Yee, 1 = Cole-Karkkainen (the solver of the paper's
+ * single-particle and LWFA runs, App. A).  The CK scheme (Cole 1997, 2002;
+ * Karkkainen et al. 2006) keeps Yee's staggering and Ampere's law and
+ * replaces each difference of E in Faraday's law by its average over the two
+ * transverse axes with the weights (1/4, 1/2, 1/4) per axis.  The discrete
+ * curl of a Fourier mode then carries, for the derivative along a, the factor
+ * prod_{b != a} cos^2(k_b d_b / 2), which gives the dispersion relation
+ *   sin^2(w dt/2) = (c dt)^2 sum_a sin^2(k_a d_a/2)/d_a^2 prod_{b!=a} cos^2(k_b d_b/2):
+ * stable up to c dt = min d_a, and free of dispersion along an axis at
+ * c dt = d_a (cubic cells: along every axis at c dt = d). */
+void ora_set_solver(ora_sim* s, int ck) { s->ck = ck ? 1 : 0; }
+
+/* E_c at index (i, j, k), continued beyond the grid by its images across the
+ * conducting outer walls: odd across a wall the component is tangential to
+ * (a node axis b != c: E(-m) = -E(m), E(N_b + m) = -E(N_b - m)), even across
+ * a wall it is normal to (its own, centred axis: E(-1) = E(0),
+ * E(N_c) = E(N_c - 1)).  The CK averages read these images next to the
+ * walls; a PEC cavity eigenmode is then an exact discrete eigenmode. */
+static double e_img(const ora_sim* s, int c, long i, long j, long k) {
+  long x[3] = {i, j, k};
+  double sign = 1.0;
+  for (int b = 0; b < 3; ++b) {
+    if (s->dim == 2 && b == 1) { x[1] = 0; continue; }
+    const long N = s->N[b];
+    if (b == c) {
+      if (x[b] < 0) x[b] = -1 - x[b];
+      else if (x[b] > N - 1) x[b] = 2 * N - 1 - x[b];
+    } else {
+      if (x[b] < 0) { x[b] = -x[b]; sign = -sign; }
+      else if (x[b] > N) { x[b] = 2 * N - x[b]; sign = -sign; }
+    }
+  }
+  return sign * s->E[c][IX(s, x[0], x[1], x[2])];
+}
+
+/* CK difference of E_c along axis a at the B location of index (i, j, k):
+ * sum over p, q in {-1, 0, 1} of w_p w_q [E_c(n + e_a) - E_c(n)] with
+ * n = (i, j, k) + p e_b + q e_d, (b, d) the two other axes, w = (1/4, 1/2,
+ * 1/4); in 2D the y axis is not averaged. */
+static double ck_diff(const ora_sim* s, int c, int a, long i, long j, long k) {
+  static const double w[3] = {0.25, 0.5, 0.25};
+  const int b = (a + 1) % 3, d = (a + 2) % 3;
+  double acc = 0.0;
+  for (int p = -1; p <= 1; ++p)
+    for (int q = -1; q <= 1; ++q) {
+      const int flat_b = s->dim == 2 && b == 1, flat_d = s->dim == 2 && d == 1;
+      if ((flat_b && p != 0) || (flat_d && q != 0)) continue;
+      const double wt = (flat_b ? 1.0 : w[p + 1]) * (flat_d ? 1.0 : w[q + 1]);
+      long n0[3] = {i, j, k};
+      n0[b] += p;
+      n0[d] += q;
+      long n1[3] = {n0[0], n0[1], n0[2]};
+      n1[a] += 1;
+      acc += wt * (e_img(s, c, n1[0], n1[1], n1[2]) - e_img(s, c, n0[0], n0[1], n0[2]));
+    }
+  return acc;
+}
+
 /* Zeroed-field cells (the cavity run of Sec. III has cells where E and B
  * are zero; the paper gives no geometry).  A marked cell is a perfect
  * conductor: every E component on its 12 edges is zero after each E update,
@@ -797,9 +856,12 @@ void ora_field_E(ora_sim* s) {
   if (s->cond) apply_conductor(s);
 }
 
-/* B^{n+3/2} = B^{n+1/2} - dt curl E^{n+1}  (Eqs. MaxwellB, MaxwellSum). */
+/* B^{n+3/2} = B^{n+1/2} - dt curl E^{n+1}  (Eqs. MaxwellB, MaxwellSum); with
+ * the CK solver the differences of E are the transversely averaged ones of
+ * ck_diff. */
 void ora_field_B(ora_sim* s) {
   const double dt = s->dt;
+  const int ck = s->ck;
   const double dx = s->d[0], dy = s->d[1], dz = s->d[2];
   const int d3 = s->dim == 3;
   const long N0 = s->N[0], N1 = s->N[1], N2 = s->N[2];
@@ -812,8 +874,13 @@ void ora_field_B(ora_sim* s) {
       for (long i = 0; i <= N0; ++i) {
         long id = IX(s, i, j, k);
         double R[2];
-        R[0] = d3 ? -(Ez[IX(s, i, j + 1, k)] - Ez[id]) / dy : 0.0;
-        R[1] = (Ey[IX(s, i, j, k + 1)] - Ey[id]) / dz;
+        if (ck) {
+          R[0] = d3 ? -ck_diff(s, 2, 1, i, j, k) / dy : 0.0;
+          R[1] = ck_diff(s, 1, 2, i, j, k) / dz;
+        } else {
+          R[0] = d3 ? -(Ez[IX(s, i, j + 1, k)] - Ez[id]) / dy : 0.0;
+          R[1] = (Ey[IX(s, i, j, k + 1)] - Ey[id]) / dz;
+        }
         double sA = d3 ? s->s_cent[1][j] : 0.0, sB = s->s_cent[2][k];
         s->Bp[0][id] = advance(s->Bh[0][id], &s->Bs[0][0][id], &s->Bs[0][1][id], R, sA, sB, 0.0, dt);
       }
@@ -824,8 +891,13 @@ void ora_field_B(ora_sim* s) {
       for (long i = 0; i <= N0 - 1; ++i) {
         long id = IX(s, i, j, k);
         double R[2];
-        R[0] = (Ez[IX(s, i + 1, j, k)] - Ez[id]) / dx;
-        R[1] = -(Ex[IX(s, i, j, k + 1)] - Ex[id]) / dz;
+        if (ck) {
+          R[0] = ck_diff(s, 2, 0, i, j, k) / dx;
+          R[1] = -ck_diff(s, 0, 2, i, j, k) / dz;
+        } else {
+          R[0] = (Ez[IX(s, i + 1, j, k)] - Ez[id]) / dx;
+          R[1] = -(Ex[IX(s, i, j, k + 1)] - Ex[id]) / dz;
+        }
         double sA = s->s_cent[0][i], sB = s->s_cent[2][k];
         s->Bp[1][id] = advance(s->Bh[1][id], &s->Bs[1][0][id], &s->Bs[1][1][id], R, sA, sB, 0.0, dt);
       }
@@ -836,8 +908,13 @@ void ora_field_B(ora_sim* s) {
       for (long i = 0; i <= N0 - 1; ++i) {
         long id = IX(s, i, j, k);
         double R[2];
-        R[0] = -(Ey[IX(s, i + 1, j, k)] - Ey[id]) / dx;
-        R[1] = d3 ? (Ex[IX(s, i, j + 1, k)] - Ex[id]) / dy : 0.0;
+        if (ck) {
+          R[0] = -ck_diff(s, 1, 0, i, j, k) / dx;
+          R[1] = d3 ? ck_diff(s, 0, 1, i, j, k) / dy : 0.0;
+        } else {
+          R[0] = -(Ey[IX(s, i + 1, j, k)] - Ey[id]) / dx;
+          R[1] = d3 ? (Ex[IX(s, i, j + 1, k)] - Ex[id]) / dy : 0.0;
+        }
         double sA = s->s_cent[0][i], sB = d3 ? s->s_cent[1][j] : 0.0;
         s->Bp[2][id] = advance(s->Bh[2][id], &s->Bs[2][0][id], &s->Bs[2][1][id], R, sA, sB, 0.0, dt);
       }

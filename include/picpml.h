@@ -65,7 +65,9 @@ typedef enum {
 } pic_status;
 
 typedef enum {
-  PIC_FP32 = 0,         /* FP32 fields, momenta and offsets; FP64 PML splits */
+  PIC_FP32 = 0,         /* FP32 fields, momenta and offsets; PML split parts
+                           as float-float pairs, or IEEE FP64 with
+                           pic_grid_desc.split_fp64 = 1 */
   PIC_FP64 = 1,         /* everything FP64 (the plain FP64 form) */
   PIC_FP32_FIXED64 = 2  /* as PIC_FP32, current accumulated in int64 fixed
                            point: deterministic, bit-identical J (3D and 2D;
@@ -87,9 +89,24 @@ typedef enum {
                            the stored weight becomes w exp(-I) */
 } pml_alpha_mode;
 
+/* Field solvers (pic_grid_desc.solver). */
+typedef enum {
+  PIC_SOLVER_YEE = 0,   /* Yee leapfrog; Courant limit 1/(c sqrt(sum 1/d_i^2)) */
+  PIC_SOLVER_CK = 1     /* Cole-Karkkainen (the solver of the paper's
+                           single-particle and LWFA runs, App. A; Cole
+                           1997/2002, Karkkainen et al. 2006): Faraday's law
+                           takes every difference of E averaged over the two
+                           transverse axes with weights (1/4, 1/2, 1/4) per
+                           axis (images across the conducting outer walls:
+                           odd for a tangential component, even for a normal
+                           one); Ampere's law is Yee's.  Courant limit
+                           min(d_i)/c; no numerical dispersion along an axis
+                           at c dt = d on cubic cells */
+} pic_solver;
+
 /* Grid description.  n[] counts PHYSICAL cells (the PML cells of pml_desc
  * are added outside them); n[1] is ignored in 2D.  dt <= 0 selects
- * cfl * (Yee Courant limit 1/(c sqrt(sum 1/d_i^2))). */
+ * cfl * (the solver's Courant limit). */
 typedef struct pic_grid_desc {
   int dim;              /* 2 or 3 */
   int n[3];             /* physical cells per axis */
@@ -108,6 +125,8 @@ typedef struct pic_grid_desc {
                            binomial (1, 2, 1)/4 stencil along each axis (App.
                            A; values beyond the node arrays count as zero);
                            the field then conserves the filtered charge */
+  int solver;           /* pic_solver: PIC_SOLVER_YEE (0, default) or
+                           PIC_SOLVER_CK */
 } pic_grid_desc;
 
 /* PML description: conductivity sigma(d) = coef eps0 c / Delta (d/delta)^p at
@@ -215,9 +234,11 @@ int pic_set_old_positions(picpml_ctx* ctx, int sid, const void* src);
 int pic_get_current_fixed(picpml_ctx* ctx, int comp, long long* dst);
 
 /* Field update: E^{n+1} = E^n + dt (c^2 curl B^{n+1/2} - J/eps0), then
- * B^{n+3/2} = B^{n+1/2} - dt curl E^{n+1}; split-field PML components in
- * every location with sigma > 0 (Eqs. MaxwellE, MaxwellB, MaxwellSum), FP64.
- * Consumes and zeroes J. */
+ * B^{n+3/2} = B^{n+1/2} - dt curl E^{n+1} (with PIC_SOLVER_CK the curl of E
+ * takes the Cole-Karkkainen differences); split-field PML components in
+ * every location with sigma > 0 (Eqs. MaxwellE, MaxwellB, MaxwellSum), their
+ * parts in IEEE FP64 (PIC_FP64, or PIC_FP32 with split_fp64 = 1) or as
+ * float-float pairs (PIC_FP32 by default).  Consumes and zeroes J. */
 int field_step(picpml_ctx* ctx);
 
 /* The particle half of a time step in one fused kernel per species: gather,

@@ -18,6 +18,7 @@ PIC_FP32, PIC_FP64, PIC_FP32_FIXED64 = 0, 1, 2
 PREC = {"fp32": PIC_FP32, "fp64": PIC_FP64, "fixed64": PIC_FP32_FIXED64}
 ALPHA = {"zero": 0, "one": 1, "damped": 2, "weight": 3}
 TUNING_TILE = 2   # PIC_TUNING_TILE: the tile-resident particle kernel
+SOLVER = {"yee": 0, "ck": 1}
 STATUS = {0: "PIC_OK", -1: "PIC_EINVAL", -2: "PIC_ENOMEM", -3: "PIC_ECUDA", -4: "PIC_ECFL",
           -5: "PIC_EOVERFLOW", -6: "PIC_ETIMEOUT", -7: "PIC_ENOTIMPL", -8: "PIC_ESTATE",
           -9: "PIC_EPARTICLE"}
@@ -32,7 +33,8 @@ class PicError(RuntimeError):
 class GridDesc(C.Structure):
     _fields_ = [("dim", C.c_int), ("n", C.c_int * 3), ("d", C.c_double * 3), ("dt", C.c_double),
                 ("cfl", C.c_double), ("shape_order", C.c_int), ("prec", C.c_int),
-                ("sort_every", C.c_int), ("split_fp64", C.c_int), ("filter_passes", C.c_int)]
+                ("sort_every", C.c_int), ("split_fp64", C.c_int), ("filter_passes", C.c_int),
+                ("solver", C.c_int)]
 
 
 class PmlDesc(C.Structure):

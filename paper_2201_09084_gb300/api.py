@@ -85,7 +85,7 @@ class Sim:
 
     def __init__(self, dim, n, d, pml, *, dt=0.0, cfl=0.99, order=1, prec="fp32", sort_every=0,
                  alpha_mode="damped", sigma_coef=4.0, delta=6.0, exponent=2.0, v_assumed=0.0,
-                 split_fp64=False, face_alpha=None, filter_passes=0, stream=None):
+                 split_fp64=False, face_alpha=None, filter_passes=0, solver="yee", stream=None):
         self.lib = L.load()
         self.prec = prec
         self.dim = dim
@@ -98,6 +98,7 @@ class Sim:
         g.dt, g.cfl, g.shape_order, g.prec, g.sort_every = float(dt), float(cfl), int(order), L.PREC[prec], int(sort_every)
         g.split_fp64 = int(bool(split_fp64))
         g.filter_passes = int(filter_passes)
+        g.solver = L.SOLVER[solver]
         ctx = C.c_void_p()
         L.check(self.lib.pic_init(C.byref(ctx), C.byref(g), C.c_void_p(self.stream.cuda_stream)))
         self.ctx = ctx

@@ -20,6 +20,8 @@ cudaError_t launch_field_E(const Geom&, const Tables&, const FieldPtrs<T>&, int 
 template <typename T>
 cudaError_t launch_field_B(const Geom&, const Tables&, const FieldPtrs<T>&, int split_ff, int kz, cudaStream_t);
 template <typename T>
+cudaError_t launch_field_B_ck(const Geom&, const Tables&, const FieldPtrs<T>&, int split_ff, cudaStream_t);
+template <typename T>
 cudaError_t launch_filter_J(const Geom&, const FieldPtrs<T>&, T* const O[3], cudaStream_t);
 template <typename T>
 cudaError_t launch_particles(int mode, int order, const Geom&, const Tables&, const FieldPtrs<T>&,
@@ -185,7 +187,15 @@ void* dev_alloc(picpml_ctx* ctx, size_t bytes) {
   return p;
 }
 
+// Courant limit of the field solver: Yee 1/(c sqrt(sum 1/d_a^2)); the
+// Cole-Karkkainen scheme min(d_a)/c (its averaged differences keep the
+// amplification of every Fourier mode within that of a 1D wave).
 double courant_limit(const pic_grid_desc& g) {
+  if (g.solver == PIC_SOLVER_CK) {
+    double m = std::min(g.d[0], g.d[2]);
+    if (g.dim == 3) m = std::min(m, g.d[1]);
+    return m / kC;
+  }
   double s = 1.0 / (g.d[0] * g.d[0]) + 1.0 / (g.d[2] * g.d[2]);
   if (g.dim == 3) s += 1.0 / (g.d[1] * g.d[1]);
   return 1.0 / (kC * std::sqrt(s));
@@ -345,7 +355,10 @@ int run_field(picpml_ctx* ctx) {
     ctx->launches += 2;
   }
   CK(launch_field_E<T>(ctx->g, ctx->tb, f, ctx->split_ff(), ctx->kz, ctx->stream));
-  CK(launch_field_B<T>(ctx->g, ctx->tb, f, ctx->split_ff(), ctx->kz, ctx->stream));
+  if (ctx->gd.solver == PIC_SOLVER_CK)
+    CK(launch_field_B_ck<T>(ctx->g, ctx->tb, f, ctx->split_ff(), ctx->stream));
+  else
+    CK(launch_field_B<T>(ctx->g, ctx->tb, f, ctx->split_ff(), ctx->kz, ctx->stream));
   ctx->launches += 2;
   for (int c = 0; c < 3; ++c) std::swap(f.Bh[c], f.Bp[c]);
   return PIC_OK;
@@ -399,6 +412,8 @@ int pic_init(picpml_ctx** out, const pic_grid_desc* g, void* stream) {
   if (g->prec != PIC_FP32 && g->prec != PIC_FP64 && g->prec != PIC_FP32_FIXED64)
     return fail(nullptr, PIC_EINVAL, "bad prec");
   if (g->filter_passes < 0 || g->filter_passes > 8) return fail(nullptr, PIC_EINVAL, "filter_passes must be 0..8");
+  if (g->solver != PIC_SOLVER_YEE && g->solver != PIC_SOLVER_CK)
+    return fail(nullptr, PIC_EINVAL, "solver must be PIC_SOLVER_YEE or PIC_SOLVER_CK");
   for (int a = 0; a < 3; ++a) {
     if (g->dim == 2 && a == 1) continue;
     if (g->n[a] < 1 || !(g->d[a] > 0)) return fail(nullptr, PIC_EINVAL, "cells and cell sizes must be positive");
@@ -414,7 +429,7 @@ int pic_init(picpml_ctx** out, const pic_grid_desc* g, void* stream) {
     if (!(gd.cfl > 0 && gd.cfl <= 1.0)) return fail(nullptr, PIC_EINVAL, "dt <= 0 needs 0 < cfl <= 1");
     dt = gd.cfl * lim;
   }
-  if (dt > lim * (1 + 1e-12)) return fail(nullptr, PIC_ECFL, "dt above the Yee Courant limit");
+  if (dt > lim * (1 + 1e-12)) return fail(nullptr, PIC_ECFL, "dt above the field solver's Courant limit");
   picpml_ctx* ctx = new picpml_ctx();
   ctx->gd = gd;
   ctx->dt = dt;

@@ -91,6 +91,15 @@ __global__ void __launch_bounds__(256, KZ == 1 && sizeof(T) == 4 ? 6 : 4) k_fiel
   }
 }
 
+// The B pass of the Cole-Karkkainen solver (one node per thread; each B
+// component reads a 3 x 3 transverse neighbourhood of two E components).
+template <typename T, int DIM, int SPL>
+__global__ void __launch_bounds__(256) k_field_B_ck(Geom g, Tables tb, FieldPtrs<T> f) {
+  int i, j, k0;
+  if (!node_of_thread<DIM>(g, 1, i, j, k0)) return;
+  fn::b_update_ck<T, DIM, SPL>(g, tb, f, i, j, k0, g.idx(i, j, k0));
+}
+
 inline dim3 field_grid(const Geom& g, int KZ) {
   const long long nk = (g.nn[2] + KZ - 1) / KZ;
   if (g.dim == 3) return dim3((unsigned)(((long long)g.nn[0] * g.nn[1] + 255) / 256), (unsigned)nk, 1);
@@ -213,6 +222,23 @@ cudaError_t launch_field_B(const Geom& g, const Tables& tb, const FieldPtrs<T>& 
   return launch_B<T, 0, 1>(g, tb, f, s);
 }
 
+// The CK B pass (Faraday's law with the transversely averaged differences).
+template <typename T>
+cudaError_t launch_field_B_ck(const Geom& g, const Tables& tb, const FieldPtrs<T>& f, int split_ff, cudaStream_t s) {
+  const dim3 grd = field_grid(g, 1);
+  if (sizeof(T) == 4 && split_ff) {
+    if (g.dim == 3) k_field_B_ck<T, 3, 1><<<grd, 256, 0, s>>>(g, tb, f);
+    else k_field_B_ck<T, 2, 1><<<grd, 256, 0, s>>>(g, tb, f);
+  } else {
+    if (g.dim == 3) k_field_B_ck<T, 3, 0><<<grd, 256, 0, s>>>(g, tb, f);
+    else k_field_B_ck<T, 2, 0><<<grd, 256, 0, s>>>(g, tb, f);
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_field_B_ck<float>(const Geom&, const Tables&, const FieldPtrs<float>&, int, cudaStream_t);
+template cudaError_t launch_field_B_ck<double>(const Geom&, const Tables&, const FieldPtrs<double>&, int,
+                                               cudaStream_t);
 template cudaError_t launch_field_E<float>(const Geom&, const Tables&, const FieldPtrs<float>&, int, int,
                                            cudaStream_t);
 template cudaError_t launch_field_E<double>(const Geom&, const Tables&, const FieldPtrs<double>&, int, int,

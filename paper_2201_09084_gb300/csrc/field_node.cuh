@@ -224,5 +224,122 @@ __device__ __forceinline__ void b_update(const Geom& g, const Tables& tb, const 
   if (spz) store_parts<SPL>(f.Bs[2], id, qz);
 }
 
+// ---------------------------------------------------------------------------
+// Cole-Karkkainen (CK) solver (App. A: the paper's single-particle and LWFA
+// runs; the scheme of Cole 1997/2002 and Karkkainen et al. 2006): Faraday's
+// law takes each difference of E averaged over the two transverse axes with
+// weights (1/4, 1/2, 1/4) per axis; Ampere's law (e_update) is Yee's.  Next
+// to the conducting outer walls the averages read E's images: odd across a
+// wall the component is tangential to, even across a wall it is normal to.
+// ---------------------------------------------------------------------------
+
+// E_c at index (i, j, k) of the grid or of its images (|offset| <= 1 cell
+// beyond a wall).
+template <typename T, int DIM>
+__device__ __forceinline__ T e_img(const Geom& g, const T* __restrict__ E, int c, int i, int j, int k) {
+  int x[3] = {i, j, k};
+  bool neg = false;
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    if (DIM == 2 && b == 1) {
+      x[1] = 0;
+      continue;
+    }
+    const int N = g.N[b];
+    if (b == c) {              // centred along its own axis: even images
+      if (x[b] < 0) x[b] = -1 - x[b];
+      else if (x[b] > N - 1) x[b] = 2 * N - 1 - x[b];
+    } else {                   // on the nodes of the other axes: odd images
+      if (x[b] < 0) {
+        x[b] = -x[b];
+        neg = !neg;
+      } else if (x[b] > N) {
+        x[b] = 2 * N - x[b];
+        neg = !neg;
+      }
+    }
+  }
+  const T v = E[g.idx(x[0], x[1], x[2])];
+  return neg ? -v : v;
+}
+
+// CK difference of E_c along axis a at the B location of index (i, j, k).
+template <typename T, int DIM>
+__device__ __forceinline__ T ck_diff(const Geom& g, const T* __restrict__ E, int c, int a, int i, int j, int k) {
+  const int b = (a + 1) % 3, d = (a + 2) % 3;
+  T acc = T(0);
+#pragma unroll
+  for (int p = -1; p <= 1; ++p)
+#pragma unroll
+    for (int q = -1; q <= 1; ++q) {
+      const bool flat_b = DIM == 2 && b == 1, flat_d = DIM == 2 && d == 1;
+      if ((flat_b && p != 0) || (flat_d && q != 0)) continue;
+      const T w = (flat_b ? T(1) : (p == 0 ? T(0.5) : T(0.25))) * (flat_d ? T(1) : (q == 0 ? T(0.5) : T(0.25)));
+      int n0[3] = {i, j, k};
+      n0[b] += p;
+      n0[d] += q;
+      int n1[3] = {n0[0], n0[1], n0[2]};
+      n1[a] += 1;
+      acc += w * (e_img<T, DIM>(g, E, c, n1[0], n1[1], n1[2]) - e_img<T, DIM>(g, E, c, n0[0], n0[1], n0[2]));
+    }
+  return acc;
+}
+
+// B^{n+3/2} at node (i,j,k) into Bp with the CK differences (b_update's
+// split-field treatment otherwise).
+template <typename T, int DIM, int SPL>
+__device__ __forceinline__ void b_update_ck(const Geom& g, const Tables& tb, const FieldPtrs<T>& f, int i, int j,
+                                            int k, long long id) {
+  const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
+  const T Sx = courant<T>(g, 0), Sy = courant<T>(g, 1), Sz = courant<T>(g, 2);
+  const bool jc = DIM == 2 || j <= N1 - 1;
+  const bool ic = i <= N0 - 1;
+  const bool kc = k <= N2 - 1;
+  const float sxc = ic ? tb.sdtf_c[0][i] : 0.f;
+  const float syc = DIM == 3 && jc ? tb.sdtf_c[1][j] : 0.f;
+  const float szc = kc ? tb.sdtf_c[2][k] : 0.f;
+  const bool px = ic && pml_cent(g, 0, i);
+  const bool py = DIM == 3 && jc && pml_cent(g, 1, j);
+  const bool pz = kc && pml_cent(g, 2, k);
+  const bool okx = jc && kc, oky = ic && kc, okz = ic && jc;
+  const bool spx = okx && (py || pz), spy = oky && (px || pz), spz = okz && (px || py);
+  const T* __restrict__ Ex = f.E[0];
+  const T* __restrict__ Ey = f.E[1];
+  const T* __restrict__ Ez = f.E[2];
+  if (okx) {
+    const T r0 = DIM == 3 ? -Sy * ck_diff<T, DIM>(g, Ez, 2, 1, i, j, k) : T(0);
+    const T r1 = Sz * ck_diff<T, DIM>(g, Ey, 1, 2, i, j, k);
+    if (spx) {
+      Parts<SPL> q = load_parts<SPL>(f.Bs[0], id);
+      f.Bp[0][id] = advance<T, SPL, true>(tb, q, DIM == 3 ? 1 : -1, j, 2, k, r0, r1, T(0), syc, szc);
+      store_parts<SPL>(f.Bs[0], id, q);
+    } else {
+      f.Bp[0][id] = f.Bh[0][id] + (r0 + r1);
+    }
+  }
+  if (oky) {
+    const T r0 = Sx * ck_diff<T, DIM>(g, Ez, 2, 0, i, j, k);
+    const T r1 = -Sz * ck_diff<T, DIM>(g, Ex, 0, 2, i, j, k);
+    if (spy) {
+      Parts<SPL> q = load_parts<SPL>(f.Bs[1], id);
+      f.Bp[1][id] = advance<T, SPL, true>(tb, q, 0, i, 2, k, r0, r1, T(0), sxc, szc);
+      store_parts<SPL>(f.Bs[1], id, q);
+    } else {
+      f.Bp[1][id] = f.Bh[1][id] + (r0 + r1);
+    }
+  }
+  if (okz) {
+    const T r0 = -Sx * ck_diff<T, DIM>(g, Ey, 1, 0, i, j, k);
+    const T r1 = DIM == 3 ? Sy * ck_diff<T, DIM>(g, Ex, 0, 1, i, j, k) : T(0);
+    if (spz) {
+      Parts<SPL> q = load_parts<SPL>(f.Bs[2], id);
+      f.Bp[2][id] = advance<T, SPL, true>(tb, q, 0, i, DIM == 3 ? 1 : -1, j, r0, r1, T(0), sxc, syc);
+      store_parts<SPL>(f.Bs[2], id, q);
+    } else {
+      f.Bp[2][id] = f.Bh[2][id] + (r0 + r1);
+    }
+  }
+}
+
 }  // namespace fn
 }  // namespace picpml

@@ -18,17 +18,18 @@ TOL = {"fp32": 1e-5, "fp64": 1e-11, "fixed64": 1e-5}
 
 def make_pair(dim, nphys, pml, d, parts, order=1, prec="fp32", alpha_mode="damped", cfl=0.99,
               sigma_coef=4.0, delta=6.0, exponent=2.0, v_assumed=O.C_LIGHT, prescribed=False, sort_every=0,
-              split_fp64=False, face_alpha=None, filter_passes=0):
+              split_fp64=False, face_alpha=None, filter_passes=0, solver="yee", dt=None):
     import torch
     from paper_2201_09084_gb300.api import Sim, pack_particles
-    dt = O.yee_dt(d, cfl, dim)
+    if dt is None:
+        dt = O.ck_dt(d, cfl, dim) if solver == "ck" else O.yee_dt(d, cfl, dim)
     ora = O.OracleSim(dim, nphys, pml, d, dt, order=order, alpha_mode=alpha_mode, sig_coef=sigma_coef,
                       delta=delta, sig_exp=exponent, v_assumed=v_assumed, face_alpha=face_alpha,
-                      filter_passes=filter_passes)
+                      filter_passes=filter_passes, solver=solver)
     gpu = Sim(dim, nphys, d, pml, dt=dt, order=order, prec=prec, alpha_mode=alpha_mode,
               sigma_coef=sigma_coef, delta=delta, exponent=exponent, v_assumed=v_assumed,
               sort_every=sort_every, split_fp64=split_fp64, face_alpha=face_alpha,
-              filter_passes=filter_passes)
+              filter_passes=filter_passes, solver=solver)
     for sp in parts:
         X = I.absolute(sp["cell"], sp["off"])
         u = sp["u"].astype(np.float64)

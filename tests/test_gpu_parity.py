@@ -34,17 +34,20 @@ def _pulse(sim_nn, pml, dim):
     return 1e6 * f
 
 
+@pytest.mark.parametrize("solver", ["yee", "ck"])
 @pytest.mark.parametrize("prec", ["fp32", "fp32-splitfp64", "fp64"])
 @pytest.mark.parametrize("dim", [3, 2])
-def test_field_step_parity(dim, prec):
-    """Yee + split PML on every face (ragged widths): float-float parts (FP32
-    default), IEEE FP64 parts with FP32 fields, and the all-FP64 form."""
+def test_field_step_parity(dim, prec, solver):
+    """Yee (or Cole-Karkkainen) + split PML on every face (ragged widths):
+    float-float parts (FP32 default), IEEE FP64 parts with FP32 fields, and
+    the all-FP64 form.  The pulse reaches the PML and the conducting outer
+    walls (where the CK averages read E's images)."""
     nphys = (37, 21, 45)
     pml = (6, 9, 5, 7, 8, 10)
     d = D3 if dim == 3 else D2
     split64 = prec == "fp32-splitfp64"
     prec = "fp32" if split64 else prec
-    ora, gpu = make_pair(dim, nphys, pml, d, [], prec=prec, split_fp64=split64)
+    ora, gpu = make_pair(dim, nphys, pml, d, [], prec=prec, split_fp64=split64, solver=solver)
     f = _pulse(ora.nn, pml, dim)
     for s in (ora, gpu):
         s.set_field("Ey", f)
@@ -449,3 +452,22 @@ def test_thermal_plasma_chunks(prec, ppt):
         err = max_field_err(ora, gpu)
         assert max(err.values()) < TOL[prec], err
     assert int(gpu.particles(0)["alive"].sum()) == int(ora.particles()["alive"].sum())
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_single_particle_3d_ck_with_filter(prec):
+    """The paper's own single-particle set-up in small (App. A): a gamma = 10
+    electron and its motionless partner in a 3D box with an 8-cell damped PML,
+    cubic shapes, one binomial filter pass and the Cole-Karkkainen solver at
+    c dt = 0.99 d, leaving through the +z PML; fields against the oracle."""
+    nphys = (20, 20, 28)
+    pml = (8,) * 6
+    d = (1e-6, 1e-6, 1e-6)
+    parts = I.single_pair(3, nphys, pml, gamma=10.0)
+    ora, gpu = make_pair(3, nphys, pml, d, parts, order=3, prec=prec, alpha_mode="damped", filter_passes=1,
+                         solver="ck", cfl=0.99)
+    for _ in range(3):
+        ora.step(15)
+        gpu.step(15)
+        err = max_field_err(ora, gpu)
+        assert max(err.values()) < TOL[prec], err

@@ -27,8 +27,8 @@ particles), "batch2d" (4096 batched 2D runs, FP32 and FP64) and
 "cpu_baseline" (the FP64 oracle on the plasma + beam workload reduced to
 24 x 24 x 48 + 8 cells, with the GPU's max relative field error on that
 sample).  --impl reference times the oracle alone on that sample.
---beam, --plasma, --single-particle and --precision-study measure the other
-workloads (their own JSON lines).
+--beam, --plasma, --single-particle, --cavity and --precision-study measure
+the other workloads (their own JSON lines).
 """
 from __future__ import annotations
 
@@ -1047,6 +1047,95 @@ def cpu_plasma_sample(steps, gpu_check=True, threads=None):
     return psteps / t, nthreads, desc, 1e3 * t / steps, err
 
 
+# ----------------------------------------------------------------------------
+# The cavity run of Sec. III: a pillbox cavity on a beam pipe (zeroed-field
+# cells), 10-cell PMLs on the z faces only with delta = 10 cells, a proton
+# beam injected continuously inside the undamped entry face's PML.
+CAV_NPHYS = (64, 64, 108)
+CAV_PML = (0, 0, 0, 0, 10, 10)
+CAV_D = (1e-3, 1e-3, 1e-3)
+
+
+def run_cavity(args):
+    """Throughput of the cavity workload (own JSON line): 64 x 64 x 108
+    cells of 1 mm + 10-cell z PMLs (sigma with delta = 10 cells), Yee at
+    0.99 x c dt = d / sqrt(3), conducting x and y walls; a pillbox cavity
+    (radius 30 cells, 40 cells long) on a beam pipe (radius 10 cells) carved
+    out by zeroed-field cells; a 40 nC, gamma = 479 proton beam injected
+    continuously (1,000 macroparticles per step over the first `steps`
+    steps) inside the -z PML, which deposits undamped, and leaving through
+    the damped +z PML; order 1, FP32 with float-float PML parts.  Every step
+    is an injection (pic_inject) plus step_n(1)."""
+    import torch
+    from paper_2201_09084_gb300 import inputs as I
+    from paper_2201_09084_gb300.api import Sim, pack_particles
+    from paper_2201_09084_gb300 import build as B
+    B.build()
+    stream = torch.cuda.current_stream()
+    faces = ["damped", "damped", "damped", "damped", "one", "damped"]
+    per = 1000
+    nsl = args.warmup + args.steps
+
+    def make():
+        sim = Sim(3, CAV_NPHYS, CAV_D, CAV_PML, cfl=0.99, order=1, prec="fp32", alpha_mode="damped", delta=10.0,
+                  face_alpha=faces, stream=stream)
+        sim.set_conductor(I.cavity_mask(CAV_NPHYS, CAV_PML, pipe_radius=10, cavity_radius=30, cavity_z=(34, 74)))
+        cap = nsl * per
+        z = np.zeros((cap, 3))
+        pos0, mom0 = pack_particles(z.astype(np.int64), z.astype(np.float32), z.astype(np.float32),
+                                    np.zeros(cap, np.float32), "fp32")
+        sid = sim.add_species(pos0, mom0, 0, I.Q_E, I.M_P)
+        return sim, sid
+
+    sim, sid = make()
+    shift = 299792458.0 * sim.dt / CAV_D[2] * np.sqrt(1 - 1 / 479.0 ** 2)
+    b = I.cavity_beam_slices(CAV_NPHYS, CAV_PML, nsl, per, shift, sigma=3.0)
+    pos, mom = pack_particles(b["cell"], b["off"], b["u"], b["w"], "fp32")
+    for st in range(args.warmup):
+        sim.inject(sid, pos[st * per:(st + 1) * per], mom[st * per:(st + 1) * per])
+        sim.step(1)
+    sim.sync()
+    ps0, l0 = sim.particle_steps(), sim.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(torch.cuda.current_device())
+    torch.cuda.synchronize()
+    clocks.start()
+    e0.record(stream)
+    for st in range(args.warmup, nsl):
+        sim.inject(sid, pos[st * per:(st + 1) * per], mom[st * per:(st + 1) * per])
+        sim.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sim.sync()
+    ms = e0.elapsed_time(e1)
+    psteps = sim.particle_steps() - ps0
+    launches = sim.launch_count() - l0
+    N = [n + CAV_PML[2 * a] + CAV_PML[2 * a + 1] for a, n in enumerate(CAV_NPHYS)]
+    total = N[0] * N[1] * N[2]
+    interior = CAV_NPHYS[0] * CAV_NPHYS[1] * CAV_NPHYS[2]
+    _, b_field = algorithmic_bytes(0, 0, interior, total - interior, "fp32")
+    peak, kind = measured_peak()
+    achieved = (b_field + 60 * psteps / args.steps) / (ms / args.steps / 1e3) / 1e9
+    sim.close()
+    return {"metric": METRIC, "value": psteps / (ms / 1e3), "unit": "particle-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "cavity run (Sec. III): 64x64x108 cells of 1 mm + 10-cell z PMLs (delta 10 "
+                                   "cells), pillbox cavity r=30 on a beam pipe r=10 (zeroed-field cells), 40 nC "
+                                   "gamma 479 proton beam injected continuously in the undamped -z PML, damped +z "
+                                   "PML, order 1, fp32 + float-float PML parts",
+                       "cells": total, "injected_per_step": per},
+            "cell_updates_per_s": total * args.steps / (ms / 1e3),
+            "roofline": {"bound": "hbm", "kernel": "whole step (inject, particles, E pass, conductor, B pass)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": f"{kind} (copy)", "traffic": None,
+                         "note": "field bytes per step (60 B per interior cell, 228 B per PML cell) plus 60 B per "
+                                 "pushed particle, over the step time; the 0.56 M-cell box fits in L2, so the "
+                                 "step is launch- and latency-bound"},
+            "gpu_launches": int(launches), "clocks": clk}
+
+
 def run_reference_plasma(args, rank, world):
     """The reference arm: the FP64 oracle on the default workload reduced to
     the sample cpu_plasma_sample() steps (bounded: W + K steps), timed on the
@@ -1093,6 +1182,8 @@ def main():
     ap.add_argument("--plasma-cells", default="128,128,256", help="physical cells of the --plasma workload")
     ap.add_argument("--single-particle", action="store_true",
                     help="the 2D FP64 single-particle workload (run it with --steps 400; own JSON line)")
+    ap.add_argument("--cavity", action="store_true",
+                    help="the cavity workload of Sec. III (zeroed-field cells, injected beam; own JSON line)")
     ap.add_argument("--tuning", default=None,
                     help="P,KZ launch shapes instead of the autotuner (profiling captures)")
     args = ap.parse_args()
@@ -1110,6 +1201,8 @@ def main():
         out = run_plasma(args) if rank == 0 else None
     elif args.single_particle and args.impl == "gb300":
         out = run_single_particle(args) if rank == 0 else None
+    elif args.cavity and args.impl == "gb300":
+        out = run_cavity(args) if rank == 0 else None
     elif args.impl == "reference":
         out = run_reference(args, rank, world) if args.beam else run_reference_plasma(args, rank, world)
     elif args.beam:

@@ -273,6 +273,18 @@ int pic_get_field(picpml_ctx* ctx, int which, void* dst, int as_double);
  * whole value goes into the first split part. */
 int pic_set_field(picpml_ctx* ctx, int which, const void* src, int as_double);
 
+/* Zeroed-field (perfect conductor) cells, e.g. the walls of the cavity run
+ * of Sec. III (the paper zeroes the fields in some cells and gives no
+ * geometry): mask is a host array of N0*N1*N2 bytes over the cells of the
+ * whole grid (physical + PML; N1 = 1 in 2D), index i + N0 (j + N1 k), nonzero
+ * for a conductor cell.  After every E update of field_step the E components
+ * on the 12 edges of each marked cell (8 in 2D) are zero, with their split
+ * parts, so E is tangentially zero on the cell's faces.  Particles are not
+ * stopped by conductor cells; the caller keeps them out.  NULL removes the
+ * conductor.  Copies the cell list to the device (allocating when it grows)
+ * and synchronises the stream. */
+int pic_set_conductor(picpml_ctx* ctx, const unsigned char* mask);
+
 /* 1: particles keep their momentum (no gather/push; they still move and
  * deposit), for prescribed-trajectory studies. */
 int pic_set_prescribed(picpml_ctx* ctx, int flag);

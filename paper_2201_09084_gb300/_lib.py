@@ -76,6 +76,7 @@ SIGNATURES = {
     "pic_get_field": (C.c_int, [VP, C.c_int, VP, C.c_int]),
     "pic_set_field": (C.c_int, [VP, C.c_int, VP, C.c_int]),
     "pic_set_prescribed": (C.c_int, [VP, C.c_int]),
+    "pic_set_conductor": (C.c_int, [VP, VP]),
     "pic_set_old_positions": (C.c_int, [VP, C.c_int, VP]),
     "pic_get_current_fixed": (C.c_int, [VP, C.c_int, VP]),
     "pic_num_particles": (C.c_int, [VP, C.c_int, C.POINTER(C.c_longlong)]),

@@ -170,6 +170,18 @@ class Sim:
     def set_prescribed(self, flag=True):
         self._call(self.lib.pic_set_prescribed, int(bool(flag)))
 
+    def set_conductor(self, mask):
+        """Zeroed-field cells: a mask of shape (Nz, Ny, Nx) over the cells of
+        the whole grid (Ny = 1 in 2D), True for a conductor cell; None
+        removes them."""
+        if mask is None:
+            self._call(self.lib.pic_set_conductor, None)
+            return
+        m = np.ascontiguousarray(np.asarray(mask, dtype=np.uint8))
+        ny = self.nn[1] - 1 if self.dim == 3 else 1
+        assert m.shape == (self.nn[2] - 1, ny, self.nn[0] - 1), m.shape
+        self._call(self.lib.pic_set_conductor, m.ctypes.data_as(C.c_void_p))
+
     def set_old_positions(self, sid, cell, off):
         """Sets x^n (what push() saves) of species sid from host (n, 3) cells
         and offsets, so deposit() deposits the moves to the current positions.

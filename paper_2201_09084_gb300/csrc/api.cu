@@ -22,6 +22,8 @@ cudaError_t launch_field_B(const Geom&, const Tables&, const FieldPtrs<T>&, int 
 template <typename T>
 cudaError_t launch_field_B_ck(const Geom&, const Tables&, const FieldPtrs<T>&, int split_ff, cudaStream_t);
 template <typename T>
+cudaError_t launch_conductor(const Geom&, const FieldPtrs<T>&, const int* cells, long long n, cudaStream_t);
+template <typename T>
 cudaError_t launch_filter_J(const Geom&, const FieldPtrs<T>&, T* const O[3], cudaStream_t);
 template <typename T>
 cudaError_t launch_particles(int mode, int order, const Geom&, const Tables&, const FieldPtrs<T>&,
@@ -150,6 +152,9 @@ struct picpml_ctx {
                       // in 3D): 4 or 8 (0 = default 4), or 1 = one thread per particle with
                       // global atomics, or PIC_TUNING_TILE = the tile-resident kernel (3D FP32
                       // order 1, sorted species)
+  int* cond = nullptr;                   // zeroed-field cells (device list of linear indices)
+  long long ncond = 0;
+  long long cond_cap = 0;
   alignas(64) unsigned char tmap[128];   // TMA tensor map of the FP32 field arrays (3D)
   bool tmap_ok = false;
   int kz = 1;         // nodes per thread along z in the field kernels
@@ -355,6 +360,10 @@ int run_field(picpml_ctx* ctx) {
     ctx->launches += 2;
   }
   CK(launch_field_E<T>(ctx->g, ctx->tb, f, ctx->split_ff(), ctx->kz, ctx->stream));
+  if (ctx->ncond > 0) {   // zeroed-field cells: their edges' E after the E pass
+    CK(launch_conductor<T>(ctx->g, f, ctx->cond, ctx->ncond, ctx->stream));
+    ctx->launches += 1;
+  }
   if (ctx->gd.solver == PIC_SOLVER_CK)
     CK(launch_field_B_ck<T>(ctx->g, ctx->tb, f, ctx->split_ff(), ctx->stream));
   else
@@ -918,6 +927,30 @@ int pic_set_field(picpml_ctx* ctx, int which, const void* src, int as_double) {
     float* a = kind == 0 ? ctx->ff.E[c] : kind == 3 ? ctx->ff.Bh[c] : ctx->ff.Bp[c];
     CK(launch_import<float>(ctx->g, src, as_double, scale, a, s0, s1, ctx->split_ff(), ctx->stream));
   }
+  return PIC_OK;
+}
+
+int pic_set_conductor(picpml_ctx* ctx, const unsigned char* mask) {
+  int r = check_ready(ctx);
+  if (r) return r;
+  if (!mask) {
+    ctx->ncond = 0;
+    return PIC_OK;
+  }
+  const Geom& g = ctx->g;
+  const long long N0 = g.N[0], N1 = g.dim == 3 ? g.N[1] : 1, N2 = g.N[2];
+  std::vector<int> cells;
+  for (long long t = 0; t < N0 * N1 * N2; ++t)
+    if (mask[t]) cells.push_back((int)t);
+  if ((long long)cells.size() > ctx->cond_cap) {
+    ctx->cond = (int*)dev_alloc(ctx, cells.size() * sizeof(int));
+    if (!ctx->cond) return fail(ctx, PIC_ENOMEM, "conductor cells");
+    ctx->cond_cap = (long long)cells.size();
+  }
+  if (!cells.empty())
+    CK(cudaMemcpyAsync(ctx->cond, cells.data(), cells.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->ncond = (long long)cells.size();
   return PIC_OK;
 }
 

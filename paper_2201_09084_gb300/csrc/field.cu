@@ -100,6 +100,33 @@ __global__ void __launch_bounds__(256) k_field_B_ck(Geom g, Tables tb, FieldPtrs
   fn::b_update_ck<T, DIM, SPL>(g, tb, f, i, j, k0, g.idx(i, j, k0));
 }
 
+// Zeroed-field (perfect conductor) cells: after the E pass every E
+// component on the 12 edges of a marked cell (8 in 2D) is set to zero, with
+// both split parts of the location (the parts arrays exist everywhere; where
+// a location is not split its parts are unused, and zero).  One thread per
+// marked cell; neighbouring cells share edges and write the same zero.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_conductor(Geom g, FieldPtrs<T> f, const int* cells, long long n) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int lin = cells[t];
+  const int N0 = g.N[0], N1 = DIM == 3 ? g.N[1] : 1;
+  const int i = lin % N0, j = (lin / N0) % N1, k = lin / (N0 * N1);
+  auto zero = [&](int c, int a, int b, int d) {
+    const long long id = g.idx(a, b, d);
+    f.E[c][id] = T(0);
+    f.Es[c][0][id] = 0.0;
+    f.Es[c][1][id] = 0.0;
+  };
+  const int jt = DIM == 3 ? 1 : 0;
+  for (int b = 0; b <= jt; ++b)
+    for (int c = 0; c <= 1; ++c) zero(0, i, j + b, k + c);   // Ex(i+1/2, ., .)
+  for (int a = 0; a <= 1; ++a)
+    for (int c = 0; c <= 1; ++c) zero(1, i + a, j, k + c);   // Ey(., j+1/2, .)
+  for (int a = 0; a <= 1; ++a)
+    for (int b = 0; b <= jt; ++b) zero(2, i + a, j + b, k);  // Ez(., ., k+1/2)
+}
+
 inline dim3 field_grid(const Geom& g, int KZ) {
   const long long nk = (g.nn[2] + KZ - 1) / KZ;
   if (g.dim == 3) return dim3((unsigned)(((long long)g.nn[0] * g.nn[1] + 255) / 256), (unsigned)nk, 1);
@@ -221,6 +248,22 @@ cudaError_t launch_field_B(const Geom& g, const Tables& tb, const FieldPtrs<T>& 
   if (kz == 2) return launch_B<T, 0, 2>(g, tb, f, s);
   return launch_B<T, 0, 1>(g, tb, f, s);
 }
+
+// Zeroes the edges of the n marked cells (device list of linear cell
+// indices i + N0 (j + N1 k), N1 = 1 in 2D).
+template <typename T>
+cudaError_t launch_conductor(const Geom& g, const FieldPtrs<T>& f, const int* cells, long long n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (g.dim == 3) k_conductor<T, 3><<<blocks, 256, 0, s>>>(g, f, cells, n);
+  else k_conductor<T, 2><<<blocks, 256, 0, s>>>(g, f, cells, n);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_conductor<float>(const Geom&, const FieldPtrs<float>&, const int*, long long,
+                                             cudaStream_t);
+template cudaError_t launch_conductor<double>(const Geom&, const FieldPtrs<double>&, const int*, long long,
+                                              cudaStream_t);
 
 // The CK B pass (Faraday's law with the transversely averaged differences).
 template <typename T>

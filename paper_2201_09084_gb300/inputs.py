@@ -272,6 +272,53 @@ def plasma_beam(nphys, pml, d, ppc=8, u_th=0.01, beam_uz=5.0, beam_radius=16.0, 
                                beam_density))
 
 
+def cavity_mask(nphys, pml, pipe_radius, cavity_radius, cavity_z):
+    """Zeroed-field cells of a pillbox cavity on a beam pipe along z (the
+    cavity run of Sec. III; the paper gives no geometry): every cell whose
+    centre lies farther from the box's axis than the pipe radius, or than the
+    cavity radius for physical z cells in cavity_z = (z0, z1), is a
+    conductor; the pipe continues through the z PMLs.  Radii in cells.
+    Returns a uint8 mask of shape (Nz, Ny, Nx) over the whole grid."""
+    N = [n + pml[2 * a] + pml[2 * a + 1] for a, n in enumerate(nphys)]
+    cx, cy = N[0] / 2.0, N[1] / 2.0
+    i = np.arange(N[0])[None, None, :] + 0.5
+    j = np.arange(N[1])[None, :, None] + 0.5
+    k = np.arange(N[2])[:, None, None]
+    r = np.sqrt((i - cx) ** 2 + (j - cy) ** 2)
+    zin = (k >= pml[4] + cavity_z[0]) & (k < pml[4] + cavity_z[1])
+    radius = np.where(zin, float(cavity_radius), float(pipe_radius))
+    return np.broadcast_to(r > radius, (N[2], N[1], N[0])).astype(np.uint8)
+
+
+def cavity_beam_slices(nphys, pml, steps, per_step, shift, sigma=2.0, gamma=479.0, charge=40e-9,
+                       z_start=3.0, seed=SEED_BASE + 23):
+    """The proton beam of the cavity run (Sec. III: 40 nC, gamma = 479,
+    injected continuously on one side): `steps` slices of `per_step`
+    macroparticles, slice s to be injected before step s.  Each slice is the
+    stretch of a uniform-current beam that enters in one step: z uniform in
+    [z_start, z_start + shift) cells (inside the entry face's PML; shift =
+    the distance the beam moves in a step), transverse Gaussian of rms sigma
+    cells about the axis (redrawn beyond 3 sigma), u along +z.  Weights give
+    the total charge over all slices.  Returns dict(cell, off, u, w) of
+    steps * per_step records, slices consecutive."""
+    rng = np.random.default_rng(seed)
+    n = steps * per_step
+    N = [v + pml[2 * a] + pml[2 * a + 1] for a, v in enumerate(nphys)]
+    d = rng.standard_normal((n, 2))
+    bad = np.any(np.abs(d) > 3.0, axis=1)
+    while bad.any():
+        d[bad] = rng.standard_normal((int(bad.sum()), 2))
+        bad = np.any(np.abs(d) > 3.0, axis=1)
+    X = np.empty((n, 3))
+    X[:, 0] = N[0] / 2.0 + sigma * d[:, 0]
+    X[:, 1] = N[1] / 2.0 + sigma * d[:, 1]
+    X[:, 2] = z_start + shift * rng.random(n)
+    u = np.zeros((n, 3))
+    u[:, 2] = np.sqrt(gamma * gamma - 1.0)
+    w = np.full(n, charge / (Q_E * n))
+    return _pack(X, u, w, 3)
+
+
 def random_moves(n, lo, hi, max_step=0.95, seed=SEED_BASE + 9, w_range=(0.5, 4.0)):
     """Prescribed one-step moves for depositing in isolation: start positions
     uniform in [lo, hi) (cells, 3D), displacements uniform in +-max_step per

@@ -171,6 +171,48 @@ struct Runs {
   }
 };
 
+// Adds the runs straight to the grid's current with native global float
+// reductions (in L2): the 32 lanes of a warp hold runs at distinct cells of
+// one 8 x 4 layer, so each reduction instruction covers a few sectors.  The
+// node's damping alpha_c (Eq. alpha, at the component's staggered location)
+// multiplies the value unless the unit's whole box lies where alpha = 1.
+// al: the unit's alpha tables (x node, x centre, y node, y centre, z node,
+// z centre); org: the box origin in grid cells.
+__device__ __forceinline__ void flush_runs_global(const Runs& R, const Geom& g, const FieldPtrs<float>& f,
+                                                  const int org[3], const float* al, bool alpha_one) {
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    if (R.cell[r] < 0) continue;
+    const int L = R.cell[r];
+    const int lx = L % BX, ly = (L / BX) % BY, lz = L / BXY;
+    const long long base = g.idx(org[0] + lx, org[1] + ly, org[2] + lz);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      // J_x at (x centre, y node +b, z node +c): v[b + 2c]; J_y at (x node
+      // +a, y centre, z node +c): v[4 + a + 2c]; J_z at (x node +a, y node
+      // +b, z centre): v[8 + a + 2b]
+      const int e1 = c == 0 ? 1 : 0, e2 = c == 2 ? 1 : 2;   // axes of the +1, +2 slots
+      const long long s1 = e1 == 0 ? 1 : (e1 == 1 ? g.sy : g.sz);
+      const long long s2 = e2 == 1 ? g.sy : g.sz;
+      const int lc[3] = {lx, ly, lz};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        float v = R.v[r][4 * c + t];
+        if (!alpha_one) {
+          int n[3] = {lc[0], lc[1], lc[2]};
+          n[e1] += t & 1;
+          n[e2] += t >> 1;
+          const float ax = c == 0 ? al[BX + n[0]] : al[n[0]];
+          const float ay = c == 1 ? al[2 * BX + BY + n[1]] : al[2 * BX + n[1]];
+          const float az = c == 2 ? al[2 * BX + 2 * BY + BZ + n[2]] : al[2 * BX + 2 * BY + n[2]];
+          v *= ax * ay * az;
+        }
+        atomicAdd(f.J[c] + base + (t & 1) * s1 + (t >> 1) * s2, v);
+      }
+    }
+  }
+}
+
 // Esirkepov current of a move that stays in its cell (Esirkepov's density
 // decomposition with S1 - S0 nonzero only on the cell's two nodes per axis):
 // J'_x(b, c) = cj_x w (-d_x) (M_y[b] M_z[c] + (-1)^{b+c} d_y d_z / 12) with
@@ -465,7 +507,8 @@ __device__ __forceinline__ int box_particle(const Geom& g, const Hot& h, long lo
 __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, const FieldPtrs<float>& f,
                                             const SpeciesPtrs<float>& sp, long long p0, long long p1, int iters,
                                             const float* F, float* J, Queue& Q, int& qn, const int org[3],
-                                            int prescribed, unsigned* status, unsigned& pushed) {
+                                            const float* al, bool alpha_one, int prescribed, unsigned* status,
+                                            unsigned& pushed) {
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const Hot h = {reinterpret_cast<float4*>(sp.pos), reinterpret_cast<float4*>(sp.mom), sp.ke, sp.cj[0], sp.cj[1],
@@ -514,7 +557,7 @@ __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, con
       qn += __popc(m);
     }
   }
-  R.flush(J, (threadIdx.x >> 5) & 1);
+  flush_runs_global(R, g, f, org, al, alpha_one);
   while (out) {
     const int i = __ffs(out) - 1;
     out &= out - 1;
@@ -609,6 +652,10 @@ __global__ void __launch_bounds__(NT, 2)
       if (gi >= 0 && gi < g.nn[ax]) v = stag ? tb.al_cf[ax][gi] : tb.al_nf[ax][gi];
       al[tid] = v;
     }
+    // alpha = 1 over the whole box (nodes and centres org .. org + extent - 1 on every axis)
+    const bool alpha_one = org[0] >= tb.al1_lo[0] && org[0] + BX - 1 <= tb.al1_hi[0] && org[1] >= tb.al1_lo[1] &&
+                           org[1] + BY - 1 <= tb.al1_hi[1] && org[2] >= tb.al1_lo[2] &&
+                           org[2] + BZ - 1 <= tb.al1_hi[2];
     const bool got = mbar_wait_bounded(bar, parity);
     parity ^= 1u;
     if (!__syncthreads_and(got)) {
@@ -634,8 +681,8 @@ __global__ void __launch_bounds__(NT, 2)
         const long long b0 = beg + (end - beg) * k / npass, b1 = beg + (end - beg) * (k + 1) / npass;
         const long long m = b1 - b0;
         const long long p0 = b0 + m * tid / NT, p1 = b0 + m * (tid + 1) / NT;
-        thread_pass(g, tb, f, S.sp, p0, p1, (int)((m + NT - 1) / NT), F, J, Q, qn, org, L.prescribed, status,
-                    pushed);
+        thread_pass(g, tb, f, S.sp, p0, p1, (int)((m + NT - 1) / NT), F, J, Q, qn, org, al, alpha_one,
+                    L.prescribed, status, pushed);
       }
     }
     if (qn) drain_queue(Q.q, qn, J);

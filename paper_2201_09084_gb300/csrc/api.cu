@@ -257,9 +257,10 @@ SpeciesPtrs<T> species_ptrs(picpml_ctx* ctx, Species& s) {
   return p;
 }
 
-// The tile-resident kernel serves 3D FP32 (not fixed-point) order-1 boxes.
+// The tile-resident kernel serves 3D order-1 boxes with FP32 fields (its
+// deterministic form for PIC_FP32_FIXED64).
 bool tile_capable(picpml_ctx* ctx) {
-  return ctx->gd.dim == 3 && ctx->gd.prec == PIC_FP32 && ctx->gd.shape_order == 1 && ctx->tmap_ok;
+  return ctx->gd.dim == 3 && ctx->gd.prec != PIC_FP64 && ctx->gd.shape_order == 1 && ctx->tmap_ok;
 }
 
 // x^n scratch of the stage calls push() / deposit(), allocated on first use.

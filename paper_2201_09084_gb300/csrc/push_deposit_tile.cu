@@ -125,6 +125,27 @@ __device__ __forceinline__ float tri(const float* F, int x, float fx, int y, flo
   return fmaf(fz, h - e, e);
 }
 
+// The order-1 gather of the one-thread kernel (interp(): the same weights and
+// the same order of the sums) from a box array, local indices: the
+// deterministic form uses it so that a particle moves bit for bit as it does
+// in the other kernels, whichever kernel pushes it.
+__device__ __forceinline__ float interp_box(const float* F, int bx, const float* wx, int by, const float* wy, int bz,
+                                            const float* wz) {
+  float acc = 0.0f;
+#pragma unroll
+  for (int tz = 0; tz < 2; ++tz)
+#pragma unroll
+    for (int ty = 0; ty < 2; ++ty) {
+      const float wyz = wy[ty] * wz[tz];
+      const float* row = F + bx + BX * (by + ty) + BXY * (bz + tz);
+      float racc = 0.0f;
+#pragma unroll
+      for (int tx = 0; tx < 2; ++tx) racc += wx[tx] * row[tx];
+      acc += wyz * racc;
+    }
+  return acc;
+}
+
 // Index range [beg, end) of species s in the unit whose first sort tile is t0
 // (nt tiles), clamped to the live count.
 __device__ __forceinline__ void unit_range(const TileSpecies& S, long long t0, int nt, long long n, long long& beg,
@@ -334,6 +355,7 @@ __device__ __noinline__ void drain_queue(const float* q, int n, float* J) {
 // Gather from global memory, push, move and deposit with global atomics: the
 // path of a particle outside its unit's box (kept out of line so the box path
 // keeps its registers).
+template <bool FIX>
 __device__ __noinline__ void particle_global(const Geom& g, const Tables& tb, const FieldPtrs<float>& f,
                                              const SpeciesPtrs<float>& sp, long long p, int prescribed,
                                              unsigned* status, unsigned* pushed) {
@@ -381,7 +403,11 @@ __device__ __noinline__ void particle_global(const Geom& g, const Tables& tb, co
   }
   P[p] = ok ? make_float4(o1[0], o1[1], o1[2], wn) : a;
   Mo[p] = make_float4(u[0], u[1], u[2], __int_as_float(ok ? pack_cell(c1[0], c1[1], c1[2]) : -1));
-  if (ok) deposit_one<1, 3, float>(g, tb, f, sp, c, o, c1, o1, wd, 0.0f);
+  if (!ok) return;
+  if constexpr (FIX)
+    deposit_fixed<1>(g, f, sp.qn, c, o, c1, o1, wd, status);
+  else
+    deposit_one<1, 3, float>(g, tb, f, sp, c, o, c1, o1, wd, 0.0f);
 }
 
 // The values of a species the box path reads per particle, held in registers
@@ -390,6 +416,7 @@ struct Hot {
   float4* pos;
   float4* mom;
   float ke, cj0, cj1, cj2;
+  double qn;   // charge in elementary charges (deterministic deposit)
 };
 
 // What the box path leaves for the deposit: nothing (removed or refused), an
@@ -401,10 +428,18 @@ enum : int { DEP_NONE = 0, DEP_IN_CELL = 1, DEP_ACROSS = 2, DEP_OUT = 3 };
 // One particle of the box path: checks, gather from the box, Boris push,
 // move, record write-back.  Returns the deposit kind with the local cells
 // L0, L1, the offsets o (before) and o1 (after) and the mid-step weight.
-__device__ __forceinline__ int box_particle(const Geom& g, const Hot& h, long long p, float4 a, float4 b,
-                                            const float* F, const int org[3], int prescribed, unsigned* status,
-                                            unsigned& pushed, int& L0, int& L1, float o[3], float o1[3],
-                                            float& wd) {
+//
+// FIX: the deterministic form.  The gather reads E, B^{n+1/2} and B^{n-1/2}
+// from the box with the one-thread kernel's arithmetic (interp_box, B^n
+// averaged after the interpolation), the move is always the float-float one,
+// and the particle deposits its integer Esirkepov sums with int64 atomics
+// (deposit_fixed) straight away: the result does not depend on the kernel,
+// the particle order or the launch shape.
+template <bool FIX>
+__device__ __forceinline__ int box_particle(const Geom& g, const Hot& h, const FieldPtrs<float>& f, long long p,
+                                            float4 a, float4 b, const float* F, const int org[3], int prescribed,
+                                            unsigned* status, unsigned& pushed, int& L0, int& L1, float o[3],
+                                            float o1[3], float& wd) {
   const int cell = __float_as_int(b.w);
   if (cell < 0) return DEP_NONE;
   const int c[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
@@ -426,7 +461,26 @@ __device__ __forceinline__ int box_particle(const Geom& g, const Hot& h, long lo
     Mo[p] = make_float4(b.x, b.y, b.z, __int_as_float(-1));
     return DEP_NONE;
   }
-  if (!prescribed) {
+  if (FIX && !prescribed) {
+    int b0[3], bh[3];
+    float w0[3][2], wh[3][2], E[3], B[3];
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+      axis_weights<1, float>(c[ax], o[ax], b0[ax], w0[ax], bh[ax], wh[ax]);
+      b0[ax] -= org[ax];
+      bh[ax] -= org[ax];
+    }
+    E[0] = interp_box(F + 0 * BN, bh[0], wh[0], b0[1], w0[1], b0[2], w0[2]);
+    E[1] = interp_box(F + 1 * BN, b0[0], w0[0], bh[1], wh[1], b0[2], w0[2]);
+    E[2] = interp_box(F + 2 * BN, b0[0], w0[0], b0[1], w0[1], bh[2], wh[2]);
+    B[0] = 0.5f * (interp_box(F + 3 * BN, b0[0], w0[0], bh[1], wh[1], bh[2], wh[2]) +
+                   interp_box(F + 6 * BN, b0[0], w0[0], bh[1], wh[1], bh[2], wh[2]));
+    B[1] = 0.5f * (interp_box(F + 4 * BN, bh[0], wh[0], b0[1], w0[1], bh[2], wh[2]) +
+                   interp_box(F + 7 * BN, bh[0], wh[0], b0[1], w0[1], bh[2], wh[2]));
+    B[2] = 0.5f * (interp_box(F + 5 * BN, bh[0], wh[0], bh[1], wh[1], b0[2], w0[2]) +
+                   interp_box(F + 8 * BN, bh[0], wh[0], bh[1], wh[1], b0[2], w0[2]));
+    boris<float>(u, E, B, h.ke);
+  } else if (!prescribed) {
     int bc[3];
     float wc[3], E[3], B[3];
 #pragma unroll
@@ -454,7 +508,7 @@ __device__ __forceinline__ int box_particle(const Geom& g, const Hot& h, long lo
     float d[3];
 #pragma unroll
     for (int ax = 0; ax < 3; ++ax) d[ax] = g.Sf[ax] * u[ax] * ig;
-    if (fmaxf(fabsf(d[0]), fmaxf(fabsf(d[1]), fabsf(d[2]))) < 0.0625f) {
+    if (!FIX && fmaxf(fabsf(d[0]), fmaxf(fabsf(d[1]), fabsf(d[2]))) < 0.0625f) {
       bool outside = false;
 #pragma unroll
       for (int ax = 0; ax < 3; ++ax) {
@@ -480,7 +534,7 @@ __device__ __forceinline__ int box_particle(const Geom& g, const Hot& h, long lo
       ok = move_particle<3, float>(g, o, c, u, c1, o1, igg);
     }
   }
-  if (ok && !in_box(c1[0] - org[0], c1[1] - org[1], c1[2] - org[2])) return DEP_OUT;
+  if (!FIX && ok && !in_box(c1[0] - org[0], c1[1] - org[1], c1[2] - org[2])) return DEP_OUT;
   ++pushed;
   float wn = w;
   wd = w;
@@ -492,6 +546,10 @@ __device__ __forceinline__ int box_particle(const Geom& g, const Hot& h, long lo
   P[p] = ok ? make_float4(o1[0], o1[1], o1[2], wn) : a;
   Mo[p] = make_float4(u[0], u[1], u[2], __int_as_float(ok ? pack_cell(c1[0], c1[1], c1[2]) : -1));
   if (!ok) return DEP_NONE;
+  if constexpr (FIX) {
+    deposit_fixed<1>(g, f, h.qn, c, o, c1, o1, wd, status);
+    return DEP_NONE;
+  }
   L0 = l[0] + BX * l[1] + BXY * l[2];
   if (c1[0] == c[0] && c1[1] == c[1] && c1[2] == c[2]) {
     L1 = L0;
@@ -504,6 +562,7 @@ __device__ __forceinline__ int box_particle(const Geom& g, const Hot& h, long lo
 // One thread's consecutive particles [p0, p1) of a species, at most `iters`
 // (the whole block calls it together with the same `iters`): box path, register runs, deferred queue, then the
 // flush of the runs and the drain of the queue.
+template <bool FIX>
 __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, const FieldPtrs<float>& f,
                                             const SpeciesPtrs<float>& sp, long long p0, long long p1, int iters,
                                             const float* F, float* J, Queue& Q, int& qn, const int org[3],
@@ -512,7 +571,7 @@ __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, con
   const int lane = threadIdx.x & 31;
   const unsigned lt = (1u << lane) - 1u;
   const Hot h = {reinterpret_cast<float4*>(sp.pos), reinterpret_cast<float4*>(sp.mom), sp.ke, sp.cj[0], sp.cj[1],
-                 sp.cj[2]};
+                 sp.cj[2], sp.qn};
   const float4* P = h.pos;
   const float4* Mo = h.mom;
   Runs R;
@@ -532,7 +591,7 @@ __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, con
     }
     int L0 = -1, L1 = -1, kind = DEP_NONE;
     float o[3], o1[3], wd = 0.0f;
-    if (p < p1) kind = box_particle(g, h, p, a, b, F, org, prescribed, status, pushed, L0, L1, o, o1, wd);
+    if (p < p1) kind = box_particle<FIX>(g, h, f, p, a, b, F, org, prescribed, status, pushed, L0, L1, o, o1, wd);
     if (kind == DEP_OUT) out |= 1u << i;
     bool toq = kind == DEP_ACROSS;
     if (kind == DEP_IN_CELL) {
@@ -557,14 +616,15 @@ __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, con
       qn += __popc(m);
     }
   }
-  flush_runs_global(R, g, f, org, al, alpha_one);
+  if (!FIX) flush_runs_global(R, g, f, org, al, alpha_one);
   while (out) {
     const int i = __ffs(out) - 1;
     out &= out - 1;
-    particle_global(g, tb, f, sp, p0 + i, prescribed, status, &pushed);
+    particle_global<FIX>(g, tb, f, sp, p0 + i, prescribed, status, &pushed);
   }
 }
 
+template <bool FIX>
 __global__ void __launch_bounds__(NT, 2)
     k_tile(const __grid_constant__ Geom g, const __grid_constant__ Tables tb,
            const __grid_constant__ FieldPtrs<float> f, const __grid_constant__ TileLaunch L,
@@ -663,12 +723,15 @@ __global__ void __launch_bounds__(NT, 2)
       alive = false;
       break;
     }
-    // B^n in place; the B^{n-1/2} slots become the zeroed current box
-    for (int q = tid; q < 3 * BN; q += NT) {
-      F[3 * BN + q] = 0.5f * (F[3 * BN + q] + F[6 * BN + q]);
-      J[q] = 0.0f;
+    // B^n in place; the B^{n-1/2} slots become the zeroed current box (the
+    // deterministic form keeps both B half steps and deposits globally)
+    if (!FIX) {
+      for (int q = tid; q < 3 * BN; q += NT) {
+        F[3 * BN + q] = 0.5f * (F[3 * BN + q] + F[6 * BN + q]);
+        J[q] = 0.0f;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     int qn = 0;   // entries in this warp's queue (the same in every lane)
     for (int s = 0; s < L.nsp; ++s) {
       const TileSpecies& S = L.s[s];
@@ -681,12 +744,13 @@ __global__ void __launch_bounds__(NT, 2)
         const long long b0 = beg + (end - beg) * k / npass, b1 = beg + (end - beg) * (k + 1) / npass;
         const long long m = b1 - b0;
         const long long p0 = b0 + m * tid / NT, p1 = b0 + m * (tid + 1) / NT;
-        thread_pass(g, tb, f, S.sp, p0, p1, (int)((m + NT - 1) / NT), F, J, Q, qn, org, al, alpha_one,
-                    L.prescribed, status, pushed);
+        thread_pass<FIX>(g, tb, f, S.sp, p0, p1, (int)((m + NT - 1) / NT), F, J, Q, qn, org, al, alpha_one,
+                         L.prescribed, status, pushed);
       }
     }
     if (qn) drain_queue(Q.q, qn, J);
     __syncthreads();
+    if (FIX) continue;   // (the next unit's copy may overwrite the box: every thread passed the barrier)
     // the current box to the grid with alpha at each component's location
     const float* axn = al;
     const float* axc = al + BX;
@@ -713,7 +777,7 @@ __global__ void __launch_bounds__(NT, 2)
     for (int s = 0; s < L.nsp; ++s) {
       const long long b = L.s[s].tile_end[ntiles - 1];
       for (long long p = b + (long long)blockIdx.x * NT + tid; p < nlive[s]; p += (long long)gridDim.x * NT)
-        particle_global(g, tb, f, L.s[s].sp, p, L.prescribed, status, &pushed);
+        particle_global<FIX>(g, tb, f, L.s[s].sp, p, L.prescribed, status, &pushed);
     }
   }
   const unsigned wsum = __reduce_add_sync(0xffffffffu, pushed);
@@ -777,13 +841,15 @@ int tile_map_bytes() { return (int)sizeof(CUtensorMap); }
 cudaError_t launch_tile(const Geom& g, const Tables& tb, const FieldPtrs<float>& f, const TileLaunch& L,
                         const void* map, unsigned* status, unsigned long long* pushed, int nsm, cudaStream_t s) {
   if (L.nsp <= 0) return cudaSuccess;
-  static std::atomic<unsigned long long> configured{0};   // devices whose limit is set
+  const bool fix = f.Jq[0] != nullptr;   // the deterministic (int64) form
+  auto kern = fix ? k_tile<true> : k_tile<false>;
+  static std::atomic<unsigned long long> configured[2];   // devices whose limit is set, per form
   {
-    cudaError_t e = smem_limit_once(k_tile, kSmemBytes, configured);
+    cudaError_t e = smem_limit_once(kern, kSmemBytes, configured[fix ? 1 : 0]);
     if (e != cudaSuccess) return e;
   }
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile, NT, kSmemBytes);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, kSmemBytes);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const long long tx = (g.N[0] + TX - 1) / TX, ty = (g.N[1] + TY - 1) / TY, tz = (g.N[2] + TZ - 1) / TZ;
@@ -791,7 +857,7 @@ cudaError_t launch_tile(const Geom& g, const Tables& tb, const FieldPtrs<float>&
   long long blocks = (long long)nsm * per_sm;
   if (blocks > nunits) blocks = nunits;
   if (blocks < 1) blocks = 1;
-  k_tile<<<(unsigned)blocks, NT, kSmemBytes, s>>>(g, tb, f, L, *reinterpret_cast<const CUtensorMap*>(map), status,
+  kern<<<(unsigned)blocks, NT, kSmemBytes, s>>>(g, tb, f, L, *reinterpret_cast<const CUtensorMap*>(map), status,
                                                   pushed);
   return cudaGetLastError();
 }

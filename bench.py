@@ -656,8 +656,13 @@ PLASMA_NCU_BYTES_PER_PARTICLE = 557_966_080 / 8_429_785
 # capture of the 64 x 64 x 128 case; the plasma fills the box at a fixed 8 particles
 # per cell and species, so the traffic grows with the particle count and the
 # full-size figure is scaled by it.  None until captured on the current kernel.
-HEADLINE_NCU_BYTES_PER_PARTICLE = None
-HEADLINE_NCU_NOTE = None
+# Captured with
+#   ncu --set full --clock-control none -k regex:^k_tile$ -s 4 -c 1
+#       python bench.py --cells 64,64,128 --no-extra --no-cpu-baseline --steps 3 --warmup 3
+# (322,949,888 B read + 222,377,472 B written for 8,429,785 particles).
+HEADLINE_NCU_BYTES_PER_PARTICLE = (322_949_888 + 222_377_472) / 8_429_785
+HEADLINE_NCU_NOTE = ("per launch: dram__bytes_read.sum + dram__bytes_write.sum of the tile kernel on the "
+                     "64x64x128 case (64.7 B per particle), scaled by the particles pushed")
 
 # Plasma boxes with more particles per species than this are generated and
 # packed one z-plane of cells at a time (inputs.plasma_planes) instead of in
@@ -856,8 +861,8 @@ def run_headline(args, rank, world):
     n_mobile = sum(r[2] for r in recs if not r[5])
     rec_bytes = sum(2 * r[0].numel() * 4 for r in recs)
 
-    def make(split64):
-        sim = Sim(3, nphys, D, PML, cfl=0.99, order=1, prec="fp32", alpha_mode="damped", sort_every=SORT_EVERY,
+    def make(split64, prec="fp32"):
+        sim = Sim(3, nphys, D, PML, cfl=0.99, order=1, prec=prec, alpha_mode="damped", sort_every=SORT_EVERY,
                   split_fp64=split64, stream=stream)
         for pos, mom, n, q, m, imm in recs:
             sim.add_species(pos, mom, n, q, m, imm)
@@ -949,6 +954,14 @@ def run_headline(args, rank, world):
         sim.close()
         ff = {"value": ps2 / (ms2 / 1e3), "unit": "particle-steps/s", "ms_per_step": ms2 / args.steps,
               "kernel_ms": {"push_deposit": t_pd2, "field_step": t_f2}}
+        # the deterministic form: int64 fixed-point deposition (same launch shapes)
+        reload()
+        sim = make(True, prec="fixed64")
+        ms3, ps3, _, t_pd3, t_f3, _ = timed(sim, tuning)
+        sim.close()
+        fx = {"value": ps3 / (ms3 / 1e3), "unit": "particle-steps/s", "ms_per_step": ms3 / args.steps,
+              "kernel_ms": {"push_deposit": t_pd3, "field_step": t_f3},
+              "note": "int64 fixed-point deposition (bit-identical under any particle order), IEEE fp64 PML parts"}
     del recs, host
     torch.cuda.empty_cache()
 
@@ -990,6 +1003,8 @@ def run_headline(args, rank, world):
     }
     if ff is not None:
         out["float_float_parts"] = ff
+        out["deterministic_fixed64"] = fx
+        out["fixed64_over_fp32"] = fx["value"] / out["value"]
     return out
 
 

@@ -719,7 +719,13 @@ __global__ void __launch_bounds__(NT, 2)
     const bool got = mbar_wait_bounded(bar, parity);
     parity ^= 1u;
     if (!__syncthreads_and(got)) {
-      if (tid == 0) atomicOr(status, ST_TIMEOUT);
+      // give the late copy (it lands in this block's shared memory) one more
+      // bounded wait before the block leaves
+      if (tid == 0) {
+        atomicOr(status, ST_TIMEOUT);
+        (void)mbar_wait_bounded(bar, parity ^ 1u);
+      }
+      __syncthreads();
       alive = false;
       break;
     }

@@ -127,16 +127,20 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def algorithmic_bytes(n_live, occ_cells, n_int, n_pml, prec):
+def algorithmic_bytes(n_live, occ_cells, n_int, n_pml, prec, bn=False):
     """Algorithmic bytes of one step: each operand read once, each result
     written once.  Particle (3D FP32): 32 B read + 28 B written; occupied cell
-    gather/deposit: 9 field words read + 3 current words written (48 B; 96 B
-    in FP64).  Yee interior cell: E, B, J read, E, B written (60 B FP32,
-    120 B FP64); PML cell: 12 FP64 split parts read+written, J read, E, B
-    written (228 B; 252 B FP64)."""
+    gather/deposit: 9 field words read (E and both B half steps) + 3 current
+    words written (48 B; 96 B in FP64), or, with bn (the tile kernel, which
+    reads B at the integer time written by the field step), 6 field words
+    read + 3 written (36 B).  Yee interior cell: E, B, J read, E, B written
+    (60 B FP32, 120 B FP64); PML cell: 12 FP64 split parts read+written, J
+    read, E, B written (228 B; 252 B FP64); with bn the B pass also writes B
+    at the integer time (+12 B per cell)."""
     e = 8 if prec == "fp64" else 4
-    part = (60 if prec != "fp64" else 104) * n_live + 12 * e * occ_cells
-    field = (15 * e) * n_int + (192 + 9 * e) * n_pml
+    words = 9 if bn else 12
+    part = (60 if prec != "fp64" else 104) * n_live + words * e * occ_cells
+    field = (15 * e) * n_int + (192 + 9 * e) * n_pml + (12 * (n_int + n_pml) if bn else 0)
     return part, field
 
 
@@ -656,11 +660,10 @@ PLASMA_NCU_BYTES_PER_PARTICLE = 557_966_080 / 8_429_785
 # capture of the 64 x 64 x 128 case; the plasma fills the box at a fixed 8 particles
 # per cell and species, so the traffic grows with the particle count and the
 # full-size figure is scaled by it.  None until captured on the current kernel.
-# Captured with
+# To be captured with
 #   ncu --set full --clock-control none -k regex:^k_tile$ -s 4 -c 1
-#       python bench.py --cells 64,64,128 --no-extra --no-cpu-baseline --steps 3 --warmup 3
-# (322,949,888 B read + 222,377,472 B written for 8,429,785 particles).
-HEADLINE_NCU_BYTES_PER_PARTICLE = (322_949_888 + 222_377_472) / 8_429_785
+#       python bench.py --cells 64,64,128 --no-extra --no-cpu-baseline --steps 3 --warmup 3 --tuning 2,1
+HEADLINE_NCU_BYTES_PER_PARTICLE = None
 HEADLINE_NCU_NOTE = ("per launch: dram__bytes_read.sum + dram__bytes_write.sum of the tile kernel on the "
                      "64x64x128 case (64.7 B per particle), scaled by the particles pushed")
 
@@ -776,10 +779,10 @@ def run_plasma(args):
     N = [n + 2 * p for n, p in zip(nphys, PML[::2])]
     total = N[0] * N[1] * N[2]
     interior = nphys[0] * nphys[1] * nphys[2]
-    b_part, b_field = algorithmic_bytes(psteps / args.steps, occ, interior, total - interior, "fp32")
+    p_ = tuning["particles_per_thread"]
+    b_part, b_field = algorithmic_bytes(psteps / args.steps, occ, interior, total - interior, "fp32", bn=p_ == 2)
     peak, kind = measured_peak()
     achieved = b_part / (t_pd / 1e3) / 1e9
-    p_ = tuning["particles_per_thread"]
     traffic = (PLASMA_NCU_BYTES_PER_PARTICLE * psteps / args.steps
                if PLASMA_NCU_BYTES_PER_PARTICLE and p_ == 1 else None)
     sim.close()
@@ -971,10 +974,10 @@ def run_headline(args, rank, world):
     interior = nphys[0] * nphys[1] * nphys[2]
     n_live = (psteps / world) / args.steps
     # occupied cells: the plasma fills every physical cell
-    b_part, b_field = algorithmic_bytes(n_live, interior, interior, total - interior, "fp32")
+    p_ = tuning["particles_per_thread"]
+    b_part, b_field = algorithmic_bytes(n_live, interior, interior, total - interior, "fp32", bn=p_ == 2)
     peak, kind = measured_peak()
     achieved = b_part / (t_pd / 1e3) / 1e9
-    p_ = tuning["particles_per_thread"]
     traffic = (HEADLINE_NCU_BYTES_PER_PARTICLE * n_live
                if HEADLINE_NCU_BYTES_PER_PARTICLE and p_ == 2 else None)
     kname = ("k_tile (tile-resident fused gather/push/move/deposit/damp)" if p_ == 2
@@ -990,8 +993,10 @@ def run_headline(args, rank, world):
                      "frac": achieved / peak, "peak_kind": f"{kind} (copy)", "traffic": traffic,
                      "traffic_note": HEADLINE_NCU_NOTE if traffic else None,
                      "algorithmic_bytes_per_launch": b_part,
-                     "bytes_model": "60 B per live particle (32 read, 28 written) + 48 B per occupied cell "
-                                    "(9 field words read, 3 current words written)"},
+                     "bytes_model": ("60 B per live particle (32 read, 28 written) + 36 B per occupied cell "
+                                     "(E and B at the integer time read, J written)") if p_ == 2 else
+                                    ("60 B per live particle (32 read, 28 written) + 48 B per occupied cell "
+                                     "(9 field words read, 3 current words written)")},
         "e2e": {"value": ps_e2e / (ms_e2e / 1e3), "unit": "particle-steps/s",
                 "h2d_bytes_per_step": rec_bytes / nsteps_e2e, "d2h_bytes_per_step": 8,
                 "note": f"the initial particle records ({rec_bytes / 1e9:.1f} GB) copied from pinned host memory "

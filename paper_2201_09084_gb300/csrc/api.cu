@@ -58,7 +58,8 @@ cudaError_t launch_sort(const Geom&, int pbytes, void* pos, void* mom, long long
                         unsigned* scratch, void* tmp_pos, void* tmp_mom, cudaStream_t);
 long long tile_count(const Geom&);
 cudaError_t launch_tile_ends(const Geom&, const unsigned* cursor, long long* tile_end, cudaStream_t);
-cudaError_t make_tile_tensor_map(const Geom&, const float* base, void* map_out);
+cudaError_t make_tile_tensor_map(const Geom&, const float* base, int arrays, void* map_out);
+cudaError_t launch_bn_average(const Geom&, const FieldPtrs<float>&, cudaStream_t);
 int tile_map_bytes();
 cudaError_t launch_tile(const Geom&, const Tables&, const FieldPtrs<float>&, const TileLaunch&, const void* map,
                         unsigned* status, unsigned long long* pushed, int nsm, cudaStream_t);
@@ -157,6 +158,8 @@ struct picpml_ctx {
   long long cond_cap = 0;
   alignas(64) unsigned char tmap[128];   // TMA tensor map of the FP32 field arrays (3D)
   bool tmap_ok = false;
+  bool bn_stale = true;   // ff.Bn does not hold (Bh + Bp)/2 of the current B arrays
+  size_t field_bytes = 0;   // the field allocation (state arrays, then ff.Bn where present)
   int kz = 1;         // nodes per thread along z in the field kernels
   long long steps_done = 0;
   long long launches = 0;
@@ -281,6 +284,7 @@ int run_tile(picpml_ctx* ctx, std::vector<char>& done) {
     L.arr_E[c] = (int)((f.E[c] - base) / ctx->g.size);
     L.arr_Bh[c] = (int)((f.Bh[c] - base) / ctx->g.size);
     L.arr_Bp[c] = (int)((f.Bp[c] - base) / ctx->g.size);
+    L.arr_Bn[c] = f.Bn[c] ? (int)((f.Bn[c] - base) / ctx->g.size) : 0;
   }
   for (size_t i = 0; i < ctx->sp.size(); ++i) {
     Species& s = ctx->sp[i];
@@ -291,6 +295,11 @@ int run_tile(picpml_ctx* ctx, std::vector<char>& done) {
     done[i] = 1;
   }
   if (L.nsp == 0) return PIC_OK;
+  if (!ctx->fixed() && ctx->bn_stale) {   // B^n for the box path, after B was set from outside
+    CK(launch_bn_average(ctx->g, f, ctx->stream));
+    ctx->launches += 1;
+    ctx->bn_stale = false;
+  }
   CK(launch_tile(ctx->g, ctx->tb, f, L, ctx->tmap, ctx->status, ctx->pushed, ctx->nsm, ctx->stream));
   ctx->launches += 1;
   return PIC_OK;
@@ -371,6 +380,7 @@ int run_field(picpml_ctx* ctx) {
     CK(launch_field_B<T>(ctx->g, ctx->tb, f, ctx->split_ff(), ctx->kz, ctx->stream));
   ctx->launches += 2;
   for (int c = 0; c < 3; ++c) std::swap(f.Bh[c], f.Bp[c]);
+  ctx->bn_stale = f.Bn[0] == nullptr;   // the B pass wrote Bn where it exists
   return PIC_OK;
 }
 
@@ -572,9 +582,13 @@ int pml_init(picpml_ctx* ctx, const pml_desc* p) {
   CK(cudaMemcpyAsync(tf, hostf.data(), hostf.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
   CK(cudaMemcpyAsync(t2, host2.data(), host2.size() * sizeof(float2), cudaMemcpyHostToDevice, ctx->stream));
 
-  // fields: 12 arrays of the field type + 12 FP64 split arrays, zeroed
+  // fields: 12 arrays of the field type + 12 FP64 split arrays, then, for
+  // the tile kernel's box path (3D, FP32, order 1), the 3 FP32 arrays of B at
+  // the integer time; zeroed
   const size_t es = ctx->elem();
-  const size_t fbytes = (size_t)g.size * (12 * es + 12 * 8);
+  const bool bn = gd.dim == 3 && gd.prec == PIC_FP32 && gd.shape_order == 1;
+  const size_t fbytes = (size_t)g.size * (12 * es + 12 * 8 + (bn ? 12 : 0));
+  ctx->field_bytes = fbytes;
   char* fm = (char*)dev_alloc(ctx, fbytes);
   if (!fm) return fail(ctx, PIC_ENOMEM, "fields");
   CK(cudaMemsetAsync(fm, 0, fbytes, ctx->stream));
@@ -597,6 +611,12 @@ int pml_init(picpml_ctx* ctx, const pml_desc* p) {
       ctx->ff.Es[c][h] = ctx->fd.Es[c][h] = e;
       ctx->ff.Bs[c][h] = ctx->fd.Bs[c][h] = b;
     }
+  if (bn)
+    for (int c = 0; c < 3; ++c) {
+      ctx->ff.Bn[c] = (float*)q;
+      q += (size_t)g.size * 4;
+    }
+  ctx->bn_stale = true;
   if (gd.filter_passes > 0) {
     char* ft = (char*)dev_alloc(ctx, (size_t)g.size * 3 * es);
     if (!ft) return fail(ctx, PIC_ENOMEM, "filter scratch");
@@ -610,7 +630,8 @@ int pml_init(picpml_ctx* ctx, const pml_desc* p) {
     for (int c = 0; c < 3; ++c) ctx->ff.Jq[c] = jq + (size_t)c * g.size;
   }
   if (gd.dim == 3 && gd.prec != PIC_FP64 && tile_map_bytes() <= (int)sizeof(ctx->tmap))
-    ctx->tmap_ok = make_tile_tensor_map(g, ctx->ff.E[0], ctx->tmap) == cudaSuccess;
+    ctx->tmap_ok = make_tile_tensor_map(g, ctx->ff.E[0], (int)(fbytes / ((size_t)g.size * 4)), ctx->tmap) ==
+                   cudaSuccess;
   ctx->status = (unsigned*)dev_alloc(ctx, 64);
   ctx->pushed = (unsigned long long*)(ctx->status + 8);
   ctx->diag = (double*)dev_alloc(ctx, 8 * sizeof(double));
@@ -722,7 +743,9 @@ int pic_autotune(picpml_ctx* ctx, int steps, int* ppt, int* kz) {
   Snapshot sn;
   const size_t es = ctx->elem();
   void* fm = f64 ? (void*)ctx->fd.E[0] : (void*)ctx->ff.E[0];
-  sn.items.push_back({fm, (size_t)ctx->g.size * (12 * es + 12 * 8)});
+  sn.items.push_back({fm, ctx->field_bytes});
+  (void)es;
+  const bool bn_stale0 = ctx->bn_stale;
   for (auto& s : ctx->sp) {
     sn.items.push_back({s.desc.pos, (size_t)s.desc.capacity * ctx->pbytes()});
     sn.items.push_back({s.desc.mom, (size_t)s.desc.capacity * ctx->pbytes()});
@@ -781,6 +804,7 @@ int pic_autotune(picpml_ctx* ctx, int steps, int* ppt, int* kz) {
     CK(restore());
     ctx->ff = ff0;
     ctx->fd = fd0;
+    ctx->bn_stale = bn_stale0;
     return PIC_OK;
   };
   const long long launches0 = ctx->launches;
@@ -928,6 +952,7 @@ int pic_set_field(picpml_ctx* ctx, int which, const void* src, int as_double) {
     float* a = kind == 0 ? ctx->ff.E[c] : kind == 3 ? ctx->ff.Bh[c] : ctx->ff.Bp[c];
     CK(launch_import<float>(ctx->g, src, as_double, scale, a, s0, s1, ctx->split_ff(), ctx->stream));
   }
+  if (kind != 0) ctx->bn_stale = true;
   return PIC_OK;
 }
 
@@ -1119,6 +1144,7 @@ int pic_set_state(picpml_ctx* ctx, const void* host_src) {
     CK(cudaMemcpyAsync(a.first, q, a.second, cudaMemcpyHostToDevice, ctx->stream));
     q += a.second;
   }
+  ctx->bn_stale = true;
   CK(cudaStreamSynchronize(ctx->stream));
   return PIC_OK;
 }

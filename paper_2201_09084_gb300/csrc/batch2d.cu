@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(NT, MINB) k_batch_step(BatchArgs<T> a, int par
     g.rmin[1] = 0; g.rmax[1] = 1 << 30;
     g.rmin[2] = ri.rmin2; g.rmax[2] = ri.rmax2;
     const Tables tb = run_tables(a, ri);
-    FieldPtrs<T> f;
+    FieldPtrs<T> f{};
     for (int c = 0; c < 3; ++c) {
       f.E[c] = a.E[c] + ri.off;
       f.Bh[c] = (parity ? a.B1[c] : a.B0[c]) + ri.off;

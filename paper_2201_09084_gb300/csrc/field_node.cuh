@@ -199,6 +199,15 @@ __device__ __forceinline__ void b_update(const Geom& g, const Tables& tb, const 
   if (spx) qx = load_parts<SPL>(f.Bs[0], id);
   if (spy) qy = load_parts<SPL>(f.Bs[1], id);
   if (spz) qz = load_parts<SPL>(f.Bs[2], id);
+  // B at the integer time for the particle push, (old + new)/2, where asked
+  // for: the old totals (split nodes hold them only as parts)
+  const bool avg = f.Bn[0] != nullptr;
+  T bx0 = bx, by0 = by, bz0 = bz;
+  if (avg) {
+    if (spx) bx0 = f.Bh[0][id];
+    if (spy) by0 = f.Bh[1][id];
+    if (spz) bz0 = f.Bh[2][id];
+  }
   // ---- update ----
   if (okx) {
     const T r0 = DIM == 3 ? -Sy * (ez_yp - ez0) : T(0);
@@ -219,6 +228,11 @@ __device__ __forceinline__ void b_update(const Geom& g, const Tables& tb, const 
   if (okx) f.Bp[0][id] = bx;
   if (oky) f.Bp[1][id] = by;
   if (okz) f.Bp[2][id] = bz;
+  if (avg) {
+    if (okx) f.Bn[0][id] = T(0.5) * (bx0 + bx);
+    if (oky) f.Bn[1][id] = T(0.5) * (by0 + by);
+    if (okz) f.Bn[2][id] = T(0.5) * (bz0 + bz);
+  }
   if (spx) store_parts<SPL>(f.Bs[0], id, qx);
   if (spy) store_parts<SPL>(f.Bs[1], id, qy);
   if (spz) store_parts<SPL>(f.Bs[2], id, qz);
@@ -286,7 +300,8 @@ __device__ __forceinline__ T ck_diff(const Geom& g, const T* __restrict__ E, int
 }
 
 // B^{n+3/2} at node (i,j,k) into Bp with the CK differences (b_update's
-// split-field treatment otherwise).
+// split-field treatment otherwise), and (B^{n+1/2} + B^{n+3/2})/2 into Bn
+// where asked for.
 template <typename T, int DIM, int SPL>
 __device__ __forceinline__ void b_update_ck(const Geom& g, const Tables& tb, const FieldPtrs<T>& f, int i, int j,
                                             int k, long long id) {
@@ -311,10 +326,14 @@ __device__ __forceinline__ void b_update_ck(const Geom& g, const Tables& tb, con
     const T r1 = Sz * ck_diff<T, DIM>(g, Ey, 1, 2, i, j, k);
     if (spx) {
       Parts<SPL> q = load_parts<SPL>(f.Bs[0], id);
-      f.Bp[0][id] = advance<T, SPL, true>(tb, q, DIM == 3 ? 1 : -1, j, 2, k, r0, r1, T(0), syc, szc);
+      const T b1 = advance<T, SPL, true>(tb, q, DIM == 3 ? 1 : -1, j, 2, k, r0, r1, T(0), syc, szc);
+      f.Bp[0][id] = b1;
       store_parts<SPL>(f.Bs[0], id, q);
+      if (f.Bn[0]) f.Bn[0][id] = T(0.5) * (f.Bh[0][id] + b1);
     } else {
-      f.Bp[0][id] = f.Bh[0][id] + (r0 + r1);
+      const T b0 = f.Bh[0][id], b1 = b0 + (r0 + r1);
+      f.Bp[0][id] = b1;
+      if (f.Bn[0]) f.Bn[0][id] = T(0.5) * (b0 + b1);
     }
   }
   if (oky) {
@@ -322,10 +341,14 @@ __device__ __forceinline__ void b_update_ck(const Geom& g, const Tables& tb, con
     const T r1 = -Sz * ck_diff<T, DIM>(g, Ex, 0, 2, i, j, k);
     if (spy) {
       Parts<SPL> q = load_parts<SPL>(f.Bs[1], id);
-      f.Bp[1][id] = advance<T, SPL, true>(tb, q, 0, i, 2, k, r0, r1, T(0), sxc, szc);
+      const T b1 = advance<T, SPL, true>(tb, q, 0, i, 2, k, r0, r1, T(0), sxc, szc);
+      f.Bp[1][id] = b1;
       store_parts<SPL>(f.Bs[1], id, q);
+      if (f.Bn[0]) f.Bn[1][id] = T(0.5) * (f.Bh[1][id] + b1);
     } else {
-      f.Bp[1][id] = f.Bh[1][id] + (r0 + r1);
+      const T b0 = f.Bh[1][id], b1 = b0 + (r0 + r1);
+      f.Bp[1][id] = b1;
+      if (f.Bn[0]) f.Bn[1][id] = T(0.5) * (b0 + b1);
     }
   }
   if (okz) {
@@ -333,10 +356,14 @@ __device__ __forceinline__ void b_update_ck(const Geom& g, const Tables& tb, con
     const T r1 = DIM == 3 ? Sy * ck_diff<T, DIM>(g, Ex, 0, 1, i, j, k) : T(0);
     if (spz) {
       Parts<SPL> q = load_parts<SPL>(f.Bs[2], id);
-      f.Bp[2][id] = advance<T, SPL, true>(tb, q, 0, i, DIM == 3 ? 1 : -1, j, r0, r1, T(0), sxc, syc);
+      const T b1 = advance<T, SPL, true>(tb, q, 0, i, DIM == 3 ? 1 : -1, j, r0, r1, T(0), sxc, syc);
+      f.Bp[2][id] = b1;
       store_parts<SPL>(f.Bs[2], id, q);
+      if (f.Bn[0]) f.Bn[2][id] = T(0.5) * (f.Bh[2][id] + b1);
     } else {
-      f.Bp[2][id] = f.Bh[2][id] + (r0 + r1);
+      const T b0 = f.Bh[2][id], b1 = b0 + (r0 + r1);
+      f.Bp[2][id] = b1;
+      if (f.Bn[0]) f.Bn[2][id] = T(0.5) * (b0 + b1);
     }
   }
 }

@@ -83,6 +83,7 @@ struct FieldPtrs {
   double* Es[3][2];
   double* Bs[3][2];
   long long* Jq[3];   // deterministic mode: int64 current sums (else null)
+  T* Bn[3];           // B at the integer time, (B^{n-1/2} + B^{n+1/2})/2, written by the B pass (else null)
 };
 
 // Particle data of one species for a kernel.
@@ -112,7 +113,7 @@ struct TileSpecies {
 struct TileLaunch {
   int nsp;
   int prescribed;
-  int arr_E[3], arr_Bh[3], arr_Bp[3];   // field array of each component (4th tensor-map coordinate)
+  int arr_E[3], arr_Bh[3], arr_Bp[3], arr_Bn[3];   // field array of each component (4th tensor-map coordinate)
   TileSpecies s[kTileMaxSpecies];
 };
 

@@ -7,28 +7,31 @@
 // of every species that sat in those cells at the last sort (one contiguous
 // index range per species).  A block (persistent, two per SM) takes units
 // round-robin and, per unit:
-//   1. one thread issues nine TMA tensor copies (cp.async.bulk.tensor, one
-//      mbarrier) of the unit's field box -- E, B^{n+1/2}, B^{n-1/2} over
-//      24 x 8 x 8 nodes, i.e. the unit plus every node a particle that has
-//      drifted up to one cell out of it can gather from or deposit to -- and
-//      prefetches the next unit's box and particle records into L2;
-//   2. B^n = (B^{n-1/2} + B^{n+1/2})/2 is formed in place; the B^{n-1/2}
-//      slots then become the unit's current box (zeroed);
-//   3. each thread takes 8 consecutive particles of a species (about one
-//      cell: the sort orders cells inside a tile x fastest, so the 32 lanes
-//      of a warp sit in one 8 x 4 layer of cells and their gathers hit
+//   1. one thread issues six TMA tensor copies (cp.async.bulk.tensor, one
+//      mbarrier) of the unit's field box -- E^n and B^n (the field step's
+//      average of the two B half steps) over 24 x 8 x 8 nodes, i.e. the unit
+//      plus every node a particle that has drifted up to one cell out of it
+//      can gather from or deposit to -- and prefetches the next unit's box
+//      and particle records into L2;
+//   2. each thread takes about 8 consecutive particles of a species (about
+//      one cell: the sort orders cells inside a tile x fastest, so the 32
+//      lanes of a warp sit in one 8 x 4 layer of cells and their gathers hit
 //      distinct shared-memory banks), gathers from the box, pushes, moves,
 //      writes the record back, and deposits: a move that stays in its cell
 //      (almost all of them) adds its 12 Esirkepov values (4 per component)
-//      to a register run that is flushed to the current box with 12 shared
-//      atomics when the thread's cell changes; a move across a cell face
-//      adds its 2x3x3 values per component to the box directly; a particle
-//      outside the box gathers and deposits through global memory;
-//   4. the box is added to the grid with the damping alpha_c at each
-//      component's staggered location (Eq. alpha, Eq. MaxwellE source term)
-//      -- one atomic per non-zero node.
+//      to one of the thread's two runs in shared memory (private to the
+//      thread, so no atomics), flushed once per pass to the grid with the
+//      damping alpha_c at each component's staggered location (Eq. alpha,
+//      Eq. MaxwellE source term); a move across a cell face is queued per
+//      warp and deposited, one lane per entry, with global atomics and
+//      alpha_c; a particle outside the box gathers and deposits through
+//      global memory.
 // Particles injected after the last sort (beyond the sorted range) are pushed
 // one per thread through global memory after the units.
+//
+// The deterministic form (int64 deposition) loads both B half steps and
+// averages after the interpolation, as the one-thread kernel does, so its
+// particles move and deposit bit for bit as there.
 #include <cuda.h>
 
 #include "chunk_common.cuh"
@@ -48,9 +51,24 @@ constexpr int UX = TX * UXT;              // 16 cells
 constexpr int BX = 24, BY = 8, BZ = 8;
 constexpr int BXY = BX * BY, BN = BXY * BZ;
 constexpr int OX = 4, OY = 2, OZ = 2;
-constexpr int NT = 256, PT = 8;           // threads per block, particles per thread per pass
-constexpr int kBoxBytes = 9 * BN * 4;
-constexpr int kSmemBytes = kBoxBytes + 80 * 4 + (NT / 32) * 11 * 32 * 4 + 16 + 8 * 8;
+constexpr int NT = 256;                   // threads per block
+constexpr int PT = 12;                    // most particles per thread in one pass
+constexpr int kQWords = 11;               // words of a queue entry
+// Shared memory (floats): the field box (E, B^n; the deterministic form
+// keeps B^{n+1/2} and B^{n-1/2}: 9 arrays), the threads' runs (6 float4 per
+// thread, slot-major), the alpha tables (80), the warps' queues, then the
+// mbarrier and the species' live counts.
+template <bool FIX>
+struct Smem {
+  static constexpr int box = (FIX ? 9 : 6) * BN;
+  static constexpr int runs = FIX ? 0 : 24 * NT;
+  static constexpr int al = 80;
+  static constexpr int queue = FIX ? 0 : (NT / 32) * kQWords * 32;
+  static constexpr int floats = box + runs + al + queue;
+  static constexpr int bytes = floats * 4 + 16 + 8 * 8;
+  static constexpr unsigned box_bytes = (unsigned)box * 4u;
+};
+static_assert(Smem<false>::bytes <= 113 * 1024, "two blocks per SM");
 
 // A particle whose cell (local to the box) lies in [OX-1, OX+UX] x [OY-1, OY+TY]
 // x [OZ-1, OZ+TZ] gathers from nodes l-1 .. l+1 and deposits to nodes l .. l+1
@@ -156,69 +174,51 @@ __device__ __forceinline__ void unit_range(const TileSpecies& S, long long t0, i
   if (beg > end) beg = end;
 }
 
-// Register runs of in-cell moves: each thread keeps the 12 Esirkepov values
-// of the charge-scaled current J' (4 per component) at two box cells (its
-// particles span one or two sort cells), flushed to the current box with
-// full-warp shared atomics at the end of the pass.
+// Runs of in-cell moves: each thread keeps the 12 Esirkepov values of the
+// charge-scaled current J' (4 per component) at two box cells (its particles
+// span one or two sort cells) in shared memory of its own, slot-major
+// (float4 k of thread t at k * NT + t: the lanes of a warp touch consecutive
+// 16-byte words, without bank conflicts), so no atomics are needed until the
+// flush at the end of the pass.
 struct Runs {
   int cell[2];   // local linear cell index, -1 when free
-  float v[2][12];
+  float4* v;     // this thread's first float4 (stride NT between its six)
   __device__ __forceinline__ void clear() {
     cell[0] = cell[1] = -1;
 #pragma unroll
-    for (int t = 0; t < 12; ++t) v[0][t] = v[1][t] = 0.0f;
-  }
-  // odd: start with J_z (the warps of neighbouring cell layers then touch
-  // different components at the same time, and their shared-memory atomics
-  // meet less often on the nodes the layers share)
-  __device__ __forceinline__ void flush(float* J, int odd) const {
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-      if (cell[r] < 0) continue;
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const int c = odd ? 2 - k : k;
-        float* j = J + c * BN + cell[r];
-        // J_x at (x centre, y node +b, z node +c): v[b + 2c]; J_y at (x node
-        // +a, y centre, z node +c): v[4 + a + 2c]; J_z at (x node +a, y node
-        // +b, z centre): v[8 + a + 2b]
-        const int s1 = c == 0 ? BX : 1, s2 = c == 2 ? BX : BXY;
-        atomicAdd(j, v[r][4 * c + 0]);
-        atomicAdd(j + s1, v[r][4 * c + 1]);
-        atomicAdd(j + s2, v[r][4 * c + 2]);
-        atomicAdd(j + s1 + s2, v[r][4 * c + 3]);
-      }
-    }
+    for (int k = 0; k < 6; ++k) v[k * NT] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
 };
 
-// Adds the runs straight to the grid's current with native global float
-// reductions (in L2): the 32 lanes of a warp hold runs at distinct cells of
-// one 8 x 4 layer, so each reduction instruction covers a few sectors.  The
-// node's damping alpha_c (Eq. alpha, at the component's staggered location)
+// Adds the runs to the grid's current with native global float reductions
+// (in L2): the 32 lanes of a warp hold runs at distinct cells of one 8 x 4
+// layer, so each reduction instruction covers a few sectors.  The node's
+// damping alpha_c (Eq. alpha, at the component's staggered location)
 // multiplies the value unless the unit's whole box lies where alpha = 1.
 // al: the unit's alpha tables (x node, x centre, y node, y centre, z node,
 // z centre); org: the box origin in grid cells.
-__device__ __forceinline__ void flush_runs_global(const Runs& R, const Geom& g, const FieldPtrs<float>& f,
-                                                  const int org[3], const float* al, bool alpha_one) {
+__device__ __forceinline__ void flush_runs(const Runs& R, const Geom& g, const FieldPtrs<float>& f,
+                                           const int org[3], const float* al, bool alpha_one) {
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     if (R.cell[r] < 0) continue;
     const int L = R.cell[r];
     const int lx = L % BX, ly = (L / BX) % BY, lz = L / BXY;
     const long long base = g.idx(org[0] + lx, org[1] + ly, org[2] + lz);
+    const int lc[3] = {lx, ly, lz};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       // J_x at (x centre, y node +b, z node +c): v[b + 2c]; J_y at (x node
       // +a, y centre, z node +c): v[4 + a + 2c]; J_z at (x node +a, y node
       // +b, z centre): v[8 + a + 2b]
+      const float4 q = R.v[(3 * r + c) * NT];
+      const float vv[4] = {q.x, q.y, q.z, q.w};
       const int e1 = c == 0 ? 1 : 0, e2 = c == 2 ? 1 : 2;   // axes of the +1, +2 slots
       const long long s1 = e1 == 0 ? 1 : (e1 == 1 ? g.sy : g.sz);
       const long long s2 = e2 == 1 ? g.sy : g.sz;
-      const int lc[3] = {lx, ly, lz};
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
-        float v = R.v[r][4 * c + t];
+        float v = vv[t];
         if (!alpha_one) {
           int n[3] = {lc[0], lc[1], lc[2]};
           n[e1] += t & 1;
@@ -239,9 +239,9 @@ __device__ __forceinline__ void flush_runs_global(const Runs& R, const Geom& g, 
 // J'_x(b, c) = cj_x w (-d_x) (M_y[b] M_z[c] + (-1)^{b+c} d_y d_z / 12) with
 // the mid-move shape M = (1 - m, m), m = (o0 + o1)/2, d = o1 - o0 (the
 // transverse factor S0 S0' + DS S0'/2 + S0 DS'/2 + DS DS'/3 = M M' + DS DS'/12).
-// Added s0 times to run 0 and s1 times to run 1 (s0, s1 in {0, 1}).
-__device__ __forceinline__ void add_in_cell(Runs& r, const float o0[3], const float o1[3], const float qw[3],
-                                            float s0, float s1) {
+// Added to run `slot` (0 or 1).
+__device__ __forceinline__ void add_in_cell(Runs& r, int slot, const float o0[3], const float o1[3],
+                                            const float qw[3]) {
   float d[3], m[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -251,81 +251,41 @@ __device__ __forceinline__ void add_in_cell(Runs& r, const float o0[3], const fl
   const float c12 = 1.0f / 12.0f;
   const float eyz = c12 * d[1] * d[2], exz = c12 * d[0] * d[2], exy = c12 * d[0] * d[1];
   const float mx0 = 1.0f - m[0], my0 = 1.0f - m[1], mz0 = 1.0f - m[2];
-  float T[12];
-  T[0] = fmaf(my0, mz0, eyz);
-  T[1] = fmaf(m[1], mz0, -eyz);
-  T[2] = fmaf(my0, m[2], -eyz);
-  T[3] = fmaf(m[1], m[2], eyz);
-  T[4] = fmaf(mx0, mz0, exz);
-  T[5] = fmaf(m[0], mz0, -exz);
-  T[6] = fmaf(mx0, m[2], -exz);
-  T[7] = fmaf(m[0], m[2], exz);
-  T[8] = fmaf(mx0, my0, exy);
-  T[9] = fmaf(m[0], my0, -exy);
-  T[10] = fmaf(mx0, m[1], -exy);
-  T[11] = fmaf(m[0], m[1], exy);
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const float a = -qw[c] * d[c];
-    const float a0 = s0 * a, a1 = s1 * a;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      r.v[0][4 * c + t] = fmaf(a0, T[4 * c + t], r.v[0][4 * c + t]);
-      r.v[1][4 * c + t] = fmaf(a1, T[4 * c + t], r.v[1][4 * c + t]);
-    }
-  }
-}
-
-// Esirkepov current of a move between box cells c0 and c1 (local indices;
-// equal or neighbours per axis): the 2 x 3 x 3 prefix values per component
-// from the lower cell, non-zero ones added to the current box.
-__device__ __forceinline__ void add_move(float* J, const int c0[3], const float o0[3], const int c1[3],
-                                         const float o1[3], const float qw[3]) {
-  int lo[3];
-  float S0[3][3], DS[3][3], M[3][3], Q[3][3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    esk_axis<1, float>(c0[a], o0[a], c1[a], o1[a], lo[a], S0[a], DS[a]);
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      M[a][t] = S0[a][t] + 0.5f * DS[a][t];
-      Q[a][t] = (1.0f / 12.0f) * DS[a][t];
-    }
-  }
-  const int base = lo[0] + BX * lo[1] + BXY * lo[2];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const int b = c == 0 ? 1 : 0, e = c == 2 ? 1 : 2;   // transverse axes
-    const int sa = c == 0 ? 1 : (c == 1 ? BX : BXY);
-    const int sb = b == 0 ? 1 : (b == 1 ? BX : BXY);
-    const int se = e == 1 ? BX : BXY;
-    const float p0 = DS[c][0], p1 = DS[c][0] + DS[c][1];
-#pragma unroll
-    for (int tb = 0; tb < 3; ++tb)
-#pragma unroll
-      for (int te = 0; te < 3; ++te) {
-        const float line = qw[c] * (M[b][tb] * M[e][te] + Q[b][tb] * DS[e][te]);
-        float* jp = J + c * BN + base + tb * sb + te * se;
-        if (line * p0 != 0.0f) atomicAdd(jp, line * p0);
-        if (line * p1 != 0.0f) atomicAdd(jp + sa, line * p1);
-      }
-  }
+  float4* v = r.v + 3 * NT * slot;
+  const float ax = -qw[0] * d[0], ay = -qw[1] * d[1], az = -qw[2] * d[2];
+  float4 q = v[0];
+  q.x = fmaf(ax, fmaf(my0, mz0, eyz), q.x);
+  q.y = fmaf(ax, fmaf(m[1], mz0, -eyz), q.y);
+  q.z = fmaf(ax, fmaf(my0, m[2], -eyz), q.z);
+  q.w = fmaf(ax, fmaf(m[1], m[2], eyz), q.w);
+  v[0] = q;
+  q = v[NT];
+  q.x = fmaf(ay, fmaf(mx0, mz0, exz), q.x);
+  q.y = fmaf(ay, fmaf(m[0], mz0, -exz), q.y);
+  q.z = fmaf(ay, fmaf(mx0, m[2], -exz), q.z);
+  q.w = fmaf(ay, fmaf(m[0], m[2], exz), q.w);
+  v[NT] = q;
+  q = v[2 * NT];
+  q.x = fmaf(az, fmaf(mx0, my0, exy), q.x);
+  q.y = fmaf(az, fmaf(m[0], my0, -exy), q.y);
+  q.z = fmaf(az, fmaf(mx0, m[1], -exy), q.z);
+  q.w = fmaf(az, fmaf(m[0], m[1], exy), q.w);
+  v[2 * NT] = q;
 }
 
 // Deferred deposits of one warp (moves across a cell face, and in-cell moves
-// at a cell neither of the thread's runs holds), kept for the whole unit:
-// structure of arrays of 32 entries, local cells (linear) and offsets before
-// and after, and the charge-scaled weight per component.
-constexpr int kQWords = 11;
+// at a cell neither of the thread's runs holds): structure of arrays of 32
+// entries, grid cells (packed) and offsets before and after, and the
+// charge-scaled weight per component.
 struct Queue {
   float* q;   // kQWords * 32 floats of this warp
-  __device__ __forceinline__ void put(int k, int L0, const float o0[3], int L1, const float o1[3],
+  __device__ __forceinline__ void put(int k, int C0, const float o0[3], int C1, const float o1[3],
                                       const float qw[3]) {
-    q[0 * 32 + k] = __int_as_float(L0);
+    q[0 * 32 + k] = __int_as_float(C0);
     q[1 * 32 + k] = o0[0];
     q[2 * 32 + k] = o0[1];
     q[3 * 32 + k] = o0[2];
-    q[4 * 32 + k] = __int_as_float(L1);
+    q[4 * 32 + k] = __int_as_float(C1);
     q[5 * 32 + k] = o1[0];
     q[6 * 32 + k] = o1[1];
     q[7 * 32 + k] = o1[2];
@@ -335,30 +295,36 @@ struct Queue {
   }
 };
 
-// Deposits the first n entries of a warp's queue, lane k entry k (every lane
-// of the warp calls it; out of line: once per unit, or when the queue fills).
-__device__ __noinline__ void drain_queue(const float* q, int n, float* J) {
+// Deposits the first n entries of a warp's queue, lane k entry k, with the
+// global Esirkepov deposit and alpha_c at each staggered location (every lane
+// of the warp calls it: at the end of a unit, or when the queue fills).
+// Inlined: a call from the particle loop would make the loop keep its values
+// across the call (measured slower).
+__device__ __forceinline__ void drain_queue(const float* q, int n, const Geom& g, const Tables& tb,
+                                            const FieldPtrs<float>& f) {
   const int lane = threadIdx.x & 31;
   __syncwarp();
   if (lane < n) {
-    const int L0 = __float_as_int(q[lane]), L1 = __float_as_int(q[4 * 32 + lane]);
-    const int c0[3] = {L0 % BX, (L0 / BX) % BY, L0 / BXY};
-    const int c1[3] = {L1 % BX, (L1 / BX) % BY, L1 / BXY};
+    const int C0 = __float_as_int(q[lane]), C1 = __float_as_int(q[4 * 32 + lane]);
+    const int c0[3] = {cell_i(C0), cell_j(C0), cell_k(C0)};
+    const int c1[3] = {cell_i(C1), cell_j(C1), cell_k(C1)};
     const float o0[3] = {q[1 * 32 + lane], q[2 * 32 + lane], q[3 * 32 + lane]};
     const float o1[3] = {q[5 * 32 + lane], q[6 * 32 + lane], q[7 * 32 + lane]};
-    const float qw[3] = {q[8 * 32 + lane], q[9 * 32 + lane], q[10 * 32 + lane]};
-    add_move(J, c0, o0, c1, o1, qw);
+    SpeciesPtrs<float> sq{};
+    sq.cj[0] = q[8 * 32 + lane];
+    sq.cj[1] = q[9 * 32 + lane];
+    sq.cj[2] = q[10 * 32 + lane];
+    deposit_one<1, 3, float>(g, tb, f, sq, c0, o0, c1, o1, 1.0f, 0.0f);
   }
   __syncwarp();
 }
 
 // Gather from global memory, push, move and deposit with global atomics: the
-// path of a particle outside its unit's box (kept out of line so the box path
-// keeps its registers).
+// path of a particle outside its unit's box.
 template <bool FIX>
-__device__ __noinline__ void particle_global(const Geom& g, const Tables& tb, const FieldPtrs<float>& f,
-                                             const SpeciesPtrs<float>& sp, long long p, int prescribed,
-                                             unsigned* status, unsigned* pushed) {
+__device__ __forceinline__ void particle_global(const Geom& g, const Tables& tb, const FieldPtrs<float>& f,
+                                                const SpeciesPtrs<float>& sp, long long p, int prescribed,
+                                                unsigned* status, unsigned* pushed) {
   float4* P = reinterpret_cast<float4*>(sp.pos);
   float4* Mo = reinterpret_cast<float4*>(sp.mom);
   const float4 a = P[p], b = Mo[p];
@@ -426,8 +392,9 @@ struct Hot {
 enum : int { DEP_NONE = 0, DEP_IN_CELL = 1, DEP_ACROSS = 2, DEP_OUT = 3 };
 
 // One particle of the box path: checks, gather from the box, Boris push,
-// move, record write-back.  Returns the deposit kind with the local cells
-// L0, L1, the offsets o (before) and o1 (after) and the mid-step weight.
+// move, record write-back.  Returns the deposit kind with the local cell L0,
+// the packed grid cells C0 (before) and C1 (after), the offsets o (before)
+// and o1 (after) and the mid-step weight.
 //
 // FIX: the deterministic form.  The gather reads E, B^{n+1/2} and B^{n-1/2}
 // from the box with the one-thread kernel's arithmetic (interp_box, B^n
@@ -438,8 +405,8 @@ enum : int { DEP_NONE = 0, DEP_IN_CELL = 1, DEP_ACROSS = 2, DEP_OUT = 3 };
 template <bool FIX>
 __device__ __forceinline__ int box_particle(const Geom& g, const Hot& h, const FieldPtrs<float>& f, long long p,
                                             float4 a, float4 b, const float* F, const int org[3], int prescribed,
-                                            unsigned* status, unsigned& pushed, int& L0, int& L1, float o[3],
-                                            float o1[3], float& wd) {
+                                            unsigned* status, unsigned& pushed, int& L0, int& C0, int& C1,
+                                            float o[3], float o1[3], float& wd) {
   const int cell = __float_as_int(b.w);
   if (cell < 0) return DEP_NONE;
   const int c[3] = {cell_i(cell), cell_j(cell), cell_k(cell)};
@@ -543,29 +510,28 @@ __device__ __forceinline__ int box_particle(const Geom& g, const Hot& h, const F
     wd = w * expf(-0.5f * I);
     wn = w * expf(-I);
   }
+  const int cell1 = pack_cell(c1[0], c1[1], c1[2]);
   P[p] = ok ? make_float4(o1[0], o1[1], o1[2], wn) : a;
-  Mo[p] = make_float4(u[0], u[1], u[2], __int_as_float(ok ? pack_cell(c1[0], c1[1], c1[2]) : -1));
+  Mo[p] = make_float4(u[0], u[1], u[2], __int_as_float(ok ? cell1 : -1));
   if (!ok) return DEP_NONE;
   if constexpr (FIX) {
     deposit_fixed<1>(g, f, h.qn, c, o, c1, o1, wd, status);
     return DEP_NONE;
   }
   L0 = l[0] + BX * l[1] + BXY * l[2];
-  if (c1[0] == c[0] && c1[1] == c[1] && c1[2] == c[2]) {
-    L1 = L0;
-    return DEP_IN_CELL;
-  }
-  L1 = (c1[0] - org[0]) + BX * (c1[1] - org[1]) + BXY * (c1[2] - org[2]);
-  return DEP_ACROSS;
+  C0 = cell;
+  C1 = cell1;
+  return cell1 == cell ? DEP_IN_CELL : DEP_ACROSS;
 }
 
 // One thread's consecutive particles [p0, p1) of a species, at most `iters`
-// (the whole block calls it together with the same `iters`): box path, register runs, deferred queue, then the
-// flush of the runs and the drain of the queue.
+// (every lane of the warp calls it with the same `iters`): box path, runs,
+// deferred queue, then the flush of the runs.  Particles outside the box go
+// through the global path after the loop.
 template <bool FIX>
 __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, const FieldPtrs<float>& f,
                                             const SpeciesPtrs<float>& sp, long long p0, long long p1, int iters,
-                                            const float* F, float* J, Queue& Q, int& qn, const int org[3],
+                                            const float* F, Runs& R, Queue& Q, int& qn, const int org[3],
                                             const float* al, bool alpha_one, int prescribed, unsigned* status,
                                             unsigned& pushed) {
   const int lane = threadIdx.x & 31;
@@ -574,8 +540,7 @@ __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, con
                  sp.cj[2], sp.qn};
   const float4* P = h.pos;
   const float4* Mo = h.mom;
-  Runs R;
-  R.clear();
+  if (!FIX) R.clear();
   unsigned out = 0;   // particles of this thread for the global path
   float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
   if (p0 < p1) {
@@ -589,10 +554,12 @@ __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, con
       na = P[p + 1];
       nb = Mo[p + 1];
     }
-    int L0 = -1, L1 = -1, kind = DEP_NONE;
+    int L0 = -1, C0 = 0, C1 = 0, kind = DEP_NONE;
     float o[3], o1[3], wd = 0.0f;
-    if (p < p1) kind = box_particle<FIX>(g, h, f, p, a, b, F, org, prescribed, status, pushed, L0, L1, o, o1, wd);
+    if (p < p1)
+      kind = box_particle<FIX>(g, h, f, p, a, b, F, org, prescribed, status, pushed, L0, C0, C1, o, o1, wd);
     if (kind == DEP_OUT) out |= 1u << i;
+    if (FIX) continue;
     bool toq = kind == DEP_ACROSS;
     if (kind == DEP_IN_CELL) {
       const bool r0 = R.cell[0] == L0 || R.cell[0] < 0;
@@ -600,23 +567,25 @@ __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, con
       if (r0) R.cell[0] = L0;
       if (r1) R.cell[1] = L0;
       toq = !r0 && !r1;
-      const float qw[3] = {h.cj0 * wd, h.cj1 * wd, h.cj2 * wd};
-      add_in_cell(R, o, o1, qw, r0 ? 1.0f : 0.0f, r1 ? 1.0f : 0.0f);
+      if (!toq) {
+        const float qw[3] = {h.cj0 * wd, h.cj1 * wd, h.cj2 * wd};
+        add_in_cell(R, r0 ? 0 : 1, o, o1, qw);
+      }
     }
     const unsigned m = __ballot_sync(0xffffffffu, toq);
     if (m) {
       if (qn + __popc(m) > 32) {
-        drain_queue(Q.q, qn, J);
+        drain_queue(Q.q, qn, g, tb, f);
         qn = 0;
       }
       if (toq) {
         const float qw[3] = {h.cj0 * wd, h.cj1 * wd, h.cj2 * wd};
-        Q.put(qn + __popc(m & lt), L0, o, L1, o1, qw);
+        Q.put(qn + __popc(m & lt), C0, o, C1, o1, qw);
       }
       qn += __popc(m);
     }
   }
-  if (!FIX) flush_runs_global(R, g, f, org, al, alpha_one);
+  if (!FIX) flush_runs(R, g, f, org, al, alpha_one);
   while (out) {
     const int i = __ffs(out) - 1;
     out &= out - 1;
@@ -629,14 +598,16 @@ __global__ void __launch_bounds__(NT, 2)
     k_tile(const __grid_constant__ Geom g, const __grid_constant__ Tables tb,
            const __grid_constant__ FieldPtrs<float> f, const __grid_constant__ TileLaunch L,
            const __grid_constant__ CUtensorMap tmap, unsigned* status, unsigned long long* pushed_total) {
+  using S = Smem<FIX>;
   extern __shared__ __align__(128) float smem[];
-  float* F = smem;                       // E (3), B^n (3, formed in place), B^{n-1/2} / current box (3)
-  float* J = smem + 6 * BN;
-  float* al = smem + 9 * BN;             // alpha at the box's nodes / centres: x n, x c, y n, y c, z n, z c
-  Queue Q;
-  Q.q = al + 80 + (threadIdx.x >> 5) * (kQWords * 32);
-  unsigned long long* bar = reinterpret_cast<unsigned long long*>(al + 80 + (NT / 32) * kQWords * 32);
+  float* F = smem;   // E (3), then B^n (3), or B^{n+1/2} (3) and B^{n-1/2} (3) in the deterministic form
   const int tid = threadIdx.x;
+  Runs R;
+  R.v = reinterpret_cast<float4*>(smem + S::box) + tid;
+  float* al = smem + S::box + S::runs;   // alpha at the box's nodes / centres: x n, x c, y n, y c, z n, z c
+  Queue Q;
+  Q.q = al + S::al + (tid >> 5) * (kQWords * 32);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + S::floats);
 
   const int tx = (g.N[0] + TX - 1) / TX, ty = (g.N[1] + TY - 1) / TY, tz = (g.N[2] + TZ - 1) / TZ;
   const int ux = (tx + UXT - 1) / UXT;
@@ -650,6 +621,15 @@ __global__ void __launch_bounds__(NT, 2)
   __syncthreads();
   unsigned parity = 0, pushed = 0;
   bool alive = true;
+  // tensor-map arrays of the box: E, then B^n (or B^{n+1/2}, B^{n-1/2})
+  int arr[9];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    arr[c] = L.arr_E[c];
+    arr[3 + c] = FIX ? L.arr_Bh[c] : L.arr_Bn[c];
+    arr[6 + c] = L.arr_Bp[c];
+  }
+  constexpr int kArrays = FIX ? 9 : 6;
 
   for (long long u = blockIdx.x; u < nunits && alive; u += gridDim.x) {
     const int iu = (int)(u % ux);
@@ -667,13 +647,9 @@ __global__ void __launch_bounds__(NT, 2)
     const int org[3] = {iu * UX - OX, jt * TY - OY, kt * TZ - OZ};
     if (tid == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_expect_tx(bar, kBoxBytes);
+      mbar_expect_tx(bar, S::box_bytes);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        tma_box(F + c * BN, &tmap, org[0], org[1], org[2], L.arr_E[c], bar);
-        tma_box(F + (3 + c) * BN, &tmap, org[0], org[1], org[2], L.arr_Bh[c], bar);
-        tma_box(F + (6 + c) * BN, &tmap, org[0], org[1], org[2], L.arr_Bp[c], bar);
-      }
+      for (int c = 0; c < kArrays; ++c) tma_box(F + c * BN, &tmap, org[0], org[1], org[2], arr[c], bar);
       // the block's next unit: its field box and particle records into L2
       const long long un = u + gridDim.x;
       if (un < nunits) {
@@ -693,11 +669,7 @@ __global__ void __launch_bounds__(NT, 2)
         if (tot2 > 0) {
           const int x2 = iu2 * UX - OX, y2 = jt2 * TY - OY, z2 = kt2 * TZ - OZ;
 #pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            tma_prefetch_box(&tmap, x2, y2, z2, L.arr_E[c]);
-            tma_prefetch_box(&tmap, x2, y2, z2, L.arr_Bh[c]);
-            tma_prefetch_box(&tmap, x2, y2, z2, L.arr_Bp[c]);
-          }
+          for (int c = 0; c < kArrays; ++c) tma_prefetch_box(&tmap, x2, y2, z2, arr[c]);
         }
       }
     }
@@ -729,53 +701,29 @@ __global__ void __launch_bounds__(NT, 2)
       alive = false;
       break;
     }
-    // B^n in place; the B^{n-1/2} slots become the zeroed current box (the
-    // deterministic form keeps both B half steps and deposits globally)
-    if (!FIX) {
-      for (int q = tid; q < 3 * BN; q += NT) {
-        F[3 * BN + q] = 0.5f * (F[3 * BN + q] + F[6 * BN + q]);
-        J[q] = 0.0f;
-      }
-      __syncthreads();
-    }
     int qn = 0;   // entries in this warp's queue (the same in every lane)
+    const int warp0 = tid & ~31;
     for (int s = 0; s < L.nsp; ++s) {
-      const TileSpecies& S = L.s[s];
+      const TileSpecies& Sp = L.s[s];
       long long beg, end;
-      unit_range(S, t0, nt, nlive[s], beg, end);
-      // passes of at most NT * PT particles, split evenly over the threads
-      // (consecutive runs of ceil or floor of the pass size / NT)
+      unit_range(Sp, t0, nt, nlive[s], beg, end);
+      // passes of at most NT * PT particles; in a pass of m particles thread
+      // t takes q or q + 1 consecutive ones (q = m / NT, the first m % NT
+      // threads one more), so only the warps holding the extra particles
+      // run the extra iteration
       const long long npass = (end - beg + NT * PT - 1) / (NT * PT);
       for (long long k = 0; k < npass; ++k) {
         const long long b0 = beg + (end - beg) * k / npass, b1 = beg + (end - beg) * (k + 1) / npass;
-        const long long m = b1 - b0;
-        const long long p0 = b0 + m * tid / NT, p1 = b0 + m * (tid + 1) / NT;
-        thread_pass<FIX>(g, tb, f, S.sp, p0, p1, (int)((m + NT - 1) / NT), F, J, Q, qn, org, al, alpha_one,
+        const int m = (int)(b1 - b0);
+        const int q = m / NT, rem = m % NT;
+        const long long p0 = b0 + (long long)q * tid + min(tid, rem);
+        const long long p1 = p0 + q + (tid < rem ? 1 : 0);
+        thread_pass<FIX>(g, tb, f, Sp.sp, p0, p1, q + (warp0 < rem ? 1 : 0), F, R, Q, qn, org, al, alpha_one,
                          L.prescribed, status, pushed);
       }
     }
-    if (qn) drain_queue(Q.q, qn, J);
-    __syncthreads();
-    if (FIX) continue;   // (the next unit's copy may overwrite the box: every thread passed the barrier)
-    // the current box to the grid with alpha at each component's location
-    const float* axn = al;
-    const float* axc = al + BX;
-    const float* ayn = al + 2 * BX;
-    const float* ayc = al + 2 * BX + BY;
-    const float* azn = al + 2 * BX + 2 * BY;
-    const float* azc = al + 2 * BX + 2 * BY + BZ;
-    for (int q = tid; q < 3 * BN; q += NT) {
-      const float v = J[q];
-      if (v == 0.0f) continue;
-      const int c = q / BN, nidx = q - c * BN;
-      const int lx = nidx % BX, ly = (nidx / BX) % BY, lz = nidx / BXY;
-      const int gx = org[0] + lx, gy = org[1] + ly, gz = org[2] + lz;
-      if (gx < 0 || gy < 0 || gz < 0 || gx >= g.nn[0] || gy >= g.nn[1] || gz >= g.nn[2]) continue;
-      const float a = c == 0 ? axc[lx] * ayn[ly] * azn[lz]
-                             : (c == 1 ? axn[lx] * ayc[ly] * azn[lz] : axn[lx] * ayn[ly] * azc[lz]);
-      atomicAdd(f.J[c] + g.idx(gx, gy, gz), v * a);
-    }
-    __syncthreads();
+    if (!FIX && qn) drain_queue(Q.q, qn, g, tb, f);
+    __syncthreads();   // the next unit's copy may overwrite the box: every thread is past it
   }
   // particles added after the last sort: one per thread, through global memory
   if (alive) {
@@ -814,11 +762,12 @@ cudaError_t launch_tile_ends(const Geom& g, const unsigned* cursor, long long* t
   return cudaGetLastError();
 }
 
-// Tensor map of the 12 FP32 field arrays (E, B^{n+1/2}, B^{n-1/2}, J per
-// component, each `size` elements) as one 4D tensor (x, y, z, array) whose
-// boxes are the 24 x 8 x 8-node field boxes of the tile kernel.  Out-of-grid
-// parts of a box read as zero.
-cudaError_t make_tile_tensor_map(const Geom& g, const float* base, void* map_out) {
+// Tensor map of the field allocation from its first FP32 array on, as
+// `arrays` arrays of `size` FP32 elements (E, B^{n+1/2}, B^{n-1/2}, J per
+// component; the FP64 split parts; B^n per component where present): one 4D
+// tensor (x, y, z, array) whose boxes are the 24 x 8 x 8-node field boxes of
+// the tile kernel.  Out-of-grid parts of a box read as zero.
+cudaError_t make_tile_tensor_map(const Geom& g, const float* base, int arrays, void* map_out) {
   using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                               const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                               CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -831,7 +780,7 @@ cudaError_t make_tile_tensor_map(const Geom& g, const float* base, void* map_out
     if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
     encode = reinterpret_cast<Encode>(fn);
   }
-  const cuuint64_t dims[4] = {(cuuint64_t)g.nn[0], (cuuint64_t)g.nn[1], (cuuint64_t)g.nn[2], 12};
+  const cuuint64_t dims[4] = {(cuuint64_t)g.nn[0], (cuuint64_t)g.nn[1], (cuuint64_t)g.nn[2], (cuuint64_t)arrays};
   const cuuint64_t strides[3] = {(cuuint64_t)g.sy * 4, (cuuint64_t)g.sz * 4, (cuuint64_t)g.size * 4};
   const cuuint32_t box[4] = {BX, BY, BZ, 1};
   const cuuint32_t es[4] = {1, 1, 1, 1};
@@ -844,18 +793,36 @@ cudaError_t make_tile_tensor_map(const Geom& g, const float* base, void* map_out
 
 int tile_map_bytes() { return (int)sizeof(CUtensorMap); }
 
+// B at the integer time from the two B half steps, (Bh + Bp)/2 per node, for
+// the box path when B was set from outside the field step.
+__global__ void k_bn_average(FieldPtrs<float> f, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) f.Bn[c][i] = 0.5f * (f.Bh[c][i] + f.Bp[c][i]);
+}
+
+cudaError_t launch_bn_average(const Geom& g, const FieldPtrs<float>& f, cudaStream_t s) {
+  if (!f.Bn[0]) return cudaErrorInvalidValue;
+  long long blocks = (g.size + 255) / 256;
+  if (blocks > 65536) blocks = 65536;
+  k_bn_average<<<(unsigned)blocks, 256, 0, s>>>(f, g.size);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tile(const Geom& g, const Tables& tb, const FieldPtrs<float>& f, const TileLaunch& L,
                         const void* map, unsigned* status, unsigned long long* pushed, int nsm, cudaStream_t s) {
   if (L.nsp <= 0) return cudaSuccess;
   const bool fix = f.Jq[0] != nullptr;   // the deterministic (int64) form
+  if (!fix && !f.Bn[0]) return cudaErrorInvalidValue;   // the box path reads B^n
   auto kern = fix ? k_tile<true> : k_tile<false>;
+  const int smem = fix ? Smem<true>::bytes : Smem<false>::bytes;
   static std::atomic<unsigned long long> configured[2];   // devices whose limit is set, per form
   {
-    cudaError_t e = smem_limit_once(kern, kSmemBytes, configured[fix ? 1 : 0]);
+    cudaError_t e = smem_limit_once(kern, smem, configured[fix ? 1 : 0]);
     if (e != cudaSuccess) return e;
   }
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, kSmemBytes);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   const long long tx = (g.N[0] + TX - 1) / TX, ty = (g.N[1] + TY - 1) / TY, tz = (g.N[2] + TZ - 1) / TZ;
@@ -863,7 +830,7 @@ cudaError_t launch_tile(const Geom& g, const Tables& tb, const FieldPtrs<float>&
   long long blocks = (long long)nsm * per_sm;
   if (blocks > nunits) blocks = nunits;
   if (blocks < 1) blocks = 1;
-  kern<<<(unsigned)blocks, NT, kSmemBytes, s>>>(g, tb, f, L, *reinterpret_cast<const CUtensorMap*>(map), status,
+  kern<<<(unsigned)blocks, NT, smem, s>>>(g, tb, f, L, *reinterpret_cast<const CUtensorMap*>(map), status,
                                                   pushed);
   return cudaGetLastError();
 }

@@ -19,10 +19,10 @@
 //      distinct shared-memory banks), gathers from the box, pushes, moves,
 //      writes the record back, and deposits: a move that stays in its cell
 //      (almost all of them) adds its 12 Esirkepov values (4 per component)
-//      to one of the thread's two runs in shared memory (private to the
-//      thread, so no atomics), flushed once per pass to the grid with the
-//      damping alpha_c at each component's staggered location (Eq. alpha,
-//      Eq. MaxwellE source term); a move across a cell face is queued per
+//      to one of the thread's two runs in registers (no atomics), flushed
+//      once per pass to the grid with the damping alpha_c at each
+//      component's staggered location (Eq. alpha, Eq. MaxwellE source
+//      term); a move across a cell face is queued per
 //      warp and deposited, one lane per entry, with global atomics and
 //      alpha_c; a particle outside the box gathers and deposits through
 //      global memory.
@@ -55,16 +55,14 @@ constexpr int NT = 256;                   // threads per block
 constexpr int PT = 12;                    // most particles per thread in one pass
 constexpr int kQWords = 11;               // words of a queue entry
 // Shared memory (floats): the field box (E, B^n; the deterministic form
-// keeps B^{n+1/2} and B^{n-1/2}: 9 arrays), the threads' runs (6 float4 per
-// thread, slot-major), the alpha tables (80), the warps' queues, then the
-// mbarrier and the species' live counts.
+// keeps B^{n+1/2} and B^{n-1/2}: 9 arrays), the alpha tables (80), the
+// warps' queues, then the mbarrier and the species' live counts.
 template <bool FIX>
 struct Smem {
   static constexpr int box = (FIX ? 9 : 6) * BN;
-  static constexpr int runs = FIX ? 0 : 24 * NT;
   static constexpr int al = 80;
   static constexpr int queue = FIX ? 0 : (NT / 32) * kQWords * 32;
-  static constexpr int floats = box + runs + al + queue;
+  static constexpr int floats = box + al + queue;
   static constexpr int bytes = floats * 4 + 16 + 8 * 8;
   static constexpr unsigned box_bytes = (unsigned)box * 4u;
 };
@@ -176,17 +174,17 @@ __device__ __forceinline__ void unit_range(const TileSpecies& S, long long t0, i
 
 // Runs of in-cell moves: each thread keeps the 12 Esirkepov values of the
 // charge-scaled current J' (4 per component) at two box cells (its particles
-// span one or two sort cells) in shared memory of its own, slot-major
-// (float4 k of thread t at k * NT + t: the lanes of a warp touch consecutive
-// 16-byte words, without bank conflicts), so no atomics are needed until the
-// flush at the end of the pass.
+// span one or two sort cells) in registers, so no atomics are needed until
+// the flush at the end of the pass.  (Runs in per-thread shared memory freed
+// the registers but were slower: they add six 16-byte shared accesses per
+// particle to a shared-memory pipe the gather already loads heavily.)
 struct Runs {
   int cell[2];   // local linear cell index, -1 when free
-  float4* v;     // this thread's first float4 (stride NT between its six)
+  float v[2][12];
   __device__ __forceinline__ void clear() {
     cell[0] = cell[1] = -1;
 #pragma unroll
-    for (int k = 0; k < 6; ++k) v[k * NT] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int t = 0; t < 12; ++t) v[0][t] = v[1][t] = 0.0f;
   }
 };
 
@@ -211,8 +209,7 @@ __device__ __forceinline__ void flush_runs(const Runs& R, const Geom& g, const F
       // J_x at (x centre, y node +b, z node +c): v[b + 2c]; J_y at (x node
       // +a, y centre, z node +c): v[4 + a + 2c]; J_z at (x node +a, y node
       // +b, z centre): v[8 + a + 2b]
-      const float4 q = R.v[(3 * r + c) * NT];
-      const float vv[4] = {q.x, q.y, q.z, q.w};
+      const float vv[4] = {R.v[r][4 * c], R.v[r][4 * c + 1], R.v[r][4 * c + 2], R.v[r][4 * c + 3]};
       const int e1 = c == 0 ? 1 : 0, e2 = c == 2 ? 1 : 2;   // axes of the +1, +2 slots
       const long long s1 = e1 == 0 ? 1 : (e1 == 1 ? g.sy : g.sz);
       const long long s2 = e2 == 1 ? g.sy : g.sz;
@@ -239,9 +236,9 @@ __device__ __forceinline__ void flush_runs(const Runs& R, const Geom& g, const F
 // J'_x(b, c) = cj_x w (-d_x) (M_y[b] M_z[c] + (-1)^{b+c} d_y d_z / 12) with
 // the mid-move shape M = (1 - m, m), m = (o0 + o1)/2, d = o1 - o0 (the
 // transverse factor S0 S0' + DS S0'/2 + S0 DS'/2 + DS DS'/3 = M M' + DS DS'/12).
-// Added to run `slot` (0 or 1).
-__device__ __forceinline__ void add_in_cell(Runs& r, int slot, const float o0[3], const float o1[3],
-                                            const float qw[3]) {
+// Added s0 times to run 0 and s1 times to run 1 (s0, s1 in {0, 1}).
+__device__ __forceinline__ void add_in_cell(Runs& r, const float o0[3], const float o1[3], const float qw[3],
+                                            float s0, float s1) {
   float d[3], m[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -251,26 +248,29 @@ __device__ __forceinline__ void add_in_cell(Runs& r, int slot, const float o0[3]
   const float c12 = 1.0f / 12.0f;
   const float eyz = c12 * d[1] * d[2], exz = c12 * d[0] * d[2], exy = c12 * d[0] * d[1];
   const float mx0 = 1.0f - m[0], my0 = 1.0f - m[1], mz0 = 1.0f - m[2];
-  float4* v = r.v + 3 * NT * slot;
-  const float ax = -qw[0] * d[0], ay = -qw[1] * d[1], az = -qw[2] * d[2];
-  float4 q = v[0];
-  q.x = fmaf(ax, fmaf(my0, mz0, eyz), q.x);
-  q.y = fmaf(ax, fmaf(m[1], mz0, -eyz), q.y);
-  q.z = fmaf(ax, fmaf(my0, m[2], -eyz), q.z);
-  q.w = fmaf(ax, fmaf(m[1], m[2], eyz), q.w);
-  v[0] = q;
-  q = v[NT];
-  q.x = fmaf(ay, fmaf(mx0, mz0, exz), q.x);
-  q.y = fmaf(ay, fmaf(m[0], mz0, -exz), q.y);
-  q.z = fmaf(ay, fmaf(mx0, m[2], -exz), q.z);
-  q.w = fmaf(ay, fmaf(m[0], m[2], exz), q.w);
-  v[NT] = q;
-  q = v[2 * NT];
-  q.x = fmaf(az, fmaf(mx0, my0, exy), q.x);
-  q.y = fmaf(az, fmaf(m[0], my0, -exy), q.y);
-  q.z = fmaf(az, fmaf(mx0, m[1], -exy), q.z);
-  q.w = fmaf(az, fmaf(m[0], m[1], exy), q.w);
-  v[2 * NT] = q;
+  float T[12];
+  T[0] = fmaf(my0, mz0, eyz);
+  T[1] = fmaf(m[1], mz0, -eyz);
+  T[2] = fmaf(my0, m[2], -eyz);
+  T[3] = fmaf(m[1], m[2], eyz);
+  T[4] = fmaf(mx0, mz0, exz);
+  T[5] = fmaf(m[0], mz0, -exz);
+  T[6] = fmaf(mx0, m[2], -exz);
+  T[7] = fmaf(m[0], m[2], exz);
+  T[8] = fmaf(mx0, my0, exy);
+  T[9] = fmaf(m[0], my0, -exy);
+  T[10] = fmaf(mx0, m[1], -exy);
+  T[11] = fmaf(m[0], m[1], exy);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float a = -qw[c] * d[c];
+    const float a0 = s0 * a, a1 = s1 * a;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      r.v[0][4 * c + t] = fmaf(a0, T[4 * c + t], r.v[0][4 * c + t]);
+      r.v[1][4 * c + t] = fmaf(a1, T[4 * c + t], r.v[1][4 * c + t]);
+    }
+  }
 }
 
 // Deferred deposits of one warp (moves across a cell face, and in-cell moves
@@ -531,7 +531,7 @@ __device__ __forceinline__ int box_particle(const Geom& g, const Hot& h, const F
 template <bool FIX>
 __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, const FieldPtrs<float>& f,
                                             const SpeciesPtrs<float>& sp, long long p0, long long p1, int iters,
-                                            const float* F, Runs& R, Queue& Q, int& qn, const int org[3],
+                                            const float* F, Queue& Q, int& qn, const int org[3],
                                             const float* al, bool alpha_one, int prescribed, unsigned* status,
                                             unsigned& pushed) {
   const int lane = threadIdx.x & 31;
@@ -540,7 +540,8 @@ __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, con
                  sp.cj[2], sp.qn};
   const float4* P = h.pos;
   const float4* Mo = h.mom;
-  if (!FIX) R.clear();
+  Runs R;
+  R.clear();
   unsigned out = 0;   // particles of this thread for the global path
   float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
   if (p0 < p1) {
@@ -569,7 +570,7 @@ __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, con
       toq = !r0 && !r1;
       if (!toq) {
         const float qw[3] = {h.cj0 * wd, h.cj1 * wd, h.cj2 * wd};
-        add_in_cell(R, r0 ? 0 : 1, o, o1, qw);
+        add_in_cell(R, o, o1, qw, r0 ? 1.0f : 0.0f, r0 ? 0.0f : 1.0f);
       }
     }
     const unsigned m = __ballot_sync(0xffffffffu, toq);
@@ -602,9 +603,7 @@ __global__ void __launch_bounds__(NT, 2)
   extern __shared__ __align__(128) float smem[];
   float* F = smem;   // E (3), then B^n (3), or B^{n+1/2} (3) and B^{n-1/2} (3) in the deterministic form
   const int tid = threadIdx.x;
-  Runs R;
-  R.v = reinterpret_cast<float4*>(smem + S::box) + tid;
-  float* al = smem + S::box + S::runs;   // alpha at the box's nodes / centres: x n, x c, y n, y c, z n, z c
+  float* al = smem + S::box;   // alpha at the box's nodes / centres: x n, x c, y n, y c, z n, z c
   Queue Q;
   Q.q = al + S::al + (tid >> 5) * (kQWords * 32);
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + S::floats);
@@ -718,7 +717,7 @@ __global__ void __launch_bounds__(NT, 2)
         const int q = m / NT, rem = m % NT;
         const long long p0 = b0 + (long long)q * tid + min(tid, rem);
         const long long p1 = p0 + q + (tid < rem ? 1 : 0);
-        thread_pass<FIX>(g, tb, f, Sp.sp, p0, p1, q + (warp0 < rem ? 1 : 0), F, R, Q, qn, org, al, alpha_one,
+        thread_pass<FIX>(g, tb, f, Sp.sp, p0, p1, q + (warp0 < rem ? 1 : 0), F, Q, qn, org, al, alpha_one,
                          L.prescribed, status, pushed);
       }
     }

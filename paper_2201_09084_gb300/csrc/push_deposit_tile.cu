@@ -55,18 +55,20 @@ constexpr int NT = 256;                   // threads per block
 constexpr int PT = 12;                    // most particles per thread in one pass
 constexpr int kQWords = 11;               // words of a queue entry
 // Shared memory (floats): the field box (E, B^n; the deterministic form
-// keeps B^{n+1/2} and B^{n-1/2}: 9 arrays), the alpha tables (80), the
+// keeps B^{n+1/2} and B^{n-1/2}: 9 arrays), the alpha tables (node and
+// centre per axis: 2 (BX + BY + BZ)), the
 // warps' queues, then the mbarrier and the species' live counts.
 template <bool FIX>
 struct Smem {
   static constexpr int box = (FIX ? 9 : 6) * BN;
-  static constexpr int al = 80;
+  static constexpr int al = 2 * (BX + BY + BZ);
   static constexpr int queue = FIX ? 0 : (NT / 32) * kQWords * 32;
   static constexpr int floats = box + al + queue;
   static constexpr int bytes = floats * 4 + 16 + 8 * 8;
   static constexpr unsigned box_bytes = (unsigned)box * 4u;
 };
 static_assert(Smem<false>::bytes <= 113 * 1024, "two blocks per SM");
+static_assert(2 * (BX + BY + BZ) <= NT, "one thread per alpha-table entry");
 
 // A particle whose cell (local to the box) lies in [OX-1, OX+UX] x [OY-1, OY+TY]
 // x [OZ-1, OZ+TZ] gathers from nodes l-1 .. l+1 and deposits to nodes l .. l+1
@@ -673,11 +675,11 @@ __global__ void __launch_bounds__(NT, 2)
       }
     }
     // alpha tables of this box (0 outside the grid, where no current lands)
-    if (tid < 80) {
+    if (tid < S::al) {
       int ax, i, stag;
-      if (tid < 48) { ax = 0; i = tid % BX; stag = tid / BX; }
-      else if (tid < 64) { ax = 1; i = (tid - 48) % BY; stag = (tid - 48) / BY; }
-      else { ax = 2; i = (tid - 64) % BZ; stag = (tid - 64) / BZ; }
+      if (tid < 2 * BX) { ax = 0; i = tid % BX; stag = tid / BX; }
+      else if (tid < 2 * (BX + BY)) { ax = 1; i = (tid - 2 * BX) % BY; stag = (tid - 2 * BX) / BY; }
+      else { ax = 2; i = (tid - 2 * (BX + BY)) % BZ; stag = (tid - 2 * (BX + BY)) / BZ; }
       const int gi = org[ax] + i;
       float v = 0.0f;
       if (gi >= 0 && gi < g.nn[ax]) v = stag ? tb.al_cf[ax][gi] : tb.al_nf[ax][gi];

@@ -660,12 +660,13 @@ PLASMA_NCU_BYTES_PER_PARTICLE = 557_966_080 / 8_429_785
 # capture of the 64 x 64 x 128 case; the plasma fills the box at a fixed 8 particles
 # per cell and species, so the traffic grows with the particle count and the
 # full-size figure is scaled by it.  None until captured on the current kernel.
-# To be captured with
+# Captured with
 #   ncu --set full --clock-control none -k regex:^k_tile$ -s 4 -c 1
 #       python bench.py --cells 64,64,128 --no-extra --no-cpu-baseline --steps 3 --warmup 3 --tuning 2,1
-HEADLINE_NCU_BYTES_PER_PARTICLE = None
+# (310,212,352 B read + 222,766,592 B written for 8,429,785 particles).
+HEADLINE_NCU_BYTES_PER_PARTICLE = (310_212_352 + 222_766_592) / 8_429_785
 HEADLINE_NCU_NOTE = ("per launch: dram__bytes_read.sum + dram__bytes_write.sum of the tile kernel on the "
-                     "64x64x128 case (64.7 B per particle), scaled by the particles pushed")
+                     "64x64x128 case (63.2 B per particle), scaled by the particles pushed")
 
 # Plasma boxes with more particles per species than this are generated and
 # packed one z-plane of cells at a time (inputs.plasma_planes) instead of in

@@ -190,47 +190,49 @@ struct Runs {
   }
 };
 
-// Adds the runs to the grid's current with native global float reductions
-// (in L2): the 32 lanes of a warp hold runs at distinct cells of one 8 x 4
-// layer, so each reduction instruction covers a few sectors.  The node's
-// damping alpha_c (Eq. alpha, at the component's staggered location)
-// multiplies the value unless the unit's whole box lies where alpha = 1.
-// al: the unit's alpha tables (x node, x centre, y node, y centre, z node,
-// z centre); org: the box origin in grid cells.
+// Adds the 12 values v of local box cell L to the grid's current with native
+// global float reductions (in L2).  The node's damping alpha_c (Eq. alpha, at
+// the component's staggered location) multiplies the value unless the unit's
+// whole box lies where alpha = 1.  al: the unit's alpha tables (x node,
+// x centre, y node, y centre, z node, z centre); org: the box origin in grid
+// cells.  Slots: J_x at (x centre, y node +b, z node +c): v[b + 2c]; J_y at
+// (x node +a, y centre, z node +c): v[4 + a + 2c]; J_z at (x node +a, y node
+// +b, z centre): v[8 + a + 2b].
+__device__ __forceinline__ void red_cell(const float v[12], int L, const Geom& g, const FieldPtrs<float>& f,
+                                         const int org[3], const float* al, bool alpha_one) {
+  const int lx = L % BX, ly = (L / BX) % BY, lz = L / BXY;
+  const long long base = g.idx(org[0] + lx, org[1] + ly, org[2] + lz);
+  const int lc[3] = {lx, ly, lz};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const int e1 = c == 0 ? 1 : 0, e2 = c == 2 ? 1 : 2;   // axes of the +1, +2 slots
+    const long long s1 = e1 == 0 ? 1 : (e1 == 1 ? g.sy : g.sz);
+    const long long s2 = e2 == 1 ? g.sy : g.sz;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      float x = v[4 * c + t];
+      if (!alpha_one) {
+        int n[3] = {lc[0], lc[1], lc[2]};
+        n[e1] += t & 1;
+        n[e2] += t >> 1;
+        const float ax = c == 0 ? al[BX + n[0]] : al[n[0]];
+        const float ay = c == 1 ? al[2 * BX + BY + n[1]] : al[2 * BX + n[1]];
+        const float az = c == 2 ? al[2 * BX + 2 * BY + BZ + n[2]] : al[2 * BX + 2 * BY + n[2]];
+        x *= ax * ay * az;
+      }
+      atomicAdd(f.J[c] + base + (t & 1) * s1 + (t >> 1) * s2, x);
+    }
+  }
+}
+
+// Adds the runs to the grid's current (red_cell): the 32 lanes of a warp
+// hold runs at distinct cells of one 8 x 4 layer, so each reduction
+// instruction covers a few sectors.
 __device__ __forceinline__ void flush_runs(const Runs& R, const Geom& g, const FieldPtrs<float>& f,
                                            const int org[3], const float* al, bool alpha_one) {
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    if (R.cell[r] < 0) continue;
-    const int L = R.cell[r];
-    const int lx = L % BX, ly = (L / BX) % BY, lz = L / BXY;
-    const long long base = g.idx(org[0] + lx, org[1] + ly, org[2] + lz);
-    const int lc[3] = {lx, ly, lz};
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      // J_x at (x centre, y node +b, z node +c): v[b + 2c]; J_y at (x node
-      // +a, y centre, z node +c): v[4 + a + 2c]; J_z at (x node +a, y node
-      // +b, z centre): v[8 + a + 2b]
-      const float vv[4] = {R.v[r][4 * c], R.v[r][4 * c + 1], R.v[r][4 * c + 2], R.v[r][4 * c + 3]};
-      const int e1 = c == 0 ? 1 : 0, e2 = c == 2 ? 1 : 2;   // axes of the +1, +2 slots
-      const long long s1 = e1 == 0 ? 1 : (e1 == 1 ? g.sy : g.sz);
-      const long long s2 = e2 == 1 ? g.sy : g.sz;
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        float v = vv[t];
-        if (!alpha_one) {
-          int n[3] = {lc[0], lc[1], lc[2]};
-          n[e1] += t & 1;
-          n[e2] += t >> 1;
-          const float ax = c == 0 ? al[BX + n[0]] : al[n[0]];
-          const float ay = c == 1 ? al[2 * BX + BY + n[1]] : al[2 * BX + n[1]];
-          const float az = c == 2 ? al[2 * BX + 2 * BY + BZ + n[2]] : al[2 * BX + 2 * BY + n[2]];
-          v *= ax * ay * az;
-        }
-        atomicAdd(f.J[c] + base + (t & 1) * s1 + (t >> 1) * s2, v);
-      }
-    }
-  }
+  for (int r = 0; r < 2; ++r)
+    if (R.cell[r] >= 0) red_cell(R.v[r], R.cell[r], g, f, org, al, alpha_one);
 }
 
 // Esirkepov current of a move that stays in its cell (Esirkepov's density
@@ -238,7 +240,35 @@ __device__ __forceinline__ void flush_runs(const Runs& R, const Geom& g, const F
 // J'_x(b, c) = cj_x w (-d_x) (M_y[b] M_z[c] + (-1)^{b+c} d_y d_z / 12) with
 // the mid-move shape M = (1 - m, m), m = (o0 + o1)/2, d = o1 - o0 (the
 // transverse factor S0 S0' + DS S0'/2 + S0 DS'/2 + DS DS'/3 = M M' + DS DS'/12).
-// Added s0 times to run 0 and s1 times to run 1 (s0, s1 in {0, 1}).
+// in_cell_values: the 12 values (slots as in red_cell).
+__device__ __forceinline__ void in_cell_values(const float o0[3], const float o1[3], const float qw[3],
+                                               float v[12]) {
+  float d[3], m[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    d[a] = o1[a] - o0[a];
+    m[a] = 0.5f * (o0[a] + o1[a]);
+  }
+  const float c12 = 1.0f / 12.0f;
+  const float eyz = c12 * d[1] * d[2], exz = c12 * d[0] * d[2], exy = c12 * d[0] * d[1];
+  const float mx0 = 1.0f - m[0], my0 = 1.0f - m[1], mz0 = 1.0f - m[2];
+  const float ax = -qw[0] * d[0], ay = -qw[1] * d[1], az = -qw[2] * d[2];
+  v[0] = ax * fmaf(my0, mz0, eyz);
+  v[1] = ax * fmaf(m[1], mz0, -eyz);
+  v[2] = ax * fmaf(my0, m[2], -eyz);
+  v[3] = ax * fmaf(m[1], m[2], eyz);
+  v[4] = ay * fmaf(mx0, mz0, exz);
+  v[5] = ay * fmaf(m[0], mz0, -exz);
+  v[6] = ay * fmaf(mx0, m[2], -exz);
+  v[7] = ay * fmaf(m[0], m[2], exz);
+  v[8] = az * fmaf(mx0, my0, exy);
+  v[9] = az * fmaf(m[0], my0, -exy);
+  v[10] = az * fmaf(mx0, m[1], -exy);
+  v[11] = az * fmaf(m[0], m[1], exy);
+}
+
+// add_in_cell: added s0 times to run 0 and s1 times to run 1 (s0, s1 in
+// {0, 1}).
 __device__ __forceinline__ void add_in_cell(Runs& r, const float o0[3], const float o1[3], const float qw[3],
                                             float s0, float s1) {
   float d[3], m[3];
@@ -275,10 +305,9 @@ __device__ __forceinline__ void add_in_cell(Runs& r, const float o0[3], const fl
   }
 }
 
-// Deferred deposits of one warp (moves across a cell face, and in-cell moves
-// at a cell neither of the thread's runs holds): structure of arrays of 32
-// entries, grid cells (packed) and offsets before and after, and the
-// charge-scaled weight per component.
+// Deferred deposits of one warp (moves across a cell face): structure of
+// arrays of 32 entries, grid cells (packed) and offsets before and after,
+// and the charge-scaled weight per component.
 struct Queue {
   float* q;   // kQWords * 32 floats of this warp
   __device__ __forceinline__ void put(int k, int C0, const float o0[3], int C1, const float o1[3],
@@ -563,16 +592,19 @@ __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, con
       kind = box_particle<FIX>(g, h, f, p, a, b, F, org, prescribed, status, pushed, L0, C0, C1, o, o1, wd);
     if (kind == DEP_OUT) out |= 1u << i;
     if (FIX) continue;
-    bool toq = kind == DEP_ACROSS;
+    const bool toq = kind == DEP_ACROSS;
     if (kind == DEP_IN_CELL) {
       const bool r0 = R.cell[0] == L0 || R.cell[0] < 0;
       const bool r1 = !r0 && (R.cell[1] == L0 || R.cell[1] < 0);
       if (r0) R.cell[0] = L0;
       if (r1) R.cell[1] = L0;
-      toq = !r0 && !r1;
-      if (!toq) {
-        const float qw[3] = {h.cj0 * wd, h.cj1 * wd, h.cj2 * wd};
+      const float qw[3] = {h.cj0 * wd, h.cj1 * wd, h.cj2 * wd};
+      if (r0 || r1) {
         add_in_cell(R, o, o1, qw, r0 ? 1.0f : 0.0f, r0 ? 0.0f : 1.0f);
+      } else {   // a third cell (particles that left their sorted cell): straight to the grid
+        float v[12];
+        in_cell_values(o, o1, qw, v);
+        red_cell(v, L0, g, f, org, al, alpha_one);
       }
     }
     const unsigned m = __ballot_sync(0xffffffffu, toq);

@@ -2,7 +2,9 @@
 configuration the benchmark times: the thermal plasma + drifting beam in
 256 x 256 x 512 physical cells + a 16-cell PML on every face (288 x 288 x 544
 cells), electrons and protons 8 per cell (536,870,912) plus the u_z = 5 beam,
-FP32 fields with IEEE FP64 PML parts, the tile kernel, a sort every 20 steps.
+FP32 fields with IEEE FP64 PML parts, the tile kernel, a sort every 20 steps;
+and the precision-study workload, the same at 128 x 128 x 256 (67 M
+particles), in FP32 and in the deterministic int64 form.
 
 No oracle box of this size runs; the checks are the ones that hold at any
 size or that the oracle can make one particle at a time:
@@ -38,12 +40,14 @@ def _neighbourhood(fields, c):
     return {n: a[sl].cpu().numpy() for n, a in fields.items()}
 
 
-def test_headline_full_size_sampled_push_and_gauss():
+@pytest.mark.parametrize("cells,prec", [((256, 256, 512), "fp32"), ((128, 128, 256), "fp32"),
+                                        ((128, 128, 256), "fixed64")], ids=["537M-fp32", "67M-fp32", "67M-fixed64"])
+def test_headline_full_size_sampled_push_and_gauss(cells, prec):
     import torch
     import bench
     from paper_2201_09084_gb300.api import Sim
-    recs = bench.headline_records(bench.HL_NPHYS, "cuda")
-    sim = Sim(3, bench.HL_NPHYS, bench.D, bench.PML, cfl=0.99, order=1, prec="fp32", alpha_mode="damped",
+    recs = bench.headline_records(cells, "cuda")
+    sim = Sim(3, cells, bench.D, bench.PML, cfl=0.99, order=1, prec=prec, alpha_mode="damped",
               sort_every=bench.SORT_EVERY, split_fp64=True)
     for pos, mom, n, q, m, imm in recs:
         sim.add_species(pos, mom, n, q, m, imm)
@@ -118,5 +122,5 @@ def test_headline_full_size_sampled_push_and_gauss():
     assert dg["rho_scale"] > 0
     assert dg["gauss"] <= 1e-5 * dg["rho_scale"], dg
     sim.sync()
-    print(f"\nfull-size default workload: {checked} sampled pushes against the oracle, "
+    print(f"\n{cells} {prec}: {checked} sampled pushes against the oracle, "
           f"Gauss residual {dg['gauss'] / dg['rho_scale']:.2e} of max rho/eps0")

@@ -500,13 +500,20 @@ __device__ __forceinline__ int box_particle(const Geom& g, const Hot& h, const F
   {
     // A displacement below 1/16 cell (slow particles) is formed in FP32: its
     // rounding error (a few 2^-24 of at most 1/16 cell) is far below the
-    // offset's own rounding.  Longer ones take the float-float move, so a
-    // fast particle's position carries no systematic per-step error.
-    const float ig = rsqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    float d[3];
+    // offset's own rounding.  Longer ones need the float-float move, so that
+    // a fast particle's position carries no systematic per-step error; the
+    // box path leaves them to the global path (the record is not written
+    // yet), which keeps the float-float move out of the particle loop.  The
+    // deterministic form always takes the float-float move.
+    if (FIX) {
+      float igg;
+      ok = move_particle<3, float>(g, o, c, u, c1, o1, igg);
+    } else {
+      const float ig = rsqrtf(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+      float d[3];
 #pragma unroll
-    for (int ax = 0; ax < 3; ++ax) d[ax] = g.Sf[ax] * u[ax] * ig;
-    if (!FIX && fmaxf(fabsf(d[0]), fmaxf(fabsf(d[1]), fabsf(d[2]))) < 0.0625f) {
+      for (int ax = 0; ax < 3; ++ax) d[ax] = g.Sf[ax] * u[ax] * ig;
+      if (!(fmaxf(fabsf(d[0]), fmaxf(fabsf(d[1]), fabsf(d[2]))) < 0.0625f)) return DEP_OUT;
       bool outside = false;
 #pragma unroll
       for (int ax = 0; ax < 3; ++ax) {
@@ -527,9 +534,6 @@ __device__ __forceinline__ int box_particle(const Geom& g, const Hot& h, const F
         if (c1[ax] < g.rmin[ax] || c1[ax] > g.rmax[ax] || (c1[ax] == g.rmax[ax] && x > 0.0f)) outside = true;
       }
       ok = !outside;
-    } else {
-      float igg;
-      ok = move_particle<3, float>(g, o, c, u, c1, o1, igg);
     }
   }
   if (!FIX && ok && !in_box(c1[0] - org[0], c1[1] - org[1], c1[2] - org[2])) return DEP_OUT;

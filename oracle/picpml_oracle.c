@@ -1041,10 +1041,14 @@ void ora_dims(const ora_sim* s, long* nn) { nn[0] = s->nn[0]; nn[1] = s->nn[1]; 
  *      and acc_x(i) = sum_{i' <= i} 6 W_x(i') (likewise y, z), in units of
  *      2^-60 of the macroparticle's charge; sum_c 6 W_c = 6 (S1 S1 S1 - S0 S0 S0)
  *      holds exactly;
- *   3. each nonzero acc becomes one integer contribution
- *        val = rint( (double(acc) * (double(w) * qn)) * 2^-36 ),
- *      qn = q / e (the charge in units of the elementary charge), i.e. units of
- *      e / (6 * 2^24) per cell face; the sum over particles is exact.
+ *   3. each nonzero acc becomes one integer contribution in units of
+ *      e / (6 * 2^24) per cell face: with the particle's integer charge factor
+ *        Wq = rint( (double(w) * qn) * 2^28 ),
+ *      qn = q / e (the charge in units of the elementary charge),
+ *        val = floor( (acc * Wq + 2^63) / 2^64 ),
+ *      i.e. acc * w q/e * 2^-36 rounded to the nearest integer (halves up),
+ *      formed exactly in 128-bit integer arithmetic; the sum over particles
+ *      is exact.
  * The physical current is J_x = -(e / (dy dz dt)) val_x / (6 * 2^24) before
  * the PML damping (likewise for y, z).  raw != 0 skips step 3 and adds acc
  * itself (for the continuity check; weights and qn are ignored).
@@ -1054,6 +1058,16 @@ void ora_dims(const ora_sim* s, long* nn) { nn[0] = s->nn[0]; nn[1] = s->nn[1]; 
  * arrays are skipped. */
 
 #define FIX_QB 20
+#define FIX_WQB 28
+
+/* round(acc * Wq / 2^s), halves up, exactly (|acc| < 2^63, |Wq| <= 2^60). */
+static long long fix_scale(long long acc, long long Wq, int s) {
+  const __int128 P = (__int128)acc * (__int128)Wq + ((__int128)1 << (s - 1));
+  return (long long)(P >> s);
+}
+
+/* The particle's integer charge factor rint(w q/e 2^28). */
+static long long fix_wq(float w, double qn) { return llrint(ldexp((double)w * qn, FIX_WQB)); }
 
 /* B-spline shape values of an in-cell offset f, computed in FP32 and
  * quantised to 2^-20 with the remainder on one node so the values sum to
@@ -1097,13 +1111,12 @@ void ora_fixed_deposit3d(int order, long long n, const int* cell0, const float* 
                          const float* off1, const float* w, double qn, int raw, long long nx, long long ny,
                          long long nz, long long* Jx, long long* Jy, long long* Jz) {
   const int W = order + 2;
-  const double down = ldexp(1.0, -36);
   for (long long p = 0; p < n; ++p) {
     long long S0[3][5], DS[3][5];
     int lo[3];
     for (int a = 0; a < 3; ++a)
       lo[a] = fixed_axis(order, cell0[3 * p + a], off0[3 * p + a], cell1[3 * p + a], off1[3 * p + a], S0[a], DS[a]);
-    const double wq = (double)w[p] * qn;
+    const long long Wq = fix_wq(w[p], qn);
     for (int c = 0; c < 3; ++c) {
       /* component c: prefix sums along axis c; the two transverse axes b < d */
       const int b = c == 0 ? 1 : 0, d = c == 2 ? 1 : 2;
@@ -1121,7 +1134,7 @@ void ora_fixed_deposit3d(int order, long long n, const int* cell0, const float* 
             idx[b] = lo[b] + tb;
             idx[d] = lo[d] + td;
             if (idx[0] < 0 || idx[0] >= nx || idx[1] < 0 || idx[1] >= ny || idx[2] < 0 || idx[2] >= nz) continue;
-            const long long v = raw ? acc : llrint(((double)acc * wq) * down);
+            const long long v = raw ? acc : fix_scale(acc, Wq, 36 + FIX_WQB);
             J[idx[0] + nx * (idx[1] + ny * idx[2])] += v;
           }
         }
@@ -1132,7 +1145,8 @@ void ora_fixed_deposit3d(int order, long long n, const int* cell0, const float* 
 /* The replay for 2D (x, z) boxes (d/dy = 0).  J_x and J_z come from the
  * integer Esirkepov sums of the two in-plane axes, 6 W_x = DS_x (6 S0_z +
  * 3 DS_z) (prefix sums along x; likewise z), in units 2^-40, so one rounding
- * val = rint((acc w q/e) 2^-16) gives the unit of the 3D replay, e/(6 2^24).
+ * val = floor((acc Wq + 2^43) / 2^44) (acc w q/e 2^-16 to the nearest integer, halves up;
+ * Wq as in the 3D replay) gives the unit of the 3D replay, e/(6 2^24).
  * J_y (out of the plane) is the mid-move shape product 6 S0_x S0_z +
  * 3 DS_x S0_z + 3 S0_x DS_z + 2 DS_x DS_z times v_y/c, which is formed in
  * FP64 from the FP32 momentum with correctly rounded operations in a fixed
@@ -1151,6 +1165,7 @@ void ora_fixed_deposit2d(int order, long long n, const int* cell0, const float* 
     for (int a = 0; a < 3; a += 2)
       lo[a] = fixed_axis(order, cell0[3 * p + a], off0[3 * p + a], cell1[3 * p + a], off1[3 * p + a], S0[a], DS[a]);
     const double wq = (double)w[p] * qn;
+    const long long Wq = fix_wq(w[p], qn);
     const double ux = u[3 * p], uy = u[3 * p + 1], uz = u[3 * p + 2];
     const double vyc = uy / sqrt(((1.0 + ux * ux) + uy * uy) + uz * uz);
     for (int tk = 0; tk < W; ++tk) {        /* J_x: prefix sums along x */
@@ -1160,7 +1175,7 @@ void ora_fixed_deposit2d(int order, long long n, const int* cell0, const float* 
         acc += DS[0][ti] * T;
         const long long i = lo[0] + ti, k = lo[2] + tk;
         if (acc == 0 || i < 0 || i >= nx || k < 0 || k >= nz) continue;
-        Jx[i + nx * k] += raw ? acc : llrint(((double)acc * wq) * down);
+        Jx[i + nx * k] += raw ? acc : fix_scale(acc, Wq, 16 + FIX_WQB);
       }
     }
     for (int ti = 0; ti < W; ++ti) {        /* J_z: prefix sums along z */
@@ -1170,7 +1185,7 @@ void ora_fixed_deposit2d(int order, long long n, const int* cell0, const float* 
         acc += DS[2][tk] * T;
         const long long i = lo[0] + ti, k = lo[2] + tk;
         if (acc == 0 || i < 0 || i >= nx || k < 0 || k >= nz) continue;
-        Jz[i + nx * k] += raw ? acc : llrint(((double)acc * wq) * down);
+        Jz[i + nx * k] += raw ? acc : fix_scale(acc, Wq, 16 + FIX_WQB);
       }
     }
     for (int tk = 0; tk < W; ++tk)          /* J_y: mid-move shape product */

@@ -437,8 +437,10 @@ __device__ __forceinline__ void deposit_one(const Geom& g, const Tables& tb, con
 //      6 W_x = DSx (6 S0y S0z + 3 DSy S0z + 3 S0y DSz + 2 DSy DSz), prefix
 //      sums along x (likewise y, z); the continuity equation then holds
 //      exactly in integers.
-//   3. One rounding per node: val = rint((double(acc) * (w q/e)) 2^-36),
-//      added with an int64 atomic.
+//   3. One rounding per node, in integers: with the particle's
+//      Wq = rint((w q/e) 2^28) (one FP64 product, rounded once),
+//      val = round((acc Wq) 2^-64), halves up, from the exact 128-bit
+//      product (fix_scale), added with an int64 atomic.
 // ---------------------------------------------------------------------------
 template <int ORDER>
 __device__ __forceinline__ void fixed_shape(float f, long long* w) {
@@ -492,6 +494,7 @@ __device__ __forceinline__ void deposit_fixed(const Geom& g, const FieldPtrs<flo
     atomicOr(status, ST_FIXED_OVERFLOW);
     return;
   }
+  const long long Wq = __double2ll_rn(__dmul_rn(wq, kFixWqScale));
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const int b = c == 0 ? 1 : 0, d = c == 2 ? 1 : 2;   // transverse axes, b < d
@@ -511,7 +514,7 @@ __device__ __forceinline__ void deposit_fixed(const Geom& g, const FieldPtrs<flo
           idx[c] = lo[c] + ta;
           idx[b] = lo[b] + tb;
           idx[d] = lo[d] + td;
-          const long long v = __double2ll_rn(__dmul_rn(__dmul_rn(__ll2double_rn(acc), wq), kFixDown));
+          const long long v = fix_scale<36 + kFixWqBits>(acc, Wq);
           atomicAdd(reinterpret_cast<unsigned long long*>(f.Jq[c] + g.idx(idx[0], idx[1], idx[2])),
                     static_cast<unsigned long long>(v));
         }
@@ -520,8 +523,8 @@ __device__ __forceinline__ void deposit_fixed(const Geom& g, const FieldPtrs<flo
 }
 
 // The 2D (x, z) form: J_x and J_z from the in-plane integer sums,
-// 6 W_x = DSx (6 S0z + 3 DSz) (units 2^-40, so the rounding factor is 2^-16
-// for the same unit e/(6 2^24)); J_y (out of the plane) from the mid-move
+// 6 W_x = DSx (6 S0z + 3 DSz) (units 2^-40, so the scale is 2^-16 for the
+// same unit e/(6 2^24): val = round((acc Wq) 2^-44)); J_y (out of the plane) from the mid-move
 // shape product 6 S0x S0z + 3 DSx S0z + 3 S0x DSz + 2 DSx DSz times v_y/c,
 // which is formed in FP64 from the FP32 momentum with correctly rounded
 // operations in a fixed order, u_y / sqrt(((1 + u_x^2) + u_y^2) + u_z^2).
@@ -539,6 +542,7 @@ __device__ __forceinline__ void deposit_fixed2d(const Geom& g, const FieldPtrs<f
     atomicOr(status, ST_FIXED_OVERFLOW);
     return;
   }
+  const long long Wq = __double2ll_rn(__dmul_rn(wq, kFixWqScale));
   const double ux = u[0], uy = u[1], uz = u[2];
   const double g2 = __dadd_rn(__dadd_rn(__dadd_rn(1.0, __dmul_rn(ux, ux)), __dmul_rn(uy, uy)), __dmul_rn(uz, uz));
   const double vyc = __ddiv_rn(uy, __dsqrt_rn(g2));
@@ -552,7 +556,7 @@ __device__ __forceinline__ void deposit_fixed2d(const Geom& g, const FieldPtrs<f
 #pragma unroll
     for (int ti = 0; ti < W - 1; ++ti) {
       acc += DS[0][ti] * T;
-      if (acc != 0) add(0, lox + ti, loz + tk, __double2ll_rn(__dmul_rn(__dmul_rn(__ll2double_rn(acc), wq), kDown2)));
+      if (acc != 0) add(0, lox + ti, loz + tk, fix_scale<16 + kFixWqBits>(acc, Wq));
     }
   }
 #pragma unroll
@@ -562,7 +566,7 @@ __device__ __forceinline__ void deposit_fixed2d(const Geom& g, const FieldPtrs<f
 #pragma unroll
     for (int tk = 0; tk < W - 1; ++tk) {
       acc += DS[1][tk] * T;
-      if (acc != 0) add(2, lox + ti, loz + tk, __double2ll_rn(__dmul_rn(__dmul_rn(__ll2double_rn(acc), wq), kDown2)));
+      if (acc != 0) add(2, lox + ti, loz + tk, fix_scale<16 + kFixWqBits>(acc, Wq));
     }
   }
   if (vyc == 0.0) return;

@@ -125,11 +125,31 @@ struct __align__(32) dbl4 {
 // Deterministic deposition: shape quantum 2^-kFixShapeBits; one integer
 // current unit is e / (6 * 2^24) of charge crossing a cell face, reached from
 // the exact integer Esirkepov sums (units 2^-60 of the particle charge, times
-// 6) by the factor w q/e 2^-36.
+// 6) by the factor w q/e 2^-36.  The factor is the integer
+// Wq = rint(w q/e 2^kFixWqBits) of the particle, and each sum's contribution
+// is (sum * Wq) 2^-(36 + kFixWqBits) rounded to the nearest integer (halves
+// up), formed exactly in 128-bit integer arithmetic (fix_scale).
 constexpr int kFixShapeBits = 20;
-constexpr double kFixDown = 1.0 / 68719476736.0;   // 2^-36
+constexpr int kFixWqBits = 28;
+constexpr double kFixWqScale = 268435456.0;        // 2^kFixWqBits
 constexpr double kFixUnit = 6.0 * 16777216.0;      // 6 * 2^24
 constexpr double kFixMaxWq = 4294967296.0;         // |w q/e| above 2^32 is refused
+
+#ifdef __CUDACC__
+// round(acc * Wq / 2^S), halves up, from the exact 128-bit product
+// (|acc| < 2^63, |Wq| <= 2^60, 0 < S <= 64).
+template <int S>
+__device__ __forceinline__ long long fix_scale(long long acc, long long Wq) {
+  const unsigned long long lo = (unsigned long long)acc * (unsigned long long)Wq;
+  long long hi = __mul64hi(acc, Wq);
+  const unsigned long long lo2 = lo + (1ull << (S - 1));
+  hi += lo2 < lo ? 1 : 0;
+  if constexpr (S == 64)
+    return hi;
+  else
+    return (long long)(((unsigned long long)hi << (64 - S)) | (lo2 >> S));
+}
+#endif
 constexpr double kQe = 1.602176634e-19;
 
 // Raises a kernel's dynamic shared-memory limit to `bytes` on the current

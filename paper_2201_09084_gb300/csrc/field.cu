@@ -13,7 +13,9 @@
 // z-PML is exactly Eq. MaxwellE; J was multiplied by alpha when deposited.
 //
 // Split parts are accumulated in one of two FP64-class representations:
-//   SPL = 0: IEEE FP64;
+//   SPL = 0: IEEE FP64 (with FP32 fields the increment eb (r dt + source) is
+//            formed in FP32 from its FP32 inputs and added to the decayed
+//            part with one FP64 FMA);
 //   SPL = 1: float-float pairs (hi + lo, about 48 significant bits) updated
 //            with error-free FP32 transformations.  GB300's FP64 pipe runs at
 //            a small fraction of its FP32 rate, and with FP64 parts the E pass

@@ -63,6 +63,22 @@ __device__ __forceinline__ T advance(const Tables& tb, Parts<SPL>& pv, int A, in
     pv.b = make_float2(e1.h, e1.l);
     const ff t = ff_add(e0, e1);
     return (T)__fadd_rn(t.h, t.l);
+  } else if constexpr (sizeof(T) == 4) {
+    // FP32 fields, IEEE FP64 parts: the increment eb (r + source) is formed in
+    // FP32 from its FP32 inputs (eb rounded to FP32: the hi word of its
+    // float-float pair) and added to the decayed part in FP64, so a part costs
+    // one conversion and one FP64 FMA on GB300's narrow FP64 pipe.
+    const float eb0 = A >= 0 ? (CENT ? tb.eb2_c[A][ia].x : tb.eb2_n[A][ia].x) : 1.0f;
+    const float eb1 = B >= 0 ? (CENT ? tb.eb2_c[B][ib].x : tb.eb2_n[B][ib].x) : 1.0f;
+    const double ea0 = A >= 0 ? (CENT ? tb.ea_c[A][ia] : tb.ea_n[A][ia]) : 1.0;
+    const double ea1 = B >= 0 ? (CENT ? tb.ea_c[B][ib] : tb.ea_n[B][ib]) : 1.0;
+    const float i0 = eb0 * ((float)r0 + (into1 ? 0.0f : (float)src));
+    const float i1 = eb1 * ((float)r1 + (into1 ? (float)src : 0.0f));
+    const double e0 = fma(ea0, pv.a, (double)i0);
+    const double e1 = fma(ea1, pv.b, (double)i1);
+    pv.a = e0;
+    pv.b = e1;
+    return (T)(e0 + e1);
   } else {
     const double ea0 = A >= 0 ? (CENT ? tb.ea_c[A][ia] : tb.ea_n[A][ia]) : 1.0;
     const double eb0 = A >= 0 ? (CENT ? tb.eb_c[A][ia] : tb.eb_n[A][ia]) : 1.0;

@@ -19,10 +19,11 @@
 //      distinct shared-memory banks), gathers from the box, pushes, moves,
 //      writes the record back, and deposits: a move that stays in its cell
 //      (almost all of them) adds its 12 Esirkepov values (4 per component)
-//      to one of the thread's two runs in registers (no atomics), flushed
-//      once per pass to the grid with the damping alpha_c at each
-//      component's staggered location (Eq. alpha, Eq. MaxwellE source
-//      term); a move across a cell face is queued per
+//      to one of the thread's two runs in registers (no atomics; a move in
+//      a third cell sends the run used less recently to the grid and takes
+//      its place), flushed once per pass to the grid with the damping
+//      alpha_c at each component's staggered location (Eq. alpha, Eq.
+//      MaxwellE source term); a move across a cell face is queued per
 //      warp and deposited, one lane per entry, with global atomics and
 //      alpha_c; a particle outside the box gathers and deposits through
 //      global memory.
@@ -177,7 +178,8 @@ __device__ __forceinline__ void unit_range(const TileSpecies& S, long long t0, i
 // Runs of in-cell moves: each thread keeps the 12 Esirkepov values of the
 // charge-scaled current J' (4 per component) at two box cells (its particles
 // span one or two sort cells) in registers, so no atomics are needed until
-// the flush at the end of the pass.  (Runs in per-thread shared memory freed
+// the flush at the end of the pass, or until a move in a third cell evicts
+// the run used less recently.  (Runs in per-thread shared memory freed
 // the registers but were slower: they add six 16-byte shared accesses per
 // particle to a shared-memory pipe the gather already loads heavily.)
 struct Runs {
@@ -577,6 +579,7 @@ __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, con
   const float4* Mo = h.mom;
   Runs R;
   R.clear();
+  int mru = 0;        // the run used last
   unsigned out = 0;   // particles of this thread for the global path
   float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
   if (p0 < p1) {
@@ -598,18 +601,31 @@ __device__ __forceinline__ void thread_pass(const Geom& g, const Tables& tb, con
     if (FIX) continue;
     const bool toq = kind == DEP_ACROSS;
     if (kind == DEP_IN_CELL) {
-      const bool r0 = R.cell[0] == L0 || R.cell[0] < 0;
-      const bool r1 = !r0 && (R.cell[1] == L0 || R.cell[1] < 0);
+      bool r0 = R.cell[0] == L0 || R.cell[0] < 0;
+      bool r1 = !r0 && (R.cell[1] == L0 || R.cell[1] < 0);
+      if (!r0 && !r1) {
+        // a third cell: the run used less recently goes to the grid and
+        // takes this cell, so the particles of each cell visited in turn
+        // (the thread's next sorted cell after a particle that had moved)
+        // still accumulate in registers
+        const bool v1 = mru == 0;
+        float v[12];
+#pragma unroll
+        for (int t = 0; t < 12; ++t) v[t] = v1 ? R.v[1][t] : R.v[0][t];
+        red_cell(v, v1 ? R.cell[1] : R.cell[0], g, f, org, al, alpha_one);
+#pragma unroll
+        for (int t = 0; t < 12; ++t) {
+          R.v[0][t] = v1 ? R.v[0][t] : 0.0f;
+          R.v[1][t] = v1 ? 0.0f : R.v[1][t];
+        }
+        r0 = !v1;
+        r1 = v1;
+      }
       if (r0) R.cell[0] = L0;
       if (r1) R.cell[1] = L0;
+      mru = r0 ? 0 : 1;
       const float qw[3] = {h.cj0 * wd, h.cj1 * wd, h.cj2 * wd};
-      if (r0 || r1) {
-        add_in_cell(R, o, o1, qw, r0 ? 1.0f : 0.0f, r0 ? 0.0f : 1.0f);
-      } else {   // a third cell (particles that left their sorted cell): straight to the grid
-        float v[12];
-        in_cell_values(o, o1, qw, v);
-        red_cell(v, L0, g, f, org, al, alpha_one);
-      }
+      add_in_cell(R, o, o1, qw, r0 ? 1.0f : 0.0f, r0 ? 0.0f : 1.0f);
     }
     const unsigned m = __ballot_sync(0xffffffffu, toq);
     if (m) {

@@ -58,14 +58,15 @@ constexpr int kQWords = 11;               // words of a queue entry
 // Shared memory (floats): the field box (E, B^n; the deterministic form
 // keeps B^{n+1/2} and B^{n-1/2}: 9 arrays), the alpha tables (node and
 // centre per axis: 2 (BX + BY + BZ)), the
-// warps' queues, then the mbarrier and the species' live counts.
+// warps' queues, then the mbarrier, the species' live counts and two
+// buffers of the species' index ranges of a unit.
 template <bool FIX>
 struct Smem {
   static constexpr int box = (FIX ? 9 : 6) * BN;
   static constexpr int al = 2 * (BX + BY + BZ);
   static constexpr int queue = FIX ? 0 : (NT / 32) * kQWords * 32;
   static constexpr int floats = box + al + queue;
-  static constexpr int bytes = floats * 4 + 16 + 8 * 8;
+  static constexpr int bytes = floats * 4 + 16 + 8 * kTileMaxSpecies + 2 * 16 * kTileMaxSpecies;
   static constexpr unsigned box_bytes = (unsigned)box * 4u;
 };
 static_assert(Smem<false>::bytes <= 113 * 1024, "two blocks per SM");
@@ -666,6 +667,10 @@ __global__ void __launch_bounds__(NT, 2)
   const int ux = (tx + UXT - 1) / UXT;
   const long long nunits = (long long)ux * ty * tz;
   long long* nlive = reinterpret_cast<long long*>(bar + 1);   // live count of each species
+  // [beg, end) of every species in a unit, two buffers: thread 0 fills the
+  // other buffer with the block's next unit while this one is worked on, so
+  // a unit starts without waiting on global loads of the tile ends
+  long long* urange = nlive + kTileMaxSpecies;
   if (tid < L.nsp) nlive[tid] = *L.s[tid].sp.n_dev;
   if (tid == 0) {
     mbar_init(bar, 1);
@@ -684,19 +689,26 @@ __global__ void __launch_bounds__(NT, 2)
   }
   constexpr int kArrays = FIX ? 9 : 6;
 
+  int buf = 0;          // the urange buffer of the current unit
+  bool ahead = false;   // it was filled during the previous unit
   for (long long u = blockIdx.x; u < nunits && alive; u += gridDim.x) {
     const int iu = (int)(u % ux);
     const long long r = u / ux;
     const int jt = (int)(r % ty), kt = (int)(r / ty);
     const long long t0 = (long long)iu * UXT + (long long)tx * (jt + (long long)ty * kt);
     const int nt = min(UXT, tx - iu * UXT);
-    long long total = 0;
-    for (int s = 0; s < L.nsp; ++s) {
-      long long b, e;
-      unit_range(L.s[s], t0, nt, nlive[s], b, e);
-      total += e - b;
+    long long* ur = urange + buf * 2 * kTileMaxSpecies;
+    if (!ahead) {
+      if (tid < L.nsp) unit_range(L.s[tid], t0, nt, nlive[tid], ur[2 * tid], ur[2 * tid + 1]);
+      __syncthreads();
     }
-    if (total == 0) continue;   // uniform across the block
+    long long total = 0;
+    for (int s = 0; s < L.nsp; ++s) total += ur[2 * s + 1] - ur[2 * s];
+    if (total == 0) {   // uniform across the block; the next unit fills the other buffer
+      buf ^= 1;
+      ahead = false;
+      continue;
+    }
     const int org[3] = {iu * UX - OX, jt * TY - OY, kt * TZ - OZ};
     if (tid == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -712,9 +724,12 @@ __global__ void __launch_bounds__(NT, 2)
         const long long t2 = (long long)iu2 * UXT + (long long)tx * (jt2 + (long long)ty * kt2);
         const int nt2 = min(UXT, tx - iu2 * UXT);
         long long tot2 = 0;
+        long long* ur2 = urange + (buf ^ 1) * 2 * kTileMaxSpecies;
         for (int s = 0; s < L.nsp; ++s) {
           long long b, e;
           unit_range(L.s[s], t2, nt2, nlive[s], b, e);
+          ur2[2 * s] = b;
+          ur2[2 * s + 1] = e;
           tot2 += e - b;
           prefetch_l2(reinterpret_cast<const float4*>(L.s[s].sp.pos) + b, (e - b) * 16);
           prefetch_l2(reinterpret_cast<const float4*>(L.s[s].sp.mom) + b, (e - b) * 16);
@@ -758,8 +773,7 @@ __global__ void __launch_bounds__(NT, 2)
     const int warp0 = tid & ~31;
     for (int s = 0; s < L.nsp; ++s) {
       const TileSpecies& Sp = L.s[s];
-      long long beg, end;
-      unit_range(Sp, t0, nt, nlive[s], beg, end);
+      const long long beg = ur[2 * s], end = ur[2 * s + 1];
       // passes of at most NT * PT particles; in a pass of m particles thread
       // t takes q or q + 1 consecutive ones (q = m / NT, the first m % NT
       // threads one more), so only the warps holding the extra particles
@@ -777,6 +791,8 @@ __global__ void __launch_bounds__(NT, 2)
     }
     if (!FIX && qn) drain_queue(Q.q, qn, g, tb, f);
     __syncthreads();   // the next unit's copy may overwrite the box: every thread is past it
+    buf ^= 1;
+    ahead = u + gridDim.x < nunits;   // thread 0 filled the other buffer with it
   }
   // particles added after the last sort: one per thread, through global memory
   if (alive) {

@@ -52,7 +52,7 @@ constexpr int UX = TX * UXT;              // 16 cells
 constexpr int BX = 24, BY = 8, BZ = 8;
 constexpr int BXY = BX * BY, BN = BXY * BZ;
 constexpr int OX = 4, OY = 2, OZ = 2;
-constexpr int NT = 256;                   // threads per block
+constexpr int NT = 256;                   // threads per block (a power of two)
 constexpr int PT = 12;                    // most particles per thread in one pass
 constexpr int kQWords = 11;               // words of a queue entry
 // Shared memory (floats): the field box (E, B^n; the deterministic form
@@ -71,6 +71,7 @@ struct Smem {
 };
 static_assert(Smem<false>::bytes <= 113 * 1024, "two blocks per SM");
 static_assert(2 * (BX + BY + BZ) <= NT, "one thread per alpha-table entry");
+static_assert((NT & (NT - 1)) == 0 && NT % 32 == 0, "thread ranks wrap with a mask");
 
 // A particle whose cell (local to the box) lies in [OX-1, OX+UX] x [OY-1, OY+TY]
 // x [OZ-1, OZ+TZ] gathers from nodes l-1 .. l+1 and deposits to nodes l .. l+1
@@ -770,23 +771,27 @@ __global__ void __launch_bounds__(NT, 2)
       break;
     }
     int qn = 0;   // entries in this warp's queue (the same in every lane)
-    const int warp0 = tid & ~31;
+    int xs = 0;   // first thread of the next pass's extra particles (a multiple of 32)
     for (int s = 0; s < L.nsp; ++s) {
       const TileSpecies& Sp = L.s[s];
       const long long beg = ur[2 * s], end = ur[2 * s + 1];
-      // passes of at most NT * PT particles; in a pass of m particles thread
-      // t takes q or q + 1 consecutive ones (q = m / NT, the first m % NT
-      // threads one more), so only the warps holding the extra particles
-      // run the extra iteration
+      // passes of at most NT * PT particles; in a pass of m particles the
+      // thread of rank t = (tid - xs) mod NT takes q or q + 1 consecutive
+      // ones (q = m / NT, ranks below m % NT one more), so only the warps
+      // holding the extra particles run the extra iteration; the extras of
+      // the next pass start at the warp after them, which spreads the extra
+      // iterations of a unit's passes over its warps
       const long long npass = (end - beg + NT * PT - 1) / (NT * PT);
       for (long long k = 0; k < npass; ++k) {
         const long long b0 = beg + (end - beg) * k / npass, b1 = beg + (end - beg) * (k + 1) / npass;
         const int m = (int)(b1 - b0);
         const int q = m / NT, rem = m % NT;
-        const long long p0 = b0 + (long long)q * tid + min(tid, rem);
-        const long long p1 = p0 + q + (tid < rem ? 1 : 0);
-        thread_pass<FIX>(g, tb, f, Sp.sp, p0, p1, q + (warp0 < rem ? 1 : 0), F, Q, qn, org, al, alpha_one,
+        const int t = (tid - xs) & (NT - 1);
+        const long long p0 = b0 + (long long)q * t + min(t, rem);
+        const long long p1 = p0 + q + (t < rem ? 1 : 0);
+        thread_pass<FIX>(g, tb, f, Sp.sp, p0, p1, q + ((t & ~31) < rem ? 1 : 0), F, Q, qn, org, al, alpha_one,
                          L.prescribed, status, pushed);
+        xs = (xs + ((rem + 31) & ~31)) & (NT - 1);
       }
     }
     if (!FIX && qn) drain_queue(Q.q, qn, g, tb, f);

@@ -192,7 +192,7 @@ def run_gpu(args, rank, world):
     parts = I.beam(3, npart, NPHYS, PML, beam_center(), theta_deg=args.theta)[0]
     stream = torch.cuda.current_stream()
     sim = Sim(3, NPHYS, D, PML, cfl=0.99, order=args.order, prec=args.prec, alpha_mode="damped",
-              sort_every=0, stream=stream)
+              sort_every=0, split_fp64=True, stream=stream)
     pos, mom = pack_particles(parts["cell"], parts["off"], parts["u"], parts["w"], args.prec)
     sim.add_species(pos, mom, npart, parts["q"], parts["m"])
     pos0, mom0 = pos.clone(), mom.clone()

@@ -4,9 +4,9 @@ benchmark times, against the oracle on the whole grid.
 128^3 physical cells + 16-cell PML on every face (160^3), 4,194,304
 macroparticles in the relativistic beam (Gaussian, sigma 4 / 4 / 8 cells,
 u ~ N(50, 0.5) along the beam axis, 1 nC) centred 24 cells before the +z
-interface, damped-current PML, dt = 0.99 x Courant limit, sorted before the
-first step; the GPU uses the launch shapes its autotuner picks (as the
-benchmark does).  Order-1 shapes at normal incidence for 100 steps (by then
+interface, damped-current PML, dt = 0.99 x Courant limit, FP32 fields with
+IEEE FP64 PML split parts, sorted before the first step; the GPU uses the
+launch shapes its autotuner picks (as the benchmark does).  Order-1 shapes at normal incidence for 100 steps (by then
 the beam's head has crossed the damped PML and left through the outer
 wall); order 1 at 15 degrees and order 3 at 0 and 30 degrees (the other
 incidences and shape of the workload) for 20 steps.  After 10 steps and at
@@ -39,7 +39,8 @@ def test_beam_3d_160_full_size(order, theta, steps):
     from paper_2201_09084_gb300.api import Sim, pack_particles
     parts = I.beam(3, bench.NPART, bench.NPHYS, bench.PML, bench.beam_center(), theta_deg=theta)[0]
     dt = O.yee_dt(bench.D, 0.99, 3)
-    gpu = Sim(3, bench.NPHYS, bench.D, bench.PML, dt=dt, order=order, prec="fp32", alpha_mode="damped")
+    gpu = Sim(3, bench.NPHYS, bench.D, bench.PML, dt=dt, order=order, prec="fp32", alpha_mode="damped",
+              split_fp64=True)
     pos, mom = pack_particles(parts["cell"], parts["off"], parts["u"], parts["w"], "fp32")
     gpu.add_species(pos, mom, bench.NPART, parts["q"], parts["m"])
     gpu.sort()

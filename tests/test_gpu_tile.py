@@ -3,13 +3,15 @@ order 1 whose species are sorted by tile) against the FP64 oracle, through the
 C ABI.
 
 The kernel gathers from a TMA-loaded field box, keeps the Esirkepov current of
-in-cell moves in register runs, adds moves across cell faces to a shared
-current box, sends particles outside the box through global memory, and adds
-the box to the grid with alpha once per node.  These tests put every one of
-those paths on ragged grids (tile and unit counts that do not divide the
-grid), with particles inside the damped PML, particles removed at the outer
-edge, records injected after the last sort (the unsorted tail) and a species
-added after it.  Particles are matched to the oracle's by a unique FP32
+in-cell moves in two register runs per thread (a move in a third cell flushes
+the run used less recently), queues moves across cell faces per warp, adds
+the runs and the queue to the grid with global reductions and alpha, and sends
+particles outside the box (or moving 1/16 cell or more) through global memory.
+These tests put every one of those paths on ragged grids (tile and unit counts
+that do not divide the grid), with particles inside the damped PML, particles
+removed at the outer edge, units whose species take several passes, records
+injected after the last sort (the unsorted tail) and a species added after
+it.  Particles are matched to the oracle's by a unique FP32
 weight, since the sort permutes them.
 """
 import numpy as np
@@ -109,6 +111,40 @@ def test_tile_one_step_matches_oracle():
         assert np.abs(X[a] - Xo[a]).max() < 2e-6
         assert np.abs(u[a] - uo[a]).max() < 1e-5 * np.abs(uo).max()
     assert (~po["alive"]).sum() > 0, "some particles should leave through the outer edge"
+
+
+def test_tile_dense_units_take_several_passes():
+    """Two species packed into eight units (about 94 and 56 particles per
+    cell): each unit's species take several passes of at most 12 particles
+    per thread, whose extra particles rotate over the warps from pass to
+    pass and from species to species; one fused push + deposit against the
+    oracle, every particle pushed once."""
+    nphys = (40, 12, 12)
+    pml = (4,) * 6
+    lo, hi = [6.0, 5.0, 5.0], [26.0, 9.0, 9.0]
+    a = I.random_particles(3, 30000, lo, hi, u_rms=0.05, seed=321)
+    b = I.random_particles(3, 18000, lo, hi, u_rms=0.2, seed=322, q=O.Q_E, m=O.M_P * 0.05)
+    parts = _tag(a + b, 1.0)
+    ora, gpu = make_pair(3, nphys, pml, D3, parts, order=1, prec="fp32", alpha_mode="damped")
+    _set_fields((ora, gpu), ora.nn)
+    gpu.sort()
+    gpu.set_tuning(TILE, 1)
+    ps0 = gpu.particle_steps()
+    ora.push()
+    ora.deposit()
+    gpu.push_deposit()
+    assert gpu.particle_steps() - ps0 == 48000
+    err = max_field_err(ora, gpu, ("Jx", "Jy", "Jz"))
+    print(f"\ndense units, current error (of max |J|): {err}")
+    assert max(err.values()) < TOL["fp32"], err
+    po = ora.particles()
+    for sid, sel in ((0, slice(0, 30000)), (1, slice(30000, None))):
+        X, u, alive = _match(gpu, sid, po, sel)
+        assert np.array_equal(alive, po["alive"][sel])
+        Xo = np.stack([po["X"][sel], po["Y"][sel], po["Z"][sel]], 1)
+        uo = np.stack([po["ux"][sel], po["uy"][sel], po["uz"][sel]], 1)
+        assert np.abs(X - Xo).max() < 2e-6
+        assert np.abs(u - uo).max() < 1e-5 * np.abs(uo).max()
 
 
 @pytest.fixture(scope="module")

@@ -157,9 +157,9 @@ def count_cells():
 # theta, particles).  Reset to {} whenever that kernel changes.  Captured with
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
 #       --clock-control none -k regex:k_pd1 -s 3 -c 1
-#       python bench.py --tuning 4,1 --steps 3 --warmup 3 --no-cpu-baseline --no-batch --no-fp64
-# (the first timed step: 138.7 MB read + 79.1 MB written).
-NCU_TRAFFIC = {(1, 4, "fp32", 0.0, 4194304): 217.80e6}
+#       python bench.py --beam --tuning 4,1 --steps 3 --warmup 3 --no-cpu-baseline --no-batch --no-fp64
+# (the first timed step: 138,749,696 B read + 78,776,320 B written).
+NCU_TRAFFIC = {(1, 4, "fp32", 0.0, 4194304): 138_749_696 + 78_776_320}
 
 
 def combine_ranks(ms, psteps, ms_e2e, ps_e2e, world, device):

@@ -784,8 +784,9 @@ def run_plasma(args):
     b_part, b_field = algorithmic_bytes(psteps / args.steps, occ, interior, total - interior, "fp32", bn=p_ == 2)
     peak, kind = measured_peak()
     achieved = b_part / (t_pd / 1e3) / 1e9
-    traffic = (PLASMA_NCU_BYTES_PER_PARTICLE * psteps / args.steps
-               if PLASMA_NCU_BYTES_PER_PARTICLE and p_ == 1 else None)
+    # measured DRAM bytes per particle of the kernel the launch shape selects
+    per_particle = {1: PLASMA_NCU_BYTES_PER_PARTICLE, 2: HEADLINE_NCU_BYTES_PER_PARTICLE}.get(p_)
+    traffic = per_particle * psteps / args.steps if per_particle else None
     sim.close()
     return {"metric": METRIC, "value": psteps / (ms / 1e3), "unit": "particle-steps/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

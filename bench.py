@@ -663,10 +663,10 @@ PLASMA_NCU_BYTES_PER_PARTICLE = 557_966_080 / 8_429_785
 # Captured with
 #   ncu --set full --clock-control none -k regex:^k_tile$ -s 4 -c 1
 #       python bench.py --cells 64,64,128 --no-extra --no-cpu-baseline --steps 3 --warmup 3 --tuning 2,1
-# (310,989,568 B read + 222,630,912 B written for 8,429,785 particles).
-HEADLINE_NCU_BYTES_PER_PARTICLE = (310_989_568 + 222_630_912) / 8_429_785
+# (308,050,176 B read + 223,579,392 B written for 8,429,785 particles).
+HEADLINE_NCU_BYTES_PER_PARTICLE = (308_050_176 + 223_579_392) / 8_429_785
 HEADLINE_NCU_NOTE = ("per launch: dram__bytes_read.sum + dram__bytes_write.sum of the tile kernel on the "
-                     "64x64x128 case (63.3 B per particle), scaled by the particles pushed")
+                     "64x64x128 case (63.1 B per particle), scaled by the particles pushed")
 
 # Plasma boxes with more particles per species than this are generated and
 # packed one z-plane of cells at a time (inputs.plasma_planes) instead of in

@@ -550,8 +550,10 @@ __device__ __forceinline__ int box_particle(const Geom& g, const Hot& h, const F
     wn = w * expf(-I);
   }
   const int cell1 = pack_cell(c1[0], c1[1], c1[2]);
-  P[p] = ok ? make_float4(o1[0], o1[1], o1[2], wn) : a;
-  Mo[p] = make_float4(u[0], u[1], u[2], __int_as_float(ok ? cell1 : -1));
+  // streaming stores: the records are not read again in this launch, so they
+  // need not displace the next unit's prefetched box and records in L2
+  __stcs(P + p, ok ? make_float4(o1[0], o1[1], o1[2], wn) : a);
+  __stcs(Mo + p, make_float4(u[0], u[1], u[2], __int_as_float(ok ? cell1 : -1)));
   if (!ok) return DEP_NONE;
   if constexpr (FIX) {
     deposit_fixed<1>(g, f, h.qn, c, o, c1, o1, wd, status);

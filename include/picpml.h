@@ -117,7 +117,9 @@ typedef struct pic_grid_desc {
   int prec;             /* pic_prec */
   int sort_every;       /* step_n sorts particles by cell every this many
                            steps (0 = never) */
-  int split_fp64;       /* PIC_FP32 only: 1 = PML split parts in IEEE FP64;
+  int split_fp64;       /* PIC_FP32 only: 1 = PML split parts in IEEE FP64
+                           (each step's increment formed in FP32 from its
+                           FP32 inputs, added with one FP64 FMA);
                            0 (default) = float-float pairs (hi + lo, ~48-bit
                            significand, 8 bytes) computed on the FP32 pipes */
   int filter_passes;    /* 0 (default): none.  n = 1..8: field_step first
@@ -331,10 +333,11 @@ int pic_autotune(picpml_ctx* ctx, int steps, int* particles_per_thread, int* z_n
  * the default), one launch for every species sorted since it was added
  * (pic_sort or sort_every; the others run one thread per particle): a block
  * per 16x4x4-cell unit loads the unit's E and B box with TMA, pushes the
- * particles that sat in the unit at the last sort, and adds the unit's
- * current box to the grid once, damped by alpha (a thermal plasma's few
- * particles per cell and short moves).  z nodes per thread of the field
- * kernels: 1, 2 or 4. */
+ * particles that sat in the unit at the last sort, keeps the current of
+ * moves inside a cell in two register runs per thread and queues moves
+ * across a face per warp, and adds both to J with global reductions, damped
+ * by alpha (a thermal plasma's few particles per cell and short moves).  z
+ * nodes per thread of the field kernels: 1, 2 or 4. */
 #define PIC_TUNING_TILE 2
 int pic_set_tuning(picpml_ctx* ctx, int particles_per_thread, int z_nodes_per_thread);
 

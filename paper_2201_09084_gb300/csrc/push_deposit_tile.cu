@@ -244,35 +244,8 @@ __device__ __forceinline__ void flush_runs(const Runs& R, const Geom& g, const F
 // J'_x(b, c) = cj_x w (-d_x) (M_y[b] M_z[c] + (-1)^{b+c} d_y d_z / 12) with
 // the mid-move shape M = (1 - m, m), m = (o0 + o1)/2, d = o1 - o0 (the
 // transverse factor S0 S0' + DS S0'/2 + S0 DS'/2 + DS DS'/3 = M M' + DS DS'/12).
-// in_cell_values: the 12 values (slots as in red_cell).
-__device__ __forceinline__ void in_cell_values(const float o0[3], const float o1[3], const float qw[3],
-                                               float v[12]) {
-  float d[3], m[3];
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    d[a] = o1[a] - o0[a];
-    m[a] = 0.5f * (o0[a] + o1[a]);
-  }
-  const float c12 = 1.0f / 12.0f;
-  const float eyz = c12 * d[1] * d[2], exz = c12 * d[0] * d[2], exy = c12 * d[0] * d[1];
-  const float mx0 = 1.0f - m[0], my0 = 1.0f - m[1], mz0 = 1.0f - m[2];
-  const float ax = -qw[0] * d[0], ay = -qw[1] * d[1], az = -qw[2] * d[2];
-  v[0] = ax * fmaf(my0, mz0, eyz);
-  v[1] = ax * fmaf(m[1], mz0, -eyz);
-  v[2] = ax * fmaf(my0, m[2], -eyz);
-  v[3] = ax * fmaf(m[1], m[2], eyz);
-  v[4] = ay * fmaf(mx0, mz0, exz);
-  v[5] = ay * fmaf(m[0], mz0, -exz);
-  v[6] = ay * fmaf(mx0, m[2], -exz);
-  v[7] = ay * fmaf(m[0], m[2], exz);
-  v[8] = az * fmaf(mx0, my0, exy);
-  v[9] = az * fmaf(m[0], my0, -exy);
-  v[10] = az * fmaf(mx0, m[1], -exy);
-  v[11] = az * fmaf(m[0], m[1], exy);
-}
-
-// add_in_cell: added s0 times to run 0 and s1 times to run 1 (s0, s1 in
-// {0, 1}).
+// add_in_cell: the 12 values (slots as in red_cell) added s0 times to run 0
+// and s1 times to run 1 (s0, s1 in {0, 1}).
 __device__ __forceinline__ void add_in_cell(Runs& r, const float o0[3], const float o1[3], const float qw[3],
                                             float s0, float s1) {
   float d[3], m[3];
